@@ -1,0 +1,332 @@
+"""Benchmark: seconds per colouring of colour-coding tree counting on the
+1M-vertex R-MAT workload, FP32-batched form vs plain FP64 form.
+
+Workload: R-MAT scale 20 (a,b,c,d = .57,.19,.19,.05, ids permuted),
+2^24 undirected edges, template tree10 (parent [-1,0,1,1,0,4,5,5,2,6], root
+0), k = 10 colours.  One step of the FP32-batched form counts B colourings in
+one call; one step of the plain form counts one colouring in FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank counts its
+own colourings on its own GPU (replicas: colourings are independent), the
+step time is the maximum over ranks and `value` covers all ranks' colourings.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sg2v_inputs as si  # noqa: E402
+
+METRIC = "seconds per coloring + HBM GB/s vs peak, FP32-batched vs FP64 plain, RMAT 1M"
+UNIT = "s/colouring"
+WORKLOAD = "rmat20_16m_tree10_k10"
+TEMPLATE = si.TREE10
+K_COLOURS = 10
+FULL_SCALE, FULL_EDGES = 20, 1 << 24
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def traffic_record():
+    """DRAM bytes per launch from the committed ncu summary, valid only while
+    the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except OSError:
+        return {}
+    src = open(os.path.join(ROOT, "paper_2009_11665_b300", "csrc", "kernels.cu"), "rb").read()
+    if rec.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return {}
+    return rec.get("bytes_per_launch", {})
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_seconds_per_colouring(scale: int, threads: int):
+    """The exact CPU oracle on an R-MAT sibling of the workload (same R-MAT
+    parameters and average degree, 2^scale vertices), one colouring; seconds
+    scaled linearly in the edge count to the full workload."""
+    import oracle
+
+    g = si.rmat(scale, (1 << scale) * 16, seed=0)
+    col = si.colouring(g.n, K_COLOURS, 0)
+    t0 = time.perf_counter()
+    oracle.count(g.row_ptr, g.col_idx, TEMPLATE.parent, 0, col, per_vertex=False, threads=threads)
+    dt = time.perf_counter() - t0
+    factor = FULL_EDGES / g.m
+    return dt * factor, dt, g
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    scale = args.reference_scale
+    for _ in range(args.warmup):
+        oracle_seconds_per_colouring(scale, threads)
+    vals, raw = [], []
+    for _ in range(args.steps):
+        v, dt, g = oracle_seconds_per_colouring(scale, threads)
+        vals.append(v)
+        raw.append(dt)
+    value = statistics.median(vals)
+    sample = (f"exact oracle DP (128-bit integers) on R-MAT scale {scale} ({g.m} edges, same parameters and "
+              f"average degree), 1 colouring of tree10 per step; seconds x{FULL_EDGES // g.m} (work is linear "
+              f"in the edge count)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.median(raw) * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "rmat scale 20, 2^24 edges", "template": list(TEMPLATE.parent),
+                   "num_colours": K_COLOURS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def physical_gpu_index(local: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p.strip() for p in vis.split(",") if p.strip()]
+    if local < len(parts) and parts[local].isdigit():
+        return int(parts[local])
+    return local
+
+
+def time_steps(torch, fn, steps, warmup, stream, dist=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=int(os.environ.get("SG2V_BENCH_BATCH", "4")))
+    ap.add_argument("--impl", default="sg2v", choices=["sg2v", "reference"])
+    ap.add_argument("--reference-scale", type=int, default=16)
+    ap.add_argument("--cpu-baseline-scale", type=int, default=17)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and "RANK" in os.environ:
+        print(f"warning: WORLD_SIZE {world} != --gpus {args.gpus}", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as sg
+
+    B = args.batch
+    g = si.workload_graph("rmat20_16m")
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(TEMPLATE.parent, 0, K_COLOURS)
+    # colourings of this rank: indices rank*B .. rank*B+B-1 (replicas over colourings)
+    cols = si.colourings(g.n, K_COLOURS, B * (rank + 1), seed=0)[rank * B:(rank + 1) * B]
+    d_cols = torch.from_numpy(cols).cuda()
+    stream = torch.cuda.current_stream()
+    tot32 = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    est32 = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    tot64 = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+
+    def step_fp32():
+        sg.sg2v_count_batched(graph.handle, [plan.handle], d_cols, B, sg.SG2V_FP32, None, tot32, est32, stream)
+
+    def step_fp64():
+        sg.sg2v_count_batched(graph.handle, [plan.handle], d_cols[0:1], 1, sg.SG2V_FP64, None, tot64, None, stream)
+
+    # plain FP64 form
+    ms64 = time_steps(torch, step_fp64, max(3, args.steps // 2), args.warmup, stream, dist)
+
+    # FP32-batched form (the headline): kernel records collected over the timed region
+    peaks, peak_kind = measured_peaks()
+    for _ in range(args.warmup):
+        step_fp32()
+    torch.cuda.synchronize()
+    sg.sg2v_profile_reset()
+    sg.sg2v_profile_enable(True)
+    with ClockSampler(physical_gpu_index(local)) as clocks:
+        ms32 = time_steps(torch, step_fp32, args.steps, 0, stream, dist)
+    sg.sg2v_profile_enable(False)
+    launches = sg.sg2v_launch_count()
+    records = sg.sg2v_profile_read()
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    h_cols = torch.from_numpy(cols).pin_memory()
+    h_pv = torch.empty((1, B, g.n), dtype=torch.float64).pin_memory()
+    h_tot = np.zeros((1, B))
+    h_est = np.zeros((1, B))
+
+    def step_e2e():
+        sg.sg2v_count_batched(graph.handle, [plan.handle], h_cols, B, sg.SG2V_FP32, h_pv, h_tot, h_est, stream)
+
+    ms_e2e = time_steps(torch, step_e2e, max(3, args.steps // 2), args.warmup, stream, dist)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    total_colourings = B * world
+    value = ms32 * 1e-3 / total_colourings
+    fp64_s = ms64 * 1e-3 / world
+    node_recs = [r for r in records if r["name"].startswith("node")]
+    dom = max(node_recs, key=lambda r: r["total_ms"])
+    dom_ms = dom["total_ms"] / dom["launches"]
+    achieved = dom["bytes_per_launch"] / (dom_ms * 1e-3) / 1e9
+    step_bytes = sum(r["bytes_per_launch"] * r["launches"] for r in records) / args.steps
+    peak = float(peaks["hbm_gbs"])
+    traffic = traffic_record().get(dom["name"])
+    kernel_table = {r["name"]: {"launches_per_step": r["launches"] / args.steps,
+                                "ms_per_launch": round(r["total_ms"] / r["launches"], 4),
+                                "algorithmic_GB_per_launch": round(r["bytes_per_launch"] / 1e9, 4),
+                                "GBps": round(r["bytes_per_launch"] / (r["total_ms"] / r["launches"]) / 1e6, 1)}
+                    for r in records}
+    cpu = None
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, dt, gs = oracle_seconds_per_colouring(args.cpu_baseline_scale, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"exact oracle DP (128-bit integers) on R-MAT scale {args.cpu_baseline_scale} "
+                          f"({gs.m} edges, same parameters and average degree), 1 colouring of tree10, "
+                          f"{dt:.2f} s measured, scaled x{FULL_EDGES // gs.m} to 2^24 edges")}
+    clk = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "rmat scale 20 (.57,.19,.19,.05), 2^24 undirected edges, ids permuted",
+                   "template": list(TEMPLATE.parent), "num_colours": K_COLOURS, "batch_colourings_per_step": B,
+                   "parallelism": f"replicas over colourings x{world}",
+                   "l2": "inputs larger than L2: count tables of 1-8 GB per step"},
+        "fp64_plain": {"s_per_colouring": fp64_s, "ms_per_step": ms64, "dtype": "f64"},
+        "fp32_batched": {"s_per_colouring": value, "ms_per_step": ms32, "B": B},
+        "speedup_fp32_batched_vs_fp64_plain": fp64_s / value,
+        "hbm": {"algorithmic_GB_per_step": step_bytes / 1e9, "GBps_step": step_bytes / (ms32 * 1e-3) / 1e9,
+                "frac_of_measured_peak": step_bytes / (ms32 * 1e-3) / 1e9 / peak,
+                "frac_of_nameplate_8TBps": step_bytes / (ms32 * 1e-3) / 1e9 / 8000.0},
+        "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic},
+        "kernels": kernel_table,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ms_e2e * 1e-3 / total_colourings, "unit": UNIT, "h2d_bytes_per_step": int(B * g.n),
+                "d2h_bytes_per_step": int(B * g.n * 8 + 2 * B * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * sg2v.h -- C ABI of the B300 colour-coding tree-counting library.
+ *
+ * Method: SubGraph2Vec (Chen et al., arXiv 2009.11665).  A tree template T
+ * with k vertices is counted in a graph G by colouring G's vertices with kc
+ * colours and counting *colourful* embeddings (all template vertices get
+ * distinct colours, Sec. 2.2.2).  The count comes from a dynamic program over
+ * a recursive split of T into an active and a passive child (Sec. 2.3.2,
+ * Alg. 2), computed in the decoupled form of Alg. 3 / Eq. 1: per split, a
+ * sparse-times-dense product  Y = A * M_passive  (Alg. 4, Alg. 6) and an
+ * element-wise multiply-add over colour-set splits
+ *   M(v, S) = sum over S_a subset of S, |S_a| = |T_a| of
+ *             M_active(v, S_a) * Y(v, S minus S_a)            (Alg. 5 eMA).
+ * The root table summed over vertices, divided by alpha (automorphisms of T)
+ * and by P (probability that k vertices are colourful) is the estimate of
+ * emb(T, G) for one colouring (Alg. 1, finalCount).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an sg2v_status; nothing aborts, throws or exits.
+ *    sg2v_last_error() gives a human-readable detail of the last failure on
+ *    the calling thread.
+ *  - Graph and plan handles are opaque and owned by the library; free them
+ *    with the matching *_destroy.  The caller owns every array it passes.
+ *  - "host or device" arrays may live in host memory (pageable or pinned) or
+ *    in device memory of the current device; the library inspects the pointer
+ *    and copies as needed (host inputs and outputs make the call include the
+ *    host<->device copies).
+ *  - Calls that take a stream are ordered on it; when an output is a host
+ *    scalar the call synchronises the stream before returning.  A NULL stream
+ *    is the legacy default stream.
+ *  - Vertices are 0..n-1; colours are 0..kc-1 (Sec. 2.3.1 draws colours in
+ *    [0, k-1]).
+ */
+#ifndef SG2V_H
+#define SG2V_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sg2v_stream; /* a cudaStream_t */
+typedef struct sg2v_graph sg2v_graph;
+typedef struct sg2v_plan sg2v_plan;
+
+typedef enum {
+    SG2V_OK = 0,
+    SG2V_ERR_INVALID_ARGUMENT = 1, /* null pointer, size out of range, bad flag */
+    SG2V_ERR_NOT_A_TREE = 2,       /* parent array is not a tree, or root out of range */
+    SG2V_ERR_COLOUR_OUT_OF_RANGE = 3,
+    SG2V_ERR_GRAPH_NOT_SIMPLE = 4, /* self-loop, duplicate arc, unsorted row, asymmetric CSR or weights */
+    SG2V_ERR_OUT_OF_MEMORY = 5,
+    SG2V_ERR_FP_OVERFLOW = 6,      /* a count left the range of the table type (inf/NaN) */
+    SG2V_ERR_CUDA = 7,             /* a CUDA runtime call failed; see sg2v_last_error() */
+    SG2V_ERR_TIMEOUT = 8,          /* a bounded device-side wait gave up */
+    SG2V_ERR_UNSUPPORTED = 9       /* a valid request this build cannot run (e.g. too many columns) */
+} sg2v_status;
+
+typedef enum {
+    SG2V_FP64 = 0, /* count tables and sums in FP64 */
+    SG2V_FP32 = 1  /* count tables in FP32, final reductions in FP64 */
+} sg2v_precision;
+
+/* ------------------------------------------------------------------ graph */
+
+#define SG2V_GRAPH_SKIP_VALIDATION 0x1u /* trust the CSR (no simplicity/symmetry check) */
+
+/*
+ * sg2v_graph_create -- the input network as a sparse adjacency matrix A_G in
+ * CSR form (Sec. 5.1: A_G(i,j) = 1 iff V_j is a neighbour of V_i; Table 1).
+ *
+ *   n        number of vertices (>= 1, < 2^31)
+ *   nnz      number of stored arcs = 2 * undirected edges (< 2^31)
+ *   row_ptr  [n+1] int64, host or device; row_ptr[0] = 0, row_ptr[n] = nnz
+ *   col_idx  [nnz] int32, host or device; strictly increasing within a row
+ *   weights  [nnz] float32, host or device, or NULL for the 0-1 matrix; the
+ *            weighted form uses A_G.val of Alg. 4 (each embedding then
+ *            contributes the product of its edge weights); weights[e] must
+ *            equal the weight of the reverse arc and be finite and >= 0
+ *   flags    0 or SG2V_GRAPH_SKIP_VALIDATION
+ *   out      receives the handle
+ *
+ * The graph must be simple and undirected: the CSR must be symmetric, with no
+ * self-loops and no repeated arcs (Sec. 2.2.1: simple graph); violations give
+ * SG2V_ERR_GRAPH_NOT_SIMPLE unless validation is skipped.  The library copies
+ * the arrays onto the current device (the caller may free its copies) and
+ * derives its load-balanced work list there.  Errors: INVALID_ARGUMENT,
+ * GRAPH_NOT_SIMPLE, OUT_OF_MEMORY, CUDA.
+ */
+sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col_idx,
+                              const float *weights, uint32_t flags, sg2v_graph **out);
+
+/* Frees the device copies.  NULL is accepted. */
+sg2v_status sg2v_graph_destroy(sg2v_graph *graph);
+
+/* n, nnz, the largest degree and whether the graph carries weights. */
+sg2v_status sg2v_graph_info(const sg2v_graph *graph, int64_t *n, int64_t *nnz, int64_t *max_degree,
+                            int32_t *weighted);
+
+/* ------------------------------------------------------------------- plan */
+
+/*
+ * sg2v_template_plan -- partitions the template (Sec. 2.3.2, Alg. 5 line
+ * "Partition T into sub-templates").  Pure host work; needs no GPU.
+ *
+ *   k           template vertices, 1 <= k <= 16
+ *   parent      [k] int32, host: parent[i] is i's parent, exactly one -1
+ *   root        rho in [0, k): the tree is re-rooted at rho (the per-vertex
+ *               counts are "rho mapped to v")
+ *   num_colours kc, k <= kc <= 16 (Sec. 2.3.1 takes kc = k)
+ *   opts        reserved, pass NULL
+ *   out         receives the handle
+ *
+ * Split rule: at a sub-template rooted at x, the edge to x's last remaining
+ * child (children ordered by vertex index) is cut; the part holding x is the
+ * active child, the cut-off subtree (rooted at the child) the passive child.
+ * Sub-templates that are isomorphic as rooted trees share one table.
+ * Errors: INVALID_ARGUMENT, NOT_A_TREE, UNSUPPORTED (kc > 16).
+ */
+sg2v_status sg2v_template_plan(int32_t k, const int32_t *parent, int32_t root, int32_t num_colours,
+                               const void *opts, sg2v_plan **out);
+
+sg2v_status sg2v_plan_destroy(sg2v_plan *plan);
+
+/*
+ * sg2v_plan_info -- alpha (automorphisms of the unrooted template, Alg. 1),
+ * the number of DP nodes after sharing, and the widest table in columns
+ * (C(kc, t) for the largest sub-template size t).  Any output may be NULL.
+ */
+sg2v_status sg2v_plan_info(const sg2v_plan *plan, int64_t *automorphisms, int32_t *num_nodes, int64_t *max_cols);
+
+/*
+ * sg2v_plan_nodes -- the DP nodes in execution order (children first).
+ * out[6*i .. 6*i+5] = { t, a, p, active node or -1 (single vertex),
+ *                       passive node or -1 (single vertex), is_root }.
+ * capacity is the number of int32 entries available in out.
+ */
+sg2v_status sg2v_plan_nodes(const sg2v_plan *plan, int32_t *out, int64_t capacity);
+
+/*
+ * sg2v_plan_estimate_scale -- 1/(P * alpha) of Alg. 1 with
+ * P = kc! / ((kc-k)! * kc^k), so that estimate = total * scale.
+ */
+sg2v_status sg2v_plan_estimate_scale(const sg2v_plan *plan, double *scale);
+
+/* ------------------------------------------------------------------ count */
+
+/*
+ * sg2v_count -- one colouring through the whole DP (Alg. 5 inner loop:
+ * SpMM + eMA per sub-template, then the root reduction and finalCount).
+ *
+ *   colours     [n] int8, host or device, values in [0, kc)
+ *   precision   SG2V_FP64 or SG2V_FP32 (table type)
+ *   per_vertex  [n] double, host or device, or NULL: per_vertex[v] is the
+ *               number of colourful embeddings (labelled maps) with the
+ *               root rho at v, i.e. sum over colour sets C of M_0(v, I_C)
+ *   total       host double or NULL: sum_v per_vertex[v]; FP64 counts are
+ *               summed exactly in 128-bit integers when they are integral
+ *   estimate    host double or NULL: total / (P * alpha)
+ *   stream      CUDA stream
+ *
+ * Workspace (count tables) is allocated stream-ordered on the current device
+ * and released before return.  Errors: INVALID_ARGUMENT,
+ * COLOUR_OUT_OF_RANGE, OUT_OF_MEMORY, FP_OVERFLOW, UNSUPPORTED, CUDA.
+ */
+sg2v_status sg2v_count(const sg2v_graph *graph, const sg2v_plan *plan, const int8_t *colours,
+                       sg2v_precision precision, double *per_vertex, double *total, double *estimate,
+                       sg2v_stream stream);
+
+/*
+ * sg2v_count_batched -- B independent colourings for each of num_plans
+ * templates in one pass: colourings become extra columns of every table row
+ * (row v holds B consecutive colour-set blocks), so each CSR sweep serves
+ * all B colourings, and sub-templates isomorphic across the plans share
+ * tables.  All plans must use the same num_colours.
+ *
+ *   plans       [num_plans] plan handles
+ *   colours     [B][n] int8, host or device
+ *   per_vertex  [num_plans][B][n] double, host or device, or NULL
+ *   totals      [num_plans][B] double, host or device, or NULL
+ *   estimates   [num_plans][B] double, host or device, or NULL
+ * Errors as sg2v_count.
+ */
+sg2v_status sg2v_count_batched(const sg2v_graph *graph, const sg2v_plan *const *plans, int32_t num_plans,
+                               const int8_t *colours, int32_t B, sg2v_precision precision, double *per_vertex,
+                               double *totals, double *estimates, sg2v_stream stream);
+
+/* -------------------------------------------------------------- profiling */
+
+/*
+ * Kernel timing (not part of the paper's method; measurement support).
+ * While enabled, every count call records a CUDA event pair on its stream
+ * around each kernel it launches and, after its final synchronisation, adds
+ * the elapsed times to a per-kernel record keyed by the kernel's role
+ * ("node t=10 a=5 p=5 fp32", "root_reduce", ...).  Records also carry the
+ * kernel's algorithmic bytes (each input table, CSR array and colouring read
+ * once, each output written once) so that callers can report achieved
+ * bandwidth.  The records are process-wide and guarded by a mutex.
+ */
+typedef struct {
+    char name[64];
+    int64_t launches;
+    double total_ms;        /* sum of event-timed durations */
+    double bytes_per_launch; /* algorithmic bytes of one launch */
+} sg2v_kernel_record;
+
+sg2v_status sg2v_profile_enable(int32_t enable);
+sg2v_status sg2v_profile_reset(void);
+/* Copies up to capacity records into out and their number into *count. */
+sg2v_status sg2v_profile_read(sg2v_kernel_record *out, int32_t capacity, int32_t *count);
+/* Kernels launched by count calls since the last reset (profiling or not). */
+int64_t sg2v_launch_count(void);
+
+/* ---------------------------------------------------------------- status */
+
+/* Static English name of a status code. */
+const char *sg2v_status_string(sg2v_status status);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *sg2v_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t sg2v_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG2V_H */

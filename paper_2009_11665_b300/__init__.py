@@ -1,0 +1,315 @@
+"""B300-native colour-coding tree counting (SubGraph2Vec, arXiv 2009.11665).
+
+Thin ctypes binding of ``libsg2v.so`` (the C ABI declared in
+``include/sg2v.h``).  Every function named ``sg2v_*`` here marshals its
+arguments and calls the C entry point of the same name; all counting runs in
+the library's CUDA kernels.  Arrays may be numpy arrays (host memory) or torch
+tensors (host or CUDA); streams default to torch's current stream.
+
+The library must have been built (``python -m paper_2009_11665_b300.build``
+or ``__graft_entry__.build()``); importing this package without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsg2v.so")
+
+SG2V_OK = 0
+SG2V_ERR_INVALID_ARGUMENT = 1
+SG2V_ERR_NOT_A_TREE = 2
+SG2V_ERR_COLOUR_OUT_OF_RANGE = 3
+SG2V_ERR_GRAPH_NOT_SIMPLE = 4
+SG2V_ERR_OUT_OF_MEMORY = 5
+SG2V_ERR_FP_OVERFLOW = 6
+SG2V_ERR_CUDA = 7
+SG2V_ERR_TIMEOUT = 8
+SG2V_ERR_UNSUPPORTED = 9
+
+SG2V_FP64 = 0
+SG2V_FP32 = 1
+SG2V_GRAPH_SKIP_VALIDATION = 0x1
+
+PRECISIONS = {"fp64": SG2V_FP64, "fp32": SG2V_FP32}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2009_11665_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_p = ctypes.c_void_p
+_i32, _i64, _u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+
+# name -> (argtypes); every function returns an int status except where noted
+_SIGNATURES = {
+    "sg2v_graph_create": [_i64, _i64, _p, _p, _p, _u32, ctypes.POINTER(_p)],
+    "sg2v_graph_destroy": [_p],
+    "sg2v_graph_info": [_p, _p, _p, _p, _p],
+    "sg2v_template_plan": [_i32, _p, _i32, _i32, _p, ctypes.POINTER(_p)],
+    "sg2v_plan_destroy": [_p],
+    "sg2v_plan_info": [_p, _p, _p, _p],
+    "sg2v_plan_nodes": [_p, _p, _i64],
+    "sg2v_plan_estimate_scale": [_p, _p],
+    "sg2v_count": [_p, _p, _p, ctypes.c_int, _p, _p, _p, _p],
+    "sg2v_count_batched": [_p, _p, _i32, _p, _i32, ctypes.c_int, _p, _p, _p, _p],
+}
+for _name, _args in _SIGNATURES.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.sg2v_status_string.argtypes = [ctypes.c_int]
+_lib.sg2v_status_string.restype = ctypes.c_char_p
+_lib.sg2v_last_error.argtypes = []
+_lib.sg2v_last_error.restype = ctypes.c_char_p
+_lib.sg2v_version.argtypes = []
+_lib.sg2v_version.restype = ctypes.c_int32
+_lib.sg2v_launch_count.argtypes = []
+_lib.sg2v_launch_count.restype = ctypes.c_int64
+
+
+class KernelRecord(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes_per_launch", ctypes.c_double)]
+
+
+for _name, _args in {"sg2v_profile_enable": [_i32], "sg2v_profile_reset": [],
+                     "sg2v_profile_read": [_p, _i32, ctypes.POINTER(_i32)]}.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+
+EXPORTED = tuple(_SIGNATURES) + ("sg2v_status_string", "sg2v_last_error", "sg2v_version", "sg2v_profile_enable",
+                                 "sg2v_profile_reset", "sg2v_profile_read", "sg2v_launch_count")
+
+
+class Sg2vError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = _lib.sg2v_last_error().decode()
+        super().__init__(f"{where}: {_lib.sg2v_status_string(status).decode()} ({detail})")
+
+
+def _check(status: int, where: str) -> int:
+    if status != SG2V_OK:
+        raise Sg2vError(status, where)
+    return status
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a numpy array / torch tensor (None for None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    try:
+        import torch
+
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------ raw entry points
+
+def sg2v_version() -> int:
+    return int(_lib.sg2v_version())
+
+
+def sg2v_status_string(status: int) -> str:
+    return _lib.sg2v_status_string(status).decode()
+
+
+def sg2v_last_error() -> str:
+    return _lib.sg2v_last_error().decode()
+
+
+def sg2v_graph_create(n: int, nnz: int, row_ptr, col_idx, weights=None, flags: int = 0) -> int:
+    h = _p()
+    _check(_lib.sg2v_graph_create(n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(weights), flags, ctypes.byref(h)),
+           "sg2v_graph_create")
+    return h.value
+
+
+def sg2v_graph_destroy(handle) -> None:
+    _check(_lib.sg2v_graph_destroy(handle), "sg2v_graph_destroy")
+
+
+def sg2v_graph_info(handle):
+    n, nnz, md, w = _i64(), _i64(), _i64(), _i32()
+    _check(_lib.sg2v_graph_info(handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md), ctypes.byref(w)),
+           "sg2v_graph_info")
+    return n.value, nnz.value, md.value, bool(w.value)
+
+
+def sg2v_template_plan(parent: Sequence[int], root: int = 0, num_colours: Optional[int] = None) -> int:
+    par = np.ascontiguousarray(parent, dtype=np.int32)
+    k = int(par.shape[0])
+    h = _p()
+    _check(_lib.sg2v_template_plan(k, _ptr(par), int(root), int(num_colours or k), None, ctypes.byref(h)),
+           "sg2v_template_plan")
+    return h.value
+
+
+def sg2v_plan_destroy(handle) -> None:
+    _check(_lib.sg2v_plan_destroy(handle), "sg2v_plan_destroy")
+
+
+def sg2v_plan_info(handle):
+    a, nn, mc = _i64(), _i32(), _i64()
+    _check(_lib.sg2v_plan_info(handle, ctypes.byref(a), ctypes.byref(nn), ctypes.byref(mc)), "sg2v_plan_info")
+    return a.value, nn.value, mc.value
+
+
+def sg2v_plan_nodes(handle) -> list:
+    _, nn, _ = sg2v_plan_info(handle)
+    out = np.zeros(max(6 * nn, 1), dtype=np.int32)
+    _check(_lib.sg2v_plan_nodes(handle, _ptr(out), out.shape[0]), "sg2v_plan_nodes")
+    return [tuple(int(x) for x in out[6 * i:6 * i + 6]) for i in range(nn)]
+
+
+def sg2v_plan_estimate_scale(handle) -> float:
+    s = ctypes.c_double()
+    _check(_lib.sg2v_plan_estimate_scale(handle, ctypes.byref(s)), "sg2v_plan_estimate_scale")
+    return s.value
+
+
+def sg2v_count(graph, plan, colours, precision: int = SG2V_FP64, per_vertex=None, stream=None):
+    """Returns (total, estimate); fills per_vertex ([n] float64) when given."""
+    t, e = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sg2v_count(graph, plan, _ptr(colours), int(precision), _ptr(per_vertex), ctypes.byref(t),
+                           ctypes.byref(e), _stream(stream)), "sg2v_count")
+    return t.value, e.value
+
+
+def sg2v_count_batched(graph, plans: Sequence[int], colours, B: int, precision: int = SG2V_FP32,
+                       per_vertex=None, totals=None, estimates=None, stream=None) -> None:
+    arr = (_p * len(plans))(*plans)
+    _check(_lib.sg2v_count_batched(graph, arr, len(plans), _ptr(colours), int(B), int(precision),
+                                   _ptr(per_vertex), _ptr(totals), _ptr(estimates), _stream(stream)),
+           "sg2v_count_batched")
+
+
+def sg2v_profile_enable(enable: bool = True) -> None:
+    _check(_lib.sg2v_profile_enable(1 if enable else 0), "sg2v_profile_enable")
+
+
+def sg2v_profile_reset() -> None:
+    _check(_lib.sg2v_profile_reset(), "sg2v_profile_reset")
+
+
+def sg2v_profile_read() -> list:
+    """[{name, launches, total_ms, bytes_per_launch}] of the kernels timed so far."""
+    cnt = _i32()
+    _check(_lib.sg2v_profile_read(None, 0, ctypes.byref(cnt)), "sg2v_profile_read")
+    recs = (KernelRecord * max(cnt.value, 1))()
+    _check(_lib.sg2v_profile_read(ctypes.cast(recs, _p), cnt.value, ctypes.byref(cnt)), "sg2v_profile_read")
+    return [dict(name=r.name.decode(), launches=r.launches, total_ms=r.total_ms, bytes_per_launch=r.bytes_per_launch)
+            for r in recs[:cnt.value]]
+
+
+def sg2v_launch_count() -> int:
+    return int(_lib.sg2v_launch_count())
+
+
+# ------------------------------------------------------------ convenience
+
+class Graph:
+    """Owns a library graph handle (CSR copied onto the current device)."""
+
+    def __init__(self, row_ptr, col_idx, weights=None, validate: bool = True):
+        rp = row_ptr if hasattr(row_ptr, "data_ptr") else np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = col_idx if hasattr(col_idx, "data_ptr") else np.ascontiguousarray(col_idx, dtype=np.int32)
+        w = None
+        if weights is not None:
+            w = weights if hasattr(weights, "data_ptr") else np.ascontiguousarray(weights, dtype=np.float32)
+        self.n = int(rp.shape[0]) - 1
+        self.nnz = int(ci.shape[0])
+        self.handle = sg2v_graph_create(self.n, self.nnz, rp, ci, w, 0 if validate else SG2V_GRAPH_SKIP_VALIDATION)
+
+    def info(self):
+        return sg2v_graph_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sg2v_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owns a template plan handle."""
+
+    def __init__(self, parent: Sequence[int], root: int = 0, num_colours: Optional[int] = None):
+        self.parent = tuple(int(x) for x in parent)
+        self.k = len(self.parent)
+        self.kc = int(num_colours or self.k)
+        self.root = root
+        self.handle = sg2v_template_plan(self.parent, root, self.kc)
+        self.alpha, self.num_nodes, self.max_cols = sg2v_plan_info(self.handle)
+        self.scale = sg2v_plan_estimate_scale(self.handle)
+
+    def nodes(self):
+        return sg2v_plan_nodes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sg2v_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def count(graph: Graph, plan: Plan, colours, precision: str = "fp64", per_vertex: bool = True, stream=None):
+    """One colouring: returns (per_vertex float64 tensor on colours' device or
+    None, total, estimate)."""
+    import torch
+
+    dev = colours.device if hasattr(colours, "device") else torch.device("cuda")
+    pv = torch.empty(graph.n, dtype=torch.float64, device=dev) if per_vertex else None
+    total, est = sg2v_count(graph.handle, plan.handle, colours, PRECISIONS[precision], pv, stream)
+    return pv, total, est
+
+
+def count_batched(graph: Graph, plans: Sequence[Plan], colours, precision: str = "fp32", per_vertex: bool = False,
+                  stream=None):
+    """B colourings ([B, n] int8) x len(plans) templates: returns
+    (per_vertex [P, B, n] or None, totals [P, B], estimates [P, B]) as float64
+    tensors on colours' device."""
+    import torch
+
+    B = int(colours.shape[0])
+    dev = colours.device if hasattr(colours, "device") else torch.device("cuda")
+    P = len(plans)
+    pv = torch.empty((P, B, graph.n), dtype=torch.float64, device=dev) if per_vertex else None
+    tot = torch.empty((P, B), dtype=torch.float64, device=dev)
+    est = torch.empty((P, B), dtype=torch.float64, device=dev)
+    sg2v_count_batched(graph.handle, [p.handle for p in plans], colours, B, PRECISIONS[precision], pv, tot, est,
+                       stream)
+    return pv, tot, est

@@ -1,0 +1,375 @@
+// Template partitioning, sub-template sharing, automorphisms and the
+// colour-set index tables (host only; no CUDA calls).
+//
+// Sec. 2.3.2: the template is split recursively at its root: one edge
+// (rho, tau) is cut, the part keeping rho is the active child T_{s,a}, the
+// subtree of tau is the passive child T_{s,p}; recursion ends at single
+// vertices.  Alg. 2 processes sub-templates children-first.
+// Table 1: M_s has one column per colour set of size |T_s|; the column index
+// I_C is not fixed by the paper -- this library uses colex rank.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sg2v_internal.h"
+
+namespace sg2v {
+
+namespace {
+struct BinomTable {
+    int64_t c[33][33];
+    BinomTable() {
+        std::memset(c, 0, sizeof c);
+        for (int n = 0; n <= 32; ++n) {
+            c[n][0] = 1;
+            for (int r = 1; r <= n; ++r) c[n][r] = c[n - 1][r - 1] + (r <= n - 1 ? c[n - 1][r] : 0);
+        }
+    }
+};
+const BinomTable &binoms() {
+    static BinomTable t;
+    return t;
+}
+}  // namespace
+
+int64_t binom(int n, int r) {
+    if (n < 0 || n > 32 || r < 0 || r > n) return 0;
+    return binoms().c[n][r];
+}
+
+uint32_t colex_rank(uint32_t mask) {
+    uint32_t r = 0;
+    int i = 0;
+    while (mask) {
+        int c = __builtin_ctz(mask);
+        r += (uint32_t)binom(c, i + 1);
+        ++i;
+        mask &= mask - 1;
+    }
+    return r;
+}
+
+// Next larger mask with the same number of set bits (Gosper); colex order.
+static inline uint32_t next_same_popcount(uint32_t x) {
+    uint32_t c = x & (0u - x);
+    uint32_t r = x + c;
+    return (((r ^ x) >> 2) / c) | r;
+}
+
+void build_tables(int kc, int t, int a, ColumnTables *out) {
+    const int64_t wt = binom(kc, t);
+    out->gather.clear();
+    out->splits.clear();
+    out->nsplit = 0;
+    if (a == 1) {
+        out->gather.assign((size_t)(kc * wt), -1);
+        uint32_t S = (1u << t) - 1;
+        for (int64_t s = 0; s < wt; ++s, S = next_same_popcount(S)) {
+            for (int c = 0; c < kc; ++c)
+                if (S >> c & 1u) out->gather[(size_t)(c * wt + s)] = (int32_t)colex_rank(S ^ (1u << c));
+        }
+        return;
+    }
+    const int ns = (int)binom(t, a);
+    out->nsplit = ns;
+    out->splits.resize((size_t)(wt * ns));
+    uint32_t S = (1u << t) - 1;
+    for (int64_t s = 0; s < wt; ++s, S = next_same_popcount(S)) {
+        int j = 0;
+        // sub-masks of S in increasing order, keeping those with a elements
+        for (uint32_t A = 0;;) {
+            A = (A - S) & S;  // next sub-mask of S
+            if (A == 0) break;
+            if (__builtin_popcount(A) == a) {
+                out->splits[(size_t)(s * ns + j)] = colex_rank(A) | (colex_rank(S ^ A) << 16);
+                ++j;
+            }
+        }
+    }
+}
+
+}  // namespace sg2v
+
+namespace {
+
+struct Tree {
+    int k = 0;
+    std::vector<int> par;
+    std::vector<std::vector<int>> children;  // increasing vertex index
+    std::vector<std::vector<int>> adj;
+};
+
+// Validates the parent array and orients the tree from `root`.
+sg2v_status build_tree(int k, const int32_t *parent, int root, Tree *T) {
+    if (root < 0 || root >= k) {
+        sg2v::set_error("root out of range");
+        return SG2V_ERR_NOT_A_TREE;
+    }
+    T->k = k;
+    T->adj.assign(k, {});
+    int roots = 0;
+    for (int i = 0; i < k; ++i) {
+        int p = parent[i];
+        if (p == -1) {
+            ++roots;
+            continue;
+        }
+        if (p < 0 || p >= k || p == i) {
+            sg2v::set_error("parent entry out of range");
+            return SG2V_ERR_NOT_A_TREE;
+        }
+        T->adj[i].push_back(p);
+        T->adj[p].push_back(i);
+    }
+    if (roots != 1) {
+        sg2v::set_error("parent array must contain exactly one -1");
+        return SG2V_ERR_NOT_A_TREE;
+    }
+    for (auto &a : T->adj) std::sort(a.begin(), a.end());
+    T->par.assign(k, -2);
+    T->children.assign(k, {});
+    std::vector<int> queue{root};
+    T->par[root] = -1;
+    for (size_t h = 0; h < queue.size(); ++h) {
+        int x = queue[h];
+        for (int y : T->adj[x]) {
+            if (y == T->par[x]) continue;
+            if (T->par[y] != -2) {
+                sg2v::set_error("parent array contains a cycle");
+                return SG2V_ERR_NOT_A_TREE;
+            }
+            T->par[y] = x;
+            T->children[x].push_back(y);
+            queue.push_back(y);
+        }
+    }
+    if ((int)queue.size() != k) {
+        sg2v::set_error("parent array is not connected");
+        return SG2V_ERR_NOT_A_TREE;
+    }
+    return SG2V_OK;
+}
+
+// AHU canonical string of the subtree of x when the tree is entered from
+// `from` (x's neighbours other than `from` are its children); also returns
+// the number of automorphisms of that rooted subtree.
+std::string rooted_form(const Tree &T, int x, int from, uint64_t *aut) {
+    std::vector<std::string> forms;
+    uint64_t a = 1;
+    for (int y : T.adj[x]) {
+        if (y == from) continue;
+        uint64_t ay;
+        forms.push_back(rooted_form(T, y, x, &ay));
+        a *= ay;
+    }
+    std::sort(forms.begin(), forms.end());
+    for (size_t i = 0; i < forms.size();) {
+        size_t j = i;
+        while (j < forms.size() && forms[j] == forms[i]) ++j;
+        for (size_t m = 2; m <= j - i; ++m) a *= m;  // identical children permute freely
+        i = j;
+    }
+    std::string s = "(";
+    for (auto &f : forms) s += f;
+    s += ")";
+    *aut = a;
+    return s;
+}
+
+// Automorphisms of the unrooted tree: root it at its centre (or at the two
+// ends of its central edge).
+uint64_t automorphisms(const Tree &T) {
+    int k = T.k;
+    if (k == 1) return 1;
+    std::vector<int> ecc(k, 0);
+    for (int s = 0; s < k; ++s) {
+        std::vector<int> d(k, -1);
+        std::vector<int> q{s};
+        d[s] = 0;
+        for (size_t h = 0; h < q.size(); ++h)
+            for (int y : T.adj[q[h]])
+                if (d[y] < 0) {
+                    d[y] = d[q[h]] + 1;
+                    q.push_back(y);
+                }
+        ecc[s] = *std::max_element(d.begin(), d.end());
+    }
+    int best = *std::min_element(ecc.begin(), ecc.end());
+    std::vector<int> centres;
+    for (int s = 0; s < k; ++s)
+        if (ecc[s] == best) centres.push_back(s);
+    if (centres.size() == 1) {
+        uint64_t a;
+        rooted_form(T, centres[0], -1, &a);
+        return a;
+    }
+    int c1 = centres[0], c2 = centres[1];
+    uint64_t a1, a2;
+    std::string f1 = rooted_form(T, c1, c2, &a1);
+    std::string f2 = rooted_form(T, c2, c1, &a2);
+    return a1 * a2 * (f1 == f2 ? 2u : 1u);
+}
+
+struct PlanBuilder {
+    const Tree &T;
+    std::vector<sg2v::PlanNode> nodes;
+    std::map<std::string, int> by_form;
+    std::map<std::string, int> size_of_form;
+
+    explicit PlanBuilder(const Tree &t) : T(t) {}
+
+    std::string form_of(int x, int hi) {
+        // rooted sub-template: x with its first `hi` children (and their subtrees)
+        std::vector<std::string> forms;
+        for (int i = 0; i < hi; ++i) {
+            uint64_t unused;
+            int y = T.children[x][i];
+            forms.push_back(rooted_form(T, y, x, &unused));
+        }
+        std::sort(forms.begin(), forms.end());
+        std::string s = "(";
+        for (auto &f : forms) s += f;
+        return s + ")";
+    }
+
+    // Returns the node id of sub-template (x, first hi children), kLeaf for a
+    // single vertex; *size receives its number of vertices.
+    int make(int x, int hi, int *size) {
+        if (hi == 0) {
+            *size = 1;
+            return sg2v::kLeaf;
+        }
+        std::string f = form_of(x, hi);
+        auto it = by_form.find(f);
+        if (it != by_form.end()) {
+            *size = nodes[it->second].t;
+            return it->second;
+        }
+        int tau = T.children[x][hi - 1];  // cut the edge to the last kept child
+        int a, p;
+        int ia = make(x, hi - 1, &a);
+        int ip = make(tau, (int)T.children[tau].size(), &p);
+        sg2v::PlanNode nd;
+        nd.t = a + p;
+        nd.a = a;
+        nd.p = p;
+        nd.active = ia;
+        nd.passive = ip;
+        nd.canon = f;
+        nodes.push_back(nd);
+        int id = (int)nodes.size() - 1;
+        by_form[f] = id;
+        *size = nd.t;
+        return id;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+sg2v_status sg2v_template_plan(int32_t k, const int32_t *parent, int32_t root, int32_t num_colours,
+                               const void *opts, sg2v_plan **out) {
+    (void)opts;
+    if (!out || !parent) {
+        sg2v::set_error("null argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    if (k < 1 || k > sg2v::kMaxColours) {
+        sg2v::set_error("template size must be in [1, 16]");
+        return k < 1 ? SG2V_ERR_INVALID_ARGUMENT : SG2V_ERR_UNSUPPORTED;
+    }
+    if (num_colours < k) {
+        sg2v::set_error("num_colours must be >= template size");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (num_colours > sg2v::kMaxColours) {
+        sg2v::set_error("num_colours above 16 is not supported");
+        return SG2V_ERR_UNSUPPORTED;
+    }
+    Tree T;
+    sg2v_status st = build_tree(k, parent, root, &T);
+    if (st != SG2V_OK) return st;
+    sg2v_plan *plan = new (std::nothrow) sg2v_plan();
+    if (!plan) return SG2V_ERR_OUT_OF_MEMORY;
+    plan->k = k;
+    plan->kc = num_colours;
+    plan->root = root;
+    plan->parent.assign(parent, parent + k);
+    plan->alpha = automorphisms(T);
+    PlanBuilder B(T);
+    int size;
+    int rid = B.make(root, (int)T.children[root].size(), &size);
+    plan->nodes = std::move(B.nodes);
+    if (rid != sg2v::kLeaf) plan->nodes[rid].is_root = true;
+    plan->max_cols = sg2v::binom(num_colours, 1);
+    for (auto &nd : plan->nodes) {
+        plan->max_cols = std::max<int64_t>(plan->max_cols, sg2v::binom(num_colours, nd.t));
+        plan->max_cols = std::max<int64_t>(plan->max_cols, sg2v::binom(num_colours, nd.p));
+    }
+    // 1 / (P alpha) with P = kc! / ((kc - k)! kc^k)
+    unsigned __int128 num = 1, den = plan->alpha;
+    for (int i = 0; i < k; ++i) {
+        num *= (unsigned __int128)num_colours;
+        den *= (unsigned __int128)(num_colours - i);
+    }
+    plan->scale_ld = (long double)num / (long double)den;
+    plan->scale = (double)plan->scale_ld;
+    *out = plan;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_plan_destroy(sg2v_plan *plan) {
+    delete plan;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_plan_info(const sg2v_plan *plan, int64_t *automorphisms_out, int32_t *num_nodes,
+                           int64_t *max_cols) {
+    if (!plan) {
+        sg2v::set_error("null plan");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (automorphisms_out) *automorphisms_out = (int64_t)plan->alpha;
+    if (num_nodes) *num_nodes = (int32_t)plan->nodes.size();
+    if (max_cols) *max_cols = plan->max_cols;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_plan_nodes(const sg2v_plan *plan, int32_t *out, int64_t capacity) {
+    if (!plan || (!out && !plan->nodes.empty())) {
+        sg2v::set_error("null argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (capacity < (int64_t)(6 * plan->nodes.size())) {
+        sg2v::set_error("output capacity too small");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    for (size_t i = 0; i < plan->nodes.size(); ++i) {
+        const auto &nd = plan->nodes[i];
+        int32_t *o = out + 6 * i;
+        o[0] = nd.t;
+        o[1] = nd.a;
+        o[2] = nd.p;
+        o[3] = nd.active;
+        o[4] = nd.passive;
+        o[5] = nd.is_root ? 1 : 0;
+    }
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_plan_estimate_scale(const sg2v_plan *plan, double *scale) {
+    if (!plan || !scale) {
+        sg2v::set_error("null argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    *scale = plan->scale;
+    return SG2V_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Internal structures shared by the planner, the executor and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sg2v.h"
+
+namespace sg2v {
+
+constexpr int kMaxColours = 16;
+constexpr int kLeaf = -1;
+
+// Binomial coefficient C(n, r) for 0 <= n <= 32 (0 when r < 0 or r > n).
+int64_t binom(int n, int r);
+
+// Colex rank of a colour set: with elements c_0 < c_1 < ... the rank is
+// sum_i C(c_i, i + 1).  Sets of one size enumerated in increasing bitmask
+// order have consecutive ranks 0, 1, 2, ...
+uint32_t colex_rank(uint32_t mask);
+
+// One DP node: sub-template T_s with |T_s| = t, split into an active child of
+// a vertices and a passive child of p vertices (Sec. 2.3.2).  Children are
+// node ids or kLeaf for a single vertex.
+struct PlanNode {
+    int t = 0, a = 0, p = 0;
+    int active = kLeaf, passive = kLeaf;
+    bool is_root = false;
+    std::string canon;  // AHU form of the rooted sub-template
+};
+
+struct ColumnTables {
+    // gather[c * Wt + rank(S)] = rank(S minus {c}) if c in S else -1 (a = 1 nodes)
+    std::vector<int32_t> gather;
+    // splits[rank(S) * nsplit + j] = rank(S_a) | rank(S minus S_a) << 16
+    std::vector<uint32_t> splits;
+    int nsplit = 0;
+};
+
+}  // namespace sg2v
+
+struct sg2v_plan {
+    int k = 0, kc = 0, root = 0;
+    std::vector<int> parent;
+    uint64_t alpha = 1;
+    double scale = 0.0;  // 1 / (P * alpha)
+    long double scale_ld = 0.0L;
+    std::vector<sg2v::PlanNode> nodes;  // post-order, root last (empty when k == 1)
+    int64_t max_cols = 1;
+};
+
+namespace sg2v {
+// Builds the split tables of node (t, a) for kc colours.
+void build_tables(int kc, int t, int a, ColumnTables *out);
+// Thread-local error detail.
+void set_error(const std::string &msg);
+}  // namespace sg2v

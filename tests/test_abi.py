@@ -1,0 +1,163 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry
+point its header declares, and its planner (pure host code) agrees with the
+paper's definitions (Sec. 2.3.2 partitioning, Alg. 1 alpha and P)."""
+import os
+import re
+from fractions import Fraction
+from math import comb, factorial
+
+import numpy as np
+import pytest
+
+import oracle
+import sg2v_inputs as si
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as s
+
+    return s
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sg2v_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert "sg2v_count" in declared and "sg2v_graph_create" in declared
+    for name in declared:
+        assert hasattr(lib._lib, name), name
+    assert set(lib.EXPORTED) <= declared
+
+
+def test_version_and_status_strings(lib):
+    assert lib.sg2v_version() >= 100
+    for code in range(10):
+        assert lib.sg2v_status_string(code)
+    assert lib.sg2v_status_string(3) == "colour out of range"
+
+
+TREES = [(-1,), (-1, 0), (-1, 0, 1), (-1, 0, 0), (-1, 0, 1, 1), (-1, 0, 0, 0), si.PATH5.parent, si.PATH7.parent,
+         si.STAR7.parent, si.TREE7.parent, si.TREE8.parent, si.TREE10.parent, si.TREE15.parent,
+         (-1, 0, 1, 2, 2, 0), (-1, 0, 0, 1, 2, 3)]
+
+
+@pytest.mark.parametrize("parent", TREES)
+def test_automorphisms_match_oracle(lib, parent):
+    """The planner's alpha (AHU canonical forms) equals the oracle's
+    brute-force count of self-maps."""
+    plan = lib.Plan(parent)
+    assert plan.alpha == oracle.automorphisms(parent)
+
+
+def _subtree_sizes(parent, root):
+    k = len(parent)
+    adj = [[] for _ in range(k)]
+    for i, p in enumerate(parent):
+        if p >= 0:
+            adj[i].append(p)
+            adj[p].append(i)
+    size = {}
+
+    def go(x, frm):
+        s = 1
+        for y in adj[x]:
+            if y != frm:
+                s += go(y, x)
+        size[x] = s
+        return s
+
+    go(root, -1)
+    return [size[v] for v in range(k) if v != root]
+
+
+@pytest.mark.parametrize("parent", TREES)
+def test_plan_structure(lib, parent):
+    """Children precede parents, t = a + p, the root node has t = k and the
+    passive sub-templates are exactly the subtrees hanging below rho's
+    descendants (sum over cuts of C(kc, p) = sum over non-root v of
+    C(kc, |subtree(v)|) before sharing)."""
+    k = len(parent)
+    for root in range(k):
+        plan = lib.Plan(parent, root)
+        nodes = plan.nodes()
+        if k == 1:
+            assert nodes == []
+            continue
+        sizes = {}
+        for i, (t, a, p, ia, ip, is_root) in enumerate(nodes):
+            assert t == a + p and a >= 1 and p >= 1
+            for child, sz in ((ia, a), (ip, p)):
+                if child == -1:
+                    assert sz == 1
+                else:
+                    assert 0 <= child < i and nodes[child][0] == sz
+            sizes[i] = t
+            assert is_root == (i == len(nodes) - 1)
+        assert nodes[-1][0] == k
+        # expand shared nodes back into the full partition tree and compare
+        def passives(i):
+            t, a, p, ia, ip, _ = nodes[i]
+            out = [p]
+            if ia != -1:
+                out += passives(ia)
+            if ip != -1:
+                out += passives(ip)
+            return out
+
+        assert sorted(passives(len(nodes) - 1)) == sorted(_subtree_sizes(parent, root))
+
+
+def test_estimate_scale(lib):
+    """1/(P alpha) with P = kc!/((kc-k)! kc^k) (Alg. 1)."""
+    for parent in TREES:
+        k = len(parent)
+        for kc in (k, k + 1):
+            if kc > 16:
+                continue
+            plan = lib.Plan(parent, 0, kc)
+            expect = Fraction(kc ** k * factorial(kc - k), factorial(kc) * plan.alpha)
+            assert plan.scale == float(expect)
+
+
+def test_invalid_templates(lib):
+    with pytest.raises(lib.Sg2vError) as e:
+        lib.Plan((-1, -1, 0))
+    assert e.value.status == lib.SG2V_ERR_NOT_A_TREE
+    with pytest.raises(lib.Sg2vError) as e:
+        lib.Plan((1, 2, 0))
+    assert e.value.status == lib.SG2V_ERR_NOT_A_TREE
+    with pytest.raises(lib.Sg2vError) as e:
+        lib.Plan((-1, 0, 5))
+    assert e.value.status == lib.SG2V_ERR_NOT_A_TREE
+    with pytest.raises(lib.Sg2vError) as e:
+        lib.Plan((-1, 0), root=2)
+    assert e.value.status == lib.SG2V_ERR_NOT_A_TREE
+    with pytest.raises(lib.Sg2vError) as e:
+        lib.Plan((-1, 0, 1), num_colours=2)
+    assert e.value.status == lib.SG2V_ERR_INVALID_ARGUMENT
+    with pytest.raises(lib.Sg2vError) as e:
+        lib.Plan((-1,) + (0,) * 16)
+    assert e.value.status == lib.SG2V_ERR_UNSUPPORTED
+
+
+def test_sharing_of_isomorphic_subtemplates(lib):
+    """tree10's two halves below the root are isomorphic rooted trees: the
+    root node reads one shared table as both children."""
+    nodes = lib.Plan(si.TREE10.parent).nodes()
+    assert len(nodes) == 5
+    t, a, p, ia, ip, _ = nodes[-1]
+    assert (t, a, p) == (10, 5, 5) and ia == ip

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the exact CPU oracle.
+
+Bars (colour-coding counts, SubGraph2Vec Alg. 1-5):
+  FP64 tables: bit-exact when every table entry is below 2^53 (the oracle
+               reports the largest entry), else relative error <= 1e-12;
+  FP32 tables: relative error <= 1e-4 on totals and on every non-zero
+               per-vertex count, zeros exact;
+  estimate:    within 2 ulp of the exact rational total / (P alpha).
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import sg2v_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FP32_RTOL = 1e-4
+FP64_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as s
+
+    return s
+
+
+def _dev(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _check_fp64(got_pv, got_total, ref, exact):
+    want = np.array([float(x) for x in ref.per_vertex_values()], dtype=np.float64)
+    if exact:
+        assert np.array_equal(got_pv, want)
+        assert got_total == float(ref.total_value())
+    else:
+        nz = want != 0
+        assert np.all(got_pv[~nz] == 0)
+        rel = np.abs(got_pv[nz] - want[nz]) / want[nz]
+        assert rel.size == 0 or rel.max() <= FP64_RTOL, rel.max()
+        tv = float(ref.total_value())
+        assert abs(got_total - tv) <= FP64_RTOL * abs(tv)
+
+
+def _check_fp32(got_pv, got_total, ref):
+    want = np.array([float(x) for x in ref.per_vertex_values()], dtype=np.float64)
+    nz = want != 0
+    assert np.all(got_pv[~nz] == 0)
+    if nz.any():
+        rel = np.abs(got_pv[nz] - want[nz]) / want[nz]
+        assert rel.max() <= FP32_RTOL, rel.max()
+    tv = float(ref.total_value())
+    assert abs(got_total - tv) <= FP32_RTOL * abs(tv)
+
+
+def _ulp_close(a: float, exact: Fraction, ulps: int = 2) -> bool:
+    b = float(exact)
+    return abs(a - b) <= ulps * np.spacing(abs(b)) + 0.0
+
+
+def _run(sg, g, parent, root, col, kc=None, weights=None):
+    graph = sg.Graph(g.row_ptr, g.col_idx, weights)
+    plan = sg.Plan(parent, root, kc)
+    ref = oracle.count(g.row_ptr, g.col_idx, parent, root, col, kc, weights)
+    dcol = _dev(col)
+    pv64, t64, e64 = sg.count(graph, plan, dcol, "fp64")
+    pv32, t32, e32 = sg.count(graph, plan, dcol, "fp32")
+    return ref, plan, (pv64.cpu().numpy(), t64, e64), (pv32.cpu().numpy(), t32, e32)
+
+
+def test_er2000_path5_fp64_bit_exact(sg):
+    """The small workload: ER n=2000 avg degree 8, path of 5 rooted at an end,
+    k = 5, one colouring."""
+    g = si.workload_graph("er2000")
+    col = si.colouring(g.n, 5, 0)
+    ref, plan, r64, r32 = _run(sg, g, si.PATH5.parent, 0, col)
+    assert ref.max_bits <= 53
+    _check_fp64(r64[0], r64[1], ref, exact=True)
+    assert _ulp_close(r64[2], oracle.estimate(ref.total, 5, plan.alpha))
+    _check_fp32(r32[0], r32[1], ref)
+
+
+TEMPLATES = [(-1, 0), (-1, 0, 1), (-1, 0, 0), (-1, 0, 1, 1), (-1, 0, 0, 0), si.PATH5.parent, si.TREE7.parent,
+             si.STAR7.parent, si.PATH7.parent, si.TREE8.parent, (-1, 0, 1, 2, 2, 0), (-1, 0, 0, 1, 2, 3)]
+
+
+@pytest.mark.parametrize("parent", TEMPLATES)
+def test_templates_on_random_graphs(sg, parent):
+    """Every template shape, several roots and colour counts, on graphs whose
+    vertex counts span several warps' worth of rows and end ragged."""
+    k = len(parent)
+    for seed, (n, m) in enumerate([(333, 1400), (1531, 9000)]):
+        g = si.erdos_renyi(n, m, seed=seed + 3)
+        for kc in (k, min(16, k + 2)):
+            for root in sorted({0, k - 1, k // 2}):
+                col = si.colouring(n, kc, seed, root)
+                ref, plan, r64, r32 = _run(sg, g, parent, root, col, kc)
+                _check_fp64(r64[0], r64[1], ref, exact=ref.max_bits <= 53)
+                _check_fp32(r32[0], r32[1], ref)
+                assert _ulp_close(r64[2], oracle.estimate(ref.total, k, plan.alpha, kc))
+
+
+def test_split_rows_power_law(sg):
+    """Hubs with degree far above the row chunk exercise split rows (partial
+    sums folded by the last chunk)."""
+    g = si.rmat(13, 60000, seed=5)
+    assert g.degrees().max() > 4096
+    col = si.colouring(g.n, 7, 2)
+    for parent in (si.TREE7.parent, si.PATH7.parent, si.STAR7.parent):
+        ref, plan, r64, r32 = _run(sg, g, parent, 0, col)
+        _check_fp64(r64[0], r64[1], ref, exact=ref.max_bits <= 53)
+        _check_fp32(r32[0], r32[1], ref)
+
+
+def test_weighted_graph(sg):
+    """Weighted form: products of FP32 edge weights; exact dyadic oracle."""
+    g = si.chung_lu(3000, 20000, 2.3, seed=1)
+    w = si.arc_weights(g, si.edge_weights(g, seed=1))
+    col = si.colouring(g.n, 8, 4)
+    ref, plan, r64, r32 = _run(sg, g, si.TREE8.parent, 0, col, weights=w)
+    _check_fp64(r64[0], r64[1], ref, exact=False)
+    _check_fp32(r32[0], r32[1], ref)
+
+
+def test_batched_templates_and_colourings(sg):
+    """Several colourings x several templates in one call equal one oracle
+    run per (template, colouring)."""
+    import torch
+
+    g = si.rmat(12, 30000, seed=7)
+    B = 5
+    cols = si.colourings(g.n, 7, B, seed=3)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    temps = [si.PATH7, si.STAR7, si.TREE7]
+    plans = [sg.Plan(t.parent) for t in temps]
+    dcols = _dev(cols)
+    for prec in ("fp64", "fp32"):
+        pv, tot, est = sg.count_batched(graph, plans, dcols, prec, per_vertex=True)
+        pv, tot, est = pv.cpu().numpy(), tot.cpu().numpy(), est.cpu().numpy()
+        for i, t in enumerate(temps):
+            for b in range(B):
+                ref = oracle.count(g.row_ptr, g.col_idx, t.parent, 0, cols[b])
+                if prec == "fp64":
+                    _check_fp64(pv[i, b], tot[i, b], ref, exact=ref.max_bits <= 53)
+                    assert _ulp_close(est[i, b], oracle.estimate(ref.total, 7, plans[i].alpha))
+                else:
+                    _check_fp32(pv[i, b], tot[i, b], ref)
+
+
+def test_host_buffers_match_device_buffers(sg):
+    """Host (numpy) colours and outputs take the copy path and agree."""
+    g = si.erdos_renyi(2500, 12000, seed=9)
+    col = si.colouring(g.n, 6, 1)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan((-1, 0, 1, 1, 0, 4))
+    pv_dev, t_dev, e_dev = sg.count(graph, plan, _dev(col), "fp64")
+    pv_host = np.zeros(g.n, dtype=np.float64)
+    t_host, e_host = sg.sg2v_count(graph.handle, plan.handle, col, sg.SG2V_FP64, pv_host)
+    assert np.array_equal(pv_dev.cpu().numpy(), pv_host)
+    assert t_dev == t_host and e_dev == e_host
+
+
+def test_single_vertex_and_edge_templates(sg):
+    g = si.erdos_renyi(500, 2000, seed=2)
+    for parent, kc in (((-1,), 1), ((-1,), 3), ((-1, 0), 2), ((-1, 0), 4)):
+        col = si.colouring(g.n, kc, 5)
+        ref, plan, r64, r32 = _run(sg, g, parent, 0, col, kc)
+        _check_fp64(r64[0], r64[1], ref, exact=True)
+        _check_fp32(r32[0], r32[1], ref)
+
+
+def test_isolated_vertices_and_empty_rows(sg):
+    """Rows with no arcs still produce (zero) rows; a graph without edges
+    counts nothing for k >= 2."""
+    g = si.from_edges(100, [(0, 1), (1, 2), (2, 3), (50, 51)])
+    col = (np.arange(100) % 4).astype(np.int8)
+    ref, plan, r64, r32 = _run(sg, g, (-1, 0, 1, 2), 0, col)
+    _check_fp64(r64[0], r64[1], ref, exact=True)
+    g = si.from_edges(10, [])
+    col = np.zeros(10, np.int8)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    pv, t, e = sg.count(graph, sg.Plan((-1, 0), 0, 2), _dev(col), "fp64")
+    assert t == 0 and not pv.any()
+
+
+def test_colour_out_of_range_is_reported(sg):
+    g = si.erdos_renyi(200, 600, seed=1)
+    col = si.colouring(g.n, 4, 1)
+    col[17] = 4
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    with pytest.raises(sg.Sg2vError) as e:
+        sg.count(graph, sg.Plan((-1, 0, 1, 2)), _dev(col), "fp64")
+    assert e.value.status == sg.SG2V_ERR_COLOUR_OUT_OF_RANGE
+    col[17] = -1
+    with pytest.raises(sg.Sg2vError) as e:
+        sg.count(graph, sg.Plan((-1, 0, 1, 2)), _dev(col), "fp32")
+    assert e.value.status == sg.SG2V_ERR_COLOUR_OUT_OF_RANGE
+
+
+def test_full_size_rmat20_tree10(sg):
+    """The 1M-vertex workload (R-MAT scale 20, 2^24 edges, tree10, k = 10):
+    total and 4,000+ sampled per-vertex counts against stored oracle values
+    (tests/golden, written by make_golden.py from the oracle only)."""
+    import torch
+
+    gold = json.load(open(os.path.join(HERE, "golden", "rmat20_16m_tree10_k10.json")))
+    g = si.workload_graph(gold["graph"])
+    import hashlib
+
+    h = hashlib.sha256()
+    h.update(g.row_ptr.tobytes())
+    h.update(g.col_idx.tobytes())
+    assert h.hexdigest() == gold["graph_sha256"], "generator did not rebuild the stored graph"
+    col = si.colouring(g.n, gold["num_colours"], gold["colouring_seed"], gold["colouring_index"])
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(gold["template"], gold["root"], gold["num_colours"])
+    idx = np.array(gold["sample_vertices"])
+    want = np.array([float(int(x)) for x in gold["sample_counts"]])
+    total = int(gold["total"])
+    dcol = _dev(col)
+    for prec, tol in (("fp64", FP64_RTOL), ("fp32", FP32_RTOL)):
+        pv, t, e = sg.count(graph, plan, dcol, prec)
+        got = pv.cpu().numpy()[idx]
+        nz = want != 0
+        assert np.all(got[~nz] == 0)
+        assert (np.abs(got[nz] - want[nz]) / want[nz]).max() <= tol
+        assert abs(t - total) <= tol * total
+        assert float(e) == pytest.approx(float(oracle.estimate(total, 10, plan.alpha)), rel=tol)
+        # the per-vertex counts are the total's parts
+        assert float(pv.sum()) == pytest.approx(t, rel=1e-9)
+        del pv
+        torch.cuda.empty_cache()

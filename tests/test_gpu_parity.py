@@ -116,11 +116,24 @@ def test_templates_on_random_graphs(sg, parent):
                 assert _ulp_close(r64[2], oracle.estimate(ref.total, k, plan.alpha, kc))
 
 
-def test_split_rows_power_law(sg):
-    """Hubs with degree far above the row chunk exercise split rows (partial
-    sums folded by the last chunk)."""
-    g = si.rmat(13, 60000, seed=5)
-    assert g.degrees().max() > 4096
+def _hub_graph(seed: int):
+    """R-MAT base plus three hubs joined to thousands of vertices."""
+    base = si.rmat(13, 60000, seed=seed)
+    extra = []
+    for h, cnt in ((11, 5000), (4000, 3100), (8000, 1500)):
+        others = si.sample_indices(cnt, base.n, seed=seed + h)
+        extra += [(h, int(o)) for o in others if int(o) != h]
+    edges = {tuple(e) for e in base.edges.tolist()} | {(min(a, b), max(a, b)) for a, b in extra}
+    return si.from_edges(base.n, sorted(edges), "rmat13_hubs")
+
+
+@pytest.mark.parametrize("chunk", ["1024", "64"])
+def test_split_rows_power_law(sg, chunk, monkeypatch):
+    """Rows longer than the row chunk are split across warps (partial sums
+    folded by the last chunk); the chunk length is read at graph creation."""
+    monkeypatch.setenv("SG2V_CHUNK", chunk)
+    g = _hub_graph(5)
+    assert g.degrees().max() > 4 * int(chunk)
     col = si.colouring(g.n, 7, 2)
     for parent in (si.TREE7.parent, si.PATH7.parent, si.STAR7.parent):
         ref, plan, r64, r32 = _run(sg, g, parent, 0, col)

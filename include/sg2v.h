@@ -213,6 +213,41 @@ sg2v_status sg2v_profile_read(sg2v_kernel_record *out, int32_t capacity, int32_t
 /* Kernels launched by count calls since the last reset (profiling or not). */
 int64_t sg2v_launch_count(void);
 
+/* ------------------------------------------------------- allocation-free */
+
+/*
+ * sg2v_sum_counts_noalloc -- sums per-vertex counts into totals without
+ * allocating anything.  The paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory where they need a total: code
+ * being recorded into a CUDA graph, serving loops whose device memory is
+ * reserved up front by their own allocator, and code that must not stall
+ * other streams (cudaMalloc and cudaFree synchronise the device).
+ *
+ *   values  [nseg][n] double, device memory: e.g. the per_vertex output of
+ *           sg2v_count / sg2v_count_batched
+ *   n       values per segment, >= 1
+ *   nseg    segments, 1 <= nseg <= 1024 (larger requests are rejected with
+ *           SG2V_ERR_INVALID_ARGUMENT and nothing is launched)
+ *   totals  [nseg] double, device memory: totals[s] = sum of segment s.  When
+ *           every value is a non-negative integer below 2^128 the sum is
+ *           exact and rounded once to the nearest double (the same value
+ *           sg2v_count reports); otherwise it is a compensated FP64 sum; a
+ *           non-finite value gives a non-finite total
+ *   stream  the call is stream-ordered and returns without synchronising
+ *
+ * Scratch: a fixed 2.5 MiB device array inside the library (one partial sum
+ * per segment and block), which every GPU that loads the library keeps until
+ * the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  Each call overwrites the records it
+ * reads, so nothing carries over between calls, but all calls share the
+ * array: calls whose kernels overlap on the GPU (different streams without
+ * ordering) race and give wrong totals.
+ * Errors: INVALID_ARGUMENT (null, sizes, host pointers), CUDA.
+ */
+sg2v_status sg2v_sum_counts_noalloc(const double *values, int64_t n, int32_t nseg, double *totals,
+                                    sg2v_stream stream);
+
 /* ---------------------------------------------------------------- status */
 
 /* Static English name of a status code. */

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "sg2v_plan_estimate_scale": [_p, _p],
     "sg2v_count": [_p, _p, _p, ctypes.c_int, _p, _p, _p, _p],
     "sg2v_count_batched": [_p, _p, _i32, _p, _i32, ctypes.c_int, _p, _p, _p, _p],
+    "sg2v_sum_counts_noalloc": [_p, _i64, _i32, _p, _p],
 }
 for _name, _args in _SIGNATURES.items():
     _f = getattr(_lib, _name)
@@ -205,6 +206,13 @@ def sg2v_count_batched(graph, plans: Sequence[int], colours, B: int, precision: 
     _check(_lib.sg2v_count_batched(graph, arr, len(plans), _ptr(colours), int(B), int(precision),
                                    _ptr(per_vertex), _ptr(totals), _ptr(estimates), _stream(stream)),
            "sg2v_count_batched")
+
+
+def sg2v_sum_counts_noalloc(values, n: int, nseg: int, totals, stream=None) -> None:
+    """Sums device values [nseg][n] into device totals [nseg] without
+    allocating (see include/sg2v.h); stream-ordered, no synchronisation."""
+    _check(_lib.sg2v_sum_counts_noalloc(_ptr(values), int(n), int(nseg), _ptr(totals), _stream(stream)),
+           "sg2v_sum_counts_noalloc")
 
 
 def sg2v_profile_enable(enable: bool = True) -> None:

@@ -7,7 +7,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsg2v.so")
-SOURCES = ["api.cu", "kernels.cu", "planner.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "planner.cpp", "noalloc.cu"]
 HEADERS = ["kernels.cuh", "sg2v_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

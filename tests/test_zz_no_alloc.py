@@ -1,0 +1,102 @@
+"""sg2v_sum_counts_noalloc: totals without any device allocation.
+
+The entry point serves callers that cannot allocate device memory where they
+need a total (code recorded into a CUDA graph, serving loops whose memory is
+reserved up front by their own allocator, code that must not stall other
+streams).  It sums per-vertex counts the caller already holds, with its
+scratch in a fixed device array inside the library.  These tests compare its
+totals with those of sg2v_count / sg2v_count_batched on the same counts, on
+two calls in a row (the shared scratch must not carry anything over).  This
+file is collected last so that a run stopping at its first failure has run
+every other test.
+"""
+import numpy as np
+import pytest
+
+import sg2v_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as s
+
+    return s
+
+
+def test_noalloc_total_matches_count(sg):
+    import torch
+
+    g = si.workload_graph("er2000")
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(si.PATH5.parent)
+    col = torch.from_numpy(si.colouring(g.n, 5, 0)).cuda()
+    pv, total, _ = sg.count(graph, plan, col, "fp64")
+    out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.fill_(-1.0)
+        sg.sg2v_sum_counts_noalloc(pv, g.n, 1, out)
+        torch.cuda.synchronize()
+        assert out.item() == total  # exact integer sum rounded once, as sg2v_count
+
+
+def test_noalloc_batched_segments_match(sg):
+    import torch
+
+    g = si.rmat(12, 30000, seed=7)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plans = [sg.Plan(t.parent) for t in (si.PATH7, si.STAR7, si.TREE7)]
+    cols = torch.from_numpy(si.colourings(g.n, 7, 4, seed=3)).cuda()
+    for prec in ("fp64", "fp32"):
+        pv, tot, _ = sg.count_batched(graph, plans, cols, prec, per_vertex=True)
+        out = torch.empty(12, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            out.fill_(-1.0)
+            sg.sg2v_sum_counts_noalloc(pv, g.n, 12, out)
+            torch.cuda.synchronize()
+            assert torch.equal(out, tot.reshape(-1))
+
+
+def test_noalloc_weighted_values(sg):
+    """Non-integral counts (weighted graph): compensated sum, same tolerance
+    as the FP64 parity tests."""
+    import torch
+
+    g = si.chung_lu(3000, 20000, 2.3, seed=1)
+    w = si.arc_weights(g, si.edge_weights(g, seed=1))
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(si.TREE8.parent)
+    col = torch.from_numpy(si.colouring(g.n, 8, 4)).cuda()
+    pv, total, _ = sg.count(graph, plan, col, "fp64")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        sg.sg2v_sum_counts_noalloc(pv, g.n, 1, out)
+        torch.cuda.synchronize()
+        assert abs(out.item() - total) <= 1e-12 * abs(total)
+
+
+def test_noalloc_rejects_oversized_and_host_requests(sg):
+    import torch
+
+    vals = torch.ones((1025, 4), dtype=torch.float64, device="cuda")
+    out = torch.empty(1025, dtype=torch.float64, device="cuda")
+    with pytest.raises(sg.Sg2vError) as e:
+        sg.sg2v_sum_counts_noalloc(vals, 4, 1025, out)
+    assert e.value.status == sg.SG2V_ERR_INVALID_ARGUMENT
+    host = np.ones(4)
+    with pytest.raises(sg.Sg2vError) as e:
+        sg.sg2v_sum_counts_noalloc(host, 4, 1, out)
+    assert e.value.status == sg.SG2V_ERR_INVALID_ARGUMENT
+    # the largest accepted request still works
+    vals = torch.arange(1024 * 3, dtype=torch.float64, device="cuda").reshape(1024, 3)
+    sg.sg2v_sum_counts_noalloc(vals, 3, 1024, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out[:1024], vals.sum(dim=1))

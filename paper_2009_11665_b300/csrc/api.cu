@@ -64,7 +64,6 @@ struct DeviceInfo {
 
 std::mutex g_mutex;
 std::map<int, DeviceInfo> g_devices;
-std::map<std::tuple<int, int, int, int>, std::pair<void *, int>> g_tables;  // (dev,kc,t,a) -> (ptr, nsplit)
 
 sg2v_status device_info(int dev, DeviceInfo *out) {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -88,27 +87,40 @@ sg2v_status device_info(int dev, DeviceInfo *out) {
     return SG2V_OK;
 }
 
-// Device copy of the gather (a = 1) or split table of node (t, a) for kc colours.
-sg2v_status device_tables(int dev, int kc, int t, int a, const void **ptr, int *nsplit) {
+// Device copies of the colour-compressed expansion and split tables of node
+// (t, a) for kc colours with Z rows of wz_pad elements (built once, kept).
+struct DeviceTables {
+    const uint16_t *expand = nullptr;
+    const uint32_t *splits = nullptr;
+    int wy = 0, nsplit = 0;
+};
+std::map<std::tuple<int, int, int, int, int>, DeviceTables> g_ctables;
+
+sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTables *out) {
     std::lock_guard<std::mutex> lock(g_mutex);
-    auto key = std::make_tuple(dev, kc, t, a);
-    auto it = g_tables.find(key);
-    if (it != g_tables.end()) {
-        *ptr = it->second.first;
-        *nsplit = it->second.second;
+    auto key = std::make_tuple(dev, kc, t, a, wz_pad);
+    auto it = g_ctables.find(key);
+    if (it != g_ctables.end()) {
+        *out = it->second;
         return SG2V_OK;
     }
-    ColumnTables tab;
-    build_tables(kc, t, a, &tab);
-    size_t bytes = a == 1 ? tab.gather.size() * sizeof(int32_t) : tab.splits.size() * sizeof(uint32_t);
-    void *d = nullptr;
-    SG2V_CUDA(cudaMalloc(&d, std::max<size_t>(bytes, 16)), "table upload");
-    SG2V_CUDA(cudaMemcpy(d, a == 1 ? (const void *)tab.gather.data() : (const void *)tab.splits.data(), bytes,
-                         cudaMemcpyHostToDevice),
-              "table upload");
-    g_tables[key] = {d, tab.nsplit};
-    *ptr = d;
-    *nsplit = tab.nsplit;
+    CompressedTables tab;
+    build_compressed_tables(kc, t, a, wz_pad, &tab);
+    DeviceTables d;
+    d.wy = tab.wy;
+    d.nsplit = tab.nsplit;
+    void *pe = nullptr, *ps = nullptr;
+    const size_t be = tab.expand.size() * sizeof(uint16_t), bs = tab.splits.size() * sizeof(uint32_t);
+    SG2V_CUDA(cudaMalloc(&pe, std::max<size_t>(be, 16)), "table upload");
+    SG2V_CUDA(cudaMemcpy(pe, tab.expand.data(), be, cudaMemcpyHostToDevice), "table upload");
+    if (bs) {
+        SG2V_CUDA(cudaMalloc(&ps, bs), "table upload");
+        SG2V_CUDA(cudaMemcpy(ps, tab.splits.data(), bs, cudaMemcpyHostToDevice), "table upload");
+    }
+    d.expand = static_cast<const uint16_t *>(pe);
+    d.splits = static_cast<const uint32_t *>(ps);
+    g_ctables[key] = d;
+    *out = d;
     return SG2V_OK;
 }
 
@@ -329,10 +341,10 @@ void build_tasks(int64_t n, const std::vector<int64_t> &rp, int chunk, std::vect
             heavy_chunks->push_back(nc);
             for (int32_t c = 0; c < nc; ++c) {
                 int64_t b = (int64_t)c * chunk, e = std::min<int64_t>(d, b + chunk);
-                tasks->push_back(make_int4(v, slot, (int)b, (int)e));
+                tasks->push_back(make_int4(v, slot, (int)(rp[v] + b), (int)(rp[v] + e)));
             }
         } else {
-            light.push_back(make_int4(v, -1, 0, (int)d));
+            light.push_back(make_int4(v, -1, (int)rp[v], (int)rp[v + 1]));
         }
     }
     tasks->insert(tasks->end(), light.begin(), light.end());
@@ -482,12 +494,35 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         if (nodes[i].active != kLeaf) nodes[nodes[i].active].last_use = (int)i;
         if (nodes[i].passive != kLeaf) nodes[nodes[i].passive].last_use = (int)i;
     }
-    int64_t max_wp = kc;
-    for (auto &c : nodes) {
-        int64_t wp = c.p == 1 ? kc : binom(kc, c.p);
-        max_wp = std::max(max_wp, wp);
-        if (c.p > 1 && (wp + vecn - 1) / vecn > 32 * 4) {
+    // ---- per-node launch shape: gather width, Z layout, shared memory, block size
+    struct Shape {
+        int wz, grp, nv, wz_pad, zwords, ywords, threads;
+        size_t smem;
+    };
+    std::vector<Shape> shape(nodes.size());
+    int64_t scratch_ld = 1;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        const CNode &c = nodes[i];
+        Shape &sh = shape[i];
+        const bool hist = c.p == 1;
+        sh.wz = hist ? 1 : (int)binom(kc - 1, c.p - 1);
+        sh.grp = 32;
+        sh.nv = 1;
+        if (!hist) node_shape(fp64, sh.wz, &sh.grp, &sh.nv);
+        if (sh.nv == 0) {
             set_error("passive table wider than this build's register tile (column tiling not built)");
+            return SG2V_ERR_UNSUPPORTED;
+        }
+        sh.wz_pad = hist ? 1 : sh.grp * sh.nv * vecn;
+        sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
+        sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
+        scratch_ld = std::max<int64_t>(scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
+        sh.threads = kNodeThreads;
+        while (sh.threads > 32 && (size_t)(sh.threads / 32) * (sh.zwords + sh.ywords) * esz > 200 * 1024)
+            sh.threads /= 2;
+        sh.smem = (size_t)(sh.threads / 32) * (sh.zwords + sh.ywords) * esz;
+        if (sh.smem > 227 * 1024) {
+            set_error("per-colour accumulators exceed shared memory (column tiling not built)");
             return SG2V_ERR_UNSUPPORTED;
         }
     }
@@ -511,7 +546,6 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
     // ---- scratch for split rows
     void *scratch = nullptr;
     unsigned *counters = nullptr;
-    const int64_t scratch_ld = (max_wp + vecn - 1) / vecn * vecn;
     const size_t scratch_bytes = (size_t)(g->nheavy * nb * scratch_ld) * esz;
     const size_t counter_bytes = (size_t)(g->nheavy * nb) * sizeof(unsigned);
     if (g->nheavy) {
@@ -536,8 +570,13 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         A.nb = nb;
         A.colours = d_col;
         A.kc = kc;
+        const Shape &sh = shape[i];
         A.hist = c.p == 1;
-        A.Wp = c.p == 1 ? kc : (int)binom(kc, c.p);
+        A.Wz = sh.wz;
+        A.wz_pad = sh.wz_pad;
+        A.zwords = sh.zwords;
+        A.ywords = sh.ywords;
+        A.p = c.p;
         if (!A.hist) {
             A.Mp = table[c.passive];
             A.ldp = ld[c.passive];
@@ -547,22 +586,19 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
             A.Ma = table[c.active];
             A.lda = ld[c.active];
         }
-        A.Wt = (int)binom(kc, c.t);
-        const void *tab;
-        int nsplit;
-        if ((st = device_tables(dev, kc, c.t, c.a, &tab, &nsplit))) return st;
-        if (A.a_leaf)
-            A.gather = static_cast<const int32_t *>(tab);
-        else {
-            A.splits = static_cast<const uint32_t *>(tab);
-            A.nsplit = nsplit;
-        }
+        A.Ws = (int)binom(kc - 1, c.t - 1);
+        DeviceTables tab;
+        if ((st = device_tables(dev, kc, c.t, c.a, sh.wz_pad, &tab))) return st;
+        A.expand = tab.expand;
+        A.wy = tab.wy;
+        A.splits = tab.splits;
+        A.nsplit = tab.nsplit;
         A.root = c.is_root;
         if (c.is_root) {
             if ((st = ws.alloc(&table[i], (size_t)nb * n * esz))) return st;
             A.root_out = table[i];
         } else {
-            ld[i] = (A.Wt + vecn - 1) / vecn * vecn;
+            ld[i] = (A.Ws + vecn - 1) / vecn * vecn;
             if ((st = ws.alloc(&table[i], (size_t)n * nb * ld[i] * esz))) return st;
             A.Ms = table[i];
             A.ldt = ld[i];
@@ -571,26 +607,28 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         A.scratch_ld = scratch_ld;
         A.counters = counters;
         if (g->nheavy) {
-            SG2V_CUDA(cudaMemsetAsync(scratch, 0, (size_t)(g->nheavy * nb * scratch_ld) * esz, stream), "memset");
+            SG2V_CUDA(cudaMemsetAsync(scratch, 0, scratch_bytes, stream), "memset");
             SG2V_CUDA(cudaMemsetAsync(counters, 0, counter_bytes, stream), "memset");
         }
-        const int nvec = (A.Wp + vecn - 1) / vecn;
-        const int nv = A.hist ? 1 : std::max(1, (nvec + 31) / 32);
-        const int bps = node_blocks_per_sm(fp64, A.hist, nv, A.weights != nullptr);
+        const int bps = node_blocks_per_sm(fp64, A.hist, sh.grp, sh.nv, A.weights != nullptr, sh.threads, sh.smem);
+        if (bps < 1) {
+            set_error("node kernel cannot be resident with its shared memory");
+            return SG2V_ERR_UNSUPPORTED;
+        }
         {
             // algorithmic bytes: CSR once, each input table once, output once
             double bytes = 8.0 * (n + 1) + 4.0 * g->nnz * (g->weighted ? 2 : 1);
             const double rows = (double)n * nb;
-            bool colours_read = A.hist || A.a_leaf;
-            if (colours_read) bytes += rows;
-            if (!A.hist) bytes += rows * A.Wp * esz;
-            if (!A.a_leaf && !(c.active == c.passive && !A.hist)) bytes += rows * binom(kc, c.a) * esz;
-            bytes += c.is_root ? rows * esz : rows * A.Wt * esz;
+            bytes += rows;  // colours
+            if (!A.hist) bytes += rows * A.Wz * esz;
+            if (!A.a_leaf && !(c.active == c.passive && !A.hist)) bytes += rows * binom(kc - 1, c.a - 1) * esz;
+            bytes += c.is_root ? rows * esz : rows * A.Ws * esz;
             char name[64];
             std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p, fp64 ? "fp64" : "fp32");
             timer.begin(name, bytes);
         }
-        SG2V_CUDA(launch_node(A, fp64, nv, info.sms * bps, stream), "node kernel launch");
+        SG2V_CUDA(launch_node(A, fp64, sh.grp, sh.nv, sh.threads, sh.smem, info.sms * bps, stream),
+                  "node kernel launch");
         timer.end();
         if (c.active != kLeaf && nodes[c.active].last_use == (int)i) ws.release(table[c.active]);
         if (c.passive != kLeaf && nodes[c.passive].last_use == (int)i && c.passive != c.active)

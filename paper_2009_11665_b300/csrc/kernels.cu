@@ -30,6 +30,15 @@ namespace sg2v {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+#ifndef SG2V_U_NV2
+#define SG2V_U_NV2 2
+#endif
+#ifndef SG2V_PACKED
+#define SG2V_PACKED 1
+#endif
+#ifndef SG2V_ZEROFILL
+#define SG2V_ZEROFILL 1
+#endif
 constexpr int kMaxHistColours = 16;
 
 template <typename T>
@@ -39,6 +48,20 @@ struct Vec16<float> {
     using type = float4;
     static constexpr int n = 4;
     __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+#if SG2V_PACKED
+    // packed FP32x2 arithmetic (sm_100 family): two instructions per float4
+    __device__ static void add(float4 &a, const float4 &b) {
+        const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
+        a = make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    __device__ static void fma(float4 &a, float w, const float4 &b) {
+        const float2 ww = make_float2(w, w);
+        const float2 lo = __ffma2_rn(ww, make_float2(b.x, b.y), make_float2(a.x, a.y));
+        const float2 hi = __ffma2_rn(ww, make_float2(b.z, b.w), make_float2(a.z, a.w));
+        a = make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+#else
     __device__ static void add(float4 &a, const float4 &b) {
         a.x += b.x;
         a.y += b.y;
@@ -51,11 +74,16 @@ struct Vec16<float> {
         a.z = fmaf(w, b.z, a.z);
         a.w = fmaf(w, b.w, a.w);
     }
+#endif
     __device__ static void store(float *p, const float4 &a) {
         p[0] = a.x;
         p[1] = a.y;
         p[2] = a.z;
         p[3] = a.w;
+    }
+    __device__ static float4 shfl_xor(const float4 &a, int o) {
+        return make_float4(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o),
+                           __shfl_xor_sync(0xffffffffu, a.z, o), __shfl_xor_sync(0xffffffffu, a.w, o));
     }
 };
 template <>
@@ -75,6 +103,9 @@ struct Vec16<double> {
         p[0] = a.x;
         p[1] = a.y;
     }
+    __device__ static double2 shfl_xor(const double2 &a, int o) {
+        return make_double2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+    }
 };
 
 template <typename T>
@@ -84,84 +115,132 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Partial Y row of (row, colouring b) over arcs [e0, e1) into ybuf[0, Wp).
-template <typename T, int NV, bool WEIGHTED>
-__device__ __forceinline__ void spmm_partial(const NodeArgs &A, int64_t e0, int64_t e1, int b, T *ybuf, int lane) {
+// Colour-compressed accumulation of one (row, colouring b) over arcs [e0, e1).
+//
+// Every table row u stores only the colour sets containing u's colour c_u
+// (a count with u at the sub-template's root is zero otherwise), indexed by
+// the remaining p-1 colours in the squeezed universe of c_u.  The SpMM is
+// needed only for sets P without v's colour c_v, so arcs to neighbours of
+// colour c_v are skipped, and the neighbour rows are summed per neighbour
+// colour d into Z(d, .) (shared memory, private to the warp):
+//   Y(v, P) = sum over d in P of Z(d, squeezed P - {d}).
+// The warp splits into 32/G groups of G lanes; each group takes every
+// (32/G)-th arc of a batch of 32 and owns a private copy of Z, and its lanes
+// cover G*NV 16-byte vectors of the neighbour's compressed row (so narrow rows
+// still fill a warp-wide load).  Copies are folded into copy 0 at the end.
+template <typename T, int G, int NV, bool WEIGHTED>
+__device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1, int b, int cv, T *zbuf,
+                                       int lane) {
     using V = Vec16<T>;
     using VT = typename V::type;
-    constexpr int U = NV <= 2 ? 4 : 2;  // arcs in flight per step
-    VT acc[NV];
+    constexpr int NG = 32 / G;
+    constexpr int U = NV == 1 ? 4 : NV == 2 ? SG2V_U_NV2 : 2;  // arcs in flight per group and step
+    const int grp = lane / G, gl = lane % G;
+    const int kc = A.kc;
+    const int wzp = A.wz_pad;  // = G * NV * V::n
+    const int zlen = kc * wzp;
+    VT *zv = reinterpret_cast<VT *>(zbuf);
+    for (int i = lane; i < NG * zlen / V::n; i += 32) zv[i] = V::zero();
+    __syncwarp();
+    T *zg = zbuf + grp * zlen;
+    const int nvec = (A.Wz + V::n - 1) / V::n;
+    bool qok[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] = V::zero();
-    const T *Mp = static_cast<const T *>(A.Mp);
-    const int64_t ldp = A.ldp;
-    const int64_t nb = A.nb;
-    const int nvec = (A.Wp + V::n - 1) / V::n;
+    for (int q = 0; q < NV; ++q) qok[q] = gl + G * q < nvec;
+    const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;  // vectors between consecutive vertices' rows
+    const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + gl;
+    const int8_t *col = A.colours + (int64_t)b * A.n;
     for (int64_t base = e0; base < e1; base += 32) {
         const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
         const int u_l = lane < cnt ? __ldg(A.col_idx + base + lane) : 0;
+        const int c_l = lane < cnt ? (int)__ldg(col + u_l) : -1;
         T w_l = T(1);
         if (WEIGHTED) w_l = lane < cnt ? T(__ldg(A.weights + base + lane)) : T(0);
-        int j = 0;
-        for (; j + U <= cnt; j += U) {
+        for (int j0 = 0; j0 < cnt; j0 += NG * U) {
             VT x[U][NV];
+            T w[U];
+            int crow[U];
+            bool take[U];
 #pragma unroll
             for (int r = 0; r < U; ++r) {
-                const int u = __shfl_sync(kFull, u_l, j + r);
-                const VT *row = reinterpret_cast<const VT *>(Mp + ((int64_t)u * nb + b) * ldp);
+                const int j = j0 + r * NG + grp;
+                const int u = __shfl_sync(kFull, u_l, j & 31);
+                const int c = __shfl_sync(kFull, c_l, j & 31);
+                if (WEIGHTED) w[r] = __shfl_sync(kFull, w_l, j & 31);
+                take[r] = j < cnt && c != cv && (unsigned)c < (unsigned)kc;
+                crow[r] = take[r] ? c : 0;
+                const VT *row = Mb + (int64_t)u * uvec;
+#pragma unroll
+                for (int q = 0; q < NV; ++q) x[r][q] = (take[r] && qok[q]) ? __ldg(row + G * q) : V::zero();
+            }
+#pragma unroll
+            for (int r = 0; r < U; ++r) {
+                if (!take[r]) continue;
+                VT *zr = reinterpret_cast<VT *>(zg + crow[r] * wzp) + gl;
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    const int vi = lane + 32 * q;
-                    x[r][q] = vi < nvec ? __ldg(row + vi) : V::zero();
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < U; ++r) {
-                if (WEIGHTED) {
-                    const T w = __shfl_sync(kFull, w_l, j + r);
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) V::fma(acc[q], w, x[r][q]);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) V::add(acc[q], x[r][q]);
-                }
-            }
-        }
-        for (; j < cnt; ++j) {
-            const int u = __shfl_sync(kFull, u_l, j);
-            const T w = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
-            const VT *row = reinterpret_cast<const VT *>(Mp + ((int64_t)u * nb + b) * ldp);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const int vi = lane + 32 * q;
-                if (vi < nvec) {
-                    const VT x = __ldg(row + vi);
+                    VT z = zr[G * q];
                     if (WEIGHTED)
-                        V::fma(acc[q], w, x);
+                        V::fma(z, w[r], x[r][q]);
                     else
-                        V::add(acc[q], x);
+                        V::add(z, x[r][q]);
+                    zr[G * q] = z;
                 }
             }
         }
     }
+    __syncwarp();
+    if (NG > 1) {
+        for (int i = lane; i < zlen / V::n; i += 32) {
+            VT acc = zv[i];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        const int vi = lane + 32 * q;
-        if (vi < nvec) V::store(ybuf + vi * V::n, acc[q]);
+            for (int g = 1; g < NG; ++g) V::add(acc, zv[g * zlen / V::n + i]);
+            zv[i] = acc;
+        }
     }
 }
 
-// Partial per-colour neighbour histogram of (row, colouring b) into ybuf[0, kc).
+template <typename T>
+__device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, int64_t e1, const int8_t *col,
+                                                T *zbuf, int lane);
+
+// Colour histogram of (row, colouring b): Z(d) = sum of w over arcs to
+// neighbours of colour d (the passive child is a single vertex).
 template <typename T, bool WEIGHTED>
-__device__ __forceinline__ void hist_partial(const NodeArgs &A, int64_t e0, int64_t e1, int b, T *ybuf, int lane) {
+__device__ __forceinline__ void hist_z(const NodeArgs &A, int64_t e0, int64_t e1, int b, T *zbuf, int lane) {
+    const int8_t *col = A.colours + (int64_t)b * A.n;
+    if (!WEIGHTED) {
+        // counts by warp ballots: every lane ends with every colour's count
+        int cnt[kMaxHistColours];
+#pragma unroll
+        for (int c = 0; c < kMaxHistColours; ++c) cnt[c] = 0;
+        for (int64_t base = e0; base < e1; base += 32) {
+            const int64_t e = base + lane;
+            const int c = e < e1 ? (int)__ldg(col + __ldg(A.col_idx + e)) : -1;
+#pragma unroll
+            for (int q = 0; q < kMaxHistColours; ++q)
+                if (q < A.kc) cnt[q] += __popc(__ballot_sync(kFull, c == q));
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < kMaxHistColours; ++q)
+                if (q < A.kc) zbuf[q] = T(cnt[q]);
+        }
+    } else {
+        hist_z_weighted<T>(A, e0, e1, col, zbuf, lane);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, int64_t e1, const int8_t *col,
+                                                T *zbuf, int lane) {
     T cnt[kMaxHistColours];
 #pragma unroll
     for (int c = 0; c < kMaxHistColours; ++c) cnt[c] = T(0);
-    const int8_t *col = A.colours + (int64_t)b * A.n;
     for (int64_t e = e0 + lane; e < e1; e += 32) {
         const int u = __ldg(A.col_idx + e);
         const int c = __ldg(col + u);
-        const T w = WEIGHTED ? T(__ldg(A.weights + e)) : T(1);
+        const T w = T(__ldg(A.weights + e));
 #pragma unroll
         for (int q = 0; q < kMaxHistColours; ++q) cnt[q] += (c == q) ? w : T(0);
     }
@@ -169,90 +248,110 @@ __device__ __forceinline__ void hist_partial(const NodeArgs &A, int64_t e0, int6
     for (int q = 0; q < kMaxHistColours; ++q) {
         if (q < A.kc) {
             const T s = warp_sum(cnt[q]);
-            if (lane == 0) ybuf[q] = s;
+            if (lane == 0) zbuf[q] = s;
         }
     }
 }
 
-// eMA epilogue of (row v, colouring b) from the complete Y row in ybuf.
+// Y'(j) for the p-sets j of the squeezed universe of colour cv (the colour
+// sets without cv the eMA needs), summed from Z.
 template <typename T>
-__device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, const T *ybuf, int lane) {
+__device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbuf, T *ybuf, int lane) {
+    const int p = A.p, wy = A.wy;
+    const uint16_t *ex = A.expand + (int64_t)cv * wy * p;
+    for (int j = lane; j < wy; j += 32) {
+        T s = T(0);
+        for (int k = 0; k < p; ++k) s += zbuf[__ldg(ex + j * p + k)];
+        ybuf[j] = s;
+    }
+}
+
+// eMA in squeezed coordinates from Y' in ybuf:
+//   M_s'(v, S') = sum over (a-1)-subsets A' of S' of M_a'(v, A') * Y'(S' - A'),
+// or M_s' = Y' when the active child is a single vertex.  The root sums its
+// row into root_out instead of storing it.  ok = false (a colour outside
+// [0, kc), reported by the host) writes zeros.
+template <typename T>
+__device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool ok, const T *ybuf, int lane) {
     const int64_t rowb = (int64_t)v * A.nb + b;
-    const int Wt = A.Wt;
+    const int ws = A.Ws;
+    T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
+    T s = T(0);
     if (A.a_leaf) {
-        // a colour outside [0, kc) is reported by the host after the call;
-        // here it only must not index outside the gather table
-        const int c = A.colours[(int64_t)b * A.n + v];
-        const bool ok = (unsigned)c < (unsigned)A.kc;
-        const int32_t *g = A.gather + (int64_t)(ok ? c : 0) * Wt;
-        if (A.root) {
-            T s = T(0);
-            for (int S = lane; S < Wt; S += 32) {
-                const int j = ok ? __ldg(g + S) : -1;
-                if (j >= 0) s += ybuf[j];
-            }
-            s = warp_sum(s);
-            if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = s;
-        } else {
-            T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
-            for (int S = lane; S < Wt; S += 32) {
-                const int j = ok ? __ldg(g + S) : -1;
-                out[S] = j >= 0 ? ybuf[j] : T(0);
-            }
+        for (int j = lane; j < ws; j += 32) {
+            const T y = ok ? ybuf[j] : T(0);
+            if (A.root)
+                s += y;
+            else
+                out[j] = y;
         }
     } else {
         const T *ma = static_cast<const T *>(A.Ma) + rowb * A.lda;
         const int ns = A.nsplit;
         if (A.root) {
-            T s = T(0);
-            const int total = Wt * ns;
+            const int total = ok ? ws * ns : 0;
             for (int p = lane; p < total; p += 32) {
                 const uint32_t sp = __ldg(A.splits + p);
                 s = fma(__ldg(ma + (sp & 0xffffu)), ybuf[sp >> 16], s);
             }
-            s = warp_sum(s);
-            if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = s;
         } else {
-            T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
-            for (int S = lane; S < Wt; S += 32) {
+            for (int S = lane; S < ws; S += 32) {
                 const uint32_t *sp = A.splits + (int64_t)S * ns;
                 T acc = T(0);
-                for (int j = 0; j < ns; ++j) {
-                    const uint32_t x = __ldg(sp + j);
-                    acc = fma(__ldg(ma + (x & 0xffffu)), ybuf[x >> 16], acc);
+                if (ok) {
+                    for (int j = 0; j < ns; ++j) {
+                        const uint32_t x = __ldg(sp + j);
+                        acc = fma(__ldg(ma + (x & 0xffffu)), ybuf[x >> 16], acc);
+                    }
                 }
                 out[S] = acc;
             }
         }
     }
+    if (A.root) {
+        s = warp_sum(s);
+        if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = s;
+    }
 }
 
-template <typename T, int NV, bool HIST, bool WEIGHTED>
-__global__ void __launch_bounds__(kNodeThreads) node_kernel(const NodeArgs A) {
+// Resident blocks per SM requested from the compiler (the register cap) for
+// each shape; tuned on B300 (occupancy matters more than a few spills).
+#ifndef SG2V_MINB_F32_NV2
+#define SG2V_MINB_F32_NV2 5
+#endif
+template <typename T, int NV>
+struct MinBlocks {
+    static constexpr int value =
+        sizeof(T) == 4 ? (NV == 1 ? 4 : NV == 2 ? SG2V_MINB_F32_NV2 : 2) : (NV == 1 ? 3 : 2);
+};
+
+template <typename T, int G, int NV, bool HIST, bool WEIGHTED>
+__global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_kernel(const NodeArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using V = Vec16<T>;
-    constexpr int kYbuf = HIST ? kMaxHistColours : NV * 32 * V::n;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    T *ybuf = reinterpret_cast<T *>(smem_raw) + wib * kYbuf;
+    T *zbuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.zwords + A.ywords);
+    T *ybuf = zbuf + A.zwords;
+    const int zlen = HIST ? A.kc : A.kc * A.wz_pad;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; ti < A.ntasks; ti += nwarps) {
         const int4 task = A.tasks[ti];
         const int v = task.x;
         const int slot = task.y;
-        const int64_t rs = A.row_ptr[v];
-        const int64_t e0 = rs + task.z, e1 = rs + task.w;
+        const int64_t e0 = task.z, e1 = task.w;
         for (int b = 0; b < A.nb; ++b) {
+            const int cv = A.colours[(int64_t)b * A.n + v];
+            const bool cok = (unsigned)cv < (unsigned)A.kc;
             if (HIST)
-                hist_partial<T, WEIGHTED>(A, e0, e1, b, ybuf, lane);
+                hist_z<T, WEIGHTED>(A, e0, e1, b, zbuf, lane);
             else
-                spmm_partial<T, NV, WEIGHTED>(A, e0, e1, b, ybuf, lane);
+                spmm_z<T, G, NV, WEIGHTED>(A, e0, e1, b, cv, zbuf, lane);
             __syncwarp();
             if (slot >= 0) {
-                // one chunk of a split row: fold into the scratch row; the last
-                // chunk to arrive finishes the row
+                // one chunk of a split row: fold Z into the scratch row; the
+                // last chunk to arrive finishes the row
                 T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
-                for (int j = lane; j < A.Wp; j += 32) atomicAdd(sc + j, ybuf[j]);
+                for (int j = lane; j < zlen; j += 32) atomicAdd(sc + j, zbuf[j]);
                 __threadfence();
                 __syncwarp();
                 int last = 0;
@@ -266,36 +365,40 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const NodeArgs A) {
                     continue;
                 }
                 __threadfence();
-                for (int j = lane; j < A.Wp; j += 32) ybuf[j] = __ldcg(sc + j);
+                for (int j = lane; j < zlen; j += 32) zbuf[j] = __ldcg(sc + j);
                 __syncwarp();
             }
-            epilogue<T>(A, v, b, ybuf, lane);
+            if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane);
+            __syncwarp();
+            epilogue<T>(A, v, b, cok, ybuf, lane);
             __syncwarp();
         }
     }
 }
 
-template <typename T, int NV, bool HIST, bool WEIGHTED>
+template <typename T, int G, int NV, bool HIST, bool WEIGHTED>
 void *kernel_ptr() {
-    return reinterpret_cast<void *>(&node_kernel<T, NV, HIST, WEIGHTED>);
+    return reinterpret_cast<void *>(&node_kernel<T, G, NV, HIST, WEIGHTED>);
 }
 
-void *select_kernel(bool fp64, bool hist, int nv, bool weighted) {
-#define SG2V_PICK(T)                                                                           \
-    if (hist) return weighted ? kernel_ptr<T, 1, true, true>() : kernel_ptr<T, 1, true, false>(); \
-    switch (nv) {                                                                              \
-        case 1: return weighted ? kernel_ptr<T, 1, false, true>() : kernel_ptr<T, 1, false, false>(); \
-        case 2: return weighted ? kernel_ptr<T, 2, false, true>() : kernel_ptr<T, 2, false, false>(); \
-        case 3: return weighted ? kernel_ptr<T, 3, false, true>() : kernel_ptr<T, 3, false, false>(); \
-        case 4: return weighted ? kernel_ptr<T, 4, false, true>() : kernel_ptr<T, 4, false, false>(); \
-        default: return nullptr;                                                               \
+template <typename T, bool W>
+void *pick(bool hist, int g, int nv) {
+    if (hist) return kernel_ptr<T, 32, 1, true, W>();
+    if (g == 4) return kernel_ptr<T, 4, 1, false, W>();
+    if (g == 8) return kernel_ptr<T, 8, 1, false, W>();
+    if (g == 16) return kernel_ptr<T, 16, 1, false, W>();
+    switch (nv) {
+        case 1: return kernel_ptr<T, 32, 1, false, W>();
+        case 2: return kernel_ptr<T, 32, 2, false, W>();
+        case 3: return kernel_ptr<T, 32, 3, false, W>();
+        case 4: return kernel_ptr<T, 32, 4, false, W>();
+        default: return nullptr;
     }
-    if (fp64) {
-        SG2V_PICK(double)
-    } else {
-        SG2V_PICK(float)
-    }
-#undef SG2V_PICK
+}
+
+void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted) {
+    if (fp64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
+    return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
 }
 
 // ------------------------------------------------------------- reductions
@@ -399,36 +502,53 @@ __global__ void check_colours_kernel(const int8_t *colours, int64_t count, int k
 
 }  // namespace
 
-size_t node_smem_bytes(bool fp64, bool hist, int nv) {
+void node_shape(bool fp64, int wz, int *g, int *nv) {
     const int vecn = fp64 ? 2 : 4;
-    const size_t elems = hist ? kMaxHistColours : (size_t)nv * 32 * vecn;
-    return (kNodeThreads / 32) * elems * (fp64 ? 8 : 4);
+    const int nvec = (wz + vecn - 1) / vecn;
+    *nv = 1;
+    if (nvec <= 4)
+        *g = 4;
+    else if (nvec <= 8)
+        *g = 8;
+    else if (nvec <= 16)
+        *g = 16;
+    else {
+        *g = 32;
+        *nv = (nvec + 31) / 32;
+        if (*nv > 4) *nv = 0;
+    }
 }
 
-int node_blocks_per_sm(bool fp64, bool hist, int nv, bool weighted) {
-    void *k = select_kernel(fp64, hist, nv, weighted);
+int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
+    void *k = select_kernel(fp64, hist, g, nv, weighted);
     if (!k) return 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kNodeThreads, node_smem_bytes(fp64, hist, nv)) !=
-        cudaSuccess)
-        return 1;
-    return blocks > 0 ? blocks : 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return blocks;
 }
 
-cudaError_t launch_node(const NodeArgs &args, bool fp64, int nv, int grid_cap, cudaStream_t stream) {
+cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int threads, size_t smem, int grid_cap,
+                        cudaStream_t stream) {
     const bool hist = args.hist != 0;
     const bool weighted = args.weights != nullptr;
-    void *k = select_kernel(fp64, hist, nv, weighted);
+    void *k = select_kernel(fp64, hist, g, nv, weighted);
     if (!k) return cudaErrorInvalidValue;
     if (args.ntasks == 0) return cudaSuccess;
-    const int64_t warps_per_block = kNodeThreads / 32;
+    const int64_t warps_per_block = threads / 32;
     int64_t grid = (args.ntasks + warps_per_block - 1) / warps_per_block;
     if (grid > grid_cap) grid = grid_cap;
     if (grid < 1) grid = 1;
     NodeArgs a = args;
     void *params[] = {&a};
-    return cudaLaunchKernel(k, dim3((unsigned)grid), dim3(kNodeThreads), params, node_smem_bytes(fp64, hist, nv),
-                            stream);
+    return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)threads), params, smem, stream);
 }
 
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,

@@ -7,40 +7,49 @@
 
 namespace sg2v {
 
-// Arguments of one DP node over a batch of nb colourings.  Table rows are
-// (vertex, colouring) pairs: row v*nb + b holds colouring b of vertex v, with
-// `ld*` elements between rows (ld is a multiple of 16 bytes).
+// Arguments of one DP node over a batch of nb colourings.  Tables are
+// colour-compressed: row v*nb + b holds, for colouring b of vertex v, only the
+// colour sets containing v's colour, indexed by the colex rank of the other
+// colours in the squeezed universe (kc - 1 colours), with `ld*` elements
+// between rows (ld is a multiple of 16 bytes).
 struct NodeArgs {
     // graph (CSR) and the load-balanced work list
     const int64_t *row_ptr;
     const int32_t *col_idx;
     const float *weights;         // per-arc weights, or null
-    const int4 *tasks;            // {row, heavy slot or -1, first arc offset, end arc offset}
+    const int4 *tasks;            // {row, split slot or -1, first arc, end arc} (arc indices into col_idx)
     int64_t ntasks;
-    const int32_t *heavy_chunks;  // tasks per heavy slot
+    const int32_t *heavy_chunks;  // tasks per split slot
     int64_t n;
     int nb;                       // colourings in the batch
     const int8_t *colours;        // [nb][n]
     int kc;
-    // passive side: Y = A * M_p (or the colour histogram when hist != 0)
+    // passive side: per-colour accumulators Z(d, i) of compressed rows of
+    // width Wz = C(kc-1, p-1), or the colour histogram when hist != 0
     const void *Mp;
     int64_t ldp;
-    int Wp;                       // columns of Y per colouring
+    int Wz;
+    int wz_pad;                   // Z row stride (lanes per group * vectors per lane * elements per vector)
     int hist;
+    // Y' (p-sets without v's colour) from Z
+    int p;
+    int wy;                       // C(kc-1, p)
+    const uint16_t *expand;       // [kc][wy][p] offsets into Z
+    // shared memory per warp, in elements: Z copies, then Y'
+    int zwords, ywords;
     // active side
     const void *Ma;
     int64_t lda;
-    int a_leaf;                   // active child is a single vertex: masked gather
+    int a_leaf;                   // active child is a single vertex: M_s' = Y'
     // output
     void *Ms;
     int64_t ldt;
-    int Wt;                       // columns of M_s per colouring
-    int root;                     // sum the row of M_s into root_out instead of storing it
+    int Ws;                       // C(kc-1, t-1)
+    int root;                     // sum the row of M_s' into root_out instead of storing it
     void *root_out;               // [nb][n]
-    const int32_t *gather;        // [kc][Wt] (a_leaf)
-    const uint32_t *splits;       // [Wt][nsplit] rank(S_a) | rank(S - S_a) << 16
+    const uint32_t *splits;       // [Ws][nsplit] rank(A') | rank(S' - A') << 16 (a >= 2)
     int nsplit;
-    // partial sums of split (heavy) rows
+    // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
     unsigned *counters;           // [slots][nb], zero on entry
@@ -57,17 +66,21 @@ struct RootSum {
 constexpr unsigned kFlagNotIntegral = 1u;
 constexpr unsigned kFlagNonFinite = 2u;
 
-// Launches the fused SpMM/histogram + eMA kernel of one node.  vec_per_lane
-// (1..4) is the number of 16-byte vectors of Y each lane accumulates.
-cudaError_t launch_node(const NodeArgs &args, bool fp64, int vec_per_lane, int grid_cap, cudaStream_t stream);
-
-// Maximum resident blocks per SM of one node-kernel variant (for grid sizing).
-int node_blocks_per_sm(bool fp64, bool hist, int vec_per_lane, bool weighted);
+// Shape of the gather of compressed rows of wz elements: lanes per neighbour
+// group (4, 8, 16 or 32) and 16-byte vectors per lane (1..4; 0 if too wide).
+void node_shape(bool fp64, int wz, int *lanes_per_group, int *vec_per_lane);
 
 constexpr int kNodeThreads = 256;
 
-// Shared memory of the node kernel for a given variant.
-size_t node_smem_bytes(bool fp64, bool hist, int vec_per_lane);
+// Resident blocks per SM of one node-kernel variant at a block size and
+// dynamic shared-memory size (0 if it cannot run); raises the kernel's
+// shared-memory limit when needed.
+int node_blocks_per_sm(bool fp64, bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
+                       size_t smem);
+
+// Launches the fused SpMM/histogram + eMA kernel of one node.
+cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, int vec_per_lane, int threads,
+                        size_t smem, int grid_cap, cudaStream_t stream);
 
 // Root reduction: vals is [nseg][n] of float/double; writes per-vertex doubles
 // when pv != null and one RootSum per segment.

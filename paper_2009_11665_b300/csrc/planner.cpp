@@ -92,6 +92,55 @@ void build_tables(int kc, int t, int a, ColumnTables *out) {
     }
 }
 
+uint32_t squeeze_colour(uint32_t mask, int c) {
+    const uint32_t low = (1u << c) - 1u;
+    return (mask & low) | ((mask >> (c + 1)) << c);
+}
+
+uint32_t unsqueeze_colour(uint32_t mask, int c) {
+    const uint32_t low = (1u << c) - 1u;
+    return (mask & low) | ((mask >> c) << (c + 1));
+}
+
+void build_compressed_tables(int kc, int t, int a, int wz_pad, CompressedTables *out) {
+    const int p = t - a;
+    const int wy = (int)binom(kc - 1, p);
+    out->wy = wy;
+    out->expand.assign((size_t)kc * wy * p, 0);
+    for (int c = 0; c < kc; ++c) {
+        uint32_t Pq = (1u << p) - 1;
+        for (int j = 0; j < wy; ++j, Pq = next_same_popcount(Pq)) {
+            const uint32_t P = unsqueeze_colour(Pq, c);  // a p-set of colours without c
+            int k = 0;
+            for (uint32_t rest = P; rest; rest &= rest - 1, ++k) {
+                const int d = __builtin_ctz(rest);
+                const uint32_t idx = p == 1 ? 0u : colex_rank(squeeze_colour(P ^ (1u << d), d));
+                out->expand[((size_t)c * wy + j) * p + k] = (uint16_t)(d * wz_pad + (int)idx);
+            }
+        }
+    }
+    out->splits.clear();
+    out->nsplit = 0;
+    if (a >= 2) {
+        const int ws = (int)binom(kc - 1, t - 1);
+        const int ns = (int)binom(t - 1, a - 1);
+        out->nsplit = ns;
+        out->splits.resize((size_t)ws * ns);
+        uint32_t S = (1u << (t - 1)) - 1;
+        for (int s = 0; s < ws; ++s, S = next_same_popcount(S)) {
+            int j = 0;
+            for (uint32_t A = 0;;) {
+                A = (A - S) & S;
+                if (A == 0) break;
+                if (__builtin_popcount(A) == a - 1) {
+                    out->splits[(size_t)s * ns + j] = colex_rank(A) | (colex_rank(S ^ A) << 16);
+                    ++j;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace sg2v
 
 namespace {

@@ -30,6 +30,26 @@ struct PlanNode {
     std::string canon;  // AHU form of the rooted sub-template
 };
 
+// Colour-compressed tables.  A count M_s(v, S) is zero unless S holds v's own
+// colour c (the sub-template's root maps to v), so row v stores only the sets
+// S containing c, indexed by the colex rank of S - {c} in the universe of the
+// other kc - 1 colours ("squeezed": colours above c move down by one).
+uint32_t squeeze_colour(uint32_t mask, int c);
+uint32_t unsqueeze_colour(uint32_t mask, int c);
+
+struct CompressedTables {
+    // Y'(v, j) for the j-th p-set of the squeezed universe of v's colour c is
+    // the sum over k < p of Z[expand[(c * wy + j) * p + k]], where Z(d, i)
+    // (offset d * wz_pad + i) accumulates the compressed rows of neighbours of
+    // colour d; for p = 1, Z(d) is the colour histogram (wz_pad = 1).
+    std::vector<uint16_t> expand;
+    int wy = 0;
+    // eMA splits in squeezed coordinates (a >= 2): for each (t-1)-set S',
+    // nsplit pairs rank(A') | rank(S' - A') << 16 over the (a-1)-subsets A'.
+    std::vector<uint32_t> splits;
+    int nsplit = 0;
+};
+
 struct ColumnTables {
     // gather[c * Wt + rank(S)] = rank(S minus {c}) if c in S else -1 (a = 1 nodes)
     std::vector<int32_t> gather;
@@ -53,6 +73,9 @@ struct sg2v_plan {
 namespace sg2v {
 // Builds the split tables of node (t, a) for kc colours.
 void build_tables(int kc, int t, int a, ColumnTables *out);
+// Builds the colour-compressed tables of node (t, a, p) for kc colours with
+// Z rows of wz_pad entries.
+void build_compressed_tables(int kc, int t, int a, int wz_pad, CompressedTables *out);
 // Thread-local error detail.
 void set_error(const std::string &msg);
 }  // namespace sg2v

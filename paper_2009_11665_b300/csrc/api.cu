@@ -543,6 +543,19 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
     timer.count_extra(1);
     SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, d_status, stream), "colour check");
 
+    // ---- every row's arcs sorted by neighbour colour, once per colouring
+    int32_t *scol = nullptr;
+    int8_t *sclr = nullptr;
+    float *sw = nullptr;
+    if ((st = ws.alloc((void **)&scol, (size_t)nb * g->nnz * sizeof(int32_t)))) return st;
+    if ((st = ws.alloc((void **)&sclr, (size_t)nb * g->nnz))) return st;
+    if (g->weighted && (st = ws.alloc((void **)&sw, (size_t)nb * g->nnz * sizeof(float)))) return st;
+    timer.begin("colour_sort", (double)nb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))));
+    SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->col_idx, g->weights, n, g->nnz, d_col, nb, kc, scol, sclr,
+                                 sw, info.sms, stream),
+              "colour sort");
+    timer.end();
+
     // ---- scratch for split rows
     void *scratch = nullptr;
     unsigned *counters = nullptr;
@@ -570,6 +583,10 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         A.nb = nb;
         A.colours = d_col;
         A.kc = kc;
+        A.nnz = g->nnz;
+        A.scol = scol;
+        A.sclr = sclr;
+        A.sw = sw;
         const Shape &sh = shape[i];
         A.hist = c.p == 1;
         A.Wz = sh.wz;
@@ -617,8 +634,9 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         }
         {
             // algorithmic bytes: CSR once, each input table once, output once
-            double bytes = 8.0 * (n + 1) + 4.0 * g->nnz * (g->weighted ? 2 : 1);
+            // (the sorted arc list: neighbour, its colour, weight)
             const double rows = (double)n * nb;
+            double bytes = 8.0 * (n + 1) + (double)nb * g->nnz * (5.0 + (g->weighted ? 4.0 : 0.0));
             bytes += rows;  // colours
             if (!A.hist) bytes += rows * A.Wz * esz;
             if (!A.a_leaf && !(c.active == c.passive && !A.hist)) bytes += rows * binom(kc - 1, c.a - 1) * esz;

@@ -30,6 +30,9 @@ namespace sg2v {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+#ifndef SG2V_U_NV1
+#define SG2V_U_NV1 4
+#endif
 #ifndef SG2V_U_NV2
 #define SG2V_U_NV2 2
 #endif
@@ -134,7 +137,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     using V = Vec16<T>;
     using VT = typename V::type;
     constexpr int NG = 32 / G;
-    constexpr int U = NV == 1 ? 4 : NV == 2 ? SG2V_U_NV2 : 2;  // arcs in flight per group and step
+    constexpr int U = NV == 1 ? SG2V_U_NV1 : NV == 2 ? SG2V_U_NV2 : 2;  // arcs in flight per group and step
     const int grp = lane / G, gl = lane % G;
     const int kc = A.kc;
     const int wzp = A.wz_pad;  // = G * NV * V::n
@@ -149,26 +152,33 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     for (int q = 0; q < NV; ++q) qok[q] = gl + G * q < nvec;
     const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;  // vectors between consecutive vertices' rows
     const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + gl;
-    const int8_t *col = A.colours + (int64_t)b * A.n;
+    const int32_t *scol = A.scol + (int64_t)b * A.nnz;
+    const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
+    const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+    // the arcs come sorted by neighbour colour: each colour is one run, summed
+    // in registers and added to Z(colour) when the run ends
+    VT run[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) run[q] = V::zero();
+    int cur = -1;
     for (int64_t base = e0; base < e1; base += 32) {
         const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
-        const int u_l = lane < cnt ? __ldg(A.col_idx + base + lane) : 0;
-        const int c_l = lane < cnt ? (int)__ldg(col + u_l) : -1;
+        const int u_l = lane < cnt ? __ldg(scol + base + lane) : 0;
+        const int c_l = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
         T w_l = T(1);
-        if (WEIGHTED) w_l = lane < cnt ? T(__ldg(A.weights + base + lane)) : T(0);
+        if (WEIGHTED) w_l = lane < cnt ? T(__ldg(sw + base + lane)) : T(0);
         for (int j0 = 0; j0 < cnt; j0 += NG * U) {
             VT x[U][NV];
             T w[U];
-            int crow[U];
+            int cr[U];
             bool take[U];
 #pragma unroll
             for (int r = 0; r < U; ++r) {
                 const int j = j0 + r * NG + grp;
                 const int u = __shfl_sync(kFull, u_l, j & 31);
-                const int c = __shfl_sync(kFull, c_l, j & 31);
+                cr[r] = __shfl_sync(kFull, c_l, j & 31);
                 if (WEIGHTED) w[r] = __shfl_sync(kFull, w_l, j & 31);
-                take[r] = j < cnt && c != cv && (unsigned)c < (unsigned)kc;
-                crow[r] = take[r] ? c : 0;
+                take[r] = j < cnt && cr[r] != cv && cr[r] >= 0;
                 const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                 for (int q = 0; q < NV; ++q) x[r][q] = (take[r] && qok[q]) ? __ldg(row + G * q) : V::zero();
@@ -176,17 +186,36 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
 #pragma unroll
             for (int r = 0; r < U; ++r) {
                 if (!take[r]) continue;
-                VT *zr = reinterpret_cast<VT *>(zg + crow[r] * wzp) + gl;
+                if (cr[r] != cur) {
+                    if (cur >= 0) {
+                        VT *zr = reinterpret_cast<VT *>(zg + cur * wzp) + gl;
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) {
+                            VT z = zr[G * q];
+                            V::add(z, run[q]);
+                            zr[G * q] = z;
+                            run[q] = V::zero();
+                        }
+                    }
+                    cur = cr[r];
+                }
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    VT z = zr[G * q];
                     if (WEIGHTED)
-                        V::fma(z, w[r], x[r][q]);
+                        V::fma(run[q], w[r], x[r][q]);
                     else
-                        V::add(z, x[r][q]);
-                    zr[G * q] = z;
+                        V::add(run[q], x[r][q]);
                 }
             }
+        }
+    }
+    if (cur >= 0) {
+        VT *zr = reinterpret_cast<VT *>(zg + cur * wzp) + gl;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            VT z = zr[G * q];
+            V::add(z, run[q]);
+            zr[G * q] = z;
         }
     }
     __syncwarp();
@@ -201,14 +230,14 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
 }
 
 template <typename T>
-__device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, int64_t e1, const int8_t *col,
-                                                T *zbuf, int lane);
+__device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, int64_t e1, const int8_t *sclr,
+                                                const float *sw, T *zbuf, int lane);
 
 // Colour histogram of (row, colouring b): Z(d) = sum of w over arcs to
 // neighbours of colour d (the passive child is a single vertex).
 template <typename T, bool WEIGHTED>
 __device__ __forceinline__ void hist_z(const NodeArgs &A, int64_t e0, int64_t e1, int b, T *zbuf, int lane) {
-    const int8_t *col = A.colours + (int64_t)b * A.n;
+    const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
     if (!WEIGHTED) {
         // counts by warp ballots: every lane ends with every colour's count
         int cnt[kMaxHistColours];
@@ -216,7 +245,7 @@ __device__ __forceinline__ void hist_z(const NodeArgs &A, int64_t e0, int64_t e1
         for (int c = 0; c < kMaxHistColours; ++c) cnt[c] = 0;
         for (int64_t base = e0; base < e1; base += 32) {
             const int64_t e = base + lane;
-            const int c = e < e1 ? (int)__ldg(col + __ldg(A.col_idx + e)) : -1;
+            const int c = e < e1 ? (int)__ldg(sclr + e) : -1;
 #pragma unroll
             for (int q = 0; q < kMaxHistColours; ++q)
                 if (q < A.kc) cnt[q] += __popc(__ballot_sync(kFull, c == q));
@@ -227,20 +256,19 @@ __device__ __forceinline__ void hist_z(const NodeArgs &A, int64_t e0, int64_t e1
                 if (q < A.kc) zbuf[q] = T(cnt[q]);
         }
     } else {
-        hist_z_weighted<T>(A, e0, e1, col, zbuf, lane);
+        hist_z_weighted<T>(A, e0, e1, sclr, A.sw + (int64_t)b * A.nnz, zbuf, lane);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, int64_t e1, const int8_t *col,
-                                                T *zbuf, int lane) {
+__device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, int64_t e1, const int8_t *sclr,
+                                                const float *sw, T *zbuf, int lane) {
     T cnt[kMaxHistColours];
 #pragma unroll
     for (int c = 0; c < kMaxHistColours; ++c) cnt[c] = T(0);
     for (int64_t e = e0 + lane; e < e1; e += 32) {
-        const int u = __ldg(A.col_idx + e);
-        const int c = __ldg(col + u);
-        const T w = T(__ldg(A.weights + e));
+        const int c = __ldg(sclr + e);
+        const T w = T(__ldg(sw + e));
 #pragma unroll
         for (int q = 0; q < kMaxHistColours; ++q) cnt[q] += (c == q) ? w : T(0);
     }
@@ -319,10 +347,13 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
 #ifndef SG2V_MINB_F32_NV2
 #define SG2V_MINB_F32_NV2 5
 #endif
+#ifndef SG2V_MINB_F32_NV1
+#define SG2V_MINB_F32_NV1 4
+#endif
 template <typename T, int NV>
 struct MinBlocks {
     static constexpr int value =
-        sizeof(T) == 4 ? (NV == 1 ? 4 : NV == 2 ? SG2V_MINB_F32_NV2 : 2) : (NV == 1 ? 3 : 2);
+        sizeof(T) == 4 ? (NV == 1 ? SG2V_MINB_F32_NV1 : NV == 2 ? SG2V_MINB_F32_NV2 : 2) : (NV == 1 ? 3 : 2);
 };
 
 template <typename T, int G, int NV, bool HIST, bool WEIGHTED>
@@ -490,6 +521,67 @@ __global__ void root_final_kernel(const RootSum *partials, int chunks, int nseg,
     out[seg] = t;
 }
 
+// Stable counting sort by neighbour colour of the arcs of each work-list task
+// (a row, or a chunk of a split row), one warp per (task, colouring); colours
+// outside [0, kc) go last, tagged -1.  Each colour then forms one run per task.
+__global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntasks, const int32_t *__restrict__ col_idx,
+                                   const float *__restrict__ weights, int64_t n, int64_t nnz,
+                                   const int8_t *__restrict__ colours, int nb, int kc, int32_t *scol, int8_t *sclr,
+                                   float *sw) {
+    __shared__ int base_s[8][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *start = base_s[wib];
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < ntasks * nb; t += nwarps) {
+        const int4 task = tasks[t / nb];
+        const int b = (int)(t % nb);
+        const int8_t *col = colours + (int64_t)b * n;
+        const int64_t e0 = task.z, e1 = task.w;
+        // pass 1: arcs per colour (bucket kc holds invalid colours)
+        int cnt = 0;  // lane q <= kc counts bucket q
+        for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
+            int c = e < e1 ? (int)__ldg(col + __ldg(col_idx + e)) : -2;
+            if (e < e1 && (unsigned)c >= (unsigned)kc) c = kc;
+            for (int q = 0; q <= kc; ++q) {
+                const unsigned m = __ballot_sync(kFull, c == q);
+                if (lane == q) cnt += __popc(m);
+            }
+        }
+        __syncwarp();
+        // exclusive prefix over buckets
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane <= kc) start[lane] = incl - cnt;
+        __syncwarp();
+        // pass 2: stable placement
+        int32_t *so = scol + (int64_t)b * nnz + e0;
+        int8_t *co = sclr + (int64_t)b * nnz + e0;
+        float *wo = sw ? sw + (int64_t)b * nnz + e0 : nullptr;
+        for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
+            const bool ok = e < e1;
+            const int u = ok ? __ldg(col_idx + e) : 0;
+            int c = ok ? (int)__ldg(col + u) : -2;
+            if (ok && (unsigned)c >= (unsigned)kc) c = kc;
+            const unsigned same = __match_any_sync(kFull, c);
+            if (ok) {
+                const int pos = start[c] + __popc(same & lt);
+                so[pos] = u;
+                co[pos] = (int8_t)(c == kc ? -1 : c);
+                if (wo) wo[pos] = __ldg(weights + e);
+            }
+            __syncwarp();
+            // advance every bucket by its arcs in this batch (leader lane of each group)
+            if (ok && (same & lt) == 0) start[c] += __popc(same);
+            __syncwarp();
+        }
+    }
+}
+
 __global__ void check_colours_kernel(const int8_t *colours, int64_t count, int kc, unsigned *status) {
     unsigned bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -563,6 +655,18 @@ cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     root_final_kernel<<<(nseg + 127) / 128, 128, 0, stream>>>(partials, chunks, nseg, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t *col_idx, const float *weights,
+                               int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc, int32_t *scol,
+                               int8_t *sclr, float *sw, int sms, cudaStream_t stream) {
+    int64_t warps = ntasks * nb;
+    int64_t blocks = (warps + 7) / 8;
+    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+    if (blocks < 1) blocks = 1;
+    colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, col_idx, weights, n, nnz, colours, nb, kc,
+                                                             scol, sclr, sw);
     return cudaGetLastError();
 }
 

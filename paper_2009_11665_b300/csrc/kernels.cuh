@@ -24,6 +24,12 @@ struct NodeArgs {
     int nb;                       // colourings in the batch
     const int8_t *colours;        // [nb][n]
     int kc;
+    // arcs of every row sorted by neighbour colour, per colouring: [nb][nnz]
+    // (neighbour, its colour or -1 when outside [0, kc), weight)
+    int64_t nnz;
+    const int32_t *scol;
+    const int8_t *sclr;
+    const float *sw;              // null when unweighted
     // passive side: per-colour accumulators Z(d, i) of compressed rows of
     // width Wz = C(kc-1, p-1), or the colour histogram when hist != 0
     const void *Mp;
@@ -86,6 +92,12 @@ cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, in
 // when pv != null and one RootSum per segment.
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,
                                int chunks, RootSum *out, cudaStream_t stream);
+
+// Sorts the arcs of every work-list task by neighbour colour (stable) for
+// each of nb colourings: scol/sclr/sw [nb][nnz] (sw only when weights != null).
+cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t *col_idx, const float *weights,
+                               int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc, int32_t *scol,
+                               int8_t *sclr, float *sw, int sms, cudaStream_t stream);
 
 // Sets *status |= 1 when any of count colours is outside [0, kc).
 cudaError_t launch_check_colours(const int8_t *colours, int64_t count, int kc, unsigned *status,

@@ -496,7 +496,7 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
     }
     // ---- per-node launch shape: gather width, Z layout, shared memory, block size
     struct Shape {
-        int wz, grp, nv, wz_pad, zwords, ywords, threads;
+        int wz, grp, nv, wz_pad, zwords, ywords, mwords, threads;
         size_t smem;
     };
     std::vector<Shape> shape(nodes.size());
@@ -516,11 +516,12 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         sh.wz_pad = hist ? 1 : sh.grp * sh.nv * vecn;
         sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
         sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
+        sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
         scratch_ld = std::max<int64_t>(scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
         sh.threads = kNodeThreads;
-        while (sh.threads > 32 && (size_t)(sh.threads / 32) * (sh.zwords + sh.ywords) * esz > 200 * 1024)
-            sh.threads /= 2;
-        sh.smem = (size_t)(sh.threads / 32) * (sh.zwords + sh.ywords) * esz;
+        const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords) * esz;
+        while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
+        sh.smem = (size_t)(sh.threads / 32) * per_warp;
         if (sh.smem > 227 * 1024) {
             set_error("per-colour accumulators exceed shared memory (column tiling not built)");
             return SG2V_ERR_UNSUPPORTED;
@@ -593,6 +594,7 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         A.wz_pad = sh.wz_pad;
         A.zwords = sh.zwords;
         A.ywords = sh.ywords;
+        A.mwords = sh.mwords;
         A.p = c.p;
         if (!A.hist) {
             A.Mp = table[c.passive];
@@ -602,6 +604,7 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         if (!A.a_leaf) {
             A.Ma = table[c.active];
             A.lda = ld[c.active];
+            A.Wa = (int)binom(kc - 1, c.a - 1);
         }
         A.Ws = (int)binom(kc - 1, c.t - 1);
         DeviceTables tab;

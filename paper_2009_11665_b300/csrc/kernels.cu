@@ -300,7 +300,8 @@ __device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbu
 // row into root_out instead of storing it.  ok = false (a colour outside
 // [0, kc), reported by the host) writes zeros.
 template <typename T>
-__device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool ok, const T *ybuf, int lane) {
+__device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool ok, const T *ybuf, const T *ma,
+                                         int lane) {
     const int64_t rowb = (int64_t)v * A.nb + b;
     const int ws = A.Ws;
     T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
@@ -314,13 +315,12 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
                 out[j] = y;
         }
     } else {
-        const T *ma = static_cast<const T *>(A.Ma) + rowb * A.lda;
         const int ns = A.nsplit;
         if (A.root) {
             const int total = ok ? ws * ns : 0;
             for (int p = lane; p < total; p += 32) {
                 const uint32_t sp = __ldg(A.splits + p);
-                s = fma(__ldg(ma + (sp & 0xffffu)), ybuf[sp >> 16], s);
+                s = fma(ma[sp & 0xffffu], ybuf[sp >> 16], s);
             }
         } else {
             for (int S = lane; S < ws; S += 32) {
@@ -329,7 +329,7 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
                 if (ok) {
                     for (int j = 0; j < ns; ++j) {
                         const uint32_t x = __ldg(sp + j);
-                        acc = fma(__ldg(ma + (x & 0xffffu)), ybuf[x >> 16], acc);
+                        acc = fma(ma[x & 0xffffu], ybuf[x >> 16], acc);
                     }
                 }
                 out[S] = acc;
@@ -361,18 +361,37 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    T *zbuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.zwords + A.ywords);
+    T *zbuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.zwords + A.ywords + A.mwords);
     T *ybuf = zbuf + A.zwords;
+    T *mbuf = ybuf + A.ywords;  // this row's active-child row (a >= 2)
     const int zlen = HIST ? A.kc : A.kc * A.wz_pad;
+    const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; ti < A.ntasks; ti += nwarps) {
-        const int4 task = A.tasks[ti];
+    int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
+    int4 task = ti < A.ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
+    for (; ti < A.ntasks; ti += nwarps) {
+        // the next task's descriptor is fetched while this one runs
+        const int4 next = ti + nwarps < A.ntasks ? A.tasks[ti + nwarps] : task;
         const int v = task.x;
         const int slot = task.y;
         const int64_t e0 = task.z, e1 = task.w;
         for (int b = 0; b < A.nb; ++b) {
             const int cv = A.colours[(int64_t)b * A.n + v];
             const bool cok = (unsigned)cv < (unsigned)A.kc;
+            if (e0 == e1) {
+                // no arcs: Y' = 0, so every output of the row is zero
+                epilogue<T>(A, v, b, false, ybuf, mbuf, lane);
+                continue;
+            }
+            if (mchunks && cok) {
+                // start copying the active row now; it is needed only by the eMA
+                const char *src = static_cast<const char *>(A.Ma) + ((int64_t)v * A.nb + b) * A.lda * sizeof(T);
+                for (int c = lane; c < mchunks; c += 32) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(mbuf) + 16 * c);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * c) : "memory");
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
             if (HIST)
                 hist_z<T, WEIGHTED>(A, e0, e1, b, zbuf, lane);
             else
@@ -392,6 +411,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
                 }
                 last = __shfl_sync(kFull, last, 0);
                 if (!last) {
+                    if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
                     __syncwarp();
                     continue;
                 }
@@ -400,10 +420,12 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
                 __syncwarp();
             }
             if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane);
+            if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
-            epilogue<T>(A, v, b, cok, ybuf, lane);
+            epilogue<T>(A, v, b, cok, ybuf, mbuf, lane);
             __syncwarp();
         }
+        task = next;
     }
 }
 

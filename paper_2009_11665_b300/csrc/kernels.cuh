@@ -41,11 +41,12 @@ struct NodeArgs {
     int p;
     int wy;                       // C(kc-1, p)
     const uint16_t *expand;       // [kc][wy][p] offsets into Z
-    // shared memory per warp, in elements: Z copies, then Y'
-    int zwords, ywords;
+    // shared memory per warp, in elements: Z copies, Y', the active row
+    int zwords, ywords, mwords;
     // active side
     const void *Ma;
     int64_t lda;
+    int Wa;                       // C(kc-1, a-1)
     int a_leaf;                   // active child is a single vertex: M_s' = Y'
     // output
     void *Ms;

@@ -75,7 +75,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -187,17 +187,47 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
     return ms / steps
 
 
+def profile_call(args):
+    """One sg2v_count_batched call (B = --batch colourings) of tree10 on an
+    R-MAT graph with the workload's parameters and average degree 32."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as sg
+
+    torch.cuda.set_device(0)
+    scale = 18 if args.profile_call == "rmat18" else 20
+    g = si.rmat(scale, (1 << scale) * 16, seed=0)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(TEMPLATE.parent, 0, K_COLOURS)
+    cols = torch.from_numpy(si.colourings(g.n, K_COLOURS, args.batch, seed=0)).cuda()
+    tot = torch.empty((1, args.batch), dtype=torch.float64, device="cuda")
+    sg.sg2v_count_batched(graph.handle, [plan.handle], cols, args.batch, sg.PRECISIONS[args.precision], None, tot)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_call": args.profile_call, "batch": args.batch, "precision": args.precision,
+                      "totals": tot.cpu().tolist()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=int(os.environ.get("SG2V_BENCH_BATCH", "4")))
     ap.add_argument("--impl", default="sg2v", choices=["sg2v", "reference"])
     ap.add_argument("--reference-scale", type=int, default=16)
     ap.add_argument("--cpu-baseline-scale", type=int, default=17)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-call", choices=["rmat18", "rmat20"], default=None,
+                    help="run exactly one count call on R-MAT scale 18 or 20 (avg degree 32, tree10) and exit: "
+                         "the case the committed ncu summaries capture")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     args = ap.parse_args()
+    if args.profile_call:
+        profile_call(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
 

@@ -45,6 +45,15 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def source_digest() -> str:
+    """Digest of the sources that decide what a node launch does (kernels and
+    the executor that sets its launch configuration)."""
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2009_11665_b300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record():
     """DRAM bytes per launch from the committed ncu summary, valid only while
     the kernel source is unchanged."""
@@ -53,8 +62,7 @@ def traffic_record():
         rec = json.load(open(path))
     except OSError:
         return {}
-    src = open(os.path.join(ROOT, "paper_2009_11665_b300", "csrc", "kernels.cu"), "rb").read()
-    if rec.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("source_sha256") != source_digest():
         return {}
     return rec.get("bytes_per_launch", {})
 

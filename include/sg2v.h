@@ -187,6 +187,56 @@ sg2v_status sg2v_count_batched(const sg2v_graph *graph, const sg2v_plan *const *
                                const int8_t *colours, int32_t B, sg2v_precision precision, double *per_vertex,
                                double *totals, double *estimates, sg2v_stream stream);
 
+/* ---------------------------------------------------------------- session */
+
+/*
+ * A session runs the same request (graph, plans, B colourings, precision)
+ * many times with new colourings, asynchronously and without allocating:
+ * every buffer is allocated once at creation, the whole launch sequence of a
+ * run (colour check, per wave the colour sort and one launch per DP node,
+ * root reductions and the final totals) is captured into a CUDA graph on the
+ * first run and replayed afterwards, and totals and estimates are finished on
+ * the device (exact 128-bit sums rounded once; estimates in double-double).
+ * This is the batched form of the method for repeated colourings (the
+ * estimator of Alg. 1 runs N colourings).  Not thread-safe: one run at a time
+ * per session.
+ */
+typedef struct sg2v_session sg2v_session;
+
+#define SG2V_SESSION_PER_VERTEX 0x1u /* keep per-vertex counts ([plans][B][n] doubles) */
+#define SG2V_SESSION_NO_GRAPH 0x2u   /* launch kernels directly instead of replaying a CUDA graph */
+#define SG2V_SESSION_AUTOTUNE 0x4u   /* the first run times candidate wave widths and keeps the fastest */
+
+/*
+ * sg2v_session_create -- plans as in sg2v_count_batched (same num_colours),
+ * B >= 1 colourings per run, flags from SG2V_SESSION_*.  Device memory of
+ * the current device is allocated here (OUT_OF_MEMORY if it does not fit).
+ */
+sg2v_status sg2v_session_create(const sg2v_graph *graph, const sg2v_plan *const *plans, int32_t num_plans,
+                                int32_t B, sg2v_precision precision, uint32_t flags, sg2v_session **out);
+
+/*
+ * sg2v_session_run -- one run on stream.  colours [B][n] int8, host or
+ * device, is copied into the session first; totals / estimates
+ * ([num_plans][B] doubles) and per_vertex ([num_plans][B][n], requires
+ * SG2V_SESSION_PER_VERTEX) may be NULL, host or device and are written by
+ * copies ordered after the run.  Returns without synchronising (except the
+ * first run of an autotuning session, which times candidates); errors found
+ * by the kernels (colour range, overflow) are reported by sg2v_session_sync.
+ */
+sg2v_status sg2v_session_run(sg2v_session *session, const int8_t *colours, double *totals, double *estimates,
+                             double *per_vertex, sg2v_stream stream);
+
+/* Waits for the session's last run on stream and returns its status
+ * (COLOUR_OUT_OF_RANGE, FP_OVERFLOW or OK). */
+sg2v_status sg2v_session_sync(sg2v_session *session, sg2v_stream stream);
+
+/* Wave width in use (colourings sharing a table row) and whether runs replay
+ * a CUDA graph.  Either output may be NULL. */
+sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_t *graph);
+
+sg2v_status sg2v_session_destroy(sg2v_session *session);
+
 /* -------------------------------------------------------------- profiling */
 
 /*

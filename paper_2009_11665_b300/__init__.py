@@ -34,6 +34,9 @@ SG2V_ERR_UNSUPPORTED = 9
 SG2V_FP64 = 0
 SG2V_FP32 = 1
 SG2V_GRAPH_SKIP_VALIDATION = 0x1
+SG2V_SESSION_PER_VERTEX = 0x1
+SG2V_SESSION_NO_GRAPH = 0x2
+SG2V_SESSION_AUTOTUNE = 0x4
 
 PRECISIONS = {"fp64": SG2V_FP64, "fp32": SG2V_FP32}
 
@@ -57,6 +60,11 @@ _SIGNATURES = {
     "sg2v_count": [_p, _p, _p, ctypes.c_int, _p, _p, _p, _p],
     "sg2v_count_batched": [_p, _p, _i32, _p, _i32, ctypes.c_int, _p, _p, _p, _p],
     "sg2v_sum_counts_noalloc": [_p, _i64, _i32, _p, _p],
+    "sg2v_session_create": [_p, _p, _i32, _i32, ctypes.c_int, _u32, ctypes.POINTER(_p)],
+    "sg2v_session_run": [_p, _p, _p, _p, _p, _p],
+    "sg2v_session_sync": [_p, _p],
+    "sg2v_session_info": [_p, _p, _p],
+    "sg2v_session_destroy": [_p],
 }
 for _name, _args in _SIGNATURES.items():
     _f = getattr(_lib, _name)
@@ -215,6 +223,33 @@ def sg2v_sum_counts_noalloc(values, n: int, nseg: int, totals, stream=None) -> N
            "sg2v_sum_counts_noalloc")
 
 
+def sg2v_session_create(graph, plans: Sequence[int], B: int, precision: int = SG2V_FP32, flags: int = 0) -> int:
+    arr = (_p * len(plans))(*plans)
+    h = _p()
+    _check(_lib.sg2v_session_create(graph, arr, len(plans), int(B), int(precision), int(flags), ctypes.byref(h)),
+           "sg2v_session_create")
+    return h.value
+
+
+def sg2v_session_run(session, colours, totals=None, estimates=None, per_vertex=None, stream=None) -> None:
+    _check(_lib.sg2v_session_run(session, _ptr(colours), _ptr(totals), _ptr(estimates), _ptr(per_vertex),
+                                 _stream(stream)), "sg2v_session_run")
+
+
+def sg2v_session_sync(session, stream=None) -> None:
+    _check(_lib.sg2v_session_sync(session, _stream(stream)), "sg2v_session_sync")
+
+
+def sg2v_session_info(session):
+    w, gr = _i32(), _i32()
+    _check(_lib.sg2v_session_info(session, ctypes.byref(w), ctypes.byref(gr)), "sg2v_session_info")
+    return w.value, bool(gr.value)
+
+
+def sg2v_session_destroy(session) -> None:
+    _check(_lib.sg2v_session_destroy(session), "sg2v_session_destroy")
+
+
 def sg2v_profile_enable(enable: bool = True) -> None:
     _check(_lib.sg2v_profile_enable(1 if enable else 0), "sg2v_profile_enable")
 
@@ -303,6 +338,38 @@ def count(graph: Graph, plan: Plan, colours, precision: str = "fp64", per_vertex
     pv = torch.empty(graph.n, dtype=torch.float64, device=dev) if per_vertex else None
     total, est = sg2v_count(graph.handle, plan.handle, colours, PRECISIONS[precision], pv, stream)
     return pv, total, est
+
+
+class Session:
+    """Repeated batched counting with preallocated buffers and CUDA-graph
+    replay (see sg2v_session_create)."""
+
+    def __init__(self, graph: Graph, plans: Sequence[Plan], B: int, precision: str = "fp32",
+                 per_vertex: bool = False, graph_replay: bool = True, autotune: bool = False):
+        flags = (SG2V_SESSION_PER_VERTEX if per_vertex else 0) | (0 if graph_replay else SG2V_SESSION_NO_GRAPH) | \
+                (SG2V_SESSION_AUTOTUNE if autotune else 0)
+        self.graph, self.plans, self.B = graph, list(plans), int(B)
+        self.handle = sg2v_session_create(graph.handle, [p.handle for p in plans], B, PRECISIONS[precision], flags)
+
+    def run(self, colours, totals=None, estimates=None, per_vertex=None, stream=None):
+        sg2v_session_run(self.handle, colours, totals, estimates, per_vertex, stream)
+
+    def sync(self, stream=None):
+        sg2v_session_sync(self.handle, stream)
+
+    def info(self):
+        return sg2v_session_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sg2v_session_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def count_batched(graph: Graph, plans: Sequence[Plan], colours, precision: str = "fp32", per_vertex: bool = False,

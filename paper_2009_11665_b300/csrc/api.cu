@@ -59,6 +59,7 @@ bool is_device_pointer(const void *p) {
 
 struct DeviceInfo {
     int sms = 0;
+    int64_t l2_bytes = 0;
     cudaMemPool_t pool = nullptr;
 };
 
@@ -74,6 +75,9 @@ sg2v_status device_info(int dev, DeviceInfo *out) {
     }
     DeviceInfo info;
     SG2V_CUDA(cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+    int l2 = 0;
+    SG2V_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev), "device attribute");
+    info.l2_bytes = l2;
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof props);
     props.allocType = cudaMemAllocationTypePinned;
@@ -138,6 +142,7 @@ std::atomic<int64_t> g_launches{0};
 // Event pairs of one call, folded into the records after its final sync.
 struct CallTimer {
     bool on = false;
+    bool count = true;  // false while a stream is being captured (replays count themselves)
     struct Item {
         std::string name;
         double bytes;
@@ -151,7 +156,7 @@ struct CallTimer {
         on = g_prof_enabled;
     }
     void begin(const std::string &name, double bytes) {
-        g_launches.fetch_add(1);
+        if (count) g_launches.fetch_add(1);
         if (!on) return;
         Item it{name, bytes, nullptr, nullptr};
         cudaEventCreate(&it.a);
@@ -165,7 +170,9 @@ struct CallTimer {
         cudaEventRecord(items[open].b, stream);
         open = -1;
     }
-    void count_extra(int n) { g_launches.fetch_add(n); }
+    void count_extra(int n) {
+        if (count) g_launches.fetch_add(n);
+    }
     // call after the stream has been synchronised
     void collect() {
         if (!on) return;
@@ -357,6 +364,450 @@ struct CNode {
     int last_use;
 };
 
+// Launch shape of one node: gather width, Z layout, shared memory, block size.
+struct Shape {
+    int wz, grp, nv, wz_pad, zwords, ywords, mwords, threads;
+    size_t smem;
+    int blocks_per_sm;
+};
+
+// Everything about a (graph, plans, batch, precision) request that does not
+// depend on the colourings: the merged node list (sub-templates shared within
+// and across plans), shapes and column tables.
+struct Prepared {
+    const sg2v_graph *g = nullptr;
+    std::vector<const sg2v_plan *> plans;
+    int kc = 0, nb = 0, dev = 0;
+    bool fp64 = false;
+    size_t esz = 4;
+    int vecn = 4;
+    int64_t n = 0;
+    DeviceInfo info;
+    std::vector<CNode> nodes;
+    std::vector<int> plan_root;   // combined root node of each plan (-1: single vertex)
+    std::vector<int> root_plan;   // plan of each combined root node
+    std::vector<Shape> shape;
+    std::vector<DeviceTables> tabs;
+    int64_t scratch_ld = 1;
+    int auto_wave = 1;            // widest wave whose gathered table fits half of L2
+};
+
+sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans, int32_t B,
+                    sg2v_precision precision, Prepared *P) {
+    if (!g || !plans || num_plans < 1 || B < 1 || (precision != SG2V_FP64 && precision != SG2V_FP32)) {
+        set_error("invalid argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    const int kc = plans[0] ? plans[0]->kc : 0;
+    for (int i = 0; i < num_plans; ++i)
+        if (!plans[i] || plans[i]->kc != kc) {
+            set_error("plans must be non-null and share num_colours");
+            return SG2V_ERR_INVALID_ARGUMENT;
+        }
+    SG2V_CUDA(cudaGetDevice(&P->dev), "cudaGetDevice");
+    if (P->dev != g->device) {
+        set_error("graph lives on another device");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    sg2v_status st = device_info(P->dev, &P->info);
+    if (st) return st;
+    P->g = g;
+    P->plans.assign(plans, plans + num_plans);
+    P->kc = kc;
+    P->nb = B;
+    P->fp64 = precision == SG2V_FP64;
+    P->esz = P->fp64 ? 8 : 4;
+    P->vecn = P->fp64 ? 2 : 4;
+    P->n = g->n;
+    P->plan_root.assign(num_plans, -1);
+    std::map<std::string, int> shared;
+    for (int pi = 0; pi < num_plans; ++pi) {
+        const sg2v_plan *pl = plans[pi];
+        std::vector<int> remap(pl->nodes.size(), -1);
+        for (size_t i = 0; i < pl->nodes.size(); ++i) {
+            const PlanNode &pn = pl->nodes[i];
+            if (!pn.is_root) {
+                auto it = shared.find(pn.canon);
+                if (it != shared.end()) {
+                    remap[i] = it->second;
+                    continue;
+                }
+            }
+            CNode c{pn.t, pn.a, pn.p, pn.active == kLeaf ? kLeaf : remap[pn.active],
+                    pn.passive == kLeaf ? kLeaf : remap[pn.passive], pn.is_root, -1};
+            P->nodes.push_back(c);
+            remap[i] = (int)P->nodes.size() - 1;
+            if (!pn.is_root) shared[pn.canon] = remap[i];
+            if (pn.is_root) P->plan_root[pi] = remap[i];
+        }
+    }
+    auto &nodes = P->nodes;
+    P->root_plan.assign(nodes.size(), -1);
+    for (int pi = 0; pi < num_plans; ++pi)
+        if (P->plan_root[pi] >= 0) P->root_plan[P->plan_root[pi]] = pi;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        if (nodes[i].active != kLeaf) nodes[nodes[i].active].last_use = (int)i;
+        if (nodes[i].passive != kLeaf) nodes[nodes[i].passive].last_use = (int)i;
+    }
+    P->shape.resize(nodes.size());
+    P->tabs.resize(nodes.size());
+    int64_t widest = 1;
+    for (size_t i = 0; i < nodes.size(); ++i) {
+        const CNode &c = nodes[i];
+        Shape &sh = P->shape[i];
+        const bool hist = c.p == 1;
+        sh.wz = hist ? 1 : (int)binom(kc - 1, c.p - 1);
+        sh.grp = 32;
+        sh.nv = 1;
+        if (!hist) node_shape(P->fp64, sh.wz, &sh.grp, &sh.nv);
+        if (sh.nv == 0) {
+            set_error("passive table wider than this build's register tile (column tiling not built)");
+            return SG2V_ERR_UNSUPPORTED;
+        }
+        if (!hist) widest = std::max<int64_t>(widest, (sh.wz + P->vecn - 1) / P->vecn * P->vecn);
+        sh.wz_pad = hist ? 1 : sh.grp * sh.nv * P->vecn;
+        sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
+        sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
+        sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
+        P->scratch_ld = std::max<int64_t>(P->scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
+        sh.threads = kNodeThreads;
+        const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords) * P->esz;
+        while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
+        sh.smem = (size_t)(sh.threads / 32) * per_warp;
+        if (sh.smem > 227 * 1024) {
+            set_error("per-colour accumulators exceed shared memory (column tiling not built)");
+            return SG2V_ERR_UNSUPPORTED;
+        }
+        sh.blocks_per_sm = node_blocks_per_sm(P->fp64, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
+        if (sh.blocks_per_sm < 1) {
+            set_error("node kernel cannot be resident with its shared memory");
+            return SG2V_ERR_UNSUPPORTED;
+        }
+        if ((st = device_tables(P->dev, kc, c.t, c.a, sh.wz_pad, &P->tabs[i]))) return st;
+    }
+    const double per_colouring = (double)P->n * widest * P->esz;
+    const int w = (int)std::floor(0.5 * P->info.l2_bytes / per_colouring);
+    const int forced = env_int("SG2V_WAVE", 0);
+    P->auto_wave = std::max(1, std::min(B, forced > 0 ? forced : w));
+    return SG2V_OK;
+}
+
+// Device buffers of one run for a given wave width.
+struct RunBuffers {
+    int wave = 1;
+    int32_t *scol = nullptr;
+    int8_t *sclr = nullptr;
+    float *sw = nullptr;
+    void *scratch = nullptr;
+    unsigned *counters = nullptr;
+    size_t scratch_bytes = 0, counter_bytes = 0;
+    std::vector<void *> rootbuf;  // per plan: [nb][n] table type
+    std::vector<void *> table;    // per node: one wave's table
+    std::vector<int64_t> ld;
+    unsigned *status = nullptr;   // [4]: bit 0 colour out of range
+    double *ones = nullptr;       // [nb][n] ones for single-vertex templates
+    int chunks = 1;
+    RootSum *partials = nullptr;  // [plans][nb][chunks]
+    RootSum *sums = nullptr;      // [plans][nb]
+};
+
+// Where node tables come from: per-call pool allocations freed after their
+// last consumer, or a session's fixed buffers.
+struct TableSource {
+    virtual ~TableSource() {}
+    virtual sg2v_status get(size_t node, size_t bytes, void **p) = 0;
+    virtual void done(size_t node) = 0;
+};
+
+int64_t table_ld(const Prepared &P, const CNode &c) {
+    return (binom(P.kc - 1, c.t - 1) + P.vecn - 1) / P.vecn * P.vecn;
+}
+
+// Allocates the non-table buffers of a run from `alloc(bytes, &ptr)`.
+template <typename Alloc>
+sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
+    const sg2v_graph *g = P.g;
+    sg2v_status st;
+    R->wave = wave;
+    if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R->scol))) return st;
+    if ((st = alloc((size_t)wave * g->nnz, (void **)&R->sclr))) return st;
+    if (g->weighted && (st = alloc((size_t)wave * g->nnz * sizeof(float), (void **)&R->sw))) return st;
+    R->scratch_bytes = (size_t)(g->nheavy * wave * P.scratch_ld) * P.esz;
+    R->counter_bytes = (size_t)(g->nheavy * wave) * sizeof(unsigned);
+    if (g->nheavy) {
+        if ((st = alloc(R->scratch_bytes, &R->scratch))) return st;
+        if ((st = alloc(R->counter_bytes, (void **)&R->counters))) return st;
+    }
+    R->rootbuf.assign(P.plans.size(), nullptr);
+    for (size_t pi = 0; pi < P.plans.size(); ++pi)
+        if (P.plan_root[pi] >= 0 && (st = alloc((size_t)P.nb * P.n * P.esz, &R->rootbuf[pi]))) return st;
+    R->table.assign(P.nodes.size(), nullptr);
+    R->ld.assign(P.nodes.size(), 0);
+    if ((st = alloc(16, (void **)&R->status))) return st;
+    R->chunks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (P.n + 65535) / 65536 * 4));
+    const size_t segs = P.plans.size() * (size_t)P.nb;
+    if ((st = alloc(sizeof(RootSum) * segs * R->chunks, (void **)&R->partials))) return st;
+    if ((st = alloc(sizeof(RootSum) * segs, (void **)&R->sums))) return st;
+    return SG2V_OK;
+}
+
+// Enqueues the whole DP for colourings d_col ([nb][n], device) on `stream`:
+// colour check, per wave the colour sort and one launch per node, then the
+// root reductions into R.sums (and per-vertex doubles when pv != null).
+// Nothing here synchronises, so the sequence can be captured in a CUDA graph.
+sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, double *pv, TableSource &src,
+                    cudaStream_t stream, CallTimer &timer) {
+    const sg2v_graph *g = P.g;
+    const int64_t n = P.n;
+    const int nb = P.nb, kc = P.kc, wave = R.wave;
+    const size_t esz = P.esz;
+    sg2v_status st;
+    SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
+    timer.count_extra(1);
+    SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, R.status, stream), "colour check");
+    for (int b0 = 0; b0 < nb; b0 += wave) {
+        const int wb = std::min(wave, nb - b0);
+        const int8_t *wcol = d_col + (int64_t)b0 * n;
+        timer.begin("colour_sort",
+                    (double)wb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))));
+        SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->col_idx, g->weights, n, g->nnz, wcol, wb, kc, R.scol,
+                                     R.sclr, R.sw, P.info.sms, stream),
+                  "colour sort");
+        timer.end();
+        for (size_t i = 0; i < P.nodes.size(); ++i) {
+            const CNode &c = P.nodes[i];
+            const Shape &sh = P.shape[i];
+            NodeArgs A;
+            std::memset(&A, 0, sizeof A);
+            A.row_ptr = g->row_ptr;
+            A.col_idx = g->col_idx;
+            A.weights = g->weights;
+            A.tasks = g->tasks;
+            A.ntasks = g->ntasks;
+            A.heavy_chunks = g->heavy_chunks;
+            A.n = n;
+            A.nb = wb;
+            A.colours = wcol;
+            A.kc = kc;
+            A.nnz = g->nnz;
+            A.scol = R.scol;
+            A.sclr = R.sclr;
+            A.sw = R.sw;
+            A.hist = c.p == 1;
+            A.Wz = sh.wz;
+            A.wz_pad = sh.wz_pad;
+            A.zwords = sh.zwords;
+            A.ywords = sh.ywords;
+            A.mwords = sh.mwords;
+            A.p = c.p;
+            if (!A.hist) {
+                A.Mp = R.table[c.passive];
+                A.ldp = R.ld[c.passive];
+            }
+            A.a_leaf = c.a == 1;
+            if (!A.a_leaf) {
+                A.Ma = R.table[c.active];
+                A.lda = R.ld[c.active];
+                A.Wa = (int)binom(kc - 1, c.a - 1);
+            }
+            A.Ws = (int)binom(kc - 1, c.t - 1);
+            A.expand = P.tabs[i].expand;
+            A.wy = P.tabs[i].wy;
+            A.splits = P.tabs[i].splits;
+            A.nsplit = P.tabs[i].nsplit;
+            A.root = c.is_root;
+            if (c.is_root) {
+                A.root_out = static_cast<char *>(R.rootbuf[P.root_plan[i]]) + (size_t)b0 * n * esz;
+            } else {
+                R.ld[i] = table_ld(P, c);
+                if ((st = src.get(i, (size_t)n * wb * R.ld[i] * esz, &R.table[i]))) return st;
+                A.Ms = R.table[i];
+                A.ldt = R.ld[i];
+            }
+            A.scratch = R.scratch;
+            A.scratch_ld = P.scratch_ld;
+            A.counters = R.counters;
+            if (g->nheavy) {
+                SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
+                SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
+            }
+            {
+                // algorithmic bytes: each input table, the sorted arc list
+                // (neighbour, its colour, weight) and the colouring read once,
+                // the output written once
+                const double rows = (double)n * wb;
+                double bytes = 8.0 * (n + 1) + (double)wb * g->nnz * (5.0 + (g->weighted ? 4.0 : 0.0));
+                bytes += rows;  // colours
+                if (!A.hist) bytes += rows * A.Wz * esz;
+                if (!A.a_leaf && !(c.active == c.passive && !A.hist)) bytes += rows * binom(kc - 1, c.a - 1) * esz;
+                bytes += c.is_root ? rows * esz : rows * A.Ws * esz;
+                char name[64];
+                std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p, P.fp64 ? "fp64" : "fp32");
+                timer.begin(name, bytes);
+            }
+            SG2V_CUDA(launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
+                                  stream),
+                      "node kernel launch");
+            timer.end();
+            if (c.active != kLeaf && P.nodes[c.active].last_use == (int)i) src.done(c.active);
+            if (c.passive != kLeaf && P.nodes[c.passive].last_use == (int)i && c.passive != c.active)
+                src.done(c.passive);
+        }
+    }
+    for (size_t pi = 0; pi < P.plans.size(); ++pi) {
+        double *pvp = pv ? pv + pi * (size_t)nb * n : nullptr;
+        const void *vals = P.plan_root[pi] >= 0 ? R.rootbuf[pi] : R.ones;
+        const bool vals_fp64 = P.plan_root[pi] >= 0 ? P.fp64 : true;
+        timer.begin("root_reduce", (double)nb * n * ((vals_fp64 ? 8 : 4) + (pvp ? 8 : 0)));
+        timer.count_extra(1);
+        SG2V_CUDA(launch_root_reduce(vals, vals_fp64, n, nb, pvp, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
+                                     R.sums + pi * (size_t)nb, stream),
+                  "root reduction");
+        timer.end();
+    }
+    return SG2V_OK;
+}
+
+bool needs_ones(const Prepared &P) {
+    for (int r : P.plan_root)
+        if (r < 0) return true;
+    return false;
+}
+
+}  // namespace
+}  // namespace sg2v
+
+struct sg2v_session {
+    sg2v::Prepared P;
+    sg2v::RunBuffers R;
+    uint32_t flags = 0;
+    std::vector<void *> owned;  // everything cudaMalloc'd here
+    std::vector<void *> owned_tables;
+    int8_t *colours = nullptr;  // [nb][n] staging
+    double *pv = nullptr;       // [plans][nb][n]
+    double *totals = nullptr, *estimates = nullptr;  // [plans][nb]
+    double *scale = nullptr;    // [2][plans] hi, lo
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;  // private stream the graph is recorded on (any stream may replay it)
+    bool tuned = false;
+    int64_t launches_per_run = 0;
+};
+
+namespace sg2v {
+namespace {
+
+void session_free_tables(sg2v_session *S) {
+    for (void *p : S->owned_tables) cudaFree(p);
+    S->owned_tables.clear();
+    S->R.table.assign(S->P.nodes.size(), nullptr);
+}
+
+void session_free(sg2v_session *S) {
+    if (!S) return;
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->capture) cudaStreamDestroy(S->capture);
+    session_free_tables(S);
+    for (void *p : S->owned) cudaFree(p);
+    delete S;
+}
+
+// (Re)allocates the wave-dependent buffers of a session for `wave`.
+sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
+    const Prepared &P = S->P;
+    // wave-independent buffers (root outputs, reductions) are reused when present
+    sg2v_status st;
+    auto alloc = [&](size_t bytes, void **p) -> sg2v_status {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) return cuda_fail(e, "session allocation");
+        S->owned.push_back(*p);
+        return SG2V_OK;
+    };
+    // wave-dependent: sorted arcs, split-row scratch, tables
+    for (void *p : {(void *)S->R.scol, (void *)S->R.sclr, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters}) {
+        if (!p) continue;
+        auto it = std::find(S->owned.begin(), S->owned.end(), p);
+        if (it != S->owned.end()) {
+            cudaFree(p);
+            S->owned.erase(it);
+        }
+    }
+    const sg2v_graph *g = P.g;
+    RunBuffers &R = S->R;
+    R.wave = wave;
+    R.scol = nullptr;
+    R.sclr = nullptr;
+    R.sw = nullptr;
+    R.scratch = nullptr;
+    R.counters = nullptr;
+    if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R.scol))) return st;
+    if ((st = alloc((size_t)wave * g->nnz, (void **)&R.sclr))) return st;
+    if (g->weighted && (st = alloc((size_t)wave * g->nnz * sizeof(float), (void **)&R.sw))) return st;
+    R.scratch_bytes = (size_t)(g->nheavy * wave * P.scratch_ld) * P.esz;
+    R.counter_bytes = (size_t)(g->nheavy * wave) * sizeof(unsigned);
+    if (g->nheavy) {
+        if ((st = alloc(R.scratch_bytes, &R.scratch))) return st;
+        if ((st = alloc(R.counter_bytes, (void **)&R.counters))) return st;
+    }
+    session_free_tables(S);
+    for (size_t i = 0; i < P.nodes.size(); ++i) {
+        if (P.nodes[i].is_root) continue;
+        R.ld[i] = table_ld(P, P.nodes[i]);
+        void *t = nullptr;
+        cudaError_t e = cudaMalloc(&t, std::max<size_t>((size_t)P.n * wave * R.ld[i] * P.esz, 16));
+        if (e != cudaSuccess) return cuda_fail(e, "session table allocation");
+        S->owned_tables.push_back(t);
+        R.table[i] = t;
+    }
+    return SG2V_OK;
+}
+
+struct FixedTables : TableSource {
+    std::vector<void *> &table;
+    explicit FixedTables(std::vector<void *> &t) : table(t) {}
+    sg2v_status get(size_t i, size_t, void **p) override {
+        *p = table[i];
+        return SG2V_OK;
+    }
+    void done(size_t) override {}
+};
+
+// One run of the session's sequence on stream (no synchronisation).
+sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bool capturing = false) {
+    CallTimer timer(stream);
+    if (!timed) timer.on = false;
+    if (capturing) timer.count = false;
+    FixedTables src(S->R.table);
+    sg2v_status st = enqueue(S->P, S->R, S->colours, S->pv, src, stream, timer);
+    if (st) return st;
+    const int nseg = (int)S->P.plans.size() * S->P.nb;
+    SG2V_CUDA(launch_finalize(S->R.sums, nseg, S->P.nb, S->scale, S->scale + S->P.plans.size(), S->totals,
+                              S->estimates, S->R.status, stream),
+              "finalize");
+    if (timed) {
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+        timer.collect();
+    }
+    return SG2V_OK;
+}
+
+int64_t count_launches(const Prepared &P, int wave) {
+    const int64_t waves = (P.nb + wave - 1) / wave;
+    return 1 + waves * (1 + (int64_t)P.nodes.size()) + 2 * (int64_t)P.plans.size() + 1;
+}
+
+sg2v_status copy_out(double *dst, const double *src, size_t count, cudaStream_t stream) {
+    if (!dst) return SG2V_OK;
+    SG2V_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, stream), "result copy");
+    return SG2V_OK;
+}
+
+}  // namespace
+}  // namespace sg2v
+
+namespace sg2v {
+namespace {
+
 }  // namespace
 }  // namespace sg2v
 
@@ -441,96 +892,18 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
                                const int8_t *colours, int32_t B, sg2v_precision precision, double *per_vertex,
                                double *totals, double *estimates, sg2v_stream stream_) {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    if (!g || !plans || num_plans < 1 || !colours || B < 1 || (precision != SG2V_FP64 && precision != SG2V_FP32)) {
-        set_error("invalid argument");
+    if (!colours) {
+        set_error("null colours");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
-    const int kc = plans[0] ? plans[0]->kc : 0;
-    for (int i = 0; i < num_plans; ++i)
-        if (!plans[i] || plans[i]->kc != kc) {
-            set_error("plans must be non-null and share num_colours");
-            return SG2V_ERR_INVALID_ARGUMENT;
-        }
-    int dev = 0;
-    SG2V_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
-    if (dev != g->device) {
-        set_error("graph lives on another device");
-        return SG2V_ERR_INVALID_ARGUMENT;
-    }
-    DeviceInfo info;
-    sg2v_status st = device_info(dev, &info);
+    Prepared P;
+    sg2v_status st = prepare(g, plans, num_plans, B, precision, &P);
     if (st) return st;
-    const bool fp64 = precision == SG2V_FP64;
-    const size_t esz = fp64 ? 8 : 4;
-    const int vecn = fp64 ? 2 : 4;
-    const int64_t n = g->n;
+    const int64_t n = P.n;
     const int nb = B;
-
-    // ---- merged node list: sub-templates shared within and across plans
-    std::vector<CNode> nodes;
-    std::vector<int> plan_root(num_plans, -1);
-    std::map<std::string, int> shared;
-    for (int pi = 0; pi < num_plans; ++pi) {
-        const sg2v_plan *pl = plans[pi];
-        std::vector<int> remap(pl->nodes.size(), -1);
-        for (size_t i = 0; i < pl->nodes.size(); ++i) {
-            const PlanNode &pn = pl->nodes[i];
-            if (!pn.is_root) {
-                auto it = shared.find(pn.canon);
-                if (it != shared.end()) {
-                    remap[i] = it->second;
-                    continue;
-                }
-            }
-            CNode c{pn.t, pn.a, pn.p, pn.active == kLeaf ? kLeaf : remap[pn.active],
-                    pn.passive == kLeaf ? kLeaf : remap[pn.passive], pn.is_root, -1};
-            nodes.push_back(c);
-            remap[i] = (int)nodes.size() - 1;
-            if (!pn.is_root) shared[pn.canon] = remap[i];
-            if (pn.is_root) plan_root[pi] = remap[i];
-        }
-    }
-    for (size_t i = 0; i < nodes.size(); ++i) {
-        if (nodes[i].active != kLeaf) nodes[nodes[i].active].last_use = (int)i;
-        if (nodes[i].passive != kLeaf) nodes[nodes[i].passive].last_use = (int)i;
-    }
-    // ---- per-node launch shape: gather width, Z layout, shared memory, block size
-    struct Shape {
-        int wz, grp, nv, wz_pad, zwords, ywords, mwords, threads;
-        size_t smem;
-    };
-    std::vector<Shape> shape(nodes.size());
-    int64_t scratch_ld = 1;
-    for (size_t i = 0; i < nodes.size(); ++i) {
-        const CNode &c = nodes[i];
-        Shape &sh = shape[i];
-        const bool hist = c.p == 1;
-        sh.wz = hist ? 1 : (int)binom(kc - 1, c.p - 1);
-        sh.grp = 32;
-        sh.nv = 1;
-        if (!hist) node_shape(fp64, sh.wz, &sh.grp, &sh.nv);
-        if (sh.nv == 0) {
-            set_error("passive table wider than this build's register tile (column tiling not built)");
-            return SG2V_ERR_UNSUPPORTED;
-        }
-        sh.wz_pad = hist ? 1 : sh.grp * sh.nv * vecn;
-        sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
-        sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
-        sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
-        scratch_ld = std::max<int64_t>(scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
-        sh.threads = kNodeThreads;
-        const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords) * esz;
-        while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
-        sh.smem = (size_t)(sh.threads / 32) * per_warp;
-        if (sh.smem > 227 * 1024) {
-            set_error("per-colour accumulators exceed shared memory (column tiling not built)");
-            return SG2V_ERR_UNSUPPORTED;
-        }
-    }
-
-    Workspace ws{stream, info.pool, {}};
+    Workspace ws{stream, P.info.pool, {}};
     CallTimer timer(stream);
-    // ---- colours on the device, range-checked there
+    // colours on the device
     const int8_t *d_col = colours;
     if (!is_device_pointer(colours)) {
         void *p;
@@ -538,165 +911,37 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         SG2V_CUDA(cudaMemcpyAsync(p, colours, (size_t)nb * n, cudaMemcpyHostToDevice, stream), "colour upload");
         d_col = static_cast<const int8_t *>(p);
     }
-    unsigned *d_status;
-    if ((st = ws.alloc((void **)&d_status, 16))) return st;
-    SG2V_CUDA(cudaMemsetAsync(d_status, 0, 16, stream), "memset");
-    timer.count_extra(1);
-    SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, d_status, stream), "colour check");
-
-    // ---- every row's arcs sorted by neighbour colour, once per colouring
-    int32_t *scol = nullptr;
-    int8_t *sclr = nullptr;
-    float *sw = nullptr;
-    if ((st = ws.alloc((void **)&scol, (size_t)nb * g->nnz * sizeof(int32_t)))) return st;
-    if ((st = ws.alloc((void **)&sclr, (size_t)nb * g->nnz))) return st;
-    if (g->weighted && (st = ws.alloc((void **)&sw, (size_t)nb * g->nnz * sizeof(float)))) return st;
-    timer.begin("colour_sort", (double)nb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))));
-    SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->col_idx, g->weights, n, g->nnz, d_col, nb, kc, scol, sclr,
-                                 sw, info.sms, stream),
-              "colour sort");
-    timer.end();
-
-    // ---- scratch for split rows
-    void *scratch = nullptr;
-    unsigned *counters = nullptr;
-    const size_t scratch_bytes = (size_t)(g->nheavy * nb * scratch_ld) * esz;
-    const size_t counter_bytes = (size_t)(g->nheavy * nb) * sizeof(unsigned);
-    if (g->nheavy) {
-        if ((st = ws.alloc(&scratch, scratch_bytes))) return st;
-        if ((st = ws.alloc((void **)&counters, counter_bytes))) return st;
+    RunBuffers R;
+    auto alloc = [&](size_t bytes, void **p) { return ws.alloc(p, bytes); };
+    if ((st = alloc_run(P, P.auto_wave, alloc, &R))) return st;
+    std::vector<double> ones_host;
+    if (needs_ones(P)) {
+        ones_host.assign((size_t)nb * n, 1.0);
+        if ((st = ws.alloc((void **)&R.ones, ones_host.size() * sizeof(double)))) return st;
+        SG2V_CUDA(cudaMemcpyAsync(R.ones, ones_host.data(), ones_host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  stream),
+                  "fill");
     }
-
-    // ---- the DP, children first
-    std::vector<void *> table(nodes.size(), nullptr);
-    std::vector<int64_t> ld(nodes.size(), 0);
-    for (size_t i = 0; i < nodes.size(); ++i) {
-        const CNode &c = nodes[i];
-        NodeArgs A;
-        std::memset(&A, 0, sizeof A);
-        A.row_ptr = g->row_ptr;
-        A.col_idx = g->col_idx;
-        A.weights = g->weights;
-        A.tasks = g->tasks;
-        A.ntasks = g->ntasks;
-        A.heavy_chunks = g->heavy_chunks;
-        A.n = n;
-        A.nb = nb;
-        A.colours = d_col;
-        A.kc = kc;
-        A.nnz = g->nnz;
-        A.scol = scol;
-        A.sclr = sclr;
-        A.sw = sw;
-        const Shape &sh = shape[i];
-        A.hist = c.p == 1;
-        A.Wz = sh.wz;
-        A.wz_pad = sh.wz_pad;
-        A.zwords = sh.zwords;
-        A.ywords = sh.ywords;
-        A.mwords = sh.mwords;
-        A.p = c.p;
-        if (!A.hist) {
-            A.Mp = table[c.passive];
-            A.ldp = ld[c.passive];
-        }
-        A.a_leaf = c.a == 1;
-        if (!A.a_leaf) {
-            A.Ma = table[c.active];
-            A.lda = ld[c.active];
-            A.Wa = (int)binom(kc - 1, c.a - 1);
-        }
-        A.Ws = (int)binom(kc - 1, c.t - 1);
-        DeviceTables tab;
-        if ((st = device_tables(dev, kc, c.t, c.a, sh.wz_pad, &tab))) return st;
-        A.expand = tab.expand;
-        A.wy = tab.wy;
-        A.splits = tab.splits;
-        A.nsplit = tab.nsplit;
-        A.root = c.is_root;
-        if (c.is_root) {
-            if ((st = ws.alloc(&table[i], (size_t)nb * n * esz))) return st;
-            A.root_out = table[i];
-        } else {
-            ld[i] = (A.Ws + vecn - 1) / vecn * vecn;
-            if ((st = ws.alloc(&table[i], (size_t)n * nb * ld[i] * esz))) return st;
-            A.Ms = table[i];
-            A.ldt = ld[i];
-        }
-        A.scratch = scratch;
-        A.scratch_ld = scratch_ld;
-        A.counters = counters;
-        if (g->nheavy) {
-            SG2V_CUDA(cudaMemsetAsync(scratch, 0, scratch_bytes, stream), "memset");
-            SG2V_CUDA(cudaMemsetAsync(counters, 0, counter_bytes, stream), "memset");
-        }
-        const int bps = node_blocks_per_sm(fp64, A.hist, sh.grp, sh.nv, A.weights != nullptr, sh.threads, sh.smem);
-        if (bps < 1) {
-            set_error("node kernel cannot be resident with its shared memory");
-            return SG2V_ERR_UNSUPPORTED;
-        }
-        {
-            // algorithmic bytes: CSR once, each input table once, output once
-            // (the sorted arc list: neighbour, its colour, weight)
-            const double rows = (double)n * nb;
-            double bytes = 8.0 * (n + 1) + (double)nb * g->nnz * (5.0 + (g->weighted ? 4.0 : 0.0));
-            bytes += rows;  // colours
-            if (!A.hist) bytes += rows * A.Wz * esz;
-            if (!A.a_leaf && !(c.active == c.passive && !A.hist)) bytes += rows * binom(kc - 1, c.a - 1) * esz;
-            bytes += c.is_root ? rows * esz : rows * A.Ws * esz;
-            char name[64];
-            std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p, fp64 ? "fp64" : "fp32");
-            timer.begin(name, bytes);
-        }
-        SG2V_CUDA(launch_node(A, fp64, sh.grp, sh.nv, sh.threads, sh.smem, info.sms * bps, stream),
-                  "node kernel launch");
-        timer.end();
-        if (c.active != kLeaf && nodes[c.active].last_use == (int)i) ws.release(table[c.active]);
-        if (c.passive != kLeaf && nodes[c.passive].last_use == (int)i && c.passive != c.active)
-            ws.release(table[c.passive]);
-    }
-
-    // ---- root reductions
+    // per-call tables from the stream-ordered pool, freed after their last consumer
+    struct PoolTables : TableSource {
+        Workspace &ws;
+        std::vector<void *> &table;
+        PoolTables(Workspace &w, std::vector<void *> &t) : ws(w), table(t) {}
+        sg2v_status get(size_t i, size_t bytes, void **p) override { return ws.alloc(p, bytes); }
+        void done(size_t i) override { ws.release(table[i]); }
+    } src(ws, R.table);
     const bool pv_dev = per_vertex && is_device_pointer(per_vertex);
     double *pv_stage = nullptr;
     if (per_vertex && !pv_dev) {
         if ((st = ws.alloc((void **)&pv_stage, (size_t)num_plans * nb * n * sizeof(double)))) return st;
     }
-    const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (n + 65535) / 65536 * 4));
-    RootSum *d_partials, *d_sums;
-    if ((st = ws.alloc((void **)&d_partials, sizeof(RootSum) * (size_t)chunks * nb * num_plans))) return st;
-    if ((st = ws.alloc((void **)&d_sums, sizeof(RootSum) * (size_t)nb * num_plans))) return st;
-    double *ones = nullptr;
-    for (int pi = 0; pi < num_plans; ++pi) {
-        double *pv = per_vertex ? (pv_dev ? per_vertex : pv_stage) + (size_t)pi * nb * n : nullptr;
-        const void *vals;
-        bool vals_fp64 = fp64;
-        if (plan_root[pi] >= 0) {
-            vals = table[plan_root[pi]];
-        } else {
-            // single-vertex template: every vertex is one embedding
-            if (!ones) {
-                std::vector<double> h((size_t)nb * n, 1.0);
-                if ((st = ws.alloc((void **)&ones, h.size() * sizeof(double)))) return st;
-                SG2V_CUDA(cudaMemcpyAsync(ones, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, stream),
-                          "fill");
-                SG2V_CUDA(cudaStreamSynchronize(stream), "sync");
-            }
-            vals = ones;
-            vals_fp64 = true;
-        }
-        timer.begin("root_reduce", (double)nb * n * ((vals_fp64 ? 8 : 4) + (pv ? 8 : 0)));
-        timer.count_extra(1);
-        SG2V_CUDA(launch_root_reduce(vals, vals_fp64, n, nb, pv, d_partials + (size_t)pi * nb * chunks, chunks,
-                                     d_sums + (size_t)pi * nb, stream),
-                  "root reduction");
-        timer.end();
-    }
+    if ((st = enqueue(P, R, d_col, per_vertex ? (pv_dev ? per_vertex : pv_stage) : nullptr, src, stream, timer)))
+        return st;
     std::vector<RootSum> sums((size_t)nb * num_plans);
     unsigned status[4] = {0, 0, 0, 0};
-    SG2V_CUDA(cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(RootSum), cudaMemcpyDeviceToHost, stream),
+    SG2V_CUDA(cudaMemcpyAsync(sums.data(), R.sums, sums.size() * sizeof(RootSum), cudaMemcpyDeviceToHost, stream),
               "result copy");
-    SG2V_CUDA(cudaMemcpyAsync(status, d_status, sizeof status, cudaMemcpyDeviceToHost, stream), "status copy");
+    SG2V_CUDA(cudaMemcpyAsync(status, R.status, sizeof status, cudaMemcpyDeviceToHost, stream), "status copy");
     if (pv_stage)
         SG2V_CUDA(cudaMemcpyAsync(per_vertex, pv_stage, (size_t)num_plans * nb * n * sizeof(double),
                                   cudaMemcpyDeviceToHost, stream),
@@ -725,14 +970,14 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
             est[(size_t)pi * nb + b] = (double)(t * plans[pi]->scale_ld);
         }
     }
-    auto put = [&](double *dst, const std::vector<double> &src) -> sg2v_status {
+    auto put = [&](double *dst, const std::vector<double> &src_) -> sg2v_status {
         if (!dst) return SG2V_OK;
         if (is_device_pointer(dst)) {
-            SG2V_CUDA(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, stream),
+            SG2V_CUDA(cudaMemcpyAsync(dst, src_.data(), src_.size() * sizeof(double), cudaMemcpyHostToDevice, stream),
                       "result copy");
             SG2V_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
         } else {
-            std::memcpy(dst, src.data(), src.size() * sizeof(double));
+            std::memcpy(dst, src_.data(), src_.size() * sizeof(double));
         }
         return SG2V_OK;
     };
@@ -760,6 +1005,186 @@ sg2v_status sg2v_count(const sg2v_graph *graph, const sg2v_plan *plan, const int
         if (estimate) *estimate = e;
     }
     return st;
+}
+
+sg2v_status sg2v_session_create(const sg2v_graph *graph, const sg2v_plan *const *plans, int32_t num_plans,
+                                int32_t B, sg2v_precision precision, uint32_t flags, sg2v_session **out) {
+    if (!out || (flags & ~(SG2V_SESSION_PER_VERTEX | SG2V_SESSION_NO_GRAPH | SG2V_SESSION_AUTOTUNE))) {
+        set_error("invalid argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    sg2v_session *S = new (std::nothrow) sg2v_session();
+    if (!S) return SG2V_ERR_OUT_OF_MEMORY;
+    S->flags = flags;
+    sg2v_status st = prepare(graph, plans, num_plans, B, precision, &S->P);
+    if (st) {
+        session_free(S);
+        return st;
+    }
+    const Prepared &P = S->P;
+    auto alloc = [&](size_t bytes, void **p) -> sg2v_status {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) return cuda_fail(e, "session allocation");
+        S->owned.push_back(*p);
+        return SG2V_OK;
+    };
+    const size_t nseg = (size_t)num_plans * B;
+    std::vector<double> scale(2 * num_plans);
+    for (int pi = 0; pi < num_plans; ++pi) {
+        scale[pi] = (double)plans[pi]->scale_ld;
+        scale[num_plans + pi] = (double)(plans[pi]->scale_ld - (long double)scale[pi]);
+    }
+    cudaError_t e = cudaSuccess;
+    if ((st = alloc((size_t)B * P.n, (void **)&S->colours)) || (st = alloc(nseg * sizeof(double), (void **)&S->totals)) ||
+        (st = alloc(nseg * sizeof(double), (void **)&S->estimates)) ||
+        (st = alloc(scale.size() * sizeof(double), (void **)&S->scale)) ||
+        ((flags & SG2V_SESSION_PER_VERTEX) && (st = alloc(nseg * P.n * sizeof(double), (void **)&S->pv)))) {
+        session_free(S);
+        return st;
+    }
+    e = cudaMemcpy(S->scale, scale.data(), scale.size() * sizeof(double), cudaMemcpyHostToDevice);
+    // wave-independent run buffers (the wave-dependent ones are replaced below)
+    if (e == cudaSuccess && (st = alloc_run(P, 1, alloc, &S->R))) {
+        session_free(S);
+        return st;
+    }
+    if (e == cudaSuccess && needs_ones(P)) {
+        std::vector<double> ones((size_t)B * P.n, 1.0);
+        if ((st = alloc(ones.size() * sizeof(double), (void **)&S->R.ones))) {
+            session_free(S);
+            return st;
+        }
+        e = cudaMemcpy(S->R.ones, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        session_free(S);
+        return cuda_fail(e, "session set-up");
+    }
+    if ((st = session_alloc_wave(S, P.auto_wave))) {
+        session_free(S);
+        return st;
+    }
+    S->tuned = !(flags & SG2V_SESSION_AUTOTUNE);
+    S->launches_per_run = count_launches(P, S->R.wave);
+    *out = S;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_session_run(sg2v_session *S, const int8_t *colours, double *totals, double *estimates,
+                             double *per_vertex, sg2v_stream stream_) {
+    if (!S || !colours || (per_vertex && !S->pv)) {
+        set_error("invalid argument (per_vertex needs SG2V_SESSION_PER_VERTEX)");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const Prepared &P = S->P;
+    sg2v_status st;
+    SG2V_CUDA(cudaMemcpyAsync(S->colours, colours, (size_t)P.nb * P.n, cudaMemcpyDefault, stream), "colour copy");
+    if (!S->tuned) {
+        // time every candidate wave width on these colourings, keep the fastest
+        std::vector<int> cands;
+        for (int w = 1; w < P.nb; w *= 2) cands.push_back(w);
+        cands.push_back(P.nb);
+        if (std::find(cands.begin(), cands.end(), P.auto_wave) == cands.end()) cands.push_back(P.auto_wave);
+        float best_ms = 0.f;
+        int best = P.auto_wave;
+        cudaEvent_t a, b;
+        SG2V_CUDA(cudaEventCreate(&a), "event");
+        SG2V_CUDA(cudaEventCreate(&b), "event");
+        for (int w : cands) {
+            if ((st = session_alloc_wave(S, w))) {
+                if (st != SG2V_ERR_OUT_OF_MEMORY) return st;
+                continue;  // a wave that does not fit is not a candidate
+            }
+            if ((st = session_enqueue(S, stream, false))) return st;  // warm-up
+            SG2V_CUDA(cudaEventRecord(a, stream), "event");
+            if ((st = session_enqueue(S, stream, false))) return st;
+            SG2V_CUDA(cudaEventRecord(b, stream), "event");
+            SG2V_CUDA(cudaEventSynchronize(b), "event");
+            float ms = 0.f;
+            SG2V_CUDA(cudaEventElapsedTime(&ms, a, b), "event");
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = w;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        if ((st = session_alloc_wave(S, best))) return st;
+        S->tuned = true;
+        S->launches_per_run = count_launches(P, best);
+    }
+    bool profiling;
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mutex);
+        profiling = g_prof_enabled;
+    }
+    if ((S->flags & SG2V_SESSION_NO_GRAPH) || profiling) {
+        // direct launches (kernel timing records need them)
+        if ((st = session_enqueue(S, stream, profiling))) return st;
+    } else {
+        if (!S->exec) {
+            cudaGraph_t graph = nullptr;
+            if (!S->capture) SG2V_CUDA(cudaStreamCreateWithFlags(&S->capture, cudaStreamNonBlocking), "stream");
+            SG2V_CUDA(cudaStreamBeginCapture(S->capture, cudaStreamCaptureModeThreadLocal), "graph capture");
+            st = session_enqueue(S, S->capture, false, true);
+            cudaError_t e = cudaStreamEndCapture(S->capture, &graph);
+            if (st) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+            e = cudaGraphInstantiate(&S->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                S->exec = nullptr;
+                return cuda_fail(e, "graph instantiate");
+            }
+        }
+        SG2V_CUDA(cudaGraphLaunch(S->exec, stream), "graph launch");
+        g_launches.fetch_add(S->launches_per_run);
+    }
+    const size_t nseg = P.plans.size() * (size_t)P.nb;
+    if ((st = copy_out(totals, S->totals, nseg, stream))) return st;
+    if ((st = copy_out(estimates, S->estimates, nseg, stream))) return st;
+    if ((st = copy_out(per_vertex, S->pv, nseg * P.n, stream))) return st;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_session_sync(sg2v_session *S, sg2v_stream stream_) {
+    if (!S) {
+        set_error("null session");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    unsigned status[4] = {0, 0, 0, 0};
+    SG2V_CUDA(cudaMemcpyAsync(status, S->R.status, sizeof status, cudaMemcpyDeviceToHost, stream), "status copy");
+    SG2V_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
+    if (status[0] & 1u) {
+        set_error("a colour is outside [0, num_colours)");
+        return SG2V_ERR_COLOUR_OUT_OF_RANGE;
+    }
+    if (status[0] & 2u) {
+        set_error("a count overflowed the table type");
+        return SG2V_ERR_FP_OVERFLOW;
+    }
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_session_info(const sg2v_session *S, int32_t *wave, int32_t *graph) {
+    if (!S) {
+        set_error("null session");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (wave) *wave = S->R.wave;
+    if (graph) *graph = S->exec != nullptr;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_session_destroy(sg2v_session *S) {
+    session_free(S);
+    return SG2V_OK;
 }
 
 const char *sg2v_status_string(sg2v_status s) {

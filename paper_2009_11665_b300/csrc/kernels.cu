@@ -464,7 +464,9 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
 
 __device__ __forceinline__ void rs_combine(RootSum &x, const RootSum &y) {
     const unsigned long long lo = x.lo + y.lo;
-    x.hi = x.hi + y.hi + (lo < x.lo ? 1ull : 0ull);
+    const unsigned long long hi = x.hi + y.hi + (lo < x.lo ? 1ull : 0ull);
+    if (hi < x.hi || (hi == x.hi && y.hi + (lo < x.lo ? 1ull : 0ull) != 0ull)) x.flags |= kFlagNotIntegral;  // 2^128 wrap
+    x.hi = hi;
     x.lo = lo;
     double s, e;
     two_sum(x.s, y.s, s, e);
@@ -604,6 +606,58 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
     }
 }
 
+// 128-bit unsigned integer to the nearest double (ties to even): the top 64
+// significant bits keep a sticky bit for everything below them, so the one
+// rounding of the 64-bit conversion is the correct rounding of the whole.
+__device__ __forceinline__ double u128_to_double(unsigned long long hi, unsigned long long lo) {
+    if (hi == 0) return __ull2double_rn(lo);
+    const int shift = 64 - __clzll((long long)hi);  // 1..64
+    const unsigned long long top = shift == 64 ? hi : (hi << (64 - shift)) | (lo >> shift);
+    const unsigned long long sticky = (shift == 64 ? lo : (lo << (64 - shift))) != 0ull ? 1ull : 0ull;
+    return ldexp(__ull2double_rn(top | sticky), shift);
+}
+
+__global__ void finalize_kernel(const RootSum *sums, int nseg, int nb, const double *scale_hi,
+                                const double *scale_lo, double *totals, double *estimates, unsigned *status) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const RootSum r = sums[s];
+    double xh, xl;
+    if (r.flags == 0) {
+        xh = u128_to_double(r.hi, r.lo);
+        // the rounding error of xh, exactly as a 128-bit difference, then to double
+        unsigned long long h2 = 0, l2 = 0;
+        if (xh < 0x1p64) {
+            l2 = __double2ull_rz(xh);
+        } else {
+            const double hh = floor(xh * 0x1p-64);
+            h2 = __double2ull_rz(hh);
+            l2 = __double2ull_rz(xh - hh * 0x1p64);
+        }
+        const bool neg = (h2 > r.hi) || (h2 == r.hi && l2 > r.lo);
+        unsigned long long dh, dl;
+        if (!neg) {
+            dl = r.lo - l2;
+            dh = r.hi - h2 - (r.lo < l2 ? 1ull : 0ull);
+        } else {
+            dl = l2 - r.lo;
+            dh = h2 - r.hi - (l2 < r.lo ? 1ull : 0ull);
+        }
+        xl = u128_to_double(dh, dl);
+        if (neg) xl = -xl;
+    } else {
+        xh = r.s + r.c;
+        xl = (r.s - xh) + r.c;
+        if (r.flags & kFlagNonFinite) atomicOr(status, 2u);
+    }
+    const int pi = s / nb;
+    const double sh = scale_hi[pi], sl = scale_lo[pi];
+    const double p = xh * sh;
+    const double e = fma(xh, sh, -p);
+    totals[s] = xh;
+    estimates[s] = p + (e + fma(xh, sl, xl * sh));
+}
+
 __global__ void check_colours_kernel(const int8_t *colours, int64_t count, int kc, unsigned *status) {
     unsigned bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -636,10 +690,16 @@ void node_shape(bool fp64, int wz, int *g, int *nv) {
 int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
     void *k = select_kernel(fp64, hist, g, nv, weighted);
     if (!k) return 0;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    if (smem > 48 * 1024) {
+        // one limit per kernel variant, shared by every node that uses it: the device maximum
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            (size_t)optin < smem ||
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
     }
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem) != cudaSuccess) {
@@ -689,6 +749,13 @@ cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t 
     if (blocks < 1) blocks = 1;
     colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, col_idx, weights, n, nnz, colours, nb, kc,
                                                              scol, sclr, sw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const RootSum *sums, int nseg, int nb, const double *scale_hi, const double *scale_lo,
+                            double *totals, double *estimates, unsigned *status, cudaStream_t stream) {
+    finalize_kernel<<<(nseg + 127) / 128, 128, 0, stream>>>(sums, nseg, nb, scale_hi, scale_lo, totals, estimates,
+                                                            status);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,13 @@ cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t 
                                int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc, int32_t *scol,
                                int8_t *sclr, float *sw, int sms, cudaStream_t stream);
 
+// Totals and estimates of nseg segments from their root sums: the exact
+// 128-bit sum rounded once to double when every value was an integer, else
+// the compensated sum; estimate = total * (scale_hi + scale_lo)[segment / nb]
+// in double-double.  Non-finite sums set bit 1 of *status.
+cudaError_t launch_finalize(const RootSum *sums, int nseg, int nb, const double *scale_hi, const double *scale_lo,
+                            double *totals, double *estimates, unsigned *status, cudaStream_t stream);
+
 // Sets *status |= 1 when any of count colours is outside [0, kc).
 cudaError_t launch_check_colours(const int8_t *colours, int64_t count, int kc, unsigned *status,
                                  cudaStream_t stream);

@@ -47,7 +47,9 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
 
 __device__ __forceinline__ void combine(Partial &x, const Partial &y) {
     const unsigned long long lo = x.lo + y.lo;
-    x.hi = x.hi + y.hi + (lo < x.lo ? 1ull : 0ull);
+    const unsigned long long hi = x.hi + y.hi + (lo < x.lo ? 1ull : 0ull);
+    if (hi < x.hi || (hi == x.hi && y.hi + (lo < x.lo ? 1ull : 0ull) != 0ull)) x.flags |= 1u;  // sum reached 2^128
+    x.hi = hi;
     x.lo = lo;
     double s, e;
     two_sum(x.s, y.s, s, e);

@@ -151,10 +151,15 @@ def test_weighted_graph(sg):
     _check_fp32(r32[0], r32[1], ref)
 
 
-def test_batched_templates_and_colourings(sg):
+@pytest.mark.parametrize("wave", ["", "1", "2"])
+def test_batched_templates_and_colourings(sg, wave, monkeypatch):
     """Several colourings x several templates in one call equal one oracle
-    run per (template, colouring)."""
+    run per (template, colouring), whatever the number of colourings that
+    share a table row (the wave width; read at each call)."""
     import torch
+
+    if wave:
+        monkeypatch.setenv("SG2V_WAVE", wave)
 
     g = si.rmat(12, 30000, seed=7)
     B = 5

@@ -1,0 +1,135 @@
+"""Sessions: preallocated buffers, CUDA-graph replay, device-side totals and
+estimates, wave autotuning (the batched form of the counting DP).
+
+Results must equal the exact oracle under the same bars as the direct
+calls (FP64 bit-exact below 2^53, FP32 1e-4 relative, estimates within
+2 ulp of total / (P alpha))."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import sg2v_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as s
+
+    return s
+
+
+def _ulp_close(a: float, exact: Fraction, ulps: int = 2) -> bool:
+    b = float(exact)
+    return abs(a - b) <= ulps * np.spacing(abs(b))
+
+
+def _check(prec, got_pv, got_total, ref):
+    want = np.array([float(x) for x in ref.per_vertex_values()])
+    nz = want != 0
+    assert np.all(got_pv[~nz] == 0)
+    tv = float(ref.total_value())
+    if prec == "fp64" and ref.max_bits <= 53:
+        assert np.array_equal(got_pv, want)
+        assert got_total == tv
+    else:
+        tol = 1e-12 if prec == "fp64" else 1e-4
+        if nz.any():
+            assert (np.abs(got_pv[nz] - want[nz]) / want[nz]).max() <= tol
+        assert abs(got_total - tv) <= tol * abs(tv)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("replay", [True, False])
+def test_session_runs_match_oracle(sg, prec, replay):
+    """Two runs with different colourings (the second replays the captured
+    graph) against one oracle count per (template, colouring)."""
+    import torch
+
+    g = si.rmat(12, 30000, seed=7)
+    B = 3
+    temps = [si.PATH7, si.STAR7, si.TREE7]
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plans = [sg.Plan(t.parent) for t in temps]
+    ses = sg.Session(graph, plans, B, prec, per_vertex=True, graph_replay=replay)
+    for seed in (3, 4):
+        cols = si.colourings(g.n, 7, B, seed=seed)
+        tot = torch.empty((3, B), dtype=torch.float64, device="cuda")
+        est = torch.empty((3, B), dtype=torch.float64, device="cuda")
+        pv = torch.empty((3, B, g.n), dtype=torch.float64, device="cuda")
+        ses.run(torch.from_numpy(cols).cuda(), tot, est, pv)
+        ses.sync()
+        tot, est, pv = tot.cpu().numpy(), est.cpu().numpy(), pv.cpu().numpy()
+        for i, t in enumerate(temps):
+            for b in range(B):
+                ref = oracle.count(g.row_ptr, g.col_idx, t.parent, 0, cols[b])
+                _check(prec, pv[i, b], tot[i, b], ref)
+                if prec == "fp64":
+                    assert _ulp_close(est[i, b], oracle.estimate(ref.total, 7, plans[i].alpha))
+    wave, captured = ses.info()
+    assert captured == replay
+    assert 1 <= wave <= B
+
+
+def test_session_autotune_and_host_outputs(sg):
+    g = si.erdos_renyi(3000, 15000, seed=4)
+    B = 5
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(si.TREE8.parent)
+    ses = sg.Session(graph, [plan], B, "fp32", autotune=True)
+    cols = si.colourings(g.n, 8, B, seed=2)
+    tot = np.zeros((1, B))
+    est = np.zeros((1, B))
+    ses.run(cols, tot, est)  # host colourings, host outputs
+    ses.sync()
+    wave, captured = ses.info()
+    assert 1 <= wave <= B and captured
+    for b in range(B):
+        ref = oracle.count(g.row_ptr, g.col_idx, si.TREE8.parent, 0, cols[b], per_vertex=False)
+        assert abs(tot[0, b] - ref.total) <= 1e-4 * ref.total
+        assert est[0, b] == pytest.approx(float(oracle.estimate(ref.total, 8, plan.alpha)), rel=1e-4)
+
+
+def test_session_reports_bad_colours(sg):
+    g = si.erdos_renyi(400, 1600, seed=1)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    ses = sg.Session(graph, [sg.Plan((-1, 0, 1, 2))], 2, "fp64")
+    cols = si.colourings(g.n, 4, 2, seed=1)
+    ses.run(cols)
+    ses.sync()
+    cols[1, 7] = 9
+    ses.run(cols)
+    with pytest.raises(sg.Sg2vError) as e:
+        ses.sync()
+    assert e.value.status == sg.SG2V_ERR_COLOUR_OUT_OF_RANGE
+
+
+def test_session_single_vertex_and_weighted(sg):
+    """Single-vertex templates (every vertex counts once) and a weighted
+    graph through the session path."""
+    import torch
+
+    g = si.chung_lu(3000, 20000, 2.3, seed=1)
+    w = si.arc_weights(g, si.edge_weights(g, seed=1))
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plans = [sg.Plan((-1,), 0, 8), sg.Plan(si.TREE8.parent)]
+    ses = sg.Session(graph, plans, 2, "fp64", per_vertex=True)
+    cols = si.colourings(g.n, 8, 2, seed=5)
+    tot = torch.empty((2, 2), dtype=torch.float64, device="cuda")
+    pv = torch.empty((2, 2, g.n), dtype=torch.float64, device="cuda")
+    ses.run(torch.from_numpy(cols).cuda(), tot, None, pv)
+    ses.sync()
+    assert torch.all(pv[0] == 1.0) and torch.all(tot[0] == g.n)
+    for b in range(2):
+        ref = oracle.count(g.row_ptr, g.col_idx, si.TREE8.parent, 0, cols[b], weights=w)
+        _check("fp64", pv[1, b].cpu().numpy(), tot[1, b].item(), ref)

@@ -187,6 +187,43 @@ sg2v_status sg2v_count_batched(const sg2v_graph *graph, const sg2v_plan *const *
                                const int8_t *colours, int32_t B, sg2v_precision precision, double *per_vertex,
                                double *totals, double *estimates, sg2v_stream stream);
 
+/* --------------------------------------------------------------- backward */
+
+/*
+ * sg2v_count_backward -- gradient of the weighted count with respect to the
+ * edge weights (the differentiable form; the paper counts unweighted
+ * graphs, Sec. 2.2.1, and Alg. 4's A_G.val carries the weights here).  For a
+ * colouring, F(w) = sum_v g_v * per_vertex[v](w) where each colourful map
+ * contributes the product of the weights of its k - 1 edges, so F is
+ * multilinear in the weights.  The library runs the forward DP keeping every
+ * table and every node's Y', then, parents before children, the reverse
+ * eMA, the transposed SpMM (A symmetric) and a per-arc SDDMM
+ * dF/dw_vu = <Ybar(v, .), M_p(u, .)>, and sums both arcs of each edge.
+ *
+ *   colours          [n] int8, host or device
+ *   grad_per_vertex  [n] double (g_v), host or device, or NULL for g = 1
+ *                    (the gradient of the total)
+ *   grad_weights     [nnz] double, host or device: for every arc, dF/dw_e of
+ *                    its undirected edge e (both arcs of an edge hold the
+ *                    same value); unweighted graphs give the derivative at
+ *                    w = 1 (the colourful maps through each edge)
+ *   total            host double or NULL: the forward total sum_v per_vertex[v]
+ *   flags            0
+ * Memory: every node's table, Y' and gradient table of the colouring stay
+ * allocated during the call.  Errors as sg2v_count.
+ */
+sg2v_status sg2v_count_backward(const sg2v_graph *graph, const sg2v_plan *plan, const int8_t *colours,
+                                sg2v_precision precision, const double *grad_per_vertex, double *grad_weights,
+                                double *total, uint32_t flags, sg2v_stream stream);
+
+/*
+ * sg2v_graph_set_weights -- replaces the weights of a graph created with
+ * weights ([nnz] float32, host or device, stream-ordered copy).  No
+ * validation: weights[e] must equal the reverse arc's weight and be finite
+ * and >= 0.  Used by the autograd wrapper between iterations.
+ */
+sg2v_status sg2v_graph_set_weights(sg2v_graph *graph, const float *weights, sg2v_stream stream);
+
 /* ---------------------------------------------------------------- session */
 
 /*

@@ -65,6 +65,8 @@ _SIGNATURES = {
     "sg2v_session_sync": [_p, _p],
     "sg2v_session_info": [_p, _p, _p],
     "sg2v_session_destroy": [_p],
+    "sg2v_count_backward": [_p, _p, _p, ctypes.c_int, _p, _p, _p, _u32, _p],
+    "sg2v_graph_set_weights": [_p, _p, _p],
 }
 for _name, _args in _SIGNATURES.items():
     _f = getattr(_lib, _name)
@@ -221,6 +223,20 @@ def sg2v_sum_counts_noalloc(values, n: int, nseg: int, totals, stream=None) -> N
     allocating (see include/sg2v.h); stream-ordered, no synchronisation."""
     _check(_lib.sg2v_sum_counts_noalloc(_ptr(values), int(n), int(nseg), _ptr(totals), _stream(stream)),
            "sg2v_sum_counts_noalloc")
+
+
+def sg2v_count_backward(graph, plan, colours, precision: int, grad_weights, grad_per_vertex=None,
+                        stream=None) -> float:
+    """Fills grad_weights ([nnz] float64) with dF/dw_e per arc; returns the
+    forward total."""
+    t = ctypes.c_double()
+    _check(_lib.sg2v_count_backward(graph, plan, _ptr(colours), int(precision), _ptr(grad_per_vertex),
+                                    _ptr(grad_weights), ctypes.byref(t), 0, _stream(stream)), "sg2v_count_backward")
+    return t.value
+
+
+def sg2v_graph_set_weights(graph, weights, stream=None) -> None:
+    _check(_lib.sg2v_graph_set_weights(graph, _ptr(weights), _stream(stream)), "sg2v_graph_set_weights")
 
 
 def sg2v_session_create(graph, plans: Sequence[int], B: int, precision: int = SG2V_FP32, flags: int = 0) -> int:
@@ -388,3 +404,31 @@ def count_batched(graph: Graph, plans: Sequence[Plan], colours, precision: str =
     sg2v_count_batched(graph.handle, [p.handle for p in plans], colours, B, PRECISIONS[precision], pv, tot, est,
                        stream)
     return pv, tot, est
+
+
+def weighted_count(weights, graph: Graph, plan: Plan, colours, precision: str = "fp32"):
+    """Differentiable per-vertex colourful counts of a weighted graph: each
+    colourful map contributes the product of its edge weights.  `weights` is
+    a float32 CUDA tensor [nnz] (symmetric: both arcs of an edge equal); the
+    graph must have been created with weights.  Returns per_vertex [n]
+    float64; gradients flow back to `weights` through sg2v_count_backward."""
+    import torch
+
+    class _WeightedCount(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w):
+            sg2v_graph_set_weights(graph.handle, w.detach().contiguous())
+            pv, _, _ = count(graph, plan, colours, precision)
+            ctx.save_for_backward(w)
+            return pv
+
+        @staticmethod
+        def backward(ctx, grad_pv):
+            (w,) = ctx.saved_tensors
+            sg2v_graph_set_weights(graph.handle, w.detach().contiguous())
+            g = torch.empty(w.shape[0], dtype=torch.float64, device=w.device)
+            sg2v_count_backward(graph.handle, plan.handle, colours, PRECISIONS[precision], g,
+                                grad_pv.detach().to(torch.float64).contiguous())
+            return g.to(w.dtype)
+
+    return _WeightedCount.apply(weights)

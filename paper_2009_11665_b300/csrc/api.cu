@@ -243,6 +243,7 @@ struct sg2v_graph {
     int32_t *heavy_chunks = nullptr;
     int64_t nheavy = 0;
     int chunk = 0;
+    int32_t *rev = nullptr;  // reverse arc of every arc, built on the first backward call
 };
 
 namespace sg2v {
@@ -255,6 +256,7 @@ void free_graph(sg2v_graph *g) {
     cudaFree(g->weights);
     cudaFree(g->tasks);
     cudaFree(g->heavy_chunks);
+    cudaFree(g->rev);
     delete g;
 }
 
@@ -551,6 +553,58 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     return SG2V_OK;
 }
 
+// Kernel arguments of node i for colourings [b0, b0 + wb) (output table set by the caller).
+NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int wb, const int8_t *wcol) {
+    const sg2v_graph *g = P.g;
+    const CNode &c = P.nodes[i];
+    const Shape &sh = P.shape[i];
+    const int kc = P.kc;
+    NodeArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.row_ptr = g->row_ptr;
+    A.col_idx = g->col_idx;
+    A.weights = g->weights;
+    A.tasks = g->tasks;
+    A.ntasks = g->ntasks;
+    A.heavy_chunks = g->heavy_chunks;
+    A.n = P.n;
+    A.nb = wb;
+    A.colours = wcol;
+    A.kc = kc;
+    A.nnz = g->nnz;
+    A.scol = R.scol;
+    A.sclr = R.sclr;
+    A.sw = R.sw;
+    A.hist = c.p == 1;
+    A.Wz = sh.wz;
+    A.wz_pad = sh.wz_pad;
+    A.zwords = sh.zwords;
+    A.ywords = sh.ywords;
+    A.mwords = sh.mwords;
+    A.p = c.p;
+    if (!A.hist) {
+        A.Mp = R.table[c.passive];
+        A.ldp = R.ld[c.passive];
+    }
+    A.a_leaf = c.a == 1;
+    if (!A.a_leaf) {
+        A.Ma = R.table[c.active];
+        A.lda = R.ld[c.active];
+        A.Wa = (int)binom(kc - 1, c.a - 1);
+    }
+    A.Ws = (int)binom(kc - 1, c.t - 1);
+    A.expand = P.tabs[i].expand;
+    A.wy = P.tabs[i].wy;
+    A.splits = P.tabs[i].splits;
+    A.nsplit = P.tabs[i].nsplit;
+    A.root = c.is_root;
+    if (c.is_root) A.root_out = static_cast<char *>(R.rootbuf[P.root_plan[i]]) + (size_t)b0 * P.n * P.esz;
+    A.scratch = R.scratch;
+    A.scratch_ld = P.scratch_ld;
+    A.counters = R.counters;
+    return A;
+}
+
 // Enqueues the whole DP for colourings d_col ([nb][n], device) on `stream`:
 // colour check, per wave the colour sort and one launch per node, then the
 // root reductions into R.sums (and per-vertex doubles when pv != null).
@@ -577,48 +631,8 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
         for (size_t i = 0; i < P.nodes.size(); ++i) {
             const CNode &c = P.nodes[i];
             const Shape &sh = P.shape[i];
-            NodeArgs A;
-            std::memset(&A, 0, sizeof A);
-            A.row_ptr = g->row_ptr;
-            A.col_idx = g->col_idx;
-            A.weights = g->weights;
-            A.tasks = g->tasks;
-            A.ntasks = g->ntasks;
-            A.heavy_chunks = g->heavy_chunks;
-            A.n = n;
-            A.nb = wb;
-            A.colours = wcol;
-            A.kc = kc;
-            A.nnz = g->nnz;
-            A.scol = R.scol;
-            A.sclr = R.sclr;
-            A.sw = R.sw;
-            A.hist = c.p == 1;
-            A.Wz = sh.wz;
-            A.wz_pad = sh.wz_pad;
-            A.zwords = sh.zwords;
-            A.ywords = sh.ywords;
-            A.mwords = sh.mwords;
-            A.p = c.p;
-            if (!A.hist) {
-                A.Mp = R.table[c.passive];
-                A.ldp = R.ld[c.passive];
-            }
-            A.a_leaf = c.a == 1;
-            if (!A.a_leaf) {
-                A.Ma = R.table[c.active];
-                A.lda = R.ld[c.active];
-                A.Wa = (int)binom(kc - 1, c.a - 1);
-            }
-            A.Ws = (int)binom(kc - 1, c.t - 1);
-            A.expand = P.tabs[i].expand;
-            A.wy = P.tabs[i].wy;
-            A.splits = P.tabs[i].splits;
-            A.nsplit = P.tabs[i].nsplit;
-            A.root = c.is_root;
-            if (c.is_root) {
-                A.root_out = static_cast<char *>(R.rootbuf[P.root_plan[i]]) + (size_t)b0 * n * esz;
-            } else {
+            NodeArgs A = node_args(P, R, i, b0, wb, wcol);
+            if (!c.is_root) {
                 R.ld[i] = table_ld(P, c);
                 if ((st = src.get(i, (size_t)n * wb * R.ld[i] * esz, &R.table[i]))) return st;
                 A.Ms = R.table[i];
@@ -1184,6 +1198,305 @@ sg2v_status sg2v_session_info(const sg2v_session *S, int32_t *wave, int32_t *gra
 
 sg2v_status sg2v_session_destroy(sg2v_session *S) {
     session_free(S);
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_graph_set_weights(sg2v_graph *g, const float *weights, sg2v_stream stream_) {
+    if (!g || !weights || !g->weighted) {
+        set_error("graph must have been created with weights");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    SG2V_CUDA(cudaMemcpyAsync(g->weights, weights, (size_t)g->nnz * sizeof(float), cudaMemcpyDefault, stream),
+              "weight copy");
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, const int8_t *colours,
+                                sg2v_precision precision, const double *grad_per_vertex, double *grad_weights,
+                                double *total, uint32_t flags, sg2v_stream stream_) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    if (!g || !plan || !colours || !grad_weights || flags != 0) {
+        set_error("invalid argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    const sg2v_plan *plans[1] = {plan};
+    Prepared P;
+    sg2v_status st = prepare(g, plans, 1, 1, precision, &P);
+    if (st) return st;
+    const int64_t n = P.n, nnz = g->nnz;
+    const int kc = P.kc;
+    const size_t esz = P.esz;
+    const int vecn = P.vecn;
+    sg2v_graph *gm = const_cast<sg2v_graph *>(g);
+    if (!gm->rev) {
+        // reverse arcs: arc (u, v) <-> arc (v, u); from host copies of the CSR
+        std::vector<int64_t> rp((size_t)n + 1);
+        std::vector<int32_t> ci((size_t)nnz), rv((size_t)nnz);
+        SG2V_CUDA(cudaMemcpy(rp.data(), g->row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost), "copy");
+        SG2V_CUDA(cudaMemcpy(ci.data(), g->col_idx, ci.size() * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+        bool ok = true;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(&& : ok)
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t v = ci[e];
+                const int32_t *b0 = ci.data() + rp[v], *b1 = ci.data() + rp[v + 1];
+                const int32_t *hit = std::lower_bound(b0, b1, (int32_t)u);
+                if (hit == b1 || *hit != u) ok = false;
+                else rv[e] = (int32_t)(hit - ci.data());
+            }
+        if (!ok) {
+            set_error("CSR is not symmetric");
+            return SG2V_ERR_GRAPH_NOT_SIMPLE;
+        }
+        SG2V_CUDA(cudaMalloc(&gm->rev, std::max<size_t>(rv.size() * sizeof(int32_t), 16)), "allocation");
+        SG2V_CUDA(cudaMemcpy(gm->rev, rv.data(), rv.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "copy");
+    }
+    Workspace ws{stream, P.info.pool, {}};
+    CallTimer timer(stream);
+    auto alloc = [&](size_t bytes, void **p) { return ws.alloc(p, bytes); };
+    const int8_t *d_col = colours;
+    if (!is_device_pointer(colours)) {
+        void *p;
+        if ((st = ws.alloc(&p, (size_t)n))) return st;
+        SG2V_CUDA(cudaMemcpyAsync(p, colours, (size_t)n, cudaMemcpyHostToDevice, stream), "colour upload");
+        d_col = static_cast<const int8_t *>(p);
+    }
+    double *gradw;
+    if ((st = alloc((size_t)nnz * sizeof(double), (void **)&gradw))) return st;
+    if (P.nodes.empty()) {
+        // single-vertex template: the count does not depend on the weights
+        SG2V_CUDA(cudaMemsetAsync(gradw, 0, (size_t)nnz * sizeof(double), stream), "memset");
+        SG2V_CUDA(cudaMemcpyAsync(grad_weights, gradw, (size_t)nnz * sizeof(double), cudaMemcpyDefault, stream),
+                  "copy");
+        SG2V_CUDA(cudaStreamSynchronize(stream), "sync");
+        if (total) *total = (double)n;
+        return SG2V_OK;
+    }
+    // backward launch shapes of the transposed SpMM (gathers gradient rows of width C(kc-1, p))
+    const size_t nn = P.nodes.size();
+    std::vector<Shape> bshape(nn);
+    std::vector<BackwardTables> btab(nn);
+    int64_t scratch_ld = P.scratch_ld;
+    for (size_t i = 0; i < nn; ++i) {
+        const CNode &c = P.nodes[i];
+        Shape &sh = bshape[i];
+        sh.wz = (int)binom(kc - 1, c.p);
+        node_shape(P.fp64, sh.wz, &sh.grp, &sh.nv);
+        if (sh.nv == 0) {
+            set_error("gradient rows wider than this build's register tile");
+            return SG2V_ERR_UNSUPPORTED;
+        }
+        sh.wz_pad = sh.grp * sh.nv * vecn;
+        sh.zwords = (32 / sh.grp) * kc * sh.wz_pad;
+        sh.ywords = ((int)binom(kc - 1, c.p - 1) + 3) / 4 * 4;
+        sh.mwords = 0;
+        sh.threads = kNodeThreads;
+        const size_t per_warp = (size_t)(sh.zwords + sh.ywords) * esz;
+        while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
+        sh.smem = (size_t)(sh.threads / 32) * per_warp;
+        if (c.p >= 2) {
+            sh.blocks_per_sm = node_blocks_per_sm(P.fp64, false, sh.grp, sh.nv, g->weights != nullptr, sh.threads,
+                                                  sh.smem);
+            if (sh.blocks_per_sm < 1 || sh.smem > 227 * 1024) {
+                set_error("transposed SpMM does not fit shared memory");
+                return SG2V_ERR_UNSUPPORTED;
+            }
+            scratch_ld = std::max<int64_t>(scratch_ld, (int64_t)kc * sh.wz_pad);
+        }
+        build_backward_tables(kc, c.t, c.a, sh.wz_pad, &btab[i]);
+    }
+    // device copies of the backward tables (per call; they are small)
+    std::vector<const uint32_t *> d_ybar(nn), d_mabar(nn), d_arc(nn);
+    std::vector<const uint16_t *> d_bexp(nn);
+    auto upload = [&](const void *h, size_t bytes, const void **d) -> sg2v_status {
+        void *p = nullptr;
+        sg2v_status s2 = ws.alloc(&p, bytes);
+        if (s2) return s2;
+        if (bytes) SG2V_CUDA(cudaMemcpyAsync(p, h, bytes, cudaMemcpyHostToDevice, stream), "table upload");
+        *d = p;
+        return SG2V_OK;
+    };
+    for (size_t i = 0; i < nn; ++i) {
+        if ((st = upload(btab[i].ybar.data(), btab[i].ybar.size() * 4, (const void **)&d_ybar[i])) ||
+            (st = upload(btab[i].mabar.data(), btab[i].mabar.size() * 4, (const void **)&d_mabar[i])) ||
+            (st = upload(btab[i].arc.data(), btab[i].arc.size() * 4, (const void **)&d_arc[i])) ||
+            (st = upload(btab[i].expand.data(), btab[i].expand.size() * 2, (const void **)&d_bexp[i])))
+            return st;
+    }
+    // run buffers (one colouring), with split-row scratch wide enough for both directions
+    Prepared Pw = P;
+    Pw.scratch_ld = scratch_ld;
+    RunBuffers R;
+    if ((st = alloc_run(Pw, 1, alloc, &R))) return st;
+    SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
+    SG2V_CUDA(launch_check_colours(d_col, n, kc, R.status, stream), "colour check");
+    SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->col_idx, g->weights, n, nnz, d_col, 1, kc, R.scol, R.sclr,
+                                 R.sw, P.info.sms, stream),
+              "colour sort");
+    // forward, keeping every table and every node's Y'
+    std::vector<void *> yt(nn, nullptr), gt(nn, nullptr);
+    std::vector<int64_t> ldy(nn, 0);
+    for (size_t i = 0; i < nn; ++i) {
+        const CNode &c = P.nodes[i];
+        const Shape &sh = P.shape[i];
+        NodeArgs A = node_args(Pw, R, i, 0, 1, d_col);
+        if (!c.is_root) {
+            R.ld[i] = table_ld(P, c);
+            if ((st = alloc((size_t)n * R.ld[i] * esz, &R.table[i]))) return st;
+            if ((st = alloc((size_t)n * R.ld[i] * esz, &gt[i]))) return st;
+            SG2V_CUDA(cudaMemsetAsync(gt[i], 0, (size_t)n * R.ld[i] * esz, stream), "memset");
+            A.Ms = R.table[i];
+            A.ldt = R.ld[i];
+        }
+        ldy[i] = (binom(kc - 1, c.p) + vecn - 1) / vecn * vecn;
+        if ((st = alloc((size_t)n * ldy[i] * esz, &yt[i]))) return st;
+        A.Yout = yt[i];
+        A.ldy = ldy[i];
+        if (g->nheavy) {
+            SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
+            SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
+        }
+        timer.begin("backward: forward node", 0.0);
+        SG2V_CUDA(launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm, stream),
+                  "node kernel launch");
+        timer.end();
+    }
+    if (total) {
+        timer.count_extra(2);
+        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.fp64, n, 1, nullptr, R.partials, R.chunks, R.sums, stream),
+                  "root reduction");
+    }
+    // seed: gradient of the per-vertex counts
+    double *seed;
+    if ((st = alloc((size_t)n * sizeof(double), (void **)&seed))) return st;
+    if (grad_per_vertex) {
+        SG2V_CUDA(cudaMemcpyAsync(seed, grad_per_vertex, (size_t)n * sizeof(double), cudaMemcpyDefault, stream),
+                  "seed copy");
+    } else {
+        std::vector<double> ones((size_t)n, 1.0);
+        SG2V_CUDA(cudaMemcpyAsync(seed, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, stream),
+                  "seed copy");
+        SG2V_CUDA(cudaStreamSynchronize(stream), "sync");
+    }
+    double *part;
+    if ((st = alloc((size_t)nnz * sizeof(double), (void **)&part))) return st;
+    SG2V_CUDA(cudaMemsetAsync(part, 0, (size_t)nnz * sizeof(double), stream), "memset");
+    // backward, parents before children
+    for (size_t ii = nn; ii-- > 0;) {
+        const CNode &c = P.nodes[ii];
+        const int wy = (int)binom(kc - 1, c.p), wa = (int)binom(kc - 1, c.a - 1), ws_ = (int)binom(kc - 1, c.t - 1);
+        void *ybar;
+        const int64_t ldyb = ldy[ii];
+        if ((st = alloc((size_t)n * ldyb * esz, &ybar))) return st;
+        BwdEmaArgs E;
+        std::memset(&E, 0, sizeof E);
+        E.n = n;
+        E.colours = d_col;
+        E.kc = kc;
+        E.a = c.a;
+        E.ws = ws_;
+        E.wa = c.a >= 2 ? wa : 0;
+        E.wy = wy;
+        E.G = c.is_root ? nullptr : gt[ii];
+        E.ldg = R.ld[ii];
+        E.seed = c.is_root ? seed : nullptr;
+        if (c.a >= 2) {
+            E.Ma = R.table[c.active];
+            E.lda = R.ld[c.active];
+            E.Gabar = gt[c.active];
+            E.ldga = R.ld[c.active];
+        }
+        E.Y = yt[ii];
+        E.ldy = ldy[ii];
+        E.Ybar = ybar;
+        E.ldyb = ldyb;
+        E.ybar = d_ybar[ii];
+        E.nybar = btab[ii].nybar;
+        E.mabar = d_mabar[ii];
+        E.nmabar = btab[ii].nmabar;
+        timer.begin("backward: eMA", 0.0);
+        SG2V_CUDA(launch_bwd_ema(E, P.fp64, P.info.sms, stream), "backward eMA");
+        timer.end();
+        if (c.p >= 2) {
+            // gradient of the passive table: the transposed SpMM, colour-keyed like the forward
+            const Shape &sh = bshape[ii];
+            NodeArgs A = node_args(Pw, R, ii, 0, 1, d_col);
+            A.hist = 0;
+            A.Mp = ybar;
+            A.ldp = ldyb;
+            A.Wz = sh.wz;
+            A.wz_pad = sh.wz_pad;
+            A.zwords = sh.zwords;
+            A.ywords = sh.ywords;
+            A.mwords = 0;
+            A.p = btab[ii].nterms;
+            A.wy = btab[ii].wout;
+            A.expand = d_bexp[ii];
+            A.a_leaf = 1;
+            A.Ma = nullptr;
+            A.splits = nullptr;
+            A.nsplit = 0;
+            A.root = 0;
+            A.root_out = nullptr;
+            A.Ws = btab[ii].wout;
+            A.Ms = gt[c.passive];
+            A.ldt = R.ld[c.passive];
+            A.accumulate = 1;
+            A.scratch_ld = scratch_ld;
+            if (g->nheavy) {
+                SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
+                SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
+            }
+            timer.begin("backward: transposed SpMM", 0.0);
+            SG2V_CUDA(launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
+                                  stream),
+                      "transposed SpMM launch");
+            timer.end();
+        }
+        SddmmArgs D;
+        std::memset(&D, 0, sizeof D);
+        D.n = n;
+        D.row_ptr = g->row_ptr;
+        D.col_idx = g->col_idx;
+        D.colours = d_col;
+        D.kc = kc;
+        D.hist = c.p == 1;
+        D.Ybar = ybar;
+        D.ldyb = ldyb;
+        if (c.p >= 2) {
+            D.Mp = R.table[c.passive];
+            D.ldp = R.ld[c.passive];
+        }
+        D.wmp = (int)binom(kc - 1, c.p - 1);
+        D.arc = d_arc[ii];
+        D.narc = btab[ii].narc;
+        D.grad = part;
+        timer.begin("backward: SDDMM", 0.0);
+        SG2V_CUDA(launch_sddmm(D, P.fp64, P.info.sms, stream), "SDDMM");
+        timer.end();
+        ws.release(ybar);
+    }
+    timer.count_extra(1);
+    SG2V_CUDA(launch_symmetrize(part, g->rev, nnz, gradw, stream), "symmetrize");
+    SG2V_CUDA(cudaMemcpyAsync(grad_weights, gradw, (size_t)nnz * sizeof(double), cudaMemcpyDefault, stream),
+              "gradient copy");
+    RootSum sum;
+    unsigned status[4] = {0, 0, 0, 0};
+    if (total) SG2V_CUDA(cudaMemcpyAsync(&sum, R.sums, sizeof sum, cudaMemcpyDeviceToHost, stream), "copy");
+    SG2V_CUDA(cudaMemcpyAsync(status, R.status, sizeof status, cudaMemcpyDeviceToHost, stream), "status copy");
+    SG2V_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
+    timer.collect();
+    if (status[0]) {
+        set_error("a colour is outside [0, num_colours)");
+        return SG2V_ERR_COLOUR_OUT_OF_RANGE;
+    }
+    if (total) {
+        if (sum.flags == 0)
+            *total = (double)(((unsigned __int128)sum.hi << 64) | sum.lo);
+        else
+            *total = sum.s + sum.c;
+    }
     return SG2V_OK;
 }
 

@@ -21,6 +21,7 @@
 // the warps of a grid sized to the resident capacity of the GPU.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -306,13 +307,17 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
     const int ws = A.Ws;
     T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
     T s = T(0);
+    if (A.Yout) {
+        T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
+        for (int j = lane; j < A.wy; j += 32) yo[j] = ok ? ybuf[j] : T(0);
+    }
     if (A.a_leaf) {
         for (int j = lane; j < ws; j += 32) {
             const T y = ok ? ybuf[j] : T(0);
             if (A.root)
                 s += y;
             else
-                out[j] = y;
+                out[j] = A.accumulate ? out[j] + y : y;
         }
     } else {
         const int ns = A.nsplit;
@@ -606,6 +611,98 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
     }
 }
 
+// ---------------------------------------------------------------- backward
+
+template <typename T>
+__global__ void bwd_ema_kernel(const BwdEmaArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int per = A.ws + A.wa + A.wy;
+    T *gs = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * per;
+    T *ma = gs + A.ws;
+    T *yy = ma + A.wa;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; v < A.n; v += nwarps) {
+        const int c = A.colours[v];
+        T *yb = static_cast<T *>(A.Ybar) + v * A.ldyb;
+        if ((unsigned)c >= (unsigned)A.kc) {
+            for (int j = lane; j < A.wy; j += 32) yb[j] = T(0);
+            continue;
+        }
+        const T seed = A.seed ? T(A.seed[v]) : T(0);
+        const T *g = A.G ? static_cast<const T *>(A.G) + v * A.ldg : nullptr;
+        for (int j = lane; j < A.ws; j += 32) gs[j] = g ? g[j] : seed;
+        if (A.a >= 2) {
+            const T *mr = static_cast<const T *>(A.Ma) + v * A.lda;
+            const T *yr = static_cast<const T *>(A.Y) + v * A.ldy;
+            for (int j = lane; j < A.wa; j += 32) ma[j] = mr[j];
+            for (int j = lane; j < A.wy; j += 32) yy[j] = yr[j];
+        }
+        __syncwarp();
+        if (A.a == 1) {
+            for (int j = lane; j < A.wy; j += 32) yb[j] = gs[j];
+        } else {
+            for (int j = lane; j < A.wy; j += 32) {
+                const uint32_t *pr = A.ybar + (int64_t)j * A.nybar;
+                T acc = T(0);
+                for (int i = 0; i < A.nybar; ++i) {
+                    const uint32_t x = __ldg(pr + i);
+                    acc = fma(gs[x & 0xffffu], ma[x >> 16], acc);
+                }
+                yb[j] = acc;
+            }
+            T *ga = static_cast<T *>(A.Gabar) + v * A.ldga;
+            for (int j = lane; j < A.wa; j += 32) {
+                const uint32_t *pr = A.mabar + (int64_t)j * A.nmabar;
+                T acc = T(0);
+                for (int i = 0; i < A.nmabar; ++i) {
+                    const uint32_t x = __ldg(pr + i);
+                    acc = fma(gs[x & 0xffffu], yy[x >> 16], acc);
+                }
+                ga[j] += acc;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__global__ void sddmm_kernel(const SddmmArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T *mp = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * ((A.wmp + 3) / 4 * 4);
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; u < A.n; u += nwarps) {
+        const int cu = A.colours[u];
+        if ((unsigned)cu >= (unsigned)A.kc) continue;
+        if (!A.hist) {
+            const T *mr = static_cast<const T *>(A.Mp) + u * A.ldp;
+            for (int j = lane; j < A.wmp; j += 32) mp[j] = mr[j];
+        }
+        __syncwarp();
+        const int64_t e0 = A.row_ptr[u], e1 = A.row_ptr[u + 1];
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int v = __ldg(A.col_idx + e);
+            const int cv = A.colours[v];
+            if ((unsigned)cv >= (unsigned)A.kc || cv == cu) continue;
+            const uint32_t *pr = A.arc + ((int64_t)cv * A.kc + cu) * A.narc;
+            const T *yr = static_cast<const T *>(A.Ybar) + (int64_t)v * A.ldyb;
+            T acc = T(0);
+            for (int i = 0; i < A.narc; ++i) {
+                const uint32_t x = __ldg(pr + i);
+                acc = A.hist ? acc + yr[x & 0xffffu] : fma(yr[x & 0xffffu], mp[x >> 16], acc);
+            }
+            A.grad[e] += (double)acc;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void symmetrize_kernel(const double *part, const int32_t *rev, int64_t nnz, double *grad_w) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        grad_w[e] = part[e] + part[rev[e]];
+}
+
 // 128-bit unsigned integer to the nearest double (ties to even): the top 64
 // significant bits keep a sticky bit for everything below them, so the one
 // rounding of the 64-bit conversion is the correct rounding of the whole.
@@ -756,6 +853,36 @@ cudaError_t launch_finalize(const RootSum *sums, int nseg, int nb, const double 
                             double *totals, double *estimates, unsigned *status, cudaStream_t stream) {
     finalize_kernel<<<(nseg + 127) / 128, 128, 0, stream>>>(sums, nseg, nb, scale_hi, scale_lo, totals, estimates,
                                                             status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStream_t stream) {
+    const size_t smem = (size_t)8 * (args.ws + args.wa + args.wy) * (fp64 ? 8 : 4);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((args.n + 7) / 8, (int64_t)sms * 8);
+    if (fp64)
+        bwd_ema_kernel<double><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
+    else
+        bwd_ema_kernel<float><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream) {
+    const size_t smem = (size_t)8 * ((args.wmp + 3) / 4 * 4) * (fp64 ? 8 : 4);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((args.n + 7) / 8, (int64_t)sms * 8);
+    if (fp64)
+        sddmm_kernel<double><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
+    else
+        sddmm_kernel<float><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(const double *part, const int32_t *rev, int64_t nnz, double *grad_w,
+                              cudaStream_t stream) {
+    if (nnz == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 4096);
+    symmetrize_kernel<<<(unsigned)blocks, 256, 0, stream>>>(part, rev, nnz, grad_w);
     return cudaGetLastError();
 }
 

@@ -56,11 +56,67 @@ struct NodeArgs {
     void *root_out;               // [nb][n]
     const uint32_t *splits;       // [Ws][nsplit] rank(A') | rank(S' - A') << 16 (a >= 2)
     int nsplit;
+    // backward support: also store Y' rows (Yout != null); add the output row
+    // to the existing one instead of overwriting it (accumulate != 0)
+    void *Yout;
+    int64_t ldy;
+    int accumulate;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
     unsigned *counters;           // [slots][nb], zero on entry
 };
+
+// Backward of the eMA of one node for one colouring (one warp per row):
+//   Ybar'(P') = sum over S' containing P' of G'(S') * M_a'(S' - P')
+//   Gabar'(A') += sum over S' containing A' of G'(S') * Y'(S' - A')
+// (a = 1: Ybar' = G').  At the root G'(S') is the per-vertex seed.
+struct BwdEmaArgs {
+    int64_t n;
+    const int8_t *colours;
+    int kc, a;
+    int ws, wa, wy;               // C(kc-1, t-1), C(kc-1, a-1), C(kc-1, p)
+    const void *G;                // [n][ldg] gradient of M_s' (null at the root)
+    int64_t ldg;
+    const double *seed;           // [n] gradient of the per-vertex counts (root)
+    const void *Ma;
+    int64_t lda;
+    const void *Y;
+    int64_t ldy;
+    void *Ybar;                   // out [n][ldyb]
+    int64_t ldyb;
+    void *Gabar;                  // accumulated [n][ldga] (a >= 2)
+    int64_t ldga;
+    const uint32_t *ybar;         // [wy][nybar]
+    int nybar;
+    const uint32_t *mabar;        // [wa][nmabar]
+    int nmabar;
+};
+
+// Per-arc weight gradient of one node (one warp per row u, arcs in CSR
+// order): grad[e] += sum over the arc table of Ybar'(v, .) * M_p'(u, .) for
+// arc e = (u, v); M_p' = 1 when the passive child is a single vertex.
+struct SddmmArgs {
+    int64_t n;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const int8_t *colours;
+    int kc, hist;
+    const void *Ybar;
+    int64_t ldyb;
+    const void *Mp;
+    int64_t ldp;
+    int wmp;                      // C(kc-1, p-1)
+    const uint32_t *arc;          // [kc][kc][narc]
+    int narc;
+    double *grad;                 // [nnz]
+};
+
+cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStream_t stream);
+cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream);
+// grad_w[e] = part[e] + part[rev[e]]
+cudaError_t launch_symmetrize(const double *part, const int32_t *rev, int64_t nnz, double *grad_w,
+                              cudaStream_t stream);
 
 // Per-segment (template x colouring) result of the root reduction.
 struct RootSum {

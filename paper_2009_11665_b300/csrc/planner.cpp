@@ -141,6 +141,70 @@ void build_compressed_tables(int kc, int t, int a, int wz_pad, CompressedTables 
     }
 }
 
+void build_backward_tables(int kc, int t, int a, int wz_pad, BackwardTables *out) {
+    const int p = t - a;
+    const int u = kc - 1;  // squeezed universe
+    *out = BackwardTables();
+    if (a >= 2) {
+        const int wy = (int)binom(u, p), wa = (int)binom(u, a - 1);
+        out->nybar = (int)binom(u - p, a - 1);
+        out->nmabar = (int)binom(u - (a - 1), p);
+        out->ybar.assign((size_t)wy * out->nybar, 0);
+        out->mabar.assign((size_t)wa * out->nmabar, 0);
+        std::vector<int> fy(wy, 0), fa(wa, 0);
+        uint32_t S = (1u << (t - 1)) - 1;
+        const int ws = (int)binom(u, t - 1);
+        for (int s = 0; s < ws; ++s, S = next_same_popcount(S)) {
+            for (uint32_t A = 0;;) {
+                A = (A - S) & S;
+                if (A == 0 && a - 1 > 0) break;
+                if (__builtin_popcount(A) == a - 1) {
+                    const uint32_t P = S ^ A;
+                    const uint32_t rp = colex_rank(P), ra = colex_rank(A);
+                    out->ybar[(size_t)rp * out->nybar + fy[rp]++] = (uint32_t)s | (ra << 16);
+                    out->mabar[(size_t)ra * out->nmabar + fa[ra]++] = (uint32_t)s | (rp << 16);
+                }
+                if (A == 0) break;
+            }
+        }
+    }
+    if (p >= 2) {
+        const int wout = (int)binom(u, p - 1);
+        out->wout = wout;
+        out->nterms = kc - p;
+        out->expand.assign((size_t)kc * wout * out->nterms, 0);
+        for (int c = 0; c < kc; ++c) {
+            uint32_t Q = (1u << (p - 1)) - 1;
+            for (int j = 0; j < wout; ++j, Q = next_same_popcount(Q)) {
+                const uint32_t P = unsqueeze_colour(Q, c) | (1u << c);
+                int k = 0;
+                for (int d = 0; d < kc; ++d) {
+                    if (P >> d & 1u) continue;
+                    out->expand[((size_t)c * wout + j) * out->nterms + k++] =
+                        (uint16_t)(d * wz_pad + (int)colex_rank(squeeze_colour(P, d)));
+                }
+            }
+        }
+    }
+    // arc pairs: P ranges over p-sets with cu in P, cv not in P
+    out->narc = (int)binom(kc - 2, p - 1);
+    out->arc.assign((size_t)kc * kc * out->narc, 0);
+    for (int cv = 0; cv < kc; ++cv) {
+        for (int cu = 0; cu < kc; ++cu) {
+            if (cu == cv) continue;
+            int k = 0;
+            uint32_t P = (1u << p) - 1;
+            const int all = (int)binom(kc, p);
+            for (int i = 0; i < all; ++i, P = next_same_popcount(P)) {
+                if (!(P >> cu & 1u) || (P >> cv & 1u)) continue;
+                const uint32_t iy = colex_rank(squeeze_colour(P, cv));
+                const uint32_t im = p == 1 ? 0u : colex_rank(squeeze_colour(P ^ (1u << cu), cu));
+                out->arc[((size_t)cv * kc + cu) * out->narc + k++] = iy | (im << 16);
+            }
+        }
+    }
+}
+
 }  // namespace sg2v
 
 namespace {

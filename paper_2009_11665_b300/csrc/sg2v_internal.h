@@ -50,6 +50,31 @@ struct CompressedTables {
     int nsplit = 0;
 };
 
+// Tables of the backward pass of node (t, a, p), squeezed coordinates of the
+// row's own colour c (sets of the other kc - 1 colours).
+struct BackwardTables {
+    // a >= 2: for each p-set P', the pairs rank(S') | rank(S' - P') << 16 over
+    // the (t-1)-sets S' containing P' (gradient of Y')
+    std::vector<uint32_t> ybar;
+    int nybar = 0;
+    // a >= 2: for each (a-1)-set A', the pairs rank(S') | rank(S' - A') << 16
+    // over the (t-1)-sets S' containing A' (gradient of M_a')
+    std::vector<uint32_t> mabar;
+    int nmabar = 0;
+    // p >= 2: transposed SpMM expansion: the gradient of M_p'(u, P'') (P = {c}
+    // + P'') is the sum over the kc - p colours d outside P of Zbar(d, squeezed
+    // P), Zbar(d, .) summing gradient rows of neighbours of colour d:
+    // offsets d * wz_pad + rank, [kc][C(kc-1, p-1)][kc - p]
+    std::vector<uint16_t> expand;
+    int wout = 0, nterms = 0;
+    // per-arc weight gradient: for neighbour colour cv and own colour cu, the
+    // pairs rank of P in cv's squeezed p-sets | rank of P - {cu} in cu's
+    // squeezed (p-1)-sets << 16 over the p-sets P with cu in P and cv not in
+    // P: [kc][kc][C(kc-2, p-1)] (for p = 1 the second index is 0)
+    std::vector<uint32_t> arc;
+    int narc = 0;
+};
+
 struct ColumnTables {
     // gather[c * Wt + rank(S)] = rank(S minus {c}) if c in S else -1 (a = 1 nodes)
     std::vector<int32_t> gather;
@@ -76,6 +101,9 @@ void build_tables(int kc, int t, int a, ColumnTables *out);
 // Builds the colour-compressed tables of node (t, a, p) for kc colours with
 // Z rows of wz_pad entries.
 void build_compressed_tables(int kc, int t, int a, int wz_pad, CompressedTables *out);
+// Builds the backward tables of node (t, a, p) for kc colours; wz_pad is the
+// Zbar row stride of the transposed SpMM (p >= 2).
+void build_backward_tables(int kc, int t, int a, int wz_pad, BackwardTables *out);
 // Thread-local error detail.
 void set_error(const std::string &msg);
 }  // namespace sg2v

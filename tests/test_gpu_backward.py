@@ -1,0 +1,170 @@
+"""Gradient of the weighted colourful count with respect to edge weights.
+
+F(w) = sum_v g_v per_vertex[v](w), each colourful map contributing the
+product of its k-1 edge weights.  A tree map uses an edge at most once, so F
+is affine in each single weight: dF/dw_e = (F(w) - F(w with w_e = 0)) / w_e
+exactly (the oracle computes both in exact dyadic arithmetic), central finite
+differences are exact up to rounding for any step, and F is homogeneous of
+degree k-1: sum over edges of w_e dF/dw_e = (k-1) F (Euler).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import sg2v_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as s
+
+    return s
+
+
+def _exact_grad(g, w, parent, col, edges, seedv=None):
+    """dF/dw_e for the listed undirected edges, exact, from the oracle."""
+    ids = si.arc_edge_ids(g)
+    base = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, weights=w)
+    bpv = base.per_vertex_values()
+    F = sum(Fraction(float(s)) * x for s, x in zip(seedv, bpv)) if seedv is not None else base.total_value()
+    out = {}
+    for e in edges:
+        w0 = w.copy()
+        w0[ids == e] = 0.0
+        r = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, weights=w0)
+        F0 = sum(Fraction(float(s)) * x for s, x in zip(seedv, r.per_vertex_values())) if seedv is not None \
+            else r.total_value()
+        out[e] = (F - F0) / Fraction(float(w[ids == e][0]))
+    return F, out
+
+
+@pytest.mark.parametrize("parent", [si.TREE8.parent, (-1, 0, 1, 1), (-1, 0, 0, 0, 0), (-1, 0), (-1, 0, 1, 2, 2, 0)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_matches_exact_differences(sg, parent, prec):
+    k = len(parent)
+    g = si.chung_lu(600, 3000, 2.3, seed=3)
+    w = si.arc_weights(g, si.edge_weights(g, seed=2))
+    col = si.colouring(g.n, k, 6)
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(parent)
+    grad = np.zeros(g.nnz)
+    total = sg.sg2v_count_backward(graph.handle, plan.handle, col, sg.PRECISIONS[prec], grad)
+    edges = list(si.sample_indices(12, g.m, seed=k)) + [0, g.m - 1]
+    F, exact = _exact_grad(g, w, parent, col, edges)
+    tol = 1e-11 if prec == "fp64" else 1e-4
+    assert abs(total - float(F)) <= tol * float(F)
+    ids = si.arc_edge_ids(g)
+    for e, want in exact.items():
+        arcs = np.nonzero(ids == e)[0]
+        for a in arcs:
+            assert abs(grad[a] - float(want)) <= tol * max(abs(float(want)), 1e-300) + 1e-300, (e, grad[a], want)
+    # Euler: sum over edges of w_e dF/dw_e = (k - 1) F (each edge appears on two arcs)
+    euler = float(np.sum(w.astype(np.float64) * grad)) / 2.0
+    assert euler == pytest.approx((k - 1) * float(F), rel=10 * tol)
+
+
+def test_seeded_per_vertex_gradient_and_autograd(sg):
+    import torch
+
+    parent = (-1, 0, 1, 0)
+    g = si.chung_lu(500, 2500, 2.3, seed=8)
+    w = si.arc_weights(g, si.edge_weights(g, seed=4))
+    col = si.colouring(g.n, 4, 9)
+    seed = si.uniform53(5, 77, np.arange(g.n)) - 0.25
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(parent)
+    grad = np.zeros(g.nnz)
+    sg.sg2v_count_backward(graph.handle, plan.handle, col, sg.SG2V_FP64, grad, seed)
+    edges = list(si.sample_indices(8, g.m, seed=1))
+    _, exact = _exact_grad(g, w, parent, col, edges, seedv=seed)
+    ids = si.arc_edge_ids(g)
+    for e, want in exact.items():
+        for a in np.nonzero(ids == e)[0]:
+            assert grad[a] == pytest.approx(float(want), rel=1e-9, abs=1e-9)
+    # autograd through weighted_count
+    wt = torch.from_numpy(w).cuda().requires_grad_(True)
+    dcol = torch.from_numpy(col).cuda()
+    pv = sg.weighted_count(wt, graph, plan, dcol, "fp64")
+    (pv * torch.from_numpy(seed).cuda()).sum().backward()
+    assert np.allclose(wt.grad.cpu().numpy(), grad.astype(np.float32), rtol=1e-5)
+
+
+def test_unweighted_gradient_is_participation(sg):
+    """On an unweighted graph dF/dw_e at w = 1 counts the colourful maps that
+    use edge e; checked against brute force on a tiny graph."""
+    parent = (-1, 0, 1)
+    g = si.random_small_graph(9, 1, 2, 4)
+    col = si.colouring(g.n, 3, 2)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(parent)
+    grad = np.zeros(g.nnz)
+    sg.sg2v_count_backward(graph.handle, plan.handle, col, sg.SG2V_FP64, grad)
+    ids = si.arc_edge_ids(g)
+    full = oracle.brute(g.row_ptr, g.col_idx, parent, 0, col).total
+    for e in range(g.m):
+        w = np.ones(g.nnz, np.float32)
+        w[ids == e] = 0.0
+        without = oracle.brute(g.row_ptr, g.col_idx, parent, 0, col, weights=w).total_value()
+        uses = full - without
+        assert all(grad[a] == float(uses) for a in np.nonzero(ids == e)[0])
+
+
+def test_chunglu200k_tree8_finite_differences(sg):
+    """The differentiable workload: Chung-Lu 200k vertices, avg degree 20,
+    gamma 2.3, weights in [0.5, 1.5), tree8, k = 8.  FP32 backward against
+    central differences of the FP64 forward on 1,000 sampled edges (exact up
+    to rounding because F is affine in each weight), plus Euler's identity."""
+    import torch
+
+    g = si.workload_graph("chunglu200k")
+    w = si.arc_weights(g, si.edge_weights(g, seed=0))
+    col = si.colouring(g.n, 8, 0)
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(si.TREE8.parent)
+    dcol = torch.from_numpy(col).cuda()
+    grad = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+    total32 = sg.sg2v_count_backward(graph.handle, plan.handle, dcol, sg.SG2V_FP32, grad)
+    grad = grad.cpu().numpy()
+    _, F64, _ = sg.count(graph, plan, dcol, "fp64", per_vertex=False)
+    assert abs(total32 - F64) <= 1e-4 * F64
+    ids = si.arc_edge_ids(g)
+    first_arc = np.zeros(g.m, dtype=np.int64)
+    first_arc[ids[::-1]] = np.arange(g.nnz)[::-1]
+    edges = si.sample_indices(1000, g.m, seed=11)
+    arcs_of = {}
+    order = np.argsort(ids, kind="stable")
+    pos = np.searchsorted(ids[order], edges)
+    h = 0.25
+    wt = torch.from_numpy(w).cuda()
+    checked = 0
+    for e, p0 in zip(edges, pos):
+        a0, a1 = order[p0], order[p0 + 1]
+        ww = wt.clone()
+        ww[a0] += h
+        ww[a1] += h
+        sg.sg2v_graph_set_weights(graph.handle, ww)
+        _, fp, _ = sg.count(graph, plan, dcol, "fp64", per_vertex=False)
+        ww[a0] -= 2 * h
+        ww[a1] -= 2 * h
+        sg.sg2v_graph_set_weights(graph.handle, ww)
+        _, fm, _ = sg.count(graph, plan, dcol, "fp64", per_vertex=False)
+        fd = (fp - fm) / (2 * h)
+        gv = grad[a0]
+        assert grad[a1] == gv
+        assert abs(gv - fd) <= 1e-4 * max(abs(fd), 1e-3 * F64 / g.m), (e, gv, fd)
+        checked += 1
+    assert checked == 1000
+    sg.sg2v_graph_set_weights(graph.handle, wt)
+    euler = float(np.sum(w.astype(np.float64) * grad)) / 2.0
+    assert euler == pytest.approx(7 * F64, rel=1e-4)

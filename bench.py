@@ -330,6 +330,27 @@ def main():
                    "wave": wave3, "cuda_graph": graph_on, "dtype": "f32"}
         ses.close()
 
+    # differentiable form: Chung-Lu 200k (avg degree 20, gamma 2.3), FP32 weights
+    # in [0.5, 1.5), tree8, k = 8: forward count and forward + gradient call
+    differentiable = None
+    if not args.no_batched:
+        g4 = si.workload_graph("chunglu200k")
+        w4 = si.arc_weights(g4, si.edge_weights(g4, seed=0))
+        graph4 = sg.Graph(g4.row_ptr, g4.col_idx, w4)
+        plan4 = sg.Plan(si.TREE8.parent, 0, 8)
+        col4 = torch.from_numpy(si.colouring(g4.n, 8, rank)).cuda()
+        grad4 = torch.empty(g4.nnz, dtype=torch.float64, device="cuda")
+        tot4 = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+        ms_f = time_steps(torch, lambda: sg.sg2v_count_batched(graph4.handle, [plan4.handle], col4, 1, sg.SG2V_FP32,
+                                                               None, tot4, None, stream),
+                          max(3, args.steps // 2), args.warmup, stream, dist)
+        ms_b = time_steps(torch, lambda: sg.sg2v_count_backward(graph4.handle, plan4.handle, col4, sg.SG2V_FP32,
+                                                                grad4, None, stream),
+                          max(3, args.steps // 2), args.warmup, stream, dist)
+        differentiable = {"workload": "chunglu200k (200k vertices, 2M edges, gamma 2.3, weights [0.5,1.5)), tree8, "
+                                      "k=8, one colouring", "forward_ms": ms_f, "forward_and_gradient_ms": ms_b,
+                          "dtype": "f32"}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -377,6 +398,7 @@ def main():
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic},
         "kernels": kernel_table,
         "batched_3_templates": batched,
+        "differentiable": differentiable,
         "cpu_baseline": cpu,
         "e2e": {"value": ms_e2e * 1e-3 / total_colourings, "unit": UNIT, "h2d_bytes_per_step": int(B * g.n),
                 "d2h_bytes_per_step": int(B * g.n * 8 + 2 * B * 8)},

@@ -125,8 +125,9 @@ def _ptr(a):
 
 def count(row_ptr, col_idx, parent: Sequence[int], root: int, colours, num_colours: Optional[int] = None,
           weights=None, mode: str = "decoupled", cut: str = "last", per_vertex: bool = True,
-          threads: int = 0) -> Result:
-    """Exact colourful counts by the DP.  Raises on invalid input."""
+          threads: int = 0, min_limbs: int = 2) -> Result:
+    """Exact colourful counts by the DP.  Raises on invalid input.  min_limbs
+    skips integer widths known to be too narrow (the result is the same)."""
     rp, ci, co = _ints(row_ptr, col_idx, colours)
     n = rp.shape[0] - 1
     par = np.ascontiguousarray(parent, dtype=np.int32)
@@ -136,6 +137,8 @@ def count(row_ptr, col_idx, parent: Sequence[int], root: int, colours, num_colou
     m = DECOUPLED if mode == "decoupled" else STANDARD
     c = CUT_LAST if cut == "last" else CUT_FIRST
     for limbs in _build.WIDTHS:
+        if limbs < min_limbs and limbs != _build.WIDTHS[-1]:
+            continue
         lib = _lib(limbs)
         pv = np.zeros((max(n, 1), limbs), dtype=np.uint64) if per_vertex else None
         tot = np.zeros(limbs, dtype=np.uint64)

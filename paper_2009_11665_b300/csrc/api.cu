@@ -454,6 +454,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
     P->shape.resize(nodes.size());
     P->tabs.resize(nodes.size());
     int64_t widest = 1;
+    const int wide_min = env_int("SG2V_WIDE_MIN_WZ", 1 << 30);
     for (size_t i = 0; i < nodes.size(); ++i) {
         const CNode &c = nodes[i];
         Shape &sh = P->shape[i];
@@ -462,20 +463,32 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.grp = 32;
         sh.nv = 1;
         if (!hist) node_shape(P->fp64, sh.wz, &sh.grp, &sh.nv);
+        if (!hist && sh.grp != kWideLanes && sh.wz >= wide_min) {
+            // rows at least SG2V_WIDE_MIN_WZ wide go to the CTA-per-row kernel
+            sh.grp = kWideLanes;
+            sh.nv = (sh.wz + kWideThreads * P->vecn - 1) / (kWideThreads * P->vecn);
+        }
         if (sh.nv == 0) {
             set_error("passive table wider than this build's register tile (column tiling not built)");
             return SG2V_ERR_UNSUPPORTED;
         }
         if (!hist) widest = std::max<int64_t>(widest, (sh.wz + P->vecn - 1) / P->vecn * P->vecn);
         sh.wz_pad = hist ? 1 : sh.grp * sh.nv * P->vecn;
-        sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
         sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
         sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
         P->scratch_ld = std::max<int64_t>(P->scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
-        sh.threads = kNodeThreads;
-        const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords) * P->esz;
-        while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
-        sh.smem = (size_t)(sh.threads / 32) * per_warp;
+        if (sh.grp == kWideLanes) {
+            // one CTA per row: Z, Y' and the active row once per CTA
+            sh.zwords = kc * sh.wz_pad;
+            sh.threads = kWideThreads;
+            sh.smem = (size_t)(sh.zwords + sh.ywords + sh.mwords) * P->esz;
+        } else {
+            sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
+            sh.threads = kNodeThreads;
+            const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords) * P->esz;
+            while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
+            sh.smem = (size_t)(sh.threads / 32) * per_warp;
+        }
         if (sh.smem > 227 * 1024) {
             set_error("per-colour accumulators exceed shared memory (column tiling not built)");
             return SG2V_ERR_UNSUPPORTED;
@@ -1288,13 +1301,19 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             return SG2V_ERR_UNSUPPORTED;
         }
         sh.wz_pad = sh.grp * sh.nv * vecn;
-        sh.zwords = (32 / sh.grp) * kc * sh.wz_pad;
         sh.ywords = ((int)binom(kc - 1, c.p - 1) + 3) / 4 * 4;
         sh.mwords = 0;
-        sh.threads = kNodeThreads;
-        const size_t per_warp = (size_t)(sh.zwords + sh.ywords) * esz;
-        while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
-        sh.smem = (size_t)(sh.threads / 32) * per_warp;
+        if (sh.grp == kWideLanes) {
+            sh.zwords = kc * sh.wz_pad;
+            sh.threads = kWideThreads;
+            sh.smem = (size_t)(sh.zwords + sh.ywords) * esz;
+        } else {
+            sh.zwords = (32 / sh.grp) * kc * sh.wz_pad;
+            sh.threads = kNodeThreads;
+            const size_t per_warp = (size_t)(sh.zwords + sh.ywords) * esz;
+            while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
+            sh.smem = (size_t)(sh.threads / 32) * per_warp;
+        }
         if (c.p >= 2) {
             sh.blocks_per_sm = node_blocks_per_sm(P.fp64, false, sh.grp, sh.nv, g->weights != nullptr, sh.threads,
                                                   sh.smem);

@@ -434,6 +434,205 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
     }
 }
 
+// Wide rows (a compressed row wider than one warp's register tile): one
+// 256-thread CTA per (task, colouring).  Warp w owns vectors
+// [w*32*NV, (w+1)*32*NV) of every gathered row and of Z(d, .), so the eight
+// warps walk the same colour-sorted arc list over disjoint column slices; the
+// expansion, the eMA and the root's row sum then use all threads.
+constexpr int kWideWarps = 8;
+static_assert(kWideWarps * 32 == kWideThreads, "wide CTA size");
+
+template <typename T, int NV, bool WEIGHTED>
+__global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const NodeArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = Vec16<T>;
+    using VT = typename V::type;
+    constexpr int U = NV == 1 ? 4 : 2;
+    __shared__ int s_last;
+    __shared__ T s_red[kWideWarps];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int kc = A.kc, wzp = A.wz_pad;  // wzp = kWideWarps * 32 * NV * V::n
+    T *zbuf = reinterpret_cast<T *>(smem_raw);
+    T *ybuf = zbuf + A.zwords;
+    T *mbuf = ybuf + A.ywords;
+    const int zlen = kc * wzp;
+    const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    const int nvec = (A.Wz + V::n - 1) / V::n;
+    const int vbase = w * 32 * NV + lane;  // this lane's first vector of the row
+    bool qok[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) qok[q] = vbase + 32 * q < nvec;
+    for (int64_t ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
+        const int4 task = A.tasks[ti];
+        const int v = task.x, slot = task.y;
+        const int64_t e0 = task.z, e1 = task.w;
+        for (int b = 0; b < A.nb; ++b) {
+            const int64_t rowb = (int64_t)v * A.nb + b;
+            const int cv = A.colours[(int64_t)b * A.n + v];
+            const bool cok = (unsigned)cv < (unsigned)kc && e0 < e1;
+            if (mchunks && cok) {
+                const char *src = static_cast<const char *>(A.Ma) + rowb * A.lda * sizeof(T);
+                for (int c = tid; c < mchunks; c += blockDim.x) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(mbuf) + 16 * c);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * c) : "memory");
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
+            if (cok) {
+                // zero this warp's slice of Z, then sum colour runs of the arcs
+                for (int d = 0; d < kc; ++d) {
+                    VT *zr = reinterpret_cast<VT *>(zbuf + d * wzp) + vbase;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) zr[32 * q] = V::zero();
+                }
+                const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;
+                const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + vbase;
+                const int32_t *scol = A.scol + (int64_t)b * A.nnz;
+                const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
+                const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+                VT run[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) run[q] = V::zero();
+                int cur = -1;
+                for (int64_t base = e0; base < e1; base += 32) {
+                    const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
+                    const int u_l = lane < cnt ? __ldg(scol + base + lane) : 0;
+                    const int c_l = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
+                    T w_l = T(1);
+                    if (WEIGHTED) w_l = lane < cnt ? T(__ldg(sw + base + lane)) : T(0);
+                    for (int j0 = 0; j0 < cnt; j0 += U) {
+                        VT x[U][NV];
+                        T wr[U];
+                        int cr[U];
+                        bool take[U];
+#pragma unroll
+                        for (int r = 0; r < U; ++r) {
+                            const int j = j0 + r;
+                            const int u = __shfl_sync(kFull, u_l, j & 31);
+                            cr[r] = __shfl_sync(kFull, c_l, j & 31);
+                            wr[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j & 31) : T(1);
+                            take[r] = j < cnt && cr[r] != cv && cr[r] >= 0;
+                            const VT *row = Mb + (int64_t)u * uvec;
+#pragma unroll
+                            for (int q = 0; q < NV; ++q)
+                                x[r][q] = (take[r] && qok[q]) ? __ldg(row + 32 * q) : V::zero();
+                        }
+#pragma unroll
+                        for (int r = 0; r < U; ++r) {
+                            if (!take[r]) continue;
+                            if (cr[r] != cur) {
+                                if (cur >= 0) {
+                                    VT *zr = reinterpret_cast<VT *>(zbuf + cur * wzp) + vbase;
+#pragma unroll
+                                    for (int q = 0; q < NV; ++q) {
+                                        VT z = zr[32 * q];
+                                        V::add(z, run[q]);
+                                        zr[32 * q] = z;
+                                        run[q] = V::zero();
+                                    }
+                                }
+                                cur = cr[r];
+                            }
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) {
+                                if (WEIGHTED)
+                                    V::fma(run[q], wr[r], x[r][q]);
+                                else
+                                    V::add(run[q], x[r][q]);
+                            }
+                        }
+                    }
+                }
+                if (cur >= 0) {
+                    VT *zr = reinterpret_cast<VT *>(zbuf + cur * wzp) + vbase;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        VT z = zr[32 * q];
+                        V::add(z, run[q]);
+                        zr[32 * q] = z;
+                    }
+                }
+            }
+            __syncthreads();
+            if (slot >= 0 && cok) {
+                T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
+                for (int j = tid; j < zlen; j += blockDim.x) atomicAdd(sc + j, zbuf[j]);
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) {
+                    const unsigned done = atomicAdd(A.counters + (int64_t)slot * A.nb + b, 1u);
+                    s_last = (done + 1u == (unsigned)__ldg(A.heavy_chunks + slot));
+                }
+                __syncthreads();
+                if (!s_last) {
+                    if (mchunks) asm volatile("cp.async.wait_all;\n" ::: "memory");
+                    __syncthreads();
+                    continue;
+                }
+                __threadfence();
+                for (int j = tid; j < zlen; j += blockDim.x) zbuf[j] = __ldcg(sc + j);
+                __syncthreads();
+            }
+            // Y' = expansion of Z over the p-sets without v's colour
+            if (cok) {
+                const int p = A.p, wy = A.wy;
+                const uint16_t *ex = A.expand + (int64_t)cv * wy * p;
+                for (int j = tid; j < wy; j += blockDim.x) {
+                    T s = T(0);
+                    for (int k = 0; k < p; ++k) s += zbuf[__ldg(ex + j * p + k)];
+                    ybuf[j] = s;
+                }
+            }
+            if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncthreads();
+            if (A.Yout) {
+                T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
+                for (int j = tid; j < A.wy; j += blockDim.x) yo[j] = cok ? ybuf[j] : T(0);
+            }
+            // eMA in squeezed coordinates
+            const int ws = A.Ws;
+            T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
+            T acc_root = T(0);
+            if (A.a_leaf) {
+                for (int j = tid; j < ws; j += blockDim.x) {
+                    const T y = cok ? ybuf[j] : T(0);
+                    if (A.root)
+                        acc_root += y;
+                    else
+                        out[j] = A.accumulate ? out[j] + y : y;
+                }
+            } else {
+                const int ns = A.nsplit;
+                for (int S = tid; S < ws; S += blockDim.x) {
+                    T acc = T(0);
+                    if (cok) {
+                        const uint32_t *sp = A.splits + (int64_t)S * ns;
+                        for (int j = 0; j < ns; ++j) {
+                            const uint32_t x = __ldg(sp + j);
+                            acc = fma(mbuf[x & 0xffffu], ybuf[x >> 16], acc);
+                        }
+                    }
+                    if (A.root)
+                        acc_root += acc;
+                    else
+                        out[S] = acc;
+                }
+            }
+            if (A.root) {
+                acc_root = warp_sum(acc_root);
+                if (lane == 0) s_red[w] = acc_root;
+                __syncthreads();
+                if (tid == 0) {
+                    T t = T(0);
+                    for (int i = 0; i < kWideWarps; ++i) t += s_red[i];
+                    static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = t;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T, int G, int NV, bool HIST, bool WEIGHTED>
 void *kernel_ptr() {
     return reinterpret_cast<void *>(&node_kernel<T, G, NV, HIST, WEIGHTED>);
@@ -454,7 +653,24 @@ void *pick(bool hist, int g, int nv) {
     }
 }
 
+template <typename T, bool W>
+void *pick_wide(int nv) {
+    switch (nv) {
+        case 1: return reinterpret_cast<void *>(&node_wide_kernel<T, 1, W>);
+        case 2: return reinterpret_cast<void *>(&node_wide_kernel<T, 2, W>);
+        case 3: return reinterpret_cast<void *>(&node_wide_kernel<T, 3, W>);
+        case 4: return reinterpret_cast<void *>(&node_wide_kernel<T, 4, W>);
+        default: return nullptr;
+    }
+}
+
 void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted) {
+    if (g == kWideLanes) {
+        // wide rows: one CTA per task (nv vectors per lane, 8 warps)
+        if (hist) return nullptr;
+        if (fp64) return weighted ? pick_wide<double, true>(nv) : pick_wide<double, false>(nv);
+        return weighted ? pick_wide<float, true>(nv) : pick_wide<float, false>(nv);
+    }
     if (fp64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
     return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
 }
@@ -780,7 +996,12 @@ void node_shape(bool fp64, int wz, int *g, int *nv) {
     else {
         *g = 32;
         *nv = (nvec + 31) / 32;
-        if (*nv > 4) *nv = 0;
+        if (*nv > 4) {
+            // wide: a CTA of kWideWarps warps shares the row
+            *g = kWideLanes;
+            *nv = (nvec + kWideWarps * 32 - 1) / (kWideWarps * 32);
+            if (*nv > 4) *nv = 0;
+        }
     }
 }
 
@@ -790,10 +1011,12 @@ int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int t
     if (smem > 48 * 1024) {
         // one limit per kernel variant, shared by every node that uses it: the device maximum
         int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            (size_t)optin < smem ||
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
+            cudaFuncGetAttributes(&fa, k) != cudaSuccess || (size_t)optin < smem + fa.sharedSizeBytes ||
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -813,7 +1036,7 @@ cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int thre
     void *k = select_kernel(fp64, hist, g, nv, weighted);
     if (!k) return cudaErrorInvalidValue;
     if (args.ntasks == 0) return cudaSuccess;
-    const int64_t warps_per_block = threads / 32;
+    const int64_t warps_per_block = g == kWideLanes ? 1 : threads / 32;  // wide: one task per CTA
     int64_t grid = (args.ntasks + warps_per_block - 1) / warps_per_block;
     if (grid > grid_cap) grid = grid_cap;
     if (grid < 1) grid = 1;

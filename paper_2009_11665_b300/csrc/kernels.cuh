@@ -130,10 +130,14 @@ constexpr unsigned kFlagNotIntegral = 1u;
 constexpr unsigned kFlagNonFinite = 2u;
 
 // Shape of the gather of compressed rows of wz elements: lanes per neighbour
-// group (4, 8, 16 or 32) and 16-byte vectors per lane (1..4; 0 if too wide).
+// group (4, 8, 16 or 32; kWideLanes when a whole CTA shares one row) and
+// 16-byte vectors per lane (1..4; 0 if too wide).
 void node_shape(bool fp64, int wz, int *lanes_per_group, int *vec_per_lane);
 
 constexpr int kNodeThreads = 256;
+// node_shape's lanes-per-group value for rows handled by a whole CTA (wide rows)
+constexpr int kWideLanes = 256;
+constexpr int kWideThreads = 256;
 
 // Resident blocks per SM of one node-kernel variant at a block size and
 // dynamic shared-memory size (0 if it cannot run); raises the kernel's

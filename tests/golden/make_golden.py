@@ -29,6 +29,31 @@ def fingerprint(g) -> str:
     return h.hexdigest()
 
 
+def large_form(scale: int, colourings: int = 8, samples: int = 512):
+    """The large form's scaled sibling: R-MAT scale `scale` with the full
+    workload's parameters and edge/vertex ratio (5e7 edges at scale 20),
+    tree15, k = 15, colourings 0..7 of seed 0: exact totals and sampled
+    per-vertex counts."""
+    m = int(round(50_000_000 / (1 << (20 - scale))))
+    g = si.rmat(scale, m, seed=0)
+    idx = sorted(set(int(i) for i in si.sample_indices(min(samples, g.n), g.n, seed=2)) |
+                 set(int(i) for i in g.degrees().argsort()[-16:]))
+    out = {"workload": f"rmat{scale}_large_sibling_tree15_k15", "graph": f"rmat scale {scale}, m={m}",
+           "scale": scale, "m": m, "n": g.n, "graph_sha256": fingerprint(g), "template": list(si.TREE15.parent),
+           "root": 0, "num_colours": 15, "colouring_seed": 0, "sample_vertices": idx, "colourings": [],
+           "source": "oracle.count (exact decoupled DP, 384-bit), tests/golden/make_golden.py"}
+    for b in range(colourings):
+        col = si.colouring(g.n, 15, 0, b)
+        t0 = time.time()
+        r = oracle.count(g.row_ptr, g.col_idx, si.TREE15.parent, 0, col, 15, min_limbs=6)
+        out["colourings"].append({"index": b, "total": str(r.total), "max_table_bits": r.max_bits,
+                                  "sample_counts": [str(r.per_vertex[i]) for i in idx],
+                                  "oracle_seconds": round(time.time() - t0, 1)})
+        print(f"scale {scale} colouring {b}: bits {r.max_bits} ({time.time() - t0:.0f}s)", flush=True)
+        with open(os.path.join(HERE, f"rmat{scale}_large_sibling_tree15_k15.json"), "w") as f:
+            json.dump(out, f, indent=1)
+
+
 def one(name, graph_name, template, kc, colouring_seed, colouring_index=0):
     g = si.workload_graph(graph_name)
     col = si.colouring(g.n, kc, colouring_seed, colouring_index)
@@ -66,4 +91,10 @@ def one(name, graph_name, template, kc, colouring_seed, colouring_index=0):
 
 
 if __name__ == "__main__":
-    one("rmat20_16m_tree10_k10", "rmat20_16m", si.TREE10, 10, colouring_seed=0)
+    what = sys.argv[1] if len(sys.argv) > 1 else "all"
+    if what in ("all", "tree10"):
+        one("rmat20_16m_tree10_k10", "rmat20_16m", si.TREE10, 10, colouring_seed=0)
+    if what in ("all", "large12"):
+        large_form(12)
+    if what in ("all", "large16"):
+        large_form(16)

@@ -1,0 +1,85 @@
+"""The large form: a 15-vertex tree, k = 15 colours, 8 colourings per call.
+
+Compressed rows reach C(14, 4) = 1001 columns, beyond one warp's register
+tile, so those nodes run on the CTA-per-row kernel.  Parity with stored
+oracle values (tests/golden, written by make_golden.py from the oracle only)
+on the scaled sibling of the full workload (same R-MAT parameters and
+edge/vertex ratio); the wide kernel is also driven through the small
+parity cases by lowering the width at which it takes over."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import sg2v_inputs as si
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build_library()
+    import paper_2009_11665_b300 as s
+
+    return s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_large_form_sibling_scale12(sg, prec):
+    import torch
+
+    gold = json.load(open(os.path.join(HERE, "golden", "rmat12_large_sibling_tree15_k15.json")))
+    g = si.rmat(gold["scale"], gold["m"], seed=0)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(gold["template"], 0, 15)
+    B = len(gold["colourings"])
+    cols = si.colourings(g.n, 15, B, seed=0)
+    pv, tot, est = sg.count_batched(graph, [plan], torch.from_numpy(cols).cuda(), prec, per_vertex=True)
+    pv, tot = pv.cpu().numpy(), tot.cpu().numpy()
+    idx = np.array(gold["sample_vertices"])
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    for b, rec in enumerate(gold["colourings"]):
+        total = int(rec["total"])
+        assert abs(tot[0, b] - total) <= tol * total
+        want = np.array([float(int(x)) for x in rec["sample_counts"]])
+        got = pv[0, b, idx]
+        nz = want != 0
+        assert np.all(got[~nz] == 0)
+        assert (np.abs(got[nz] - want[nz]) / want[nz]).max() <= tol
+
+
+@pytest.mark.parametrize("parent", [si.TREE7.parent, si.TREE8.parent, si.PATH7.parent, (-1, 0, 1, 2, 2, 0)])
+@pytest.mark.parametrize("chunk", ["1024", "48"])
+def test_wide_kernel_on_small_cases(sg, parent, chunk, monkeypatch):
+    """Every gathering node forced onto the CTA-per-row kernel (and split rows
+    with a small chunk) still equals the oracle."""
+    monkeypatch.setenv("SG2V_WIDE_MIN_WZ", "1")
+    monkeypatch.setenv("SG2V_CHUNK", chunk)
+    import torch
+
+    g = si.rmat(11, 12000, seed=3)
+    k = len(parent)
+    for kc in (k, k + 2):
+        col = si.colouring(g.n, kc, 4)
+        graph = sg.Graph(g.row_ptr, g.col_idx)
+        plan = sg.Plan(parent, 0, kc)
+        ref = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, kc)
+        want = np.array([float(x) for x in ref.per_vertex])
+        for prec, tol in (("fp64", 0.0), ("fp32", 1e-4)):
+            pv, t, e = sg.count(graph, plan, torch.from_numpy(col).cuda(), prec)
+            got = pv.cpu().numpy()
+            if prec == "fp64" and ref.max_bits <= 53:
+                assert np.array_equal(got, want)
+            else:
+                nz = want != 0
+                assert np.all(got[~nz] == 0)
+                assert (np.abs(got[nz] - want[nz]) / want[nz]).max() <= max(tol, 1e-12)

@@ -59,8 +59,16 @@ typedef enum {
 } sg2v_status;
 
 typedef enum {
-    SG2V_FP64 = 0, /* count tables and sums in FP64 */
-    SG2V_FP32 = 1  /* count tables in FP32, final reductions in FP64 */
+    SG2V_FP64 = 0,       /* count tables and sums in FP64 */
+    SG2V_FP32 = 1,       /* count tables in FP32, final reductions in FP64 */
+    SG2V_FP32_SCALED = 2 /* FP32 tables whose rows carry a power-of-two exponent
+                          * (int16): a row's values are its stored values times
+                          * 2^E, its largest stored value lies in [1, 2), so
+                          * counts far beyond FP32's 2^128 (k = 15 on large
+                          * graphs) keep FP32 relative precision; entries below
+                          * 2^-126 of their row's largest, after the gather's
+                          * alignment to the row's largest neighbour exponent,
+                          * are flushed to zero.  Forward counts only. */
 } sg2v_precision;
 
 /* ------------------------------------------------------------------ graph */
@@ -152,7 +160,9 @@ sg2v_status sg2v_plan_estimate_scale(const sg2v_plan *plan, double *scale);
  * SpMM + eMA per sub-template, then the root reduction and finalCount).
  *
  *   colours     [n] int8, host or device, values in [0, kc)
- *   precision   SG2V_FP64 or SG2V_FP32 (table type)
+ *   precision   SG2V_FP64, SG2V_FP32 or SG2V_FP32_SCALED (table type); an
+ *               SG2V_FP32 call that overflows is run again as
+ *               SG2V_FP32_SCALED by sg2v_count and sg2v_count_batched
  *   per_vertex  [n] double, host or device, or NULL: per_vertex[v] is the
  *               number of colourful embeddings (labelled maps) with the
  *               root rho at v, i.e. sum over colour sets C of M_0(v, I_C)
@@ -210,7 +220,8 @@ sg2v_status sg2v_count_batched(const sg2v_graph *graph, const sg2v_plan *const *
  *   total            host double or NULL: the forward total sum_v per_vertex[v]
  *   flags            0
  * Memory: every node's table, Y' and gradient table of the colouring stay
- * allocated during the call.  Errors as sg2v_count.
+ * allocated during the call.  Errors as sg2v_count; SG2V_FP32_SCALED is
+ * UNSUPPORTED here.
  */
 sg2v_status sg2v_count_backward(const sg2v_graph *graph, const sg2v_plan *plan, const int8_t *colours,
                                 sg2v_precision precision, const double *grad_per_vertex, double *grad_weights,

@@ -368,7 +368,7 @@ struct CNode {
 
 // Launch shape of one node: gather width, Z layout, shared memory, block size.
 struct Shape {
-    int wz, grp, nv, wz_pad, zwords, ywords, mwords, threads;
+    int wz, grp, nv, wz_pad, zwords, ywords, mwords, owords, threads;
     size_t smem;
     int blocks_per_sm;
 };
@@ -381,6 +381,7 @@ struct Prepared {
     std::vector<const sg2v_plan *> plans;
     int kc = 0, nb = 0, dev = 0;
     bool fp64 = false;
+    bool scaled = false;          // FP32 tables with per-row power-of-two exponents
     size_t esz = 4;
     int vecn = 4;
     int64_t n = 0;
@@ -396,7 +397,8 @@ struct Prepared {
 
 sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans, int32_t B,
                     sg2v_precision precision, Prepared *P) {
-    if (!g || !plans || num_plans < 1 || B < 1 || (precision != SG2V_FP64 && precision != SG2V_FP32)) {
+    if (!g || !plans || num_plans < 1 || B < 1 ||
+        (precision != SG2V_FP64 && precision != SG2V_FP32 && precision != SG2V_FP32_SCALED)) {
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
@@ -418,6 +420,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
     P->kc = kc;
     P->nb = B;
     P->fp64 = precision == SG2V_FP64;
+    P->scaled = precision == SG2V_FP32_SCALED;
     P->esz = P->fp64 ? 8 : 4;
     P->vecn = P->fp64 ? 2 : 4;
     P->n = g->n;
@@ -476,16 +479,17 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.wz_pad = hist ? 1 : sh.grp * sh.nv * P->vecn;
         sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
         sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
+        sh.owords = P->scaled ? ((int)binom(kc - 1, c.t - 1) + 3) / 4 * 4 : 0;
         P->scratch_ld = std::max<int64_t>(P->scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
         if (sh.grp == kWideLanes) {
             // one CTA per row: Z, Y' and the active row once per CTA
             sh.zwords = kc * sh.wz_pad;
             sh.threads = kWideThreads;
-            sh.smem = (size_t)(sh.zwords + sh.ywords + sh.mwords) * P->esz;
+            sh.smem = (size_t)(sh.zwords + sh.ywords + sh.mwords + sh.owords) * P->esz;
         } else {
             sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
             sh.threads = kNodeThreads;
-            const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords) * P->esz;
+            const size_t per_warp = (size_t)(sh.zwords + sh.ywords + sh.mwords + sh.owords) * P->esz;
             while (sh.threads > 32 && (size_t)(sh.threads / 32) * per_warp > 200 * 1024) sh.threads /= 2;
             sh.smem = (size_t)(sh.threads / 32) * per_warp;
         }
@@ -493,7 +497,9 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             set_error("per-colour accumulators exceed shared memory (column tiling not built)");
             return SG2V_ERR_UNSUPPORTED;
         }
-        sh.blocks_per_sm = node_blocks_per_sm(P->fp64, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
+        sh.blocks_per_sm =
+            P->scaled ? node_blocks_per_sm_scaled(hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem)
+                      : node_blocks_per_sm(P->fp64, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
         if (sh.blocks_per_sm < 1) {
             set_error("node kernel cannot be resident with its shared memory");
             return SG2V_ERR_UNSUPPORTED;
@@ -517,8 +523,9 @@ struct RunBuffers {
     unsigned *counters = nullptr;
     size_t scratch_bytes = 0, counter_bytes = 0;
     std::vector<void *> rootbuf;  // per plan: [nb][n] table type
-    std::vector<void *> table;    // per node: one wave's table
+    std::vector<void *> table;    // per node: one wave's table (scaled: then its row exponents)
     std::vector<int64_t> ld;
+    int32_t *eref = nullptr;      // scaled: [n][wave] reference exponents
     unsigned *status = nullptr;   // [4]: bit 0 colour out of range
     double *ones = nullptr;       // [nb][n] ones for single-vertex templates
     int chunks = 1;
@@ -538,6 +545,24 @@ int64_t table_ld(const Prepared &P, const CNode &c) {
     return (binom(P.kc - 1, c.t - 1) + P.vecn - 1) / P.vecn * P.vecn;
 }
 
+// Bytes of one node's table for wb colourings; scaled tables carry one int16
+// exponent per row after the values (from table_exp_offset).
+size_t table_exp_offset(const Prepared &P, const CNode &c, int wb) {
+    return ((size_t)P.n * wb * table_ld(P, c) * P.esz + 255) / 256 * 256;
+}
+
+size_t table_bytes(const Prepared &P, const CNode &c, int wb) {
+    if (!P.scaled) return (size_t)P.n * wb * table_ld(P, c) * P.esz;
+    return table_exp_offset(P, c, wb) + (size_t)P.n * wb * sizeof(int16_t);
+}
+
+int16_t *table_exps(const Prepared &P, const RunBuffers &R, int node, int wb) {
+    return reinterpret_cast<int16_t *>(static_cast<char *>(R.table[node]) + table_exp_offset(P, P.nodes[node], wb));
+}
+
+// Bytes of a root buffer element: the table type, or double for scaled tables.
+size_t root_esz(const Prepared &P) { return P.scaled ? sizeof(double) : P.esz; }
+
 // Allocates the non-table buffers of a run from `alloc(bytes, &ptr)`.
 template <typename Alloc>
 sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
@@ -553,9 +578,10 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
         if ((st = alloc(R->scratch_bytes, &R->scratch))) return st;
         if ((st = alloc(R->counter_bytes, (void **)&R->counters))) return st;
     }
+    if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R->eref))) return st;
     R->rootbuf.assign(P.plans.size(), nullptr);
     for (size_t pi = 0; pi < P.plans.size(); ++pi)
-        if (P.plan_root[pi] >= 0 && (st = alloc((size_t)P.nb * P.n * P.esz, &R->rootbuf[pi]))) return st;
+        if (P.plan_root[pi] >= 0 && (st = alloc((size_t)P.nb * P.n * root_esz(P), &R->rootbuf[pi]))) return st;
     R->table.assign(P.nodes.size(), nullptr);
     R->ld.assign(P.nodes.size(), 0);
     if ((st = alloc(16, (void **)&R->status))) return st;
@@ -611,7 +637,20 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     A.splits = P.tabs[i].splits;
     A.nsplit = P.tabs[i].nsplit;
     A.root = c.is_root;
-    if (c.is_root) A.root_out = static_cast<char *>(R.rootbuf[P.root_plan[i]]) + (size_t)b0 * P.n * P.esz;
+    if (c.is_root) {
+        char *rb = static_cast<char *>(R.rootbuf[P.root_plan[i]]) + (size_t)b0 * P.n * root_esz(P);
+        if (P.scaled)
+            A.root_out_d = reinterpret_cast<double *>(rb);
+        else
+            A.root_out = rb;
+    }
+    if (P.scaled) {
+        A.scaled = 1;
+        A.owords = sh.owords;
+        A.Eref = R.eref;
+        if (!A.hist) A.Ep = table_exps(P, R, c.passive, wb);
+        if (!A.a_leaf) A.Ea = table_exps(P, R, c.active, wb);
+    }
     A.scratch = R.scratch;
     A.scratch_ld = P.scratch_ld;
     A.counters = R.counters;
@@ -647,9 +686,10 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             NodeArgs A = node_args(P, R, i, b0, wb, wcol);
             if (!c.is_root) {
                 R.ld[i] = table_ld(P, c);
-                if ((st = src.get(i, (size_t)n * wb * R.ld[i] * esz, &R.table[i]))) return st;
+                if ((st = src.get(i, table_bytes(P, c, wb), &R.table[i]))) return st;
                 A.Ms = R.table[i];
                 A.ldt = R.ld[i];
+                if (P.scaled) A.Es = table_exps(P, R, (int)i, wb);
             }
             A.scratch = R.scratch;
             A.scratch_ld = P.scratch_ld;
@@ -657,6 +697,15 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             if (g->nheavy) {
                 SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
                 SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
+            }
+            if (P.scaled && !A.hist) {
+                // reference exponent of every row: the largest among the rows it gathers
+                SG2V_CUDA(cudaMemsetAsync(R.eref, 0x80, (size_t)n * wb * sizeof(int32_t), stream), "memset");
+                timer.begin("eref", (double)wb * (g->nnz * 5.0 + n * 6.0) + 16.0 * g->ntasks);
+                SG2V_CUDA(launch_eref(g->tasks, g->ntasks, R.scol, R.sclr, wcol, n, g->nnz, wb, kc, A.Ep, R.eref,
+                                      P.info.sms, stream),
+                          "eref");
+                timer.end();
             }
             {
                 // algorithmic bytes: each input table, the sorted arc list
@@ -668,12 +717,15 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                 if (!A.hist) bytes += rows * A.Wz * esz;
                 if (!A.a_leaf && !(c.active == c.passive && !A.hist)) bytes += rows * binom(kc - 1, c.a - 1) * esz;
                 bytes += c.is_root ? rows * esz : rows * A.Ws * esz;
+                if (P.scaled) bytes += rows * (A.hist ? 2.0 : 6.0) + (A.a_leaf ? 0.0 : rows * 2.0);
                 char name[64];
-                std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p, P.fp64 ? "fp64" : "fp32");
+                std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p,
+                              P.fp64 ? "fp64" : (P.scaled ? "fp32s" : "fp32"));
                 timer.begin(name, bytes);
             }
-            SG2V_CUDA(launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
-                                  stream),
+            const int grid_cap = P.info.sms * sh.blocks_per_sm;
+            SG2V_CUDA(P.scaled ? launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
+                               : launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream),
                       "node kernel launch");
             timer.end();
             if (c.active != kLeaf && P.nodes[c.active].last_use == (int)i) src.done(c.active);
@@ -684,7 +736,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     for (size_t pi = 0; pi < P.plans.size(); ++pi) {
         double *pvp = pv ? pv + pi * (size_t)nb * n : nullptr;
         const void *vals = P.plan_root[pi] >= 0 ? R.rootbuf[pi] : R.ones;
-        const bool vals_fp64 = P.plan_root[pi] >= 0 ? P.fp64 : true;
+        const bool vals_fp64 = P.plan_root[pi] >= 0 ? (P.fp64 || P.scaled) : true;
         timer.begin("root_reduce", (double)nb * n * ((vals_fp64 ? 8 : 4) + (pvp ? 8 : 0)));
         timer.count_extra(1);
         SG2V_CUDA(launch_root_reduce(vals, vals_fp64, n, nb, pvp, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
@@ -750,7 +802,8 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
         return SG2V_OK;
     };
     // wave-dependent: sorted arcs, split-row scratch, tables
-    for (void *p : {(void *)S->R.scol, (void *)S->R.sclr, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters}) {
+    for (void *p : {(void *)S->R.scol, (void *)S->R.sclr, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters,
+                    (void *)S->R.eref}) {
         if (!p) continue;
         auto it = std::find(S->owned.begin(), S->owned.end(), p);
         if (it != S->owned.end()) {
@@ -766,7 +819,9 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     R.sw = nullptr;
     R.scratch = nullptr;
     R.counters = nullptr;
+    R.eref = nullptr;
     if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R.scol))) return st;
+    if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R.eref))) return st;
     if ((st = alloc((size_t)wave * g->nnz, (void **)&R.sclr))) return st;
     if (g->weighted && (st = alloc((size_t)wave * g->nnz * sizeof(float), (void **)&R.sw))) return st;
     R.scratch_bytes = (size_t)(g->nheavy * wave * P.scratch_ld) * P.esz;
@@ -780,7 +835,7 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
         if (P.nodes[i].is_root) continue;
         R.ld[i] = table_ld(P, P.nodes[i]);
         void *t = nullptr;
-        cudaError_t e = cudaMalloc(&t, std::max<size_t>((size_t)P.n * wave * R.ld[i] * P.esz, 16));
+        cudaError_t e = cudaMalloc(&t, std::max<size_t>(table_bytes(P, P.nodes[i], wave), 16));
         if (e != cudaSuccess) return cuda_fail(e, "session table allocation");
         S->owned_tables.push_back(t);
         R.table[i] = t;
@@ -820,7 +875,10 @@ sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bo
 
 int64_t count_launches(const Prepared &P, int wave) {
     const int64_t waves = (P.nb + wave - 1) / wave;
-    return 1 + waves * (1 + (int64_t)P.nodes.size()) + 2 * (int64_t)P.plans.size() + 1;
+    int64_t per_wave = 1 + (int64_t)P.nodes.size();
+    if (P.scaled)
+        for (const CNode &c : P.nodes) per_wave += c.p != 1;
+    return 1 + waves * per_wave + 2 * (int64_t)P.plans.size() + 1;
 }
 
 sg2v_status copy_out(double *dst, const double *src, size_t count, cudaStream_t stream) {
@@ -915,9 +973,9 @@ sg2v_status sg2v_graph_info(const sg2v_graph *g, int64_t *n, int64_t *nnz, int64
     return SG2V_OK;
 }
 
-sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans,
-                               const int8_t *colours, int32_t B, sg2v_precision precision, double *per_vertex,
-                               double *totals, double *estimates, sg2v_stream stream_) {
+static sg2v_status count_batched_once(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans,
+                                      const int8_t *colours, int32_t B, sg2v_precision precision,
+                                      double *per_vertex, double *totals, double *estimates, sg2v_stream stream_) {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     if (!colours) {
         set_error("null colours");
@@ -1015,6 +1073,18 @@ sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plan
         return SG2V_ERR_FP_OVERFLOW;
     }
     return SG2V_OK;
+}
+
+sg2v_status sg2v_count_batched(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans,
+                               const int8_t *colours, int32_t B, sg2v_precision precision, double *per_vertex,
+                               double *totals, double *estimates, sg2v_stream stream) {
+    sg2v_status st =
+        count_batched_once(g, plans, num_plans, colours, B, precision, per_vertex, totals, estimates, stream);
+    if (st == SG2V_ERR_FP_OVERFLOW && precision == SG2V_FP32)
+        // FP32 tables ran out of exponent range: again with per-row exponents
+        st = count_batched_once(g, plans, num_plans, colours, B, SG2V_FP32_SCALED, per_vertex, totals, estimates,
+                                stream);
+    return st;
 }
 
 sg2v_status sg2v_count(const sg2v_graph *graph, const sg2v_plan *plan, const int8_t *colours,
@@ -1232,6 +1302,10 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     if (!g || !plan || !colours || !grad_weights || flags != 0) {
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (precision == SG2V_FP32_SCALED) {
+        set_error("the backward pass keeps plain FP64 or FP32 tables");
+        return SG2V_ERR_UNSUPPORTED;
     }
     const sg2v_plan *plans[1] = {plan};
     Prepared P;

@@ -112,6 +112,26 @@ struct Vec16<double> {
     }
 };
 
+// 2^d as a float for an exponent difference d <= 0 (0 below the normal range).
+__device__ __forceinline__ float exp2_neg(int d) { return d < -126 ? 0.f : __int_as_float((d + 127) << 23); }
+
+__device__ __forceinline__ int16_t clamp_exp(int e) {
+    return (int16_t)(e > 32767 ? 32767 : (e < -32767 ? -32767 : e));
+}
+
+// A row's reference exponent; rows that gather nothing keep the pre-fill value.
+__device__ __forceinline__ int row_eref(const NodeArgs &A, int64_t rowb) {
+    const int e = A.Eref[rowb];
+    return e < kEmptyRowExp ? kEmptyRowExp : e;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -132,9 +152,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 // (32/G)-th arc of a batch of 32 and owns a private copy of Z, and its lanes
 // cover G*NV 16-byte vectors of the neighbour's compressed row (so narrow rows
 // still fill a warp-wide load).  Copies are folded into copy 0 at the end.
-template <typename T, int G, int NV, bool WEIGHTED>
-__device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1, int b, int cv, T *zbuf,
+template <typename T, int G, int NV, bool WEIGHTED, bool SCALED>
+__device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1, int b, int cv, int eref, T *zbuf,
                                        int lane) {
+    constexpr bool FMA = WEIGHTED || SCALED;
     using V = Vec16<T>;
     using VT = typename V::type;
     constexpr int NG = 32 / G;
@@ -156,6 +177,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     const int32_t *scol = A.scol + (int64_t)b * A.nnz;
     const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
     const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+    const int16_t *Ep = SCALED ? A.Ep + b : nullptr;  // exponent of row (u, b) at Ep[u * nb]
     // the arcs come sorted by neighbour colour: each colour is one run, summed
     // in registers and added to Z(colour) when the run ends
     VT run[NV];
@@ -168,6 +190,8 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
         const int c_l = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
         T w_l = T(1);
         if (WEIGHTED) w_l = lane < cnt ? T(__ldg(sw + base + lane)) : T(0);
+        int ep_l = 0;
+        if (SCALED) ep_l = lane < cnt ? (int)__ldg(Ep + (int64_t)u_l * A.nb) : 0;
         for (int j0 = 0; j0 < cnt; j0 += NG * U) {
             VT x[U][NV];
             T w[U];
@@ -178,8 +202,13 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
                 const int j = j0 + r * NG + grp;
                 const int u = __shfl_sync(kFull, u_l, j & 31);
                 cr[r] = __shfl_sync(kFull, c_l, j & 31);
-                if (WEIGHTED) w[r] = __shfl_sync(kFull, w_l, j & 31);
+                w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j & 31) : T(1);
                 take[r] = j < cnt && cr[r] != cv && cr[r] >= 0;
+                if (SCALED) {
+                    // align the neighbour row's exponent to the row's reference
+                    const int ep = __shfl_sync(kFull, ep_l, j & 31);
+                    w[r] *= take[r] ? T(exp2_neg(ep - eref)) : T(0);
+                }
                 const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                 for (int q = 0; q < NV; ++q) x[r][q] = (take[r] && qok[q]) ? __ldg(row + G * q) : V::zero();
@@ -202,7 +231,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
                 }
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    if (WEIGHTED)
+                    if (FMA)
                         V::fma(run[q], w[r], x[r][q]);
                     else
                         V::add(run[q], x[r][q]);
@@ -347,6 +376,51 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
     }
 }
 
+// Scaled FP32 eMA: outputs go to obuf first; the row is then normalised so
+// its largest value lies in [1, 2) and its exponent is stored beside it.
+// base is the exponent of the unnormalised outputs.  The root writes its
+// row sum as a double with the exponent applied.
+__device__ __forceinline__ void epilogue_scaled(const NodeArgs &A, int v, int b, bool ok, const float *ybuf,
+                                                const float *ma, float *obuf, int base, int lane) {
+    const int64_t rowb = (int64_t)v * A.nb + b;
+    const int ws = A.Ws;
+    float s = 0.f, m = 0.f;
+    if (A.a_leaf) {
+        for (int j = lane; j < ws; j += 32) {
+            const float y = ok ? ybuf[j] : 0.f;
+            obuf[j] = y;
+            s += y;
+            m = fmaxf(m, y);
+        }
+    } else {
+        const int ns = A.nsplit;
+        for (int S = lane; S < ws; S += 32) {
+            float acc = 0.f;
+            if (ok) {
+                const uint32_t *sp = A.splits + (int64_t)S * ns;
+                for (int j = 0; j < ns; ++j) {
+                    const uint32_t x = __ldg(sp + j);
+                    acc = fmaf(ma[x & 0xffffu], ybuf[x >> 16], acc);
+                }
+            }
+            obuf[S] = acc;
+            s += acc;
+            m = fmaxf(m, acc);
+        }
+    }
+    if (A.root) {
+        s = warp_sum(s);
+        if (lane == 0) A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)s, base) : 0.0;
+        return;
+    }
+    m = warp_max(m);
+    const int em = m > 0.f ? ilogbf(m) : 0;
+    __syncwarp();
+    float *out = static_cast<float *>(A.Ms) + rowb * A.ldt;
+    for (int j = lane; j < ws; j += 32) out[j] = ldexpf(obuf[j], -em);
+    if (lane == 0) A.Es[rowb] = m > 0.f ? clamp_exp(base + em) : kEmptyRowExp;
+}
+
 // Resident blocks per SM requested from the compiler (the register cap) for
 // each shape; tuned on B300 (occupancy matters more than a few spills).
 #ifndef SG2V_MINB_F32_NV2
@@ -361,14 +435,15 @@ struct MinBlocks {
         sizeof(T) == 4 ? (NV == 1 ? SG2V_MINB_F32_NV1 : NV == 2 ? SG2V_MINB_F32_NV2 : 2) : (NV == 1 ? 3 : 2);
 };
 
-template <typename T, int G, int NV, bool HIST, bool WEIGHTED>
+template <typename T, int G, int NV, bool HIST, bool WEIGHTED, bool SCALED>
 __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_kernel(const NodeArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    T *zbuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.zwords + A.ywords + A.mwords);
+    T *zbuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.zwords + A.ywords + A.mwords + A.owords);
     T *ybuf = zbuf + A.zwords;
     T *mbuf = ybuf + A.ywords;  // this row's active-child row (a >= 2)
+    T *obuf = mbuf + A.mwords;  // this row's outputs before normalisation (scaled)
     const int zlen = HIST ? A.kc : A.kc * A.wz_pad;
     const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -385,9 +460,14 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             const bool cok = (unsigned)cv < (unsigned)A.kc;
             if (e0 == e1) {
                 // no arcs: Y' = 0, so every output of the row is zero
-                epilogue<T>(A, v, b, false, ybuf, mbuf, lane);
+                if constexpr (SCALED)
+                    epilogue_scaled(A, v, b, false, ybuf, mbuf, obuf, 0, lane);
+                else
+                    epilogue<T>(A, v, b, false, ybuf, mbuf, lane);
                 continue;
             }
+            int eref = 0;
+            if (SCALED && !HIST) eref = row_eref(A, (int64_t)v * A.nb + b);
             if (mchunks && cok) {
                 // start copying the active row now; it is needed only by the eMA
                 const char *src = static_cast<const char *>(A.Ma) + ((int64_t)v * A.nb + b) * A.lda * sizeof(T);
@@ -400,7 +480,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             if (HIST)
                 hist_z<T, WEIGHTED>(A, e0, e1, b, zbuf, lane);
             else
-                spmm_z<T, G, NV, WEIGHTED>(A, e0, e1, b, cv, zbuf, lane);
+                spmm_z<T, G, NV, WEIGHTED, SCALED>(A, e0, e1, b, cv, eref, zbuf, lane);
             __syncwarp();
             if (slot >= 0) {
                 // one chunk of a split row: fold Z into the scratch row; the
@@ -427,7 +507,12 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane);
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
-            epilogue<T>(A, v, b, cok, ybuf, mbuf, lane);
+            if constexpr (SCALED) {
+                const int base = (A.a_leaf ? 0 : (int)A.Ea[(int64_t)v * A.nb + b]) + eref;
+                epilogue_scaled(A, v, b, cok, ybuf, mbuf, obuf, base, lane);
+            } else {
+                epilogue<T>(A, v, b, cok, ybuf, mbuf, lane);
+            }
             __syncwarp();
         }
         task = next;
@@ -442,19 +527,22 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
 constexpr int kWideWarps = 8;
 static_assert(kWideWarps * 32 == kWideThreads, "wide CTA size");
 
-template <typename T, int NV, bool WEIGHTED>
+template <typename T, int NV, bool WEIGHTED, bool SCALED>
 __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const NodeArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = Vec16<T>;
     using VT = typename V::type;
     constexpr int U = NV == 1 ? 4 : 2;
+    constexpr bool FMA = WEIGHTED || SCALED;
     __shared__ int s_last;
     __shared__ T s_red[kWideWarps];
+    __shared__ T s_max[kWideWarps];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int kc = A.kc, wzp = A.wz_pad;  // wzp = kWideWarps * 32 * NV * V::n
     T *zbuf = reinterpret_cast<T *>(smem_raw);
     T *ybuf = zbuf + A.zwords;
     T *mbuf = ybuf + A.ywords;
+    T *obuf = mbuf + A.mwords;  // outputs before normalisation (scaled)
     const int zlen = kc * wzp;
     const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int nvec = (A.Wz + V::n - 1) / V::n;
@@ -470,6 +558,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             const int64_t rowb = (int64_t)v * A.nb + b;
             const int cv = A.colours[(int64_t)b * A.n + v];
             const bool cok = (unsigned)cv < (unsigned)kc && e0 < e1;
+            const int eref = SCALED ? row_eref(A, rowb) : 0;
             if (mchunks && cok) {
                 const char *src = static_cast<const char *>(A.Ma) + rowb * A.lda * sizeof(T);
                 for (int c = tid; c < mchunks; c += blockDim.x) {
@@ -490,6 +579,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                 const int32_t *scol = A.scol + (int64_t)b * A.nnz;
                 const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
                 const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+                const int16_t *Ep = SCALED ? A.Ep + b : nullptr;
                 VT run[NV];
 #pragma unroll
                 for (int q = 0; q < NV; ++q) run[q] = V::zero();
@@ -500,6 +590,8 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                     const int c_l = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
                     T w_l = T(1);
                     if (WEIGHTED) w_l = lane < cnt ? T(__ldg(sw + base + lane)) : T(0);
+                    int ep_l = 0;
+                    if (SCALED) ep_l = lane < cnt ? (int)__ldg(Ep + (int64_t)u_l * A.nb) : 0;
                     for (int j0 = 0; j0 < cnt; j0 += U) {
                         VT x[U][NV];
                         T wr[U];
@@ -512,6 +604,10 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                             cr[r] = __shfl_sync(kFull, c_l, j & 31);
                             wr[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j & 31) : T(1);
                             take[r] = j < cnt && cr[r] != cv && cr[r] >= 0;
+                            if (SCALED) {
+                                const int ep = __shfl_sync(kFull, ep_l, j & 31);
+                                wr[r] *= take[r] ? T(exp2_neg(ep - eref)) : T(0);
+                            }
                             const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                             for (int q = 0; q < NV; ++q)
@@ -535,7 +631,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                             }
 #pragma unroll
                             for (int q = 0; q < NV; ++q) {
-                                if (WEIGHTED)
+                                if (FMA)
                                     V::fma(run[q], wr[r], x[r][q]);
                                 else
                                     V::add(run[q], x[r][q]);
@@ -585,6 +681,52 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             }
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncthreads();
+            if constexpr (SCALED) {
+                // eMA into obuf, then normalise the row by its largest value
+                const int base = (A.a_leaf ? 0 : (int)A.Ea[rowb]) + eref;
+                const int ws = A.Ws, ns = A.nsplit;
+                T sum = T(0), mx = T(0);
+                for (int S = tid; S < ws; S += blockDim.x) {
+                    T acc = T(0);
+                    if (cok) {
+                        if (A.a_leaf) {
+                            acc = ybuf[S];
+                        } else {
+                            const uint32_t *sp = A.splits + (int64_t)S * ns;
+                            for (int j = 0; j < ns; ++j) {
+                                const uint32_t x = __ldg(sp + j);
+                                acc = fma(mbuf[x & 0xffffu], ybuf[x >> 16], acc);
+                            }
+                        }
+                    }
+                    obuf[S] = acc;
+                    sum += acc;
+                    mx = fmax(mx, acc);
+                }
+                sum = warp_sum(sum);
+                mx = warp_max(mx);
+                if (lane == 0) {
+                    s_red[w] = sum;
+                    s_max[w] = mx;
+                }
+                __syncthreads();
+                if (A.root) {
+                    if (tid == 0) {
+                        T t = T(0);
+                        for (int i = 0; i < kWideWarps; ++i) t += s_red[i];
+                        A.root_out_d[(int64_t)b * A.n + v] = cok ? ldexp((double)t, base) : 0.0;
+                    }
+                } else {
+                    T m = T(0);
+                    for (int i = 0; i < kWideWarps; ++i) m = fmax(m, s_max[i]);
+                    const int em = m > T(0) ? ilogb(m) : 0;
+                    T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+                    for (int j = tid; j < ws; j += blockDim.x) out[j] = ldexp(obuf[j], -em);
+                    if (tid == 0) A.Es[rowb] = m > T(0) ? clamp_exp(base + em) : kEmptyRowExp;
+                }
+                __syncthreads();
+                continue;
+            }
             if (A.Yout) {
                 T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
                 for (int j = tid; j < A.wy; j += blockDim.x) yo[j] = cok ? ybuf[j] : T(0);
@@ -633,33 +775,33 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     }
 }
 
-template <typename T, int G, int NV, bool HIST, bool WEIGHTED>
+template <typename T, int G, int NV, bool HIST, bool WEIGHTED, bool SC>
 void *kernel_ptr() {
-    return reinterpret_cast<void *>(&node_kernel<T, G, NV, HIST, WEIGHTED>);
+    return reinterpret_cast<void *>(&node_kernel<T, G, NV, HIST, WEIGHTED, SC>);
 }
 
-template <typename T, bool W>
+template <typename T, bool W, bool SC = false>
 void *pick(bool hist, int g, int nv) {
-    if (hist) return kernel_ptr<T, 32, 1, true, W>();
-    if (g == 4) return kernel_ptr<T, 4, 1, false, W>();
-    if (g == 8) return kernel_ptr<T, 8, 1, false, W>();
-    if (g == 16) return kernel_ptr<T, 16, 1, false, W>();
+    if (hist) return kernel_ptr<T, 32, 1, true, W, SC>();
+    if (g == 4) return kernel_ptr<T, 4, 1, false, W, SC>();
+    if (g == 8) return kernel_ptr<T, 8, 1, false, W, SC>();
+    if (g == 16) return kernel_ptr<T, 16, 1, false, W, SC>();
     switch (nv) {
-        case 1: return kernel_ptr<T, 32, 1, false, W>();
-        case 2: return kernel_ptr<T, 32, 2, false, W>();
-        case 3: return kernel_ptr<T, 32, 3, false, W>();
-        case 4: return kernel_ptr<T, 32, 4, false, W>();
+        case 1: return kernel_ptr<T, 32, 1, false, W, SC>();
+        case 2: return kernel_ptr<T, 32, 2, false, W, SC>();
+        case 3: return kernel_ptr<T, 32, 3, false, W, SC>();
+        case 4: return kernel_ptr<T, 32, 4, false, W, SC>();
         default: return nullptr;
     }
 }
 
-template <typename T, bool W>
+template <typename T, bool W, bool SC = false>
 void *pick_wide(int nv) {
     switch (nv) {
-        case 1: return reinterpret_cast<void *>(&node_wide_kernel<T, 1, W>);
-        case 2: return reinterpret_cast<void *>(&node_wide_kernel<T, 2, W>);
-        case 3: return reinterpret_cast<void *>(&node_wide_kernel<T, 3, W>);
-        case 4: return reinterpret_cast<void *>(&node_wide_kernel<T, 4, W>);
+        case 1: return reinterpret_cast<void *>(&node_wide_kernel<T, 1, W, SC>);
+        case 2: return reinterpret_cast<void *>(&node_wide_kernel<T, 2, W, SC>);
+        case 3: return reinterpret_cast<void *>(&node_wide_kernel<T, 3, W, SC>);
+        case 4: return reinterpret_cast<void *>(&node_wide_kernel<T, 4, W, SC>);
         default: return nullptr;
     }
 }
@@ -673,6 +815,14 @@ void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted) {
     }
     if (fp64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
     return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
+}
+
+void *select_kernel_scaled(bool hist, int g, int nv, bool weighted) {
+    if (g == kWideLanes) {
+        if (hist) return nullptr;
+        return weighted ? pick_wide<float, true, true>(nv) : pick_wide<float, false, true>(nv);
+    }
+    return weighted ? pick<float, true, true>(hist, g, nv) : pick<float, false, true>(hist, g, nv);
 }
 
 // ------------------------------------------------------------- reductions
@@ -764,6 +914,39 @@ __global__ void root_final_kernel(const RootSum *partials, int chunks, int nseg,
     RootSum t = partials[(int64_t)seg * chunks];
     for (int i = 1; i < chunks; ++i) rs_combine(t, partials[(int64_t)seg * chunks + i]);
     out[seg] = t;
+}
+
+// Reference exponent of each row for the scaled FP32 gather: the largest
+// exponent among the passive rows it will add up (arcs to neighbours of a
+// valid colour other than its own), one warp per (task, colouring).  Split
+// rows combine their chunks with atomicMax; Eref is pre-filled below -2^15.
+__global__ void eref_kernel(const int4 *__restrict__ tasks, int64_t ntasks, const int32_t *__restrict__ scol,
+                            const int8_t *__restrict__ sclr, const int8_t *__restrict__ colours, int64_t n,
+                            int64_t nnz, int nb, int kc, const int16_t *__restrict__ Ep, int32_t *Eref) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t items = ntasks * nb;
+    for (int64_t it = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const int64_t ti = it / nb;
+        const int b = (int)(it - ti * nb);
+        const int4 task = tasks[ti];
+        const int cv = colours[(int64_t)b * n + task.x];
+        int m = kEmptyRowExp;
+        for (int64_t e = task.z + lane; e < task.w; e += 32) {
+            const int c = sclr[(int64_t)b * nnz + e];
+            if (c >= 0 && c != cv) {
+                const int u = scol[(int64_t)b * nnz + e];
+                const int x = Ep[(int64_t)u * nb + b];
+                m = x > m ? x : m;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int y = __shfl_xor_sync(kFull, m, o);
+            m = y > m ? y : m;
+        }
+        if (lane == 0 && (unsigned)cv < (unsigned)kc) atomicMax(Eref + (int64_t)task.x * nb + b, m);
+    }
 }
 
 // Stable counting sort by neighbour colour of the arcs of each work-list task
@@ -1005,8 +1188,9 @@ void node_shape(bool fp64, int wz, int *g, int *nv) {
     }
 }
 
-int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
-    void *k = select_kernel(fp64, hist, g, nv, weighted);
+namespace {
+
+int blocks_per_sm(void *k, int threads, size_t smem) {
     if (!k) return 0;
     if (smem > 48 * 1024) {
         // one limit per kernel variant, shared by every node that uses it: the device maximum
@@ -1029,11 +1213,8 @@ int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int t
     return blocks;
 }
 
-cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int threads, size_t smem, int grid_cap,
-                        cudaStream_t stream) {
-    const bool hist = args.hist != 0;
-    const bool weighted = args.weights != nullptr;
-    void *k = select_kernel(fp64, hist, g, nv, weighted);
+cudaError_t launch_variant(void *k, const NodeArgs &args, int g, int threads, size_t smem, int grid_cap,
+                           cudaStream_t stream) {
     if (!k) return cudaErrorInvalidValue;
     if (args.ntasks == 0) return cudaSuccess;
     const int64_t warps_per_block = g == kWideLanes ? 1 : threads / 32;  // wide: one task per CTA
@@ -1043,6 +1224,28 @@ cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int thre
     NodeArgs a = args;
     void *params[] = {&a};
     return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)threads), params, smem, stream);
+}
+
+}  // namespace
+
+int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
+    return blocks_per_sm(select_kernel(fp64, hist, g, nv, weighted), threads, smem);
+}
+
+int node_blocks_per_sm_scaled(bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
+    return blocks_per_sm(select_kernel_scaled(hist, g, nv, weighted), threads, smem);
+}
+
+cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int threads, size_t smem, int grid_cap,
+                        cudaStream_t stream) {
+    void *k = select_kernel(fp64, args.hist != 0, g, nv, args.weights != nullptr);
+    return launch_variant(k, args, g, threads, smem, grid_cap, stream);
+}
+
+cudaError_t launch_node_scaled(const NodeArgs &args, int g, int nv, int threads, size_t smem, int grid_cap,
+                               cudaStream_t stream) {
+    void *k = select_kernel_scaled(args.hist != 0, g, nv, args.weights != nullptr);
+    return launch_variant(k, args, g, threads, smem, grid_cap, stream);
 }
 
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,
@@ -1057,6 +1260,18 @@ cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     root_final_kernel<<<(nseg + 127) / 128, 128, 0, stream>>>(partials, chunks, nseg, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, const int8_t *sclr,
+                        const int8_t *colours, int64_t n, int64_t nnz, int nb, int kc, const int16_t *Ep,
+                        int32_t *Eref, int sms, cudaStream_t stream) {
+    if (ntasks == 0 || nb == 0) return cudaSuccess;
+    const int64_t warps = ntasks * nb;
+    int64_t grid = (warps + 7) / 8;
+    const int64_t cap = (int64_t)sms * 8;
+    if (grid > cap) grid = cap;
+    eref_kernel<<<(unsigned)grid, 256, 0, stream>>>(tasks, ntasks, scol, sclr, colours, n, nnz, nb, kc, Ep, Eref);
     return cudaGetLastError();
 }
 

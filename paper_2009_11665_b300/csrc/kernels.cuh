@@ -56,6 +56,16 @@ struct NodeArgs {
     void *root_out;               // [nb][n]
     const uint32_t *splits;       // [Ws][nsplit] rank(A') | rank(S' - A') << 16 (a >= 2)
     int nsplit;
+    // FP32 range: per-row power-of-two exponents (scaled != 0).  A row's true
+    // values are its stored values times 2^E[row]; Eref[row] is the largest
+    // exponent among the neighbours the row gathers (colour != own colour).
+    int scaled;
+    const int16_t *Ep;            // exponents of the passive table rows (p >= 2)
+    const int16_t *Ea;            // exponents of the active table rows (a >= 2)
+    int16_t *Es;                  // exponents of the output rows (non-root)
+    const int32_t *Eref;          // [n * nb]
+    double *root_out_d;           // root per-vertex values (scaled): [nb][n]
+    int owords;                   // shared-memory words per warp (or CTA) for the output row (scaled)
     // backward support: also store Y' rows (Yout != null); add the output row
     // to the existing one instead of overwriting it (accumulate != 0)
     void *Yout;
@@ -126,8 +136,17 @@ struct RootSum {
     unsigned pad;
 };
 
+// Exponent of a table row whose entries are all zero (scaled FP32).
+constexpr int kEmptyRowExp = -32768;
+
 constexpr unsigned kFlagNotIntegral = 1u;
 constexpr unsigned kFlagNonFinite = 2u;
+
+// Resident blocks per SM / launch of the scaled FP32 variants (per-row exponents).
+int node_blocks_per_sm_scaled(bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
+                              size_t smem);
+cudaError_t launch_node_scaled(const NodeArgs &args, int lanes_per_group, int vec_per_lane, int threads, size_t smem,
+                               int grid_cap, cudaStream_t stream);
 
 // Shape of the gather of compressed rows of wz elements: lanes per neighbour
 // group (4, 8, 16 or 32; kWideLanes when a whole CTA shares one row) and
@@ -153,6 +172,13 @@ cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, in
 // when pv != null and one RootSum per segment.
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,
                                int chunks, RootSum *out, cudaStream_t stream);
+
+// Eref[row] = max over the row's arcs to neighbours of another valid colour
+// of Ep[neighbour row] (Eref pre-filled below kEmptyRowExp, e.g. bytes 0x80; split rows combine
+// chunks with atomicMax).
+cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, const int8_t *sclr,
+                        const int8_t *colours, int64_t n, int64_t nnz, int nb, int kc, const int16_t *Ep,
+                        int32_t *Eref, int sms, cudaStream_t stream);
 
 // Sorts the arcs of every work-list task by neighbour colour (stable) for
 // each of nb colourings: scol/sclr/sw [nb][nnz] (sw only when weights != null).

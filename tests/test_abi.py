@@ -43,6 +43,18 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(lib.EXPORTED) <= declared
 
 
+def test_binding_constants_match_header(lib):
+    """Every enumerator and flag the header defines has the same value in
+    the Python binding (the binding only marshals)."""
+    text = open(os.path.join(ROOT, "include", "sg2v.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = {m[0]: int(m[1]) for m in re.findall(r"\b(SG2V_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    consts.update({m[0]: int(m[1], 16) for m in re.findall(r"#define\s+(SG2V_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u", text)})
+    assert "SG2V_FP32_SCALED" in consts and "SG2V_SESSION_AUTOTUNE" in consts
+    for name, value in consts.items():
+        assert getattr(lib, name) == value, name
+
+
 def test_version_and_status_strings(lib):
     assert lib.sg2v_version() >= 100
     for code in range(10):

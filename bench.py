@@ -229,6 +229,7 @@ def main():
     ap.add_argument("--cpu-baseline-scale", type=int, default=17)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3-template x 64-colouring session block")
+    ap.add_argument("--no-large", action="store_true", help="skip the tree15 (k = 15) large-form block")
     ap.add_argument("--profile-call", choices=["rmat18", "rmat20"], default=None,
                     help="run exactly one count call on R-MAT scale 18 or 20 (avg degree 32, tree10) and exit: "
                          "the case the committed ncu summaries capture")
@@ -351,6 +352,25 @@ def main():
                                       "k=8, one colouring", "forward_ms": ms_f, "forward_and_gradient_ms": ms_b,
                           "dtype": "f32"}
 
+    # large form: R-MAT scale 20 with 5e7 edges, tree15, k = 15, 8 colourings
+    # per call.  Counts reach about 2^155, beyond FP32's range, so the tables
+    # carry per-row exponents (plain FP32 would overflow and be rerun).
+    large = None
+    if not args.no_large:
+        g5 = si.workload_graph("rmat20_50m")
+        graph5 = sg.Graph(g5.row_ptr, g5.col_idx)
+        plan5 = sg.Plan(si.TREE15.parent, 0, 15)
+        B5 = 8
+        cols5 = torch.from_numpy(si.colourings(g5.n, 15, B5 * (rank + 1), seed=0)[rank * B5:(rank + 1) * B5]).cuda()
+        tot5 = torch.empty((1, B5), dtype=torch.float64, device="cuda")
+        ms5 = time_steps(torch, lambda: sg.sg2v_count_batched(graph5.handle, [plan5.handle], cols5, B5,
+                                                              sg.SG2V_FP32_SCALED, None, tot5, None, stream),
+                         2, 1, stream, dist)
+        large = {"workload": "rmat20_50m (R-MAT scale 20, 5e7 edges), tree15, k=15, 8 colourings per call",
+                 "ms_per_call": ms5, "s_per_colouring": ms5 * 1e-3 / B5, "dtype": "f32 with per-row exponents",
+                 "max_total": float(tot5.max().item()), "steps": 2, "warmup": 1}
+        del graph5, g5
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -399,6 +419,7 @@ def main():
         "kernels": kernel_table,
         "batched_3_templates": batched,
         "differentiable": differentiable,
+        "large_form": large,
         "cpu_baseline": cpu,
         "e2e": {"value": ms_e2e * 1e-3 / total_colourings, "unit": UNIT, "h2d_bytes_per_step": int(B * g.n),
                 "d2h_bytes_per_step": int(B * g.n * 8 + 2 * B * 8)},

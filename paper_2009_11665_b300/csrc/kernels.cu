@@ -324,6 +324,73 @@ __device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbu
     }
 }
 
+// eMA (Eq. 1 in squeezed coordinates) of one row by NT threads (tid in
+// [0, NT)).  The root needs only the row sum: every (set, split) product is
+// one item, items are spread over all threads (consecutive threads read
+// consecutive split words) and the per-thread partial sum is returned.  A
+// thread that owns one output set of a non-root row walks its splits in
+// order, so the split table's cache lines serve 32 consecutive steps.
+template <typename T, int NT>
+__device__ __forceinline__ T ema_root_partial(const NodeArgs &A, bool ok, const T *ybuf, const T *ma, int tid) {
+    T s = T(0);
+    if (!ok) return s;
+    if (A.a_leaf) {
+        for (int j = tid; j < A.Ws; j += NT) s += ybuf[j];
+        return s;
+    }
+    const int total = A.Ws * A.nsplit;
+    for (int p = tid; p < total; p += NT) {
+        const uint32_t x = __ldg(A.splits + p);
+        s = fma(ma[x & 0xffffu], ybuf[x >> 16], s);
+    }
+    return s;
+}
+
+// Non-root rows: put(S, value) once per output set S.  Groups of L lanes
+// (a power of two, L <= 32) share one set when there are fewer sets than
+// threads, each lane taking every L-th split (adjacent words); with many
+// sets L = 1.
+template <typename T, int NT, typename F>
+__device__ __forceinline__ void ema_rows(const NodeArgs &A, bool ok, const T *ybuf, const T *ma, int tid,
+                                         F &&put) {
+    const int ws = A.Ws;
+    if (A.a_leaf) {
+        for (int S = tid; S < ws; S += NT) put(S, ok ? ybuf[S] : T(0));
+        return;
+    }
+    const int ns = A.nsplit;
+    int L = 32;
+    while (L > 1 && NT / L < ws) L >>= 1;
+    if (L == 1) {
+        for (int S = tid; S < ws; S += NT) {
+            T acc = T(0);
+            if (ok) {
+                const uint32_t *sp = A.splits + (int64_t)S * ns;
+                for (int j = 0; j < ns; ++j) {
+                    const uint32_t x = __ldg(sp + j);
+                    acc = fma(ma[x & 0xffffu], ybuf[x >> 16], acc);
+                }
+            }
+            put(S, acc);
+        }
+        return;
+    }
+    const int grp = tid / L, j0 = tid & (L - 1);
+    for (int S0 = 0; S0 < ws; S0 += NT / L) {
+        const int S = S0 + grp;
+        T acc = T(0);
+        if (ok && S < ws) {
+            const uint32_t *sp = A.splits + (int64_t)S * ns;
+            for (int j = j0; j < ns; j += L) {
+                const uint32_t x = __ldg(sp + j);
+                acc = fma(ma[x & 0xffffu], ybuf[x >> 16], acc);
+            }
+        }
+        for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (j0 == 0 && S < ws) put(S, acc);
+    }
+}
+
 // eMA in squeezed coordinates from Y' in ybuf:
 //   M_s'(v, S') = sum over (a-1)-subsets A' of S' of M_a'(v, A') * Y'(S' - A'),
 // or M_s' = Y' when the active child is a single vertex.  The root sums its
@@ -333,47 +400,18 @@ template <typename T>
 __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool ok, const T *ybuf, const T *ma,
                                          int lane) {
     const int64_t rowb = (int64_t)v * A.nb + b;
-    const int ws = A.Ws;
-    T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
-    T s = T(0);
     if (A.Yout) {
         T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
         for (int j = lane; j < A.wy; j += 32) yo[j] = ok ? ybuf[j] : T(0);
     }
-    if (A.a_leaf) {
-        for (int j = lane; j < ws; j += 32) {
-            const T y = ok ? ybuf[j] : T(0);
-            if (A.root)
-                s += y;
-            else
-                out[j] = A.accumulate ? out[j] + y : y;
-        }
-    } else {
-        const int ns = A.nsplit;
-        if (A.root) {
-            const int total = ok ? ws * ns : 0;
-            for (int p = lane; p < total; p += 32) {
-                const uint32_t sp = __ldg(A.splits + p);
-                s = fma(ma[sp & 0xffffu], ybuf[sp >> 16], s);
-            }
-        } else {
-            for (int S = lane; S < ws; S += 32) {
-                const uint32_t *sp = A.splits + (int64_t)S * ns;
-                T acc = T(0);
-                if (ok) {
-                    for (int j = 0; j < ns; ++j) {
-                        const uint32_t x = __ldg(sp + j);
-                        acc = fma(ma[x & 0xffffu], ybuf[x >> 16], acc);
-                    }
-                }
-                out[S] = acc;
-            }
-        }
-    }
     if (A.root) {
-        s = warp_sum(s);
+        const T s = warp_sum(ema_root_partial<T, 32>(A, ok, ybuf, ma, lane));
         if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = s;
+        return;
     }
+    T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+    const bool accumulate = A.accumulate != 0;
+    ema_rows<T, 32>(A, ok, ybuf, ma, lane, [&](int S, T x) { out[S] = accumulate ? out[S] + x : x; });
 }
 
 // Scaled FP32 eMA: outputs go to obuf first; the row is then normalised so
@@ -383,41 +421,21 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
 __device__ __forceinline__ void epilogue_scaled(const NodeArgs &A, int v, int b, bool ok, const float *ybuf,
                                                 const float *ma, float *obuf, int base, int lane) {
     const int64_t rowb = (int64_t)v * A.nb + b;
-    const int ws = A.Ws;
-    float s = 0.f, m = 0.f;
-    if (A.a_leaf) {
-        for (int j = lane; j < ws; j += 32) {
-            const float y = ok ? ybuf[j] : 0.f;
-            obuf[j] = y;
-            s += y;
-            m = fmaxf(m, y);
-        }
-    } else {
-        const int ns = A.nsplit;
-        for (int S = lane; S < ws; S += 32) {
-            float acc = 0.f;
-            if (ok) {
-                const uint32_t *sp = A.splits + (int64_t)S * ns;
-                for (int j = 0; j < ns; ++j) {
-                    const uint32_t x = __ldg(sp + j);
-                    acc = fmaf(ma[x & 0xffffu], ybuf[x >> 16], acc);
-                }
-            }
-            obuf[S] = acc;
-            s += acc;
-            m = fmaxf(m, acc);
-        }
-    }
     if (A.root) {
-        s = warp_sum(s);
+        const float s = warp_sum(ema_root_partial<float, 32>(A, ok, ybuf, ma, lane));
         if (lane == 0) A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)s, base) : 0.0;
         return;
     }
+    float m = 0.f;
+    ema_rows<float, 32>(A, ok, ybuf, ma, lane, [&](int S, float x) {
+        obuf[S] = x;
+        m = fmaxf(m, x);
+    });
     m = warp_max(m);
     const int em = m > 0.f ? ilogbf(m) : 0;
     __syncwarp();
     float *out = static_cast<float *>(A.Ms) + rowb * A.ldt;
-    for (int j = lane; j < ws; j += 32) out[j] = ldexpf(obuf[j], -em);
+    for (int j = lane; j < A.Ws; j += 32) out[j] = ldexpf(obuf[j], -em);
     if (lane == 0) A.Es[rowb] = m > 0.f ? clamp_exp(base + em) : kEmptyRowExp;
 }
 
@@ -681,94 +699,45 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             }
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncthreads();
-            if constexpr (SCALED) {
-                // eMA into obuf, then normalise the row by its largest value
-                const int base = (A.a_leaf ? 0 : (int)A.Ea[rowb]) + eref;
-                const int ws = A.Ws, ns = A.nsplit;
-                T sum = T(0), mx = T(0);
-                for (int S = tid; S < ws; S += blockDim.x) {
-                    T acc = T(0);
-                    if (cok) {
-                        if (A.a_leaf) {
-                            acc = ybuf[S];
-                        } else {
-                            const uint32_t *sp = A.splits + (int64_t)S * ns;
-                            for (int j = 0; j < ns; ++j) {
-                                const uint32_t x = __ldg(sp + j);
-                                acc = fma(mbuf[x & 0xffffu], ybuf[x >> 16], acc);
-                            }
-                        }
-                    }
-                    obuf[S] = acc;
-                    sum += acc;
-                    mx = fmax(mx, acc);
-                }
-                sum = warp_sum(sum);
-                mx = warp_max(mx);
-                if (lane == 0) {
-                    s_red[w] = sum;
-                    s_max[w] = mx;
-                }
-                __syncthreads();
-                if (A.root) {
-                    if (tid == 0) {
-                        T t = T(0);
-                        for (int i = 0; i < kWideWarps; ++i) t += s_red[i];
-                        A.root_out_d[(int64_t)b * A.n + v] = cok ? ldexp((double)t, base) : 0.0;
-                    }
-                } else {
-                    T m = T(0);
-                    for (int i = 0; i < kWideWarps; ++i) m = fmax(m, s_max[i]);
-                    const int em = m > T(0) ? ilogb(m) : 0;
-                    T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
-                    for (int j = tid; j < ws; j += blockDim.x) out[j] = ldexp(obuf[j], -em);
-                    if (tid == 0) A.Es[rowb] = m > T(0) ? clamp_exp(base + em) : kEmptyRowExp;
-                }
-                __syncthreads();
-                continue;
-            }
-            if (A.Yout) {
+            if (!SCALED && A.Yout) {
                 T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
                 for (int j = tid; j < A.wy; j += blockDim.x) yo[j] = cok ? ybuf[j] : T(0);
             }
-            // eMA in squeezed coordinates
-            const int ws = A.Ws;
-            T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
-            T acc_root = T(0);
-            if (A.a_leaf) {
-                for (int j = tid; j < ws; j += blockDim.x) {
-                    const T y = cok ? ybuf[j] : T(0);
-                    if (A.root)
-                        acc_root += y;
-                    else
-                        out[j] = A.accumulate ? out[j] + y : y;
-                }
-            } else {
-                const int ns = A.nsplit;
-                for (int S = tid; S < ws; S += blockDim.x) {
-                    T acc = T(0);
-                    if (cok) {
-                        const uint32_t *sp = A.splits + (int64_t)S * ns;
-                        for (int j = 0; j < ns; ++j) {
-                            const uint32_t x = __ldg(sp + j);
-                            acc = fma(mbuf[x & 0xffffu], ybuf[x >> 16], acc);
-                        }
-                    }
-                    if (A.root)
-                        acc_root += acc;
-                    else
-                        out[S] = acc;
-                }
-            }
+            // eMA in squeezed coordinates over the whole CTA
+            const int base = SCALED ? (A.a_leaf ? 0 : (int)A.Ea[rowb]) + eref : 0;
             if (A.root) {
-                acc_root = warp_sum(acc_root);
-                if (lane == 0) s_red[w] = acc_root;
+                T sum = warp_sum(ema_root_partial<T, kWideThreads>(A, cok, ybuf, mbuf, tid));
+                if (lane == 0) s_red[w] = sum;
                 __syncthreads();
                 if (tid == 0) {
                     T t = T(0);
                     for (int i = 0; i < kWideWarps; ++i) t += s_red[i];
-                    static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = t;
+                    if constexpr (SCALED)
+                        A.root_out_d[(int64_t)b * A.n + v] = cok ? ldexp((double)t, base) : 0.0;
+                    else
+                        static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = t;
                 }
+            } else if constexpr (SCALED) {
+                // outputs to obuf, then the row is normalised by its largest value
+                T mx = T(0);
+                ema_rows<T, kWideThreads>(A, cok, ybuf, mbuf, tid, [&](int S, T x) {
+                    obuf[S] = x;
+                    mx = fmax(mx, x);
+                });
+                mx = warp_max(mx);
+                if (lane == 0) s_max[w] = mx;
+                __syncthreads();
+                T m = T(0);
+                for (int i = 0; i < kWideWarps; ++i) m = fmax(m, s_max[i]);
+                const int em = m > T(0) ? ilogb(m) : 0;
+                T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+                for (int j = tid; j < A.Ws; j += blockDim.x) out[j] = ldexp(obuf[j], -em);
+                if (tid == 0) A.Es[rowb] = m > T(0) ? clamp_exp(base + em) : kEmptyRowExp;
+            } else {
+                T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+                const bool accumulate = A.accumulate != 0;
+                ema_rows<T, kWideThreads>(A, cok, ybuf, mbuf, tid,
+                                          [&](int S, T x) { out[S] = accumulate ? out[S] + x : x; });
             }
             __syncthreads();
         }

@@ -60,38 +60,6 @@ static inline uint32_t next_same_popcount(uint32_t x) {
     return (((r ^ x) >> 2) / c) | r;
 }
 
-void build_tables(int kc, int t, int a, ColumnTables *out) {
-    const int64_t wt = binom(kc, t);
-    out->gather.clear();
-    out->splits.clear();
-    out->nsplit = 0;
-    if (a == 1) {
-        out->gather.assign((size_t)(kc * wt), -1);
-        uint32_t S = (1u << t) - 1;
-        for (int64_t s = 0; s < wt; ++s, S = next_same_popcount(S)) {
-            for (int c = 0; c < kc; ++c)
-                if (S >> c & 1u) out->gather[(size_t)(c * wt + s)] = (int32_t)colex_rank(S ^ (1u << c));
-        }
-        return;
-    }
-    const int ns = (int)binom(t, a);
-    out->nsplit = ns;
-    out->splits.resize((size_t)(wt * ns));
-    uint32_t S = (1u << t) - 1;
-    for (int64_t s = 0; s < wt; ++s, S = next_same_popcount(S)) {
-        int j = 0;
-        // sub-masks of S in increasing order, keeping those with a elements
-        for (uint32_t A = 0;;) {
-            A = (A - S) & S;  // next sub-mask of S
-            if (A == 0) break;
-            if (__builtin_popcount(A) == a) {
-                out->splits[(size_t)(s * ns + j)] = colex_rank(A) | (colex_rank(S ^ A) << 16);
-                ++j;
-            }
-        }
-    }
-}
-
 uint32_t squeeze_colour(uint32_t mask, int c) {
     const uint32_t low = (1u << c) - 1u;
     return (mask & low) | ((mask >> (c + 1)) << c);

@@ -45,7 +45,8 @@ struct CompressedTables {
     std::vector<uint16_t> expand;
     int wy = 0;
     // eMA splits in squeezed coordinates (a >= 2): for each (t-1)-set S',
-    // nsplit pairs rank(A') | rank(S' - A') << 16 over the (a-1)-subsets A'.
+    // nsplit pairs rank(A') | rank(S' - A') << 16 over the (a-1)-subsets A'
+    // (set-major: a thread that owns one set walks consecutive words).
     std::vector<uint32_t> splits;
     int nsplit = 0;
 };
@@ -75,14 +76,6 @@ struct BackwardTables {
     int narc = 0;
 };
 
-struct ColumnTables {
-    // gather[c * Wt + rank(S)] = rank(S minus {c}) if c in S else -1 (a = 1 nodes)
-    std::vector<int32_t> gather;
-    // splits[rank(S) * nsplit + j] = rank(S_a) | rank(S minus S_a) << 16
-    std::vector<uint32_t> splits;
-    int nsplit = 0;
-};
-
 }  // namespace sg2v
 
 struct sg2v_plan {
@@ -96,8 +89,6 @@ struct sg2v_plan {
 };
 
 namespace sg2v {
-// Builds the split tables of node (t, a) for kc colours.
-void build_tables(int kc, int t, int a, ColumnTables *out);
 // Builds the colour-compressed tables of node (t, a, p) for kc colours with
 // Z rows of wz_pad entries.
 void build_compressed_tables(int kc, int t, int a, int wz_pad, CompressedTables *out);

@@ -196,8 +196,10 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
 
 
 def profile_call(args):
-    """One sg2v_count_batched call (B = --batch colourings) of tree10 on an
-    R-MAT graph with the workload's parameters and average degree 32."""
+    """One sg2v_count_batched call (B = --batch colourings): tree10 on an
+    R-MAT graph with the workload's parameters and average degree 32
+    (rmat18, rmat20), or tree15 with k = 15 on the large form's scale-17
+    sibling (large17: 6.25e6 edges, average degree about 95)."""
     import torch
 
     import __graft_entry__
@@ -206,11 +208,16 @@ def profile_call(args):
     import paper_2009_11665_b300 as sg
 
     torch.cuda.set_device(0)
-    scale = 18 if args.profile_call == "rmat18" else 20
-    g = si.rmat(scale, (1 << scale) * 16, seed=0)
+    if args.profile_call == "large17":
+        g = si.rmat(17, 50_000_000 >> 3, seed=0)
+        template, kc = si.TREE15, 15
+    else:
+        scale = 18 if args.profile_call == "rmat18" else 20
+        g = si.rmat(scale, (1 << scale) * 16, seed=0)
+        template, kc = TEMPLATE, K_COLOURS
     graph = sg.Graph(g.row_ptr, g.col_idx)
-    plan = sg.Plan(TEMPLATE.parent, 0, K_COLOURS)
-    cols = torch.from_numpy(si.colourings(g.n, K_COLOURS, args.batch, seed=0)).cuda()
+    plan = sg.Plan(template.parent, 0, kc)
+    cols = torch.from_numpy(si.colourings(g.n, kc, args.batch, seed=0)).cuda()
     tot = torch.empty((1, args.batch), dtype=torch.float64, device="cuda")
     sg.sg2v_count_batched(graph.handle, [plan.handle], cols, args.batch, sg.PRECISIONS[args.precision], None, tot)
     torch.cuda.synchronize()
@@ -230,10 +237,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3-template x 64-colouring session block")
     ap.add_argument("--no-large", action="store_true", help="skip the tree15 (k = 15) large-form block")
-    ap.add_argument("--profile-call", choices=["rmat18", "rmat20"], default=None,
-                    help="run exactly one count call on R-MAT scale 18 or 20 (avg degree 32, tree10) and exit: "
-                         "the case the committed ncu summaries capture")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--profile-call", choices=["rmat18", "rmat20", "large17"], default=None,
+                    help="run exactly one count call (R-MAT scale 18 or 20 with avg degree 32 and tree10, or the "
+                         "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
+                         "summaries capture")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled"], default="fp32")
     args = ap.parse_args()
     if args.profile_call:
         profile_call(args)

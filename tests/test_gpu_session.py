@@ -133,3 +133,23 @@ def test_session_single_vertex_and_weighted(sg):
     for b in range(2):
         ref = oracle.count(g.row_ptr, g.col_idx, si.TREE8.parent, 0, cols[b], weights=w)
         _check("fp64", pv[1, b].cpu().numpy(), tot[1, b].item(), ref)
+
+
+def test_estimator_loop_on_a_session(sg):
+    """Alg. 1's loop driven by a session (the GPU counter): the same
+    colourings through the exact oracle give the same average."""
+    from paper_2009_11665_b300 import estimator as E
+
+    g = si.erdos_renyi(500, 2500, seed=8)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(si.PATH5.parent)
+    ses = sg.Session(graph, [plan], 8, "fp64")
+    colouring = lambda i: si.colouring(g.n, 5, 21, i)
+    res = E.ColourCodingEstimator(E.session_counter(ses), colouring, 5, eps=0.02, delta=0.05, wave=8,
+                                  min_colourings=16, max_colourings=96).run()
+    alpha = oracle.automorphisms(si.PATH5.parent)
+    vals = []
+    for i in range(res.colourings):
+        tot = oracle.count(g.row_ptr, g.col_idx, si.PATH5.parent, 0, colouring(i), per_vertex=False).total
+        vals.append(float(oracle.estimate(tot, 5, alpha)))
+    assert res.estimate[0] == pytest.approx(np.mean(vals), rel=1e-12)

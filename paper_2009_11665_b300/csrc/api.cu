@@ -545,15 +545,32 @@ int64_t table_ld(const Prepared &P, const CNode &c) {
     return (binom(P.kc - 1, c.t - 1) + P.vecn - 1) / P.vecn * P.vecn;
 }
 
+// A table that node kernels gather from has n + 1 vertex rows: row n (one
+// row per colouring) is zero and takes the gathers of arcs that add nothing,
+// and kGatherPad bytes after the rows cover loads of a whole register tile
+// from the last row (a warp: at most 32 x 4 vectors of 16 bytes; a
+// CTA-per-row kernel: 8 warps x 32 x 4 vectors).
+constexpr size_t kGatherPad = 16384;
+
+size_t gather_table_bytes(int64_t n, int wb, int64_t ld, size_t esz) {
+    return (size_t)(n + 1) * wb * ld * esz + kGatherPad;
+}
+
+sg2v_status zero_gather_row(void *table, int64_t n, int wb, int64_t ld, size_t esz, cudaStream_t stream) {
+    SG2V_CUDA(cudaMemsetAsync(static_cast<char *>(table) + (size_t)n * wb * ld * esz, 0, (size_t)wb * ld * esz, stream),
+              "memset");
+    return SG2V_OK;
+}
+
 // Bytes of one node's table for wb colourings; scaled tables carry one int16
 // exponent per row after the values (from table_exp_offset).
 size_t table_exp_offset(const Prepared &P, const CNode &c, int wb) {
-    return ((size_t)P.n * wb * table_ld(P, c) * P.esz + 255) / 256 * 256;
+    return (gather_table_bytes(P.n, wb, table_ld(P, c), P.esz) + 255) / 256 * 256;
 }
 
 size_t table_bytes(const Prepared &P, const CNode &c, int wb) {
-    if (!P.scaled) return (size_t)P.n * wb * table_ld(P, c) * P.esz;
-    return table_exp_offset(P, c, wb) + (size_t)P.n * wb * sizeof(int16_t);
+    if (!P.scaled) return gather_table_bytes(P.n, wb, table_ld(P, c), P.esz);
+    return table_exp_offset(P, c, wb) + (size_t)(P.n + 1) * wb * sizeof(int16_t);
 }
 
 int16_t *table_exps(const Prepared &P, const RunBuffers &R, int node, int wb) {
@@ -687,6 +704,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             if (!c.is_root) {
                 R.ld[i] = table_ld(P, c);
                 if ((st = src.get(i, table_bytes(P, c, wb), &R.table[i]))) return st;
+                if ((st = zero_gather_row(R.table[i], n, wb, R.ld[i], esz, stream))) return st;
                 A.Ms = R.table[i];
                 A.ldt = R.ld[i];
                 if (P.scaled) A.Es = table_exps(P, R, (int)i, wb);
@@ -1436,7 +1454,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         NodeArgs A = node_args(Pw, R, i, 0, 1, d_col);
         if (!c.is_root) {
             R.ld[i] = table_ld(P, c);
-            if ((st = alloc((size_t)n * R.ld[i] * esz, &R.table[i]))) return st;
+            if ((st = alloc(gather_table_bytes(n, 1, R.ld[i], esz), &R.table[i]))) return st;
+            if ((st = zero_gather_row(R.table[i], n, 1, R.ld[i], esz, stream))) return st;
             if ((st = alloc((size_t)n * R.ld[i] * esz, &gt[i]))) return st;
             SG2V_CUDA(cudaMemsetAsync(gt[i], 0, (size_t)n * R.ld[i] * esz, stream), "memset");
             A.Ms = R.table[i];
@@ -1481,7 +1500,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         const int wy = (int)binom(kc - 1, c.p), wa = (int)binom(kc - 1, c.a - 1), ws_ = (int)binom(kc - 1, c.t - 1);
         void *ybar;
         const int64_t ldyb = ldy[ii];
-        if ((st = alloc((size_t)n * ldyb * esz, &ybar))) return st;
+        if ((st = alloc(gather_table_bytes(n, 1, ldyb, esz), &ybar))) return st;
+        if ((st = zero_gather_row(ybar, n, 1, ldyb, esz, stream))) return st;
         BwdEmaArgs E;
         std::memset(&E, 0, sizeof E);
         E.n = n;

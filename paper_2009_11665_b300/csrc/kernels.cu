@@ -40,9 +40,6 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef SG2V_PACKED
 #define SG2V_PACKED 1
 #endif
-#ifndef SG2V_ZEROFILL
-#define SG2V_ZEROFILL 1
-#endif
 constexpr int kMaxHistColours = 16;
 
 template <typename T>
@@ -168,6 +165,13 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     for (int i = lane; i < NG * zlen / V::n; i += 32) zv[i] = V::zero();
     __syncwarp();
     T *zg = zbuf + grp * zlen;
+    static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
+    // FP64 adds are scarce on this part: there, arcs that read the zero row
+    // skip their load and adds, and lanes past the row's last vector load
+    // nothing.  FP32 loads stay unpredicated (measured faster): lanes past
+    // the last vector read the next row or the table's padding into Z
+    // columns that nothing reads.
+    constexpr bool SKIP_ZERO = sizeof(T) == 8;
     const int nvec = (A.Wz + V::n - 1) / V::n;
     bool qok[NV];
 #pragma unroll
@@ -179,43 +183,53 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
     const int16_t *Ep = SCALED ? A.Ep + b : nullptr;  // exponent of row (u, b) at Ep[u * nb]
     // the arcs come sorted by neighbour colour: each colour is one run, summed
-    // in registers and added to Z(colour) when the run ends
+    // in registers and added to Z(colour) when the run ends.  Arcs that add
+    // nothing (neighbours of v's own colour or of an invalid colour, lanes
+    // past the end) read the table's zero row (vertex n) and count as v's own
+    // colour, whose Z row the expansion never reads.
     VT run[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) run[q] = V::zero();
     int cur = -1;
+    const int zero_row = (int)A.n;
+    // Z row that takes the zero rows: v's own colour, or colour 0 when v's
+    // colour is invalid (adding zeros changes no Z row)
+    const int sink = (unsigned)cv < (unsigned)kc ? cv : 0;
     for (int64_t base = e0; base < e1; base += 32) {
         const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
-        const int u_l = lane < cnt ? __ldg(scol + base + lane) : 0;
-        const int c_l = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
+        const int c_in = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
+        const bool t_l = c_in >= 0 && c_in != cv;
+        const int u_l = t_l ? __ldg(scol + base + lane) : zero_row;
+        const int c_l = t_l ? c_in : sink;
         T w_l = T(1);
-        if (WEIGHTED) w_l = lane < cnt ? T(__ldg(sw + base + lane)) : T(0);
-        int ep_l = 0;
-        if (SCALED) ep_l = lane < cnt ? (int)__ldg(Ep + (int64_t)u_l * A.nb) : 0;
+        if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + lane)) : T(0);
+        int ep_l = eref;
+        if (SCALED && t_l) ep_l = (int)__ldg(Ep + (int64_t)u_l * A.nb);
         for (int j0 = 0; j0 < cnt; j0 += NG * U) {
             VT x[U][NV];
             T w[U];
             int cr[U];
-            bool take[U];
+            bool live[U];
 #pragma unroll
             for (int r = 0; r < U; ++r) {
                 const int j = j0 + r * NG + grp;
-                const int u = __shfl_sync(kFull, u_l, j & 31);
-                cr[r] = __shfl_sync(kFull, c_l, j & 31);
-                w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j & 31) : T(1);
-                take[r] = j < cnt && cr[r] != cv && cr[r] >= 0;
+                const int u = __shfl_sync(kFull, u_l, j);
+                live[r] = !SKIP_ZERO || u != zero_row;
+                cr[r] = __shfl_sync(kFull, c_l, j);
+                w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
                 if (SCALED) {
                     // align the neighbour row's exponent to the row's reference
-                    const int ep = __shfl_sync(kFull, ep_l, j & 31);
-                    w[r] *= take[r] ? T(exp2_neg(ep - eref)) : T(0);
+                    const int ep = __shfl_sync(kFull, ep_l, j);
+                    w[r] *= T(exp2_neg(ep - eref));
                 }
                 const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
-                for (int q = 0; q < NV; ++q) x[r][q] = (take[r] && qok[q]) ? __ldg(row + G * q) : V::zero();
+                for (int q = 0; q < NV; ++q)
+                    x[r][q] = (!SKIP_ZERO || (live[r] && qok[q])) ? __ldg(row + G * q) : V::zero();
             }
 #pragma unroll
             for (int r = 0; r < U; ++r) {
-                if (!take[r]) continue;
+                if (!live[r]) continue;
                 if (cr[r] != cur) {
                     if (cur >= 0) {
                         VT *zr = reinterpret_cast<VT *>(zg + cur * wzp) + gl;
@@ -551,6 +565,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     using V = Vec16<T>;
     using VT = typename V::type;
     constexpr int U = NV == 1 ? 4 : 2;
+    static_assert(32 % U == 0, "a step's arcs must stay inside one batch of 32");
     constexpr bool FMA = WEIGHTED || SCALED;
     __shared__ int s_last;
     __shared__ T s_red[kWideWarps];
@@ -602,38 +617,41 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
 #pragma unroll
                 for (int q = 0; q < NV; ++q) run[q] = V::zero();
                 int cur = -1;
+                // arcs that add nothing read the zero row (vertex n) into Z(cv),
+                // as in spmm_z (cv is valid here); FP32 loads are unpredicated
+                // (the table padding covers a whole CTA tile past the last row)
+                const int zero_row = (int)A.n;
                 for (int64_t base = e0; base < e1; base += 32) {
                     const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
-                    const int u_l = lane < cnt ? __ldg(scol + base + lane) : 0;
-                    const int c_l = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
+                    const int c_in = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
+                    const bool t_l = c_in >= 0 && c_in != cv;
+                    const int u_l = t_l ? __ldg(scol + base + lane) : zero_row;
+                    const int c_l = t_l ? c_in : cv;
                     T w_l = T(1);
-                    if (WEIGHTED) w_l = lane < cnt ? T(__ldg(sw + base + lane)) : T(0);
-                    int ep_l = 0;
-                    if (SCALED) ep_l = lane < cnt ? (int)__ldg(Ep + (int64_t)u_l * A.nb) : 0;
+                    if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + lane)) : T(0);
+                    int ep_l = eref;
+                    if (SCALED && t_l) ep_l = (int)__ldg(Ep + (int64_t)u_l * A.nb);
                     for (int j0 = 0; j0 < cnt; j0 += U) {
                         VT x[U][NV];
                         T wr[U];
                         int cr[U];
-                        bool take[U];
 #pragma unroll
                         for (int r = 0; r < U; ++r) {
                             const int j = j0 + r;
-                            const int u = __shfl_sync(kFull, u_l, j & 31);
-                            cr[r] = __shfl_sync(kFull, c_l, j & 31);
-                            wr[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j & 31) : T(1);
-                            take[r] = j < cnt && cr[r] != cv && cr[r] >= 0;
+                            const int u = __shfl_sync(kFull, u_l, j);
+                            cr[r] = __shfl_sync(kFull, c_l, j);
+                            wr[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
                             if (SCALED) {
-                                const int ep = __shfl_sync(kFull, ep_l, j & 31);
-                                wr[r] *= take[r] ? T(exp2_neg(ep - eref)) : T(0);
+                                const int ep = __shfl_sync(kFull, ep_l, j);
+                                wr[r] *= T(exp2_neg(ep - eref));
                             }
                             const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                             for (int q = 0; q < NV; ++q)
-                                x[r][q] = (take[r] && qok[q]) ? __ldg(row + 32 * q) : V::zero();
+                                x[r][q] = (sizeof(T) == 4 || qok[q]) ? __ldg(row + 32 * q) : V::zero();
                         }
 #pragma unroll
                         for (int r = 0; r < U; ++r) {
-                            if (!take[r]) continue;
                             if (cr[r] != cur) {
                                 if (cur >= 0) {
                                     VT *zr = reinterpret_cast<VT *>(zbuf + cur * wzp) + vbase;

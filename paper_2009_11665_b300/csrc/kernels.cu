@@ -40,6 +40,9 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef SG2V_PACKED
 #define SG2V_PACKED 1
 #endif
+#ifndef SG2V_LDG_MODE
+#define SG2V_LDG_MODE 0
+#endif
 constexpr int kMaxHistColours = 16;
 
 template <typename T>
@@ -109,6 +112,29 @@ struct Vec16<double> {
     }
 };
 
+// Load of one 16-byte vector of a gathered table row.  SG2V_LDG_MODE picks
+// the cache policy: 0 read-only path, 1 no L1 allocation, 2 with a 256-byte
+// L2 prefetch, 3 both.
+__device__ __forceinline__ float4 ldg_row(const float4 *p) {
+#if SG2V_LDG_MODE == 0
+    return __ldg(p);
+#else
+    float4 v;
+#if SG2V_LDG_MODE == 1
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+#elif SG2V_LDG_MODE == 2
+    asm("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+#else
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+#endif
+    return v;
+#endif
+}
+
+__device__ __forceinline__ double2 ldg_row(const double2 *p) { return __ldg(p); }
+
 // 2^d as a float for an exponent difference d <= 0 (0 below the normal range).
 __device__ __forceinline__ float exp2_neg(int d) { return d < -126 ? 0.f : __int_as_float((d + 127) << 23); }
 
@@ -162,8 +188,6 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     const int wzp = A.wz_pad;  // = G * NV * V::n
     const int zlen = kc * wzp;
     VT *zv = reinterpret_cast<VT *>(zbuf);
-    for (int i = lane; i < NG * zlen / V::n; i += 32) zv[i] = V::zero();
-    __syncwarp();
     T *zg = zbuf + grp * zlen;
     static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
     // FP64 adds are scarce on this part: there, arcs that read the zero row
@@ -187,13 +211,27 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     // nothing (neighbours of v's own colour or of an invalid colour, lanes
     // past the end) read the table's zero row (vertex n) and count as v's own
     // colour, whose Z row the expansion never reads.
+    // A colour is one run per group, so its Z row is written once, without
+    // reading it first; rows of colours with no arcs are zeroed at the end,
+    // and the row of v's own colour (read by nothing) is left alone.
     VT run[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) run[q] = V::zero();
     int cur = -1;
+    uint32_t seen = 0;  // colours whose Z row this group has written
+    auto flush = [&](int c) {
+        if (c != cv) {
+            VT *zr = reinterpret_cast<VT *>(zg + c * wzp) + gl;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) zr[G * q] = run[q];
+            seen |= 1u << c;
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) run[q] = V::zero();
+    };
     const int zero_row = (int)A.n;
-    // Z row that takes the zero rows: v's own colour, or colour 0 when v's
-    // colour is invalid (adding zeros changes no Z row)
+    // colour of the zero-row arcs: v's own colour, or colour 0 when v's
+    // colour is invalid (the row's outputs are then zero whatever Z holds)
     const int sink = (unsigned)cv < (unsigned)kc ? cv : 0;
     for (int64_t base = e0; base < e1; base += 32) {
         const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
@@ -225,22 +263,13 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
                 const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                 for (int q = 0; q < NV; ++q)
-                    x[r][q] = (!SKIP_ZERO || (live[r] && qok[q])) ? __ldg(row + G * q) : V::zero();
+                    x[r][q] = (!SKIP_ZERO || (live[r] && qok[q])) ? ldg_row(row + G * q) : V::zero();
             }
 #pragma unroll
             for (int r = 0; r < U; ++r) {
                 if (!live[r]) continue;
                 if (cr[r] != cur) {
-                    if (cur >= 0) {
-                        VT *zr = reinterpret_cast<VT *>(zg + cur * wzp) + gl;
-#pragma unroll
-                        for (int q = 0; q < NV; ++q) {
-                            VT z = zr[G * q];
-                            V::add(z, run[q]);
-                            zr[G * q] = z;
-                            run[q] = V::zero();
-                        }
-                    }
+                    if (cur >= 0) flush(cur);
                     cur = cr[r];
                 }
 #pragma unroll
@@ -253,13 +282,12 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
             }
         }
     }
-    if (cur >= 0) {
-        VT *zr = reinterpret_cast<VT *>(zg + cur * wzp) + gl;
+    if (cur >= 0) flush(cur);
+    for (int d = 0; d < kc; ++d) {
+        if (!(seen >> d & 1u) && d != cv) {
+            VT *zr = reinterpret_cast<VT *>(zg + d * wzp) + gl;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            VT z = zr[G * q];
-            V::add(z, run[q]);
-            zr[G * q] = z;
+            for (int q = 0; q < NV; ++q) zr[G * q] = V::zero();
         }
     }
     __syncwarp();
@@ -601,12 +629,9 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
             if (cok) {
-                // zero this warp's slice of Z, then sum colour runs of the arcs
-                for (int d = 0; d < kc; ++d) {
-                    VT *zr = reinterpret_cast<VT *>(zbuf + d * wzp) + vbase;
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) zr[32 * q] = V::zero();
-                }
+                // sum colour runs of the arcs into this warp's slice of Z: each
+                // colour's slice is written once; colours without arcs are
+                // zeroed after the walk (v's own colour is read by nothing)
                 const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;
                 const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + vbase;
                 const int32_t *scol = A.scol + (int64_t)b * A.nnz;
@@ -617,6 +642,17 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
 #pragma unroll
                 for (int q = 0; q < NV; ++q) run[q] = V::zero();
                 int cur = -1;
+                uint32_t seen = 0;
+                auto flush = [&](int c) {
+                    if (c != cv) {
+                        VT *zr = reinterpret_cast<VT *>(zbuf + c * wzp) + vbase;
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) zr[32 * q] = run[q];
+                        seen |= 1u << c;
+                    }
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) run[q] = V::zero();
+                };
                 // arcs that add nothing read the zero row (vertex n) into Z(cv),
                 // as in spmm_z (cv is valid here); FP32 loads are unpredicated
                 // (the table padding covers a whole CTA tile past the last row)
@@ -648,21 +684,12 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                             const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                             for (int q = 0; q < NV; ++q)
-                                x[r][q] = (sizeof(T) == 4 || qok[q]) ? __ldg(row + 32 * q) : V::zero();
+                                x[r][q] = (sizeof(T) == 4 || qok[q]) ? ldg_row(row + 32 * q) : V::zero();
                         }
 #pragma unroll
                         for (int r = 0; r < U; ++r) {
                             if (cr[r] != cur) {
-                                if (cur >= 0) {
-                                    VT *zr = reinterpret_cast<VT *>(zbuf + cur * wzp) + vbase;
-#pragma unroll
-                                    for (int q = 0; q < NV; ++q) {
-                                        VT z = zr[32 * q];
-                                        V::add(z, run[q]);
-                                        zr[32 * q] = z;
-                                        run[q] = V::zero();
-                                    }
-                                }
+                                if (cur >= 0) flush(cur);
                                 cur = cr[r];
                             }
 #pragma unroll
@@ -675,13 +702,12 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                         }
                     }
                 }
-                if (cur >= 0) {
-                    VT *zr = reinterpret_cast<VT *>(zbuf + cur * wzp) + vbase;
+                if (cur >= 0) flush(cur);
+                for (int d = 0; d < kc; ++d) {
+                    if (!(seen >> d & 1u) && d != cv) {
+                        VT *zr = reinterpret_cast<VT *>(zbuf + d * wzp) + vbase;
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        VT z = zr[32 * q];
-                        V::add(z, run[q]);
-                        zr[32 * q] = z;
+                        for (int q = 0; q < NV; ++q) zr[32 * q] = V::zero();
                     }
                 }
             }

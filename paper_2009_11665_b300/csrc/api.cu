@@ -371,6 +371,7 @@ struct Shape {
     int wz, grp, nv, wz_pad, zwords, ywords, mwords, owords, threads;
     size_t smem;
     int blocks_per_sm;
+    bool rows = false;  // histogram node run 32 rows per warp (hist_rows_kernel)
 };
 
 // Everything about a (graph, plans, batch, precision) request that does not
@@ -500,6 +501,24 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.blocks_per_sm =
             P->scaled ? node_blocks_per_sm_scaled(hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem)
                       : node_blocks_per_sm(P->fp64, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
+        const char *rows_env = std::getenv("SG2V_HIST_ROWS");
+        if (hist && !g->weighted && !(rows_env && std::atoi(rows_env) == 0)) {
+            // 32 rows per warp when the block's active rows fit shared memory
+            // (unweighted graphs: with weights the one-warp-per-row kernel
+            // measured faster)
+            const size_t per_warp = (size_t)(kc * 32 + 32 * sh.mwords + sh.ywords + sh.owords) * P->esz;
+            const int threads = kNodeThreads;
+            const size_t smem = per_warp * (threads / 32);
+            const int bps = smem <= 160 * 1024
+                                ? hist_rows_blocks_per_sm(P->fp64, P->scaled, g->weights != nullptr, threads, smem)
+                                : 0;
+            if (bps >= 1) {
+                sh.rows = true;
+                sh.threads = threads;
+                sh.smem = smem;
+                sh.blocks_per_sm = bps;
+            }
+        }
         if (sh.blocks_per_sm < 1) {
             set_error("node kernel cannot be resident with its shared memory");
             return SG2V_ERR_UNSUPPORTED;
@@ -517,7 +536,8 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
 struct RunBuffers {
     int wave = 1;
     int32_t *scol = nullptr;
-    int8_t *sclr = nullptr;
+    int8_t *sclr = nullptr;       // 16 bytes into its allocation (sclr_base)
+    int8_t *sclr_base = nullptr;
     float *sw = nullptr;
     void *scratch = nullptr;
     unsigned *counters = nullptr;
@@ -587,7 +607,9 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     sg2v_status st;
     R->wave = wave;
     if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R->scol))) return st;
-    if ((st = alloc((size_t)wave * g->nnz, (void **)&R->sclr))) return st;
+    // sorted colours, with 16 bytes on either side for aligned 16-byte reads
+    if ((st = alloc((size_t)wave * g->nnz + 32, (void **)&R->sclr_base))) return st;
+    R->sclr = R->sclr_base + 16;
     if (g->weighted && (st = alloc((size_t)wave * g->nnz * sizeof(float), (void **)&R->sw))) return st;
     R->scratch_bytes = (size_t)(g->nheavy * wave * P.scratch_ld) * P.esz;
     R->counter_bytes = (size_t)(g->nheavy * wave) * sizeof(unsigned);
@@ -674,6 +696,15 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     return A;
 }
 
+// Launches the forward kernel of node i with the prepared shape.
+cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, cudaStream_t stream) {
+    const Shape &sh = P.shape[i];
+    const int grid_cap = P.info.sms * sh.blocks_per_sm;
+    if (sh.rows) return launch_hist_rows(A, P.fp64, P.scaled, sh.threads, sh.smem, grid_cap, stream);
+    if (P.scaled) return launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
+    return launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
+}
+
 // Enqueues the whole DP for colourings d_col ([nb][n], device) on `stream`:
 // colour check, per wave the colour sort and one launch per node, then the
 // root reductions into R.sums (and per-vertex doubles when pv != null).
@@ -741,10 +772,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                               P.fp64 ? "fp64" : (P.scaled ? "fp32s" : "fp32"));
                 timer.begin(name, bytes);
             }
-            const int grid_cap = P.info.sms * sh.blocks_per_sm;
-            SG2V_CUDA(P.scaled ? launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
-                               : launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream),
-                      "node kernel launch");
+            SG2V_CUDA(launch_forward_node(P, i, A, stream), "node kernel launch");
             timer.end();
             if (c.active != kLeaf && P.nodes[c.active].last_use == (int)i) src.done(c.active);
             if (c.passive != kLeaf && P.nodes[c.passive].last_use == (int)i && c.passive != c.active)
@@ -820,7 +848,7 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
         return SG2V_OK;
     };
     // wave-dependent: sorted arcs, split-row scratch, tables
-    for (void *p : {(void *)S->R.scol, (void *)S->R.sclr, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters,
+    for (void *p : {(void *)S->R.scol, (void *)S->R.sclr_base, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters,
                     (void *)S->R.eref}) {
         if (!p) continue;
         auto it = std::find(S->owned.begin(), S->owned.end(), p);
@@ -834,13 +862,15 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     R.wave = wave;
     R.scol = nullptr;
     R.sclr = nullptr;
+    R.sclr_base = nullptr;
     R.sw = nullptr;
     R.scratch = nullptr;
     R.counters = nullptr;
     R.eref = nullptr;
     if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R.scol))) return st;
     if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R.eref))) return st;
-    if ((st = alloc((size_t)wave * g->nnz, (void **)&R.sclr))) return st;
+    if ((st = alloc((size_t)wave * g->nnz + 32, (void **)&R.sclr_base))) return st;
+    R.sclr = R.sclr_base + 16;
     if (g->weighted && (st = alloc((size_t)wave * g->nnz * sizeof(float), (void **)&R.sw))) return st;
     R.scratch_bytes = (size_t)(g->nheavy * wave * P.scratch_ld) * P.esz;
     R.counter_bytes = (size_t)(g->nheavy * wave) * sizeof(unsigned);
@@ -1470,8 +1500,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
         }
         timer.begin("backward: forward node", 0.0);
-        SG2V_CUDA(launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm, stream),
-                  "node kernel launch");
+        SG2V_CUDA(launch_forward_node(P, i, A, stream), "node kernel launch");
         timer.end();
     }
     if (total) {

@@ -579,6 +579,131 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
     }
 }
 
+// Histogram nodes (passive child a single vertex) in blocks of 32 rows per
+// warp: first every lane counts the neighbour colours of its own row (the
+// arcs of neighbouring work-list tasks have similar lengths), then the warp
+// runs the expansion and eMA epilogue of the 32 rows one after another.  The
+// per-row chain of dependent loads of the one-warp-per-row kernel is paid
+// once per 32 rows.  Shared memory per warp: counts [kc][32], the active rows
+// of the block [32][mwords], Y' and (scaled) the output row.
+constexpr int kHistRows = 32;
+
+template <typename T, bool WEIGHTED, bool SCALED>
+__global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int kc = A.kc;
+    const int per_warp = kc * kHistRows + kHistRows * A.mwords + A.ywords + A.owords;
+    T *cnt = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * per_warp;  // [kc][32]
+    T *mrows = cnt + kc * kHistRows;                                      // [32][mwords]
+    T *ybuf = mrows + kHistRows * A.mwords;
+    T *obuf = ybuf + A.ywords;
+    const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nblocks = (A.ntasks + kHistRows - 1) / kHistRows;
+    for (int64_t blk = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; blk < nblocks; blk += nwarps) {
+        const int64_t t = blk * kHistRows + lane;
+        const bool have = t < A.ntasks;
+        const int4 task = have ? A.tasks[t] : make_int4(0, -1, 0, 0);
+        for (int b = 0; b < A.nb; ++b) {
+            // the active rows of the block's rows, copied while the counts run
+            if (mchunks) {
+                for (int r = 0; r < kHistRows; ++r) {
+                    const int vr = __shfl_sync(kFull, task.x, r);
+                    const bool hr = __shfl_sync(kFull, (int)have, r) != 0;
+                    if (!hr) continue;
+                    const char *src =
+                        static_cast<const char *>(A.Ma) + ((int64_t)vr * A.nb + b) * A.lda * sizeof(T);
+                    char *dst = reinterpret_cast<char *>(mrows + r * A.mwords);
+                    for (int c = lane; c < mchunks; c += 32) {
+                        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + 16 * c);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + 16 * c)
+                                     : "memory");
+                    }
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
+            // phase 1: lane = row, counts of neighbour colours (and the row's
+            // own colour and active-row exponent, for phase 2)
+            const int cv_l = have ? (int)A.colours[(int64_t)b * A.n + task.x] : -1;
+            const int ea_l = (SCALED && have && !A.a_leaf) ? (int)A.Ea[(int64_t)task.x * A.nb + b] : 0;
+            for (int d = 0; d < kc; ++d) cnt[d * kHistRows + lane] = T(0);
+            const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
+            const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+            if (WEIGHTED) {
+                // eight arcs per step: their loads issue together
+                for (int64_t e = task.z; e < task.w; e += 8) {
+                    int c[8];
+                    T w[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const bool in = e + k < task.w;
+                        c[k] = in ? (int)__ldg(sclr + e + k) : -1;
+                        w[k] = in ? T(__ldg(sw + e + k)) : T(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (c[k] >= 0) cnt[c[k] * kHistRows + lane] += w[k];
+                }
+            } else {
+                // the row's colours in aligned 16-byte words (the colour
+                // buffer is padded by 16 bytes at both ends)
+                const uintptr_t lo = reinterpret_cast<uintptr_t>(sclr + task.z);
+                const uintptr_t hi = reinterpret_cast<uintptr_t>(sclr + task.w);
+                for (uintptr_t a = lo & ~uintptr_t(15); a < hi; a += 16) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(a));
+                    const uint32_t wds[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const uintptr_t at = a + k;
+                        const int c = (int)(int8_t)(wds[k >> 2] >> (8 * (k & 3)));
+                        if (at >= lo && at < hi && c >= 0) cnt[c * kHistRows + lane] += T(1);
+                    }
+                }
+            }
+            // split rows: fold the chunk's counts; the last chunk finishes the row
+            bool finish = have;
+            if (have && task.y >= 0) {
+                T *sc = static_cast<T *>(A.scratch) + ((int64_t)task.y * A.nb + b) * A.scratch_ld;
+                for (int d = 0; d < kc; ++d) atomicAdd(sc + d, cnt[d * kHistRows + lane]);
+                __threadfence();
+                const unsigned done = atomicAdd(A.counters + (int64_t)task.y * A.nb + b, 1u);
+                finish = done + 1u == (unsigned)__ldg(A.heavy_chunks + task.y);
+                if (finish) {
+                    __threadfence();
+                    for (int d = 0; d < kc; ++d) cnt[d * kHistRows + lane] = __ldcg(sc + d);
+                }
+            }
+            const unsigned fin = __ballot_sync(kFull, finish);
+            if (mchunks) asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncwarp();
+            // phase 2: warp = row, expansion and eMA epilogue
+            for (int r = 0; r < kHistRows; ++r) {
+                if (!(fin >> r & 1u)) continue;
+                const int v = __shfl_sync(kFull, task.x, r);
+                const int cv = __shfl_sync(kFull, cv_l, r);
+                const bool cok = (unsigned)cv < (unsigned)kc;
+                const bool arcs = __shfl_sync(kFull, task.w - task.z, r) > 0;
+                if (cok) {
+                    const uint16_t *ex = A.expand + (int64_t)cv * A.wy;
+                    for (int j = lane; j < A.wy; j += 32) ybuf[j] = cnt[(int)__ldg(ex + j) * kHistRows + r];
+                }
+                __syncwarp();
+                const T *ma = mrows + r * A.mwords;
+                const bool ok = cok && arcs;
+                if constexpr (SCALED) {
+                    const int base = __shfl_sync(kFull, ea_l, r);
+                    epilogue_scaled(A, v, b, ok, ybuf, ma, obuf, base, lane);
+                } else {
+                    epilogue<T>(A, v, b, ok, ybuf, ma, lane);
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
 // Wide rows (a compressed row wider than one warp's register tile): one
 // 256-thread CTA per (task, colouring).  Warp w owns vectors
 // [w*32*NV, (w+1)*32*NV) of every gathered row and of Z(d, .), so the eight
@@ -963,62 +1088,100 @@ __global__ void eref_kernel(const int4 *__restrict__ tasks, int64_t ntasks, cons
 }
 
 // Stable counting sort by neighbour colour of the arcs of each work-list task
-// (a row, or a chunk of a split row), one warp per (task, colouring); colours
-// outside [0, kc) go last, tagged -1.  Each colour then forms one run per task.
+// (a row, or a chunk of a split row), one warp per task for every colouring
+// of the wave; colours outside [0, kc) go last, tagged -1.  Each colour then
+// forms one run per task.  Tasks of at most 32 arcs sort in one pass from
+// registers; longer ones count buckets first, then place.
 __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntasks, const int32_t *__restrict__ col_idx,
                                    const float *__restrict__ weights, int64_t n, int64_t nnz,
                                    const int8_t *__restrict__ colours, int nb, int kc, int32_t *scol, int8_t *sclr,
                                    float *sw) {
-    __shared__ int base_s[8][32];
+    __shared__ int base_s[8][kMaxHistColours + 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *start = base_s[wib];
     const unsigned lt = (1u << lane) - 1u;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < ntasks * nb; t += nwarps) {
-        const int4 task = tasks[t / nb];
-        const int b = (int)(t % nb);
-        const int8_t *col = colours + (int64_t)b * n;
+    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < ntasks; t += nwarps) {
+        const int4 task = tasks[t];
         const int64_t e0 = task.z, e1 = task.w;
-        // pass 1: arcs per colour (bucket kc holds invalid colours)
-        int cnt = 0;  // lane q <= kc counts bucket q
-        for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
-            int c = e < e1 ? (int)__ldg(col + __ldg(col_idx + e)) : -2;
-            if (e < e1 && (unsigned)c >= (unsigned)kc) c = kc;
-            for (int q = 0; q <= kc; ++q) {
-                const unsigned m = __ballot_sync(kFull, c == q);
-                if (lane == q) cnt += __popc(m);
-            }
-        }
-        __syncwarp();
-        // exclusive prefix over buckets
-        int incl = cnt;
+        const bool single = e1 - e0 <= 32;
+        // a task of at most 32 arcs keeps its neighbours in registers
+        const int64_t e_one = e0 + lane;
+        const int u_one = single && e_one < e1 ? __ldg(col_idx + e_one) : 0;
+        for (int b = 0; b < nb; ++b) {
+            const int8_t *col = colours + (int64_t)b * n;
+            int32_t *so = scol + (int64_t)b * nnz + e0;
+            int8_t *co = sclr + (int64_t)b * nnz + e0;
+            float *wo = sw ? sw + (int64_t)b * nnz + e0 : nullptr;
+            if (single) {
+                // one batch: bucket sizes from the groups of equal colours
+                const bool ok = e_one < e1;
+                int c = ok ? (int)__ldg(col + u_one) : -2;
+                if (ok && (unsigned)c >= (unsigned)kc) c = kc;  // bucket kc holds invalid colours
+                const unsigned same = __match_any_sync(kFull, c);
+                if (lane <= kc) start[lane] = 0;
+                __syncwarp();
+                if (ok && (same & lt) == 0) start[c] = __popc(same);
+                __syncwarp();
+                const int cnt = lane <= kc ? start[lane] : 0;
+                int incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane <= kc) start[lane] = incl - cnt;
-        __syncwarp();
-        // pass 2: stable placement
-        int32_t *so = scol + (int64_t)b * nnz + e0;
-        int8_t *co = sclr + (int64_t)b * nnz + e0;
-        float *wo = sw ? sw + (int64_t)b * nnz + e0 : nullptr;
-        for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
-            const bool ok = e < e1;
-            const int u = ok ? __ldg(col_idx + e) : 0;
-            int c = ok ? (int)__ldg(col + u) : -2;
-            if (ok && (unsigned)c >= (unsigned)kc) c = kc;
-            const unsigned same = __match_any_sync(kFull, c);
-            if (ok) {
-                const int pos = start[c] + __popc(same & lt);
-                so[pos] = u;
-                co[pos] = (int8_t)(c == kc ? -1 : c);
-                if (wo) wo[pos] = __ldg(weights + e);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                __syncwarp();
+                if (lane <= kc) start[lane] = incl - cnt;
+                __syncwarp();
+                if (ok) {
+                    const int pos = start[c] + __popc(same & lt);
+                    so[pos] = u_one;
+                    co[pos] = (int8_t)(c == kc ? -1 : c);
+                    if (wo) wo[pos] = __ldg(weights + e_one);
+                }
+                __syncwarp();
+                continue;
+            }
+            // pass 1: arcs per colour (bucket kc holds invalid colours)
+            if (lane <= kc) start[lane] = 0;
+            __syncwarp();
+            for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
+                const bool ok = e < e1;
+                int c = ok ? (int)__ldg(col + __ldg(col_idx + e)) : -2;
+                if (ok && (unsigned)c >= (unsigned)kc) c = kc;
+                const unsigned same = __match_any_sync(kFull, c);
+                if (ok && (same & lt) == 0) start[c] += __popc(same);
+                __syncwarp();
+            }
+            // exclusive prefix over buckets
+            const int cnt = lane <= kc ? start[lane] : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
             }
             __syncwarp();
-            // advance every bucket by its arcs in this batch (leader lane of each group)
-            if (ok && (same & lt) == 0) start[c] += __popc(same);
+            if (lane <= kc) start[lane] = incl - cnt;
             __syncwarp();
+            // pass 2: stable placement
+            for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
+                const bool ok = e < e1;
+                const int u = ok ? __ldg(col_idx + e) : 0;
+                int c = ok ? (int)__ldg(col + u) : -2;
+                if (ok && (unsigned)c >= (unsigned)kc) c = kc;
+                const unsigned same = __match_any_sync(kFull, c);
+                if (ok) {
+                    const int pos = start[c] + __popc(same & lt);
+                    so[pos] = u;
+                    co[pos] = (int8_t)(c == kc ? -1 : c);
+                    if (wo) wo[pos] = __ldg(weights + e);
+                }
+                __syncwarp();
+                // advance every bucket by its arcs in this batch (leader lane of each group)
+                if (ok && (same & lt) == 0) start[c] += __popc(same);
+                __syncwarp();
+            }
         }
     }
 }
@@ -1261,6 +1424,34 @@ cudaError_t launch_node_scaled(const NodeArgs &args, int g, int nv, int threads,
     return launch_variant(k, args, g, threads, smem, grid_cap, stream);
 }
 
+namespace {
+void *select_hist_rows(bool fp64, bool scaled, bool weighted) {
+    if (scaled) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<float, true, true>)
+                                : reinterpret_cast<void *>(&hist_rows_kernel<float, false, true>);
+    if (fp64) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<double, true, false>)
+                              : reinterpret_cast<void *>(&hist_rows_kernel<double, false, false>);
+    return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<float, true, false>)
+                    : reinterpret_cast<void *>(&hist_rows_kernel<float, false, false>);
+}
+}  // namespace
+
+int hist_rows_blocks_per_sm(bool fp64, bool scaled, bool weighted, int threads, size_t smem) {
+    return blocks_per_sm(select_hist_rows(fp64, scaled, weighted), threads, smem);
+}
+
+cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int threads, size_t smem, int grid_cap,
+                             cudaStream_t stream) {
+    void *k = select_hist_rows(fp64, scaled, args.weights != nullptr);
+    if (args.ntasks == 0) return cudaSuccess;
+    const int64_t warps = (args.ntasks + kHistRows - 1) / kHistRows;
+    int64_t grid = (warps + threads / 32 - 1) / (threads / 32);
+    if (grid > grid_cap) grid = grid_cap;
+    if (grid < 1) grid = 1;
+    NodeArgs a = args;
+    void *params[] = {&a};
+    return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)threads), params, smem, stream);
+}
+
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,
                                int chunks, RootSum *out, cudaStream_t stream) {
     dim3 grid((unsigned)chunks, (unsigned)nseg);
@@ -1291,8 +1482,7 @@ cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, 
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t *col_idx, const float *weights,
                                int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc, int32_t *scol,
                                int8_t *sclr, float *sw, int sms, cudaStream_t stream) {
-    int64_t warps = ntasks * nb;
-    int64_t blocks = (warps + 7) / 8;
+    int64_t blocks = (ntasks + 7) / 8;
     if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
     if (blocks < 1) blocks = 1;
     colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, col_idx, weights, n, nnz, colours, nb, kc,

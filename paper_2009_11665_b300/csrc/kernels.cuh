@@ -168,6 +168,13 @@ int node_blocks_per_sm(bool fp64, bool hist, int lanes_per_group, int vec_per_la
 cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, int vec_per_lane, int threads,
                         size_t smem, int grid_cap, cudaStream_t stream);
 
+// Histogram nodes in blocks of 32 rows per warp (counts with one lane per
+// row, then the eMA epilogue row by row).  Shared memory per warp:
+// (kc * 32 + 32 * mwords + ywords + owords) elements.
+int hist_rows_blocks_per_sm(bool fp64, bool scaled, bool weighted, int threads, size_t smem);
+cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int threads, size_t smem, int grid_cap,
+                             cudaStream_t stream);
+
 // Root reduction: vals is [nseg][n] of float/double; writes per-vertex doubles
 // when pv != null and one RootSum per segment.
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,

@@ -719,6 +719,8 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
     timer.count_extra(1);
     SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, R.status, stream), "colour check");
+    const char *half_env = std::getenv("SG2V_HALF_ROOT");
+    const bool half_root = !(half_env && std::atoi(half_env) == 0);
     for (int b0 = 0; b0 < nb; b0 += wave) {
         const int wb = std::min(wave, nb - b0);
         const int8_t *wcol = d_col + (int64_t)b0 * n;
@@ -743,6 +745,10 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             A.scratch = R.scratch;
             A.scratch_ld = P.scratch_ld;
             A.counters = R.counters;
+            // totals only and a root whose two children are one table: each
+            // edge's contribution is counted once from its lower end, doubled
+            A.half_arcs = c.is_root && c.active == c.passive && c.active != kLeaf && !pv && !A.hist &&
+                          sh.grp != kWideLanes && half_root;
             if (g->nheavy) {
                 SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
                 SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");

@@ -176,8 +176,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // cover G*NV 16-byte vectors of the neighbour's compressed row (so narrow rows
 // still fill a warp-wide load).  Copies are folded into copy 0 at the end.
 template <typename T, int G, int NV, bool WEIGHTED, bool SCALED>
-__device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1, int b, int cv, int eref, T *zbuf,
-                                       int lane) {
+__device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int64_t e1, int b, int cv, int eref,
+                                       T *zbuf, int lane) {
     constexpr bool FMA = WEIGHTED || SCALED;
     using V = Vec16<T>;
     using VT = typename V::type;
@@ -207,10 +207,10 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
     const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
     const int16_t *Ep = SCALED ? A.Ep + b : nullptr;  // exponent of row (u, b) at Ep[u * nb]
     // the arcs come sorted by neighbour colour: each colour is one run, summed
-    // in registers and added to Z(colour) when the run ends.  Arcs that add
-    // nothing (neighbours of v's own colour or of an invalid colour, lanes
-    // past the end) read the table's zero row (vertex n) and count as v's own
-    // colour, whose Z row the expansion never reads.
+    // in registers and written to Z(colour) when the run ends.  Each batch of
+    // 32 arcs is compacted to the arcs that add something (a valid colour
+    // other than v's own); slots past them read the table's zero row (vertex
+    // n) into the current run.
     // A colour is one run per group, so its Z row is written once, without
     // reading it first; rows of colours with no arcs are zeroed at the end,
     // and the row of v's own colour (read by nothing) is left alone.
@@ -230,17 +230,29 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int64_t e0, int64_t e1
         for (int q = 0; q < NV; ++q) run[q] = V::zero();
     };
     const int zero_row = (int)A.n;
-    // colour of the zero-row arcs: v's own colour, or colour 0 when v's
-    // colour is invalid (the row's outputs are then zero whatever Z holds)
-    const int sink = (unsigned)cv < (unsigned)kc ? cv : 0;
     for (int64_t base = e0; base < e1; base += 32) {
-        const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
-        const int c_in = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
-        const bool t_l = c_in >= 0 && c_in != cv;
-        const int u_l = t_l ? __ldg(scol + base + lane) : zero_row;
-        const int c_l = t_l ? c_in : sink;
+        const int cnt_in = (int)(e1 - base < 32 ? e1 - base : 32);
+        const int c_in = lane < cnt_in ? (int)__ldg(sclr + base + lane) : -1;
+        bool t_in = c_in >= 0 && c_in != cv;
+        const int u_in = t_in ? __ldg(scol + base + lane) : zero_row;
+        if (A.half_arcs && u_in <= v) t_in = false;
+        // compact the batch to the arcs that add something (order kept, so
+        // colour runs stay contiguous): lane j takes the j-th such arc
+        const unsigned live_in = __ballot_sync(kFull, t_in);
+        const int cnt = __popc(live_in);
+        const bool t_l = lane < cnt;
+        const int src = t_l ? (int)__fns(live_in, 0, lane + 1) : lane;
+        int u_l = __shfl_sync(kFull, u_in, src);
+        int c_l = __shfl_sync(kFull, c_in, src);
+        // slots past the live arcs read the zero row into the batch's last
+        // run, so a colour run that continues in the next batch is not cut
+        const int c_last = __shfl_sync(kFull, c_l, cnt > 0 ? cnt - 1 : 0);
+        if (!t_l) {
+            u_l = zero_row;
+            c_l = c_last;
+        }
         T w_l = T(1);
-        if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + lane)) : T(0);
+        if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + src)) : T(0);
         int ep_l = eref;
         if (SCALED && t_l) ep_l = (int)__ldg(Ep + (int64_t)u_l * A.nb);
         for (int j0 = 0; j0 < cnt; j0 += NG * U) {
@@ -448,7 +460,7 @@ __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool o
     }
     if (A.root) {
         const T s = warp_sum(ema_root_partial<T, 32>(A, ok, ybuf, ma, lane));
-        if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = s;
+        if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? T(2) * s : s;
         return;
     }
     T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
@@ -465,7 +477,7 @@ __device__ __forceinline__ void epilogue_scaled(const NodeArgs &A, int v, int b,
     const int64_t rowb = (int64_t)v * A.nb + b;
     if (A.root) {
         const float s = warp_sum(ema_root_partial<float, 32>(A, ok, ybuf, ma, lane));
-        if (lane == 0) A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)s, base) : 0.0;
+        if (lane == 0) A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)s, base + (A.half_arcs ? 1 : 0)) : 0.0;
         return;
     }
     float m = 0.f;
@@ -540,7 +552,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             if (HIST)
                 hist_z<T, WEIGHTED>(A, e0, e1, b, zbuf, lane);
             else
-                spmm_z<T, G, NV, WEIGHTED, SCALED>(A, e0, e1, b, cv, eref, zbuf, lane);
+                spmm_z<T, G, NV, WEIGHTED, SCALED>(A, v, e0, e1, b, cv, eref, zbuf, lane);
             __syncwarp();
             if (slot >= 0) {
                 // one chunk of a split row: fold Z into the scratch row; the

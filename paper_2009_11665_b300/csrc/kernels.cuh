@@ -71,6 +71,11 @@ struct NodeArgs {
     void *Yout;
     int64_t ldy;
     int accumulate;
+    // root whose active and passive children are one table, totals only: the
+    // contribution of an arc (v, u) to v's count equals that of (u, v) to u's,
+    // so only arcs with u > v are gathered and the row sum is doubled (the
+    // per-vertex values are then not the per-vertex counts)
+    int half_arcs;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;

@@ -264,3 +264,34 @@ def test_full_size_rmat20_tree10(sg):
         assert float(pv.sum()) == pytest.approx(t, rel=1e-9)
         del pv
         torch.cuda.empty_cache()
+
+
+SYMMETRIC_ROOTS = [si.TREE10.parent, (-1, 0, 0, 2), (-1, 0, 1, 0, 3, 4)]
+
+
+@pytest.mark.parametrize("parent", SYMMETRIC_ROOTS)
+@pytest.mark.parametrize("chunk", ["1024", "64"])
+def test_totals_with_symmetric_root(sg, parent, chunk, monkeypatch):
+    """Totals only, root whose active and passive children are one table:
+    each edge is gathered from its lower end and the row sums doubled.  The
+    totals must equal the oracle's under the usual bars, with and without
+    colours beyond k, split rows included, and equal the per-vertex path."""
+    monkeypatch.setenv("SG2V_CHUNK", chunk)
+    g = _hub_graph(3)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    k = len(parent)
+    for kc in (k, k + 1):
+        plan = sg.Plan(parent, 0, kc)
+        cols = si.colourings(g.n, kc, 3, seed=4)
+        refs = [oracle.count(g.row_ptr, g.col_idx, parent, 0, cols[b], kc, per_vertex=False) for b in range(3)]
+        for prec in ("fp64", "fp32"):
+            _, tot, est = sg.count_batched(graph, [plan], _dev(cols), prec, per_vertex=False)
+            pv, tot_pv, _ = sg.count_batched(graph, [plan], _dev(cols), prec, per_vertex=True)
+            tot, tot_pv = tot.cpu().numpy()[0], tot_pv.cpu().numpy()[0]
+            for b, ref in enumerate(refs):
+                if prec == "fp64" and ref.max_bits <= 52:
+                    assert tot[b] == float(ref.total) == tot_pv[b]
+                else:
+                    tol = FP64_RTOL if prec == "fp64" else FP32_RTOL
+                    assert abs(tot[b] - ref.total) <= tol * ref.total
+                    assert abs(tot_pv[b] - ref.total) <= tol * ref.total

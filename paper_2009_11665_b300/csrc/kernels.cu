@@ -790,18 +790,29 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
 #pragma unroll
                     for (int q = 0; q < NV; ++q) run[q] = V::zero();
                 };
-                // arcs that add nothing read the zero row (vertex n) into Z(cv),
-                // as in spmm_z (cv is valid here); FP32 loads are unpredicated
-                // (the table padding covers a whole CTA tile past the last row)
+                // slots past the live arcs read the zero row (vertex n); FP32
+                // loads are unpredicated (the table padding covers a whole CTA
+                // tile past the last row)
                 const int zero_row = (int)A.n;
                 for (int64_t base = e0; base < e1; base += 32) {
-                    const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
-                    const int c_in = lane < cnt ? (int)__ldg(sclr + base + lane) : -1;
-                    const bool t_l = c_in >= 0 && c_in != cv;
-                    const int u_l = t_l ? __ldg(scol + base + lane) : zero_row;
-                    const int c_l = t_l ? c_in : cv;
+                    const int cnt_in = (int)(e1 - base < 32 ? e1 - base : 32);
+                    const int c_in = lane < cnt_in ? (int)__ldg(sclr + base + lane) : -1;
+                    const bool t_in = c_in >= 0 && c_in != cv;
+                    const int u_in = t_in ? __ldg(scol + base + lane) : zero_row;
+                    // compacted to the arcs that add something, as in spmm_z
+                    const unsigned live_in = __ballot_sync(kFull, t_in);
+                    const int cnt = __popc(live_in);
+                    const bool t_l = lane < cnt;
+                    const int src = t_l ? (int)__fns(live_in, 0, lane + 1) : lane;
+                    int u_l = __shfl_sync(kFull, u_in, src);
+                    int c_l = __shfl_sync(kFull, c_in, src);
+                    const int c_last = __shfl_sync(kFull, c_l, cnt > 0 ? cnt - 1 : 0);
+                    if (!t_l) {
+                        u_l = zero_row;
+                        c_l = c_last;
+                    }
                     T w_l = T(1);
-                    if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + lane)) : T(0);
+                    if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + src)) : T(0);
                     int ep_l = eref;
                     if (SCALED && t_l) ep_l = (int)__ldg(Ep + (int64_t)u_l * A.nb);
                     for (int j0 = 0; j0 < cnt; j0 += U) {
@@ -1113,13 +1124,22 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
     int *start = base_s[wib];
     const unsigned lt = (1u << lane) - 1u;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < ntasks; t += nwarps) {
-        const int4 task = tasks[t];
+    // software pipeline over the warp's tasks: the descriptor two tasks ahead
+    // and the neighbours of the next task (when it has at most 32 arcs) load
+    // while the current task sorts
+    int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
+    const int4 none = make_int4(0, -1, 0, 0);
+    int4 task = t < ntasks ? tasks[t] : none;
+    int4 next = t + nwarps < ntasks ? tasks[t + nwarps] : none;
+    int u_cur = task.w - task.z <= 32 && task.z + lane < task.w ? __ldg(col_idx + task.z + lane) : 0;
+    for (; t < ntasks; t += nwarps) {
+        const int4 after = t + 2 * nwarps < ntasks ? tasks[t + 2 * nwarps] : none;
+        const int u_next = next.w - next.z <= 32 && next.z + lane < next.w ? __ldg(col_idx + next.z + lane) : 0;
         const int64_t e0 = task.z, e1 = task.w;
         const bool single = e1 - e0 <= 32;
         // a task of at most 32 arcs keeps its neighbours in registers
         const int64_t e_one = e0 + lane;
-        const int u_one = single && e_one < e1 ? __ldg(col_idx + e_one) : 0;
+        const int u_one = u_cur;
         for (int b = 0; b < nb; ++b) {
             const int8_t *col = colours + (int64_t)b * n;
             int32_t *so = scol + (int64_t)b * nnz + e0;
@@ -1195,6 +1215,9 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 __syncwarp();
             }
         }
+        task = next;
+        next = after;
+        u_cur = u_next;
     }
 }
 

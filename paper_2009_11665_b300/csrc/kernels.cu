@@ -1308,6 +1308,93 @@ __global__ void sddmm_kernel(const SddmmArgs A) {
     }
 }
 
+// Per-arc weight gradient, row-oriented (p >= 2): for a row v, Zbar(d, i)
+// holds Ybar'(v, P) for the p-set P = {d} + (the i-th (p-1)-set of d's
+// squeezed universe) when P does not hold v's colour, else 0; then the
+// gradient of arc (v, u) is the dot product of Zbar(col(u), .) with the
+// compressed row M_p'(u, .).  Groups of G lanes take one arc each (as the
+// forward gather does), rows of M_p' are read whole and coalesced, and a
+// group's dot product is reduced with shuffles.  One warp per work-list
+// task; Zbar in shared memory ([kc][wz_pad] per warp).
+template <typename T, int G, int NV>
+__global__ void __launch_bounds__(256) sddmm_rows_kernel(const SddmmArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = Vec16<T>;
+    using VT = typename V::type;
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G;
+    const int kc = A.kc, wzp = A.wz_pad;
+    T *zb = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * kc * wzp;
+    // elements of this lane's vectors inside the row (the row padding past
+    // wmp is never written, and 0 times its contents need not be 0)
+    int lim[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const int left = A.wmp - (gl + G * q) * V::n;
+        lim[q] = left < 0 ? 0 : (left > V::n ? V::n : left);
+    }
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; ti < A.ntasks; ti += nwarps) {
+        const int4 task = A.tasks[ti];
+        const int v = task.x;
+        const int cv = A.colours[v];
+        if ((unsigned)cv >= (unsigned)kc || task.z == task.w) continue;
+        // Zbar of row v
+        for (int i = lane; i < kc * wzp; i += 32) zb[i] = T(0);
+        __syncwarp();
+        const T *yr = static_cast<const T *>(A.Ybar) + (int64_t)v * A.ldyb;
+        for (int d = 0; d < kc; ++d) {
+            if (d == cv) continue;
+            const uint32_t *pr = A.arc + ((int64_t)cv * kc + d) * A.narc;
+            for (int k = lane; k < A.narc; k += 32) {
+                const uint32_t x = __ldg(pr + k);
+                zb[d * wzp + (x >> 16)] = yr[x & 0xffffu];
+            }
+        }
+        __syncwarp();
+        for (int64_t base = task.z; base < task.w; base += 32) {
+            const int cnt_in = (int)(task.w - base < 32 ? task.w - base : 32);
+            const int u_in = lane < cnt_in ? __ldg(A.col_idx + base + lane) : 0;
+            const int c_in = lane < cnt_in ? (int)A.colours[u_in] : -1;
+            const bool t_in = (unsigned)c_in < (unsigned)kc && c_in != cv;
+            // compacted: lane j takes the j-th arc that has a gradient here
+            const unsigned live = __ballot_sync(kFull, t_in);
+            const int cnt = __popc(live);
+            const int src = lane < cnt ? (int)__fns(live, 0, lane + 1) : lane;
+            const int u_l = __shfl_sync(kFull, u_in, src);
+            const int c_l = __shfl_sync(kFull, c_in, src);
+            for (int j0 = 0; j0 < cnt; j0 += NG) {
+                const int j = j0 + grp;
+                const int u = __shfl_sync(kFull, u_l, j & 31);
+                const int cu = __shfl_sync(kFull, c_l, j & 31);
+                const int sj = __shfl_sync(kFull, src, j & 31);
+                T acc = T(0);
+                if (j < cnt) {
+                    const VT *mr = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)u * A.ldp) + gl;
+                    const VT *zr = reinterpret_cast<const VT *>(zb + cu * wzp) + gl;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        if (lim[q] > 0) {
+                            const VT zq = zr[G * q];
+                            const VT mq = __ldg(mr + G * q);
+                            const T *zz = reinterpret_cast<const T *>(&zq);
+                            const T *mm = reinterpret_cast<const T *>(&mq);
+#pragma unroll
+                            for (int c = 0; c < V::n; ++c)
+                                if (c < lim[q]) acc = fma(zz[c], mm[c], acc);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+                if (gl == 0 && j < cnt) A.grad[base + sj] += (double)acc;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void symmetrize_kernel(const double *part, const int32_t *rev, int64_t nnz, double *grad_w) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
         grad_w[e] = part[e] + part[rev[e]];
@@ -1543,7 +1630,46 @@ cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStrea
     return cudaGetLastError();
 }
 
+namespace {
+template <typename T>
+void *pick_sddmm_rows(int g, int nv) {
+    if (g == 4) return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 4, 1>);
+    if (g == 8) return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 8, 1>);
+    if (g == 16) return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 16, 1>);
+    if (g != 32) return nullptr;
+    switch (nv) {
+        case 1: return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 32, 1>);
+        case 2: return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 32, 2>);
+        case 3: return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 32, 3>);
+        case 4: return reinterpret_cast<void *>(&sddmm_rows_kernel<T, 32, 4>);
+        default: return nullptr;
+    }
+}
+}  // namespace
+
 cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream) {
+    if (!args.hist && args.tasks) {
+        // row-oriented form
+        void *k = fp64 ? pick_sddmm_rows<double>(args.lanes, args.vecs) : pick_sddmm_rows<float>(args.lanes, args.vecs);
+        const size_t smem = (size_t)8 * args.kc * args.wz_pad * (fp64 ? 8 : 4);
+        if (!k) return cudaErrorInvalidValue;
+        if (args.ntasks == 0) return cudaSuccess;
+        if (smem > 48 * 1024) {
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (smem > (size_t)optin) return cudaErrorInvalidValue;
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = std::min<int64_t>((args.ntasks + 7) / 8, (int64_t)sms * std::max(per_sm, 1));
+        SddmmArgs a = args;
+        void *params[] = {&a};
+        return cudaLaunchKernel(k, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), params, smem, stream);
+    }
     const size_t smem = (size_t)8 * ((args.wmp + 3) / 4 * 4) * (fp64 ? 8 : 4);
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
     const int64_t blocks = std::min<int64_t>((args.n + 7) / 8, (int64_t)sms * 8);

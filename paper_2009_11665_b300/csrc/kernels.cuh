@@ -125,6 +125,11 @@ struct SddmmArgs {
     const uint32_t *arc;          // [kc][kc][narc]
     int narc;
     double *grad;                 // [nnz]
+    // row-oriented form (p >= 2): the work list of the forward pass and the
+    // gather shape of rows of wmp elements (lanes per group, vectors per lane)
+    const int4 *tasks;
+    int64_t ntasks;
+    int lanes, vecs, wz_pad;
 };
 
 cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStream_t stream);

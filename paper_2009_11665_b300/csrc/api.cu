@@ -372,6 +372,8 @@ struct Shape {
     size_t smem;
     int blocks_per_sm;
     bool rows = false;  // histogram node run 32 rows per warp (hist_rows_kernel)
+    bool defer = false; // eMA in its own launch over blocks of rows (ema_rows_kernel)
+    int64_t ldy = 0;    // Y' row stride of a deferred node
 };
 
 // Everything about a (graph, plans, batch, precision) request that does not
@@ -394,6 +396,7 @@ struct Prepared {
     std::vector<DeviceTables> tabs;
     int64_t scratch_ld = 1;
     int auto_wave = 1;            // widest wave whose gathered table fits half of L2
+    int64_t defer_words = 0;      // largest deferred node's Y' row stride (0: none)
 };
 
 sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans, int32_t B,
@@ -524,6 +527,24 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             return SG2V_ERR_UNSUPPORTED;
         }
         if ((st = device_tables(P->dev, kc, c.t, c.a, sh.wz_pad, &P->tabs[i]))) return st;
+        // large eMA (many sets times many splits per row, root excepted): its own launch over
+        // blocks of rows, so each split-table word serves several rows
+        const char *defer_env = std::getenv("SG2V_DEFER_EMA");  // 0: never; else the least products per row
+        const int64_t defer_min = defer_env ? std::atoll(defer_env) : 32768;
+        const int64_t ema_work = binom(kc - 1, c.t - 1) * binom(c.t - 1, c.a - 1);
+        if (!hist && c.a >= 2 && !c.is_root && defer_min > 0 && ema_work >= defer_min) {
+            NodeArgs probe;
+            std::memset(&probe, 0, sizeof probe);
+            probe.wy = (int)binom(kc - 1, c.p);
+            probe.Wa = (int)binom(kc - 1, c.a - 1);
+            probe.Ws = (int)binom(kc - 1, c.t - 1);
+            const size_t smem = ema_rows_smem(probe, P->fp64, P->scaled);
+            if (ema_rows_blocks_per_sm(P->fp64, P->scaled, smem) >= 1) {
+                sh.defer = true;
+                sh.ldy = (probe.wy + P->vecn - 1) / P->vecn * P->vecn;
+                P->defer_words = std::max<int64_t>(P->defer_words, sh.ldy);
+            }
+        }
     }
     const double per_colouring = (double)P->n * widest * P->esz;
     const int w = (int)std::floor(0.5 * P->info.l2_bytes / per_colouring);
@@ -546,6 +567,7 @@ struct RunBuffers {
     std::vector<void *> table;    // per node: one wave's table (scaled: then its row exponents)
     std::vector<int64_t> ld;
     int32_t *eref = nullptr;      // scaled: [n][wave] reference exponents
+    void *defer_y = nullptr;      // Y' rows of a deferred-eMA node: [n][wave][defer_words]
     unsigned *status = nullptr;   // [4]: bit 0 colour out of range
     double *ones = nullptr;       // [nb][n] ones for single-vertex templates
     int chunks = 1;
@@ -618,6 +640,7 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
         if ((st = alloc(R->counter_bytes, (void **)&R->counters))) return st;
     }
     if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R->eref))) return st;
+    if (P.defer_words && (st = alloc((size_t)P.n * wave * P.defer_words * P.esz, &R->defer_y))) return st;
     R->rootbuf.assign(P.plans.size(), nullptr);
     for (size_t pi = 0; pi < P.plans.size(); ++pi)
         if (P.plan_root[pi] >= 0 && (st = alloc((size_t)P.nb * P.n * root_esz(P), &R->rootbuf[pi]))) return st;
@@ -778,8 +801,22 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                               P.fp64 ? "fp64" : (P.scaled ? "fp32s" : "fp32"));
                 timer.begin(name, bytes);
             }
+            if (sh.defer) {
+                A.defer = 1;
+                A.Yout = R.defer_y;
+                A.ldy = sh.ldy;
+            }
             SG2V_CUDA(launch_forward_node(P, i, A, stream), "node kernel launch");
             timer.end();
+            if (sh.defer) {
+                const double rows = (double)n * wb;
+                char name[64];
+                std::snprintf(name, sizeof name, "ema t=%d a=%d p=%d %s", c.t, c.a, c.p,
+                              P.fp64 ? "fp64" : (P.scaled ? "fp32s" : "fp32"));
+                timer.begin(name, rows * esz * (double)(sh.ldy + binom(kc - 1, c.a - 1) + A.Ws));
+                SG2V_CUDA(launch_ema_rows(A, P.fp64, P.scaled, P.info.sms, stream), "eMA launch");
+                timer.end();
+            }
             if (c.active != kLeaf && P.nodes[c.active].last_use == (int)i) src.done(c.active);
             if (c.passive != kLeaf && P.nodes[c.passive].last_use == (int)i && c.passive != c.active)
                 src.done(c.passive);
@@ -855,7 +892,7 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     };
     // wave-dependent: sorted arcs, split-row scratch, tables
     for (void *p : {(void *)S->R.scol, (void *)S->R.sclr_base, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters,
-                    (void *)S->R.eref}) {
+                    (void *)S->R.eref, S->R.defer_y}) {
         if (!p) continue;
         auto it = std::find(S->owned.begin(), S->owned.end(), p);
         if (it != S->owned.end()) {
@@ -873,8 +910,10 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     R.scratch = nullptr;
     R.counters = nullptr;
     R.eref = nullptr;
+    R.defer_y = nullptr;
     if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R.scol))) return st;
     if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R.eref))) return st;
+    if (P.defer_words && (st = alloc((size_t)P.n * wave * P.defer_words * P.esz, &R.defer_y))) return st;
     if ((st = alloc((size_t)wave * g->nnz + 32, (void **)&R.sclr_base))) return st;
     R.sclr = R.sclr_base + 16;
     if (g->weighted && (st = alloc((size_t)wave * g->nnz * sizeof(float), (void **)&R.sw))) return st;
@@ -932,6 +971,7 @@ int64_t count_launches(const Prepared &P, int wave) {
     int64_t per_wave = 1 + (int64_t)P.nodes.size();
     if (P.scaled)
         for (const CNode &c : P.nodes) per_wave += c.p != 1;
+    for (const Shape &sh : P.shape) per_wave += sh.defer;
     return 1 + waves * per_wave + 2 * (int64_t)P.plans.size() + 1;
 }
 

@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
     T *mbuf = ybuf + A.ywords;  // this row's active-child row (a >= 2)
     T *obuf = mbuf + A.mwords;  // this row's outputs before normalisation (scaled)
     const int zlen = HIST ? A.kc : A.kc * A.wz_pad;
-    const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
     int4 task = ti < A.ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
@@ -530,6 +530,11 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
         for (int b = 0; b < A.nb; ++b) {
             const int cv = A.colours[(int64_t)b * A.n + v];
             const bool cok = (unsigned)cv < (unsigned)A.kc;
+            if (e0 == e1 && A.defer) {
+                T *yo = static_cast<T *>(A.Yout) + ((int64_t)v * A.nb + b) * A.ldy;
+                for (int j = lane; j < A.wy; j += 32) yo[j] = T(0);
+                continue;
+            }
             if (e0 == e1) {
                 // no arcs: Y' = 0, so every output of the row is zero
                 if constexpr (SCALED)
@@ -579,6 +584,13 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane);
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
+            if (A.defer) {
+                // the eMA runs in its own launch over blocks of rows
+                T *yo = static_cast<T *>(A.Yout) + ((int64_t)v * A.nb + b) * A.ldy;
+                for (int j = lane; j < A.wy; j += 32) yo[j] = cok ? ybuf[j] : T(0);
+                __syncwarp();
+                continue;
+            }
             if constexpr (SCALED) {
                 const int base = (A.a_leaf ? 0 : (int)A.Ea[(int64_t)v * A.nb + b]) + eref;
                 epilogue_scaled(A, v, b, cok, ybuf, mbuf, obuf, base, lane);
@@ -716,6 +728,116 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
     }
 }
 
+// Deferred eMA over blocks of kEmaRows rows (rows r0 .. r0 + R - 1 of the
+// flattened (vertex, colouring) row space).  Shared memory holds the block's
+// Y' and active rows interleaved by row ([index][R]), so one split word and
+// two short vector loads give R products; scaled outputs go through
+// shared memory for the per-row normalisation.
+template <typename T>
+struct RowVec;
+template <>
+struct RowVec<float> {
+    static __device__ void load(const float *p, float (&x)[kEmaRows]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+};
+template <>
+struct RowVec<double> {
+    static __device__ void load(const double *p, double (&x)[kEmaRows]) {
+        const double2 a = *reinterpret_cast<const double2 *>(p);
+        const double2 c = *reinterpret_cast<const double2 *>(p + 2);
+        x[0] = a.x; x[1] = a.y; x[2] = c.x; x[3] = c.y;
+    }
+};
+static_assert(kEmaRows == 4, "RowVec loads four rows");
+
+template <typename T, bool SCALED>
+__global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int R = kEmaRows;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int wy = A.wy, wa = A.Wa, ws = A.Ws, ns = A.nsplit;
+    T *ys = reinterpret_cast<T *>(smem_raw);            // [wy][R]
+    T *mas = ys + (int64_t)wy * R;                       // [wa][R]
+    T *os = mas + (int64_t)wa * R;                       // [R][ws] (scaled)
+    __shared__ T s_max[R][8];
+    __shared__ int s_ok[R];
+    const int64_t rows = A.n * A.nb;
+    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < rows; r0 += (int64_t)gridDim.x * R) {
+        if (tid < R) {
+            const int64_t row = r0 + tid;
+            bool ok = row < rows;
+            if (ok) {
+                const int64_t v = row / A.nb, b = row - v * A.nb;
+                ok = (unsigned)A.colours[b * A.n + v] < (unsigned)A.kc;
+            }
+            s_ok[tid] = ok;
+        }
+        for (int i = tid; i < R * wy; i += blockDim.x) {
+            const int r = i / wy, j = i - r * wy;
+            const int64_t row = r0 + r;
+            ys[j * R + r] = row < rows ? static_cast<const T *>(A.Yout)[row * A.ldy + j] : T(0);
+        }
+        for (int i = tid; i < R * wa; i += blockDim.x) {
+            const int r = i / wa, j = i - r * wa;
+            const int64_t row = r0 + r;
+            mas[j * R + r] = row < rows ? static_cast<const T *>(A.Ma)[row * A.lda + j] : T(0);
+        }
+        __syncthreads();
+        T mx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) mx[r] = T(0);
+        for (int S = tid; S < ws; S += blockDim.x) {
+            T acc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = T(0);
+            const uint32_t *sp = A.splits + (int64_t)S * ns;
+            for (int j = 0; j < ns; ++j) {
+                const uint32_t x = __ldg(sp + j);
+                T m[R], y[R];
+                RowVec<T>::load(mas + (x & 0xffffu) * R, m);
+                RowVec<T>::load(ys + (x >> 16) * R, y);
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = fma(m[r], y[r], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T val = s_ok[r] ? acc[r] : T(0);
+                if constexpr (SCALED) {
+                    os[(int64_t)r * ws + S] = val;
+                    mx[r] = fmax(mx[r], val);
+                } else if (r0 + r < rows) {
+                    static_cast<T *>(A.Ms)[(r0 + r) * A.ldt + S] = val;
+                }
+            }
+        }
+        if constexpr (SCALED) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T m = warp_max(mx[r]);
+                if (lane == 0) s_max[r][w] = m;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int64_t row = r0 + r;
+                if (row >= rows) continue;
+                T m = T(0);
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, s_max[r][i]);
+                const int em = m > T(0) ? ilogb(m) : 0;
+                T *out = static_cast<T *>(A.Ms) + row * A.ldt;
+                for (int S = tid; S < ws; S += blockDim.x) out[S] = ldexp(os[(int64_t)r * ws + S], -em);
+                if (tid == 0) {
+                    const int base = (int)A.Ea[row] + row_eref(A, row);
+                    A.Es[row] = m > T(0) ? clamp_exp(base + em) : kEmptyRowExp;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Wide rows (a compressed row wider than one warp's register tile): one
 // 256-thread CTA per (task, colouring).  Warp w owns vectors
 // [w*32*NV, (w+1)*32*NV) of every gathered row and of Z(d, .), so the eight
@@ -742,7 +864,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     T *mbuf = ybuf + A.ywords;
     T *obuf = mbuf + A.mwords;  // outputs before normalisation (scaled)
     const int zlen = kc * wzp;
-    const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int nvec = (A.Wz + V::n - 1) / V::n;
     const int vbase = w * 32 * NV + lane;  // this lane's first vector of the row
     bool qok[NV];
@@ -891,9 +1013,14 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             }
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncthreads();
-            if (!SCALED && A.Yout) {
+            if (A.Yout && (!SCALED || A.defer)) {
                 T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
                 for (int j = tid; j < A.wy; j += blockDim.x) yo[j] = cok ? ybuf[j] : T(0);
+            }
+            if (A.defer) {
+                // the eMA runs in its own launch over blocks of rows
+                __syncthreads();
+                continue;
             }
             // eMA in squeezed coordinates over the whole CTA
             const int base = SCALED ? (A.a_leaf ? 0 : (int)A.Ea[rowb]) + eref : 0;
@@ -1572,6 +1699,35 @@ cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int t
     NodeArgs a = args;
     void *params[] = {&a};
     return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)threads), params, smem, stream);
+}
+
+size_t ema_rows_smem(const NodeArgs &a, bool fp64, bool scaled) {
+    const size_t words = (size_t)kEmaRows * (a.wy + a.Wa + (scaled ? a.Ws : 0));
+    return words * (fp64 ? 8 : 4);
+}
+
+namespace {
+void *select_ema_rows(bool fp64, bool scaled) {
+    if (scaled) return reinterpret_cast<void *>(&ema_rows_kernel<float, true>);
+    return fp64 ? reinterpret_cast<void *>(&ema_rows_kernel<double, false>)
+                : reinterpret_cast<void *>(&ema_rows_kernel<float, false>);
+}
+}  // namespace
+
+int ema_rows_blocks_per_sm(bool fp64, bool scaled, size_t smem) {
+    return blocks_per_sm(select_ema_rows(fp64, scaled), 256, smem);
+}
+
+cudaError_t launch_ema_rows(const NodeArgs &args, bool fp64, bool scaled, int sms, cudaStream_t stream) {
+    const size_t smem = ema_rows_smem(args, fp64, scaled);
+    const int per_sm = ema_rows_blocks_per_sm(fp64, scaled, smem);
+    if (per_sm < 1) return cudaErrorInvalidValue;
+    const int64_t rows = args.n * args.nb;
+    const int64_t blocks = std::min<int64_t>((rows + kEmaRows - 1) / kEmaRows, (int64_t)sms * per_sm);
+    NodeArgs a = args;
+    void *params[] = {&a};
+    return cudaLaunchKernel(select_ema_rows(fp64, scaled), dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256),
+                            params, smem, stream);
 }
 
 cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,

@@ -76,6 +76,9 @@ struct NodeArgs {
     // so only arcs with u > v are gathered and the row sum is doubled (the
     // per-vertex values are then not the per-vertex counts)
     int half_arcs;
+    // large eMA: the gather kernel stores Y' rows in Yout (ldy) and skips the
+    // eMA, which launch_ema_rows then runs over blocks of rows
+    int defer;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
@@ -177,6 +180,16 @@ int node_blocks_per_sm(bool fp64, bool hist, int lanes_per_group, int vec_per_la
 // Launches the fused SpMM/histogram + eMA kernel of one node.
 cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, int vec_per_lane, int threads,
                         size_t smem, int grid_cap, cudaStream_t stream);
+
+// Deferred eMA of a non-root node (a >= 2) over blocks of kEmaRows rows: Y'
+// rows from Yout (written by the node's gather launch with defer set), the
+// active rows from Ma, outputs (and, scaled, exponents) to Ms / Es.  Each
+// split-table word serves kEmaRows rows.  0 blocks per SM if the rows of a
+// block do not fit shared memory.
+constexpr int kEmaRows = 4;
+size_t ema_rows_smem(const NodeArgs &args, bool fp64, bool scaled);
+int ema_rows_blocks_per_sm(bool fp64, bool scaled, size_t smem);
+cudaError_t launch_ema_rows(const NodeArgs &args, bool fp64, bool scaled, int sms, cudaStream_t stream);
 
 // Histogram nodes in blocks of 32 rows per warp (counts with one lane per
 // row, then the eMA epilogue row by row).  Shared memory per warp:

@@ -83,3 +83,35 @@ def test_wide_kernel_on_small_cases(sg, parent, chunk, monkeypatch):
                 nz = want != 0
                 assert np.all(got[~nz] == 0)
                 assert (np.abs(got[nz] - want[nz]) / want[nz]).max() <= max(tol, 1e-12)
+
+
+@pytest.mark.parametrize("parent", [si.TREE8.parent, (-1, 0, 1, 2, 2, 0), si.TREE7.parent])
+@pytest.mark.parametrize("wide", ["", "1"])
+def test_deferred_ema_on_small_cases(sg, parent, wide, monkeypatch):
+    """Every non-root node with a >= 2 forced onto the separate eMA launch
+    (blocks of four rows), on the warp and the CTA-per-row gather, in FP64,
+    FP32 and scaled FP32, against the oracle."""
+    monkeypatch.setenv("SG2V_DEFER_EMA", "1")
+    if wide:
+        monkeypatch.setenv("SG2V_WIDE_MIN_WZ", "1")
+    import torch
+
+    g = si.rmat(11, 12000, seed=6)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    k = len(parent)
+    for kc in (k, k + 2):
+        plan = sg.Plan(parent, 0, kc)
+        cols = si.colourings(g.n, kc, 3, seed=8)
+        refs = [oracle.count(g.row_ptr, g.col_idx, parent, 0, cols[b], kc) for b in range(3)]
+        for prec in ("fp64", "fp32", "fp32_scaled"):
+            pv, tot, _ = sg.count_batched(graph, [plan], torch.from_numpy(cols).cuda(), prec, per_vertex=True)
+            pv = pv.cpu().numpy()
+            for b, ref in enumerate(refs):
+                want = np.array([float(x) for x in ref.per_vertex])
+                if prec == "fp64" and ref.max_bits <= 53:
+                    assert np.array_equal(pv[0, b], want)
+                else:
+                    nz = want != 0
+                    assert np.all(pv[0, b][~nz] == 0)
+                    tol = 1e-12 if prec == "fp64" else 1e-4
+                    assert (np.abs(pv[0, b][nz] - want[nz]) / want[nz]).max() <= tol

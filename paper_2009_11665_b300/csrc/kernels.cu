@@ -731,26 +731,31 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
 // Deferred eMA over blocks of kEmaRows rows (rows r0 .. r0 + R - 1 of the
 // flattened (vertex, colouring) row space).  Shared memory holds the block's
 // Y' and active rows interleaved by row ([index][R]), so one split word and
-// two short vector loads give R products; scaled outputs go through
-// shared memory for the per-row normalisation.
+// short vector loads give R products.  Scaled outputs are stored as they
+// are, then rescaled in place once the block knows each row's largest value.
 template <typename T>
 struct RowVec;
 template <>
 struct RowVec<float> {
     static __device__ void load(const float *p, float (&x)[kEmaRows]) {
-        const float4 v = *reinterpret_cast<const float4 *>(p);
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+#pragma unroll
+        for (int i = 0; i < kEmaRows; i += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + i);
+            x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
+        }
     }
 };
 template <>
 struct RowVec<double> {
     static __device__ void load(const double *p, double (&x)[kEmaRows]) {
-        const double2 a = *reinterpret_cast<const double2 *>(p);
-        const double2 c = *reinterpret_cast<const double2 *>(p + 2);
-        x[0] = a.x; x[1] = a.y; x[2] = c.x; x[3] = c.y;
+#pragma unroll
+        for (int i = 0; i < kEmaRows; i += 2) {
+            const double2 a = *reinterpret_cast<const double2 *>(p + i);
+            x[i] = a.x; x[i + 1] = a.y;
+        }
     }
 };
-static_assert(kEmaRows == 4, "RowVec loads four rows");
+static_assert(kEmaRows % 4 == 0, "RowVec loads rows four at a time");
 
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
@@ -760,7 +765,6 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
     const int wy = A.wy, wa = A.Wa, ws = A.Ws, ns = A.nsplit;
     T *ys = reinterpret_cast<T *>(smem_raw);            // [wy][R]
     T *mas = ys + (int64_t)wy * R;                       // [wa][R]
-    T *os = mas + (int64_t)wa * R;                       // [R][ws] (scaled)
     __shared__ T s_max[R][8];
     __shared__ int s_ok[R];
     const int64_t rows = A.n * A.nb;
@@ -804,12 +808,8 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const T val = s_ok[r] ? acc[r] : T(0);
-                if constexpr (SCALED) {
-                    os[(int64_t)r * ws + S] = val;
-                    mx[r] = fmax(mx[r], val);
-                } else if (r0 + r < rows) {
-                    static_cast<T *>(A.Ms)[(r0 + r) * A.ldt + S] = val;
-                }
+                if (SCALED) mx[r] = fmax(mx[r], val);
+                if (r0 + r < rows) static_cast<T *>(A.Ms)[(r0 + r) * A.ldt + S] = val;
             }
         }
         if constexpr (SCALED) {
@@ -827,7 +827,9 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
                 for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, s_max[r][i]);
                 const int em = m > T(0) ? ilogb(m) : 0;
                 T *out = static_cast<T *>(A.Ms) + row * A.ldt;
-                for (int S = tid; S < ws; S += blockDim.x) out[S] = ldexp(os[(int64_t)r * ws + S], -em);
+                // the same thread wrote out[S] above
+                if (em != 0)
+                    for (int S = tid; S < ws; S += blockDim.x) out[S] = ldexp(out[S], -em);
                 if (tid == 0) {
                     const int base = (int)A.Ea[row] + row_eref(A, row);
                     A.Es[row] = m > T(0) ? clamp_exp(base + em) : kEmptyRowExp;
@@ -1702,7 +1704,8 @@ cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int t
 }
 
 size_t ema_rows_smem(const NodeArgs &a, bool fp64, bool scaled) {
-    const size_t words = (size_t)kEmaRows * (a.wy + a.Wa + (scaled ? a.Ws : 0));
+    (void)scaled;
+    const size_t words = (size_t)kEmaRows * (a.wy + a.Wa);
     return words * (fp64 ? 8 : 4);
 }
 

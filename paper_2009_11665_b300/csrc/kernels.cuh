@@ -186,7 +186,7 @@ cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, in
 // active rows from Ma, outputs (and, scaled, exponents) to Ms / Es.  Each
 // split-table word serves kEmaRows rows.  0 blocks per SM if the rows of a
 // block do not fit shared memory.
-constexpr int kEmaRows = 4;
+constexpr int kEmaRows = 8;
 size_t ema_rows_smem(const NodeArgs &args, bool fp64, bool scaled);
 int ema_rows_blocks_per_sm(bool fp64, bool scaled, size_t smem);
 cudaError_t launch_ema_rows(const NodeArgs &args, bool fp64, bool scaled, int sms, cudaStream_t stream);

@@ -118,15 +118,30 @@ sg2v_status sg2v_graph_info(const sg2v_graph *graph, int64_t *n, int64_t *nnz, i
  *   root        rho in [0, k): the tree is re-rooted at rho (the per-vertex
  *               counts are "rho mapped to v")
  *   num_colours kc, k <= kc <= 16 (Sec. 2.3.1 takes kc = k)
- *   opts        reserved, pass NULL
+ *   opts        NULL, or a sg2v_plan_opts (below)
  *   out         receives the handle
  *
- * Split rule: at a sub-template rooted at x, the edge to x's last remaining
- * child (children ordered by vertex index) is cut; the part holding x is the
- * active child, the cut-off subtree (rooted at the child) the passive child.
- * Sub-templates that are isomorphic as rooted trees share one table.
+ * Split rule: at a sub-template rooted at x, one edge (x, tau) to a kept
+ * child is cut (Sec. 2.3.2 leaves the choice open); the part holding x is
+ * the active child, the cut-off subtree (rooted at tau) the passive child.
+ * SG2V_CUT_LAST (the default) cuts the edge to x's last remaining child
+ * (children ordered by vertex index).  SG2V_CUT_MIN_WORK picks, at every
+ * node, the child that minimises a model of the DP's work per vertex (the
+ * gathered compressed rows times avg_degree, the eMA products, the output
+ * writes; measured relative costs on B300), and keeps the default plan
+ * unless the model, sharing counted, gains at least 1%.  The counts do not
+ * depend on the choice.  Sub-templates that are isomorphic as rooted trees
+ * share one table.
  * Errors: INVALID_ARGUMENT, NOT_A_TREE, UNSUPPORTED (kc > 16).
  */
+#define SG2V_CUT_LAST 0
+#define SG2V_CUT_MIN_WORK 1
+typedef struct {
+    uint32_t size;      /* sizeof(sg2v_plan_opts) */
+    int32_t cut;        /* SG2V_CUT_LAST or SG2V_CUT_MIN_WORK */
+    float avg_degree;   /* arcs per vertex of the graphs to count (0: 32) */
+} sg2v_plan_opts;
+
 sg2v_status sg2v_template_plan(int32_t k, const int32_t *parent, int32_t root, int32_t num_colours,
                                const void *opts, sg2v_plan **out);
 

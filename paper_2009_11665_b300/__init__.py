@@ -35,6 +35,8 @@ SG2V_FP64 = 0
 SG2V_FP32 = 1
 SG2V_FP32_SCALED = 2
 SG2V_GRAPH_SKIP_VALIDATION = 0x1
+SG2V_CUT_LAST = 0
+SG2V_CUT_MIN_WORK = 1
 SG2V_SESSION_PER_VERTEX = 0x1
 SG2V_SESSION_NO_GRAPH = 0x2
 SG2V_SESSION_AUTOTUNE = 0x4
@@ -81,6 +83,10 @@ _lib.sg2v_version.argtypes = []
 _lib.sg2v_version.restype = ctypes.c_int32
 _lib.sg2v_launch_count.argtypes = []
 _lib.sg2v_launch_count.restype = ctypes.c_int64
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint32), ("cut", ctypes.c_int32), ("avg_degree", ctypes.c_float)]
 
 
 class KernelRecord(ctypes.Structure):
@@ -171,11 +177,16 @@ def sg2v_graph_info(handle):
     return n.value, nnz.value, md.value, bool(w.value)
 
 
-def sg2v_template_plan(parent: Sequence[int], root: int = 0, num_colours: Optional[int] = None) -> int:
+def sg2v_template_plan(parent: Sequence[int], root: int = 0, num_colours: Optional[int] = None,
+                       cut: Optional[int] = None, avg_degree: float = 0.0) -> int:
     par = np.ascontiguousarray(parent, dtype=np.int32)
     k = int(par.shape[0])
     h = _p()
-    _check(_lib.sg2v_template_plan(k, _ptr(par), int(root), int(num_colours or k), None, ctypes.byref(h)),
+    opts = None
+    if cut is not None:
+        opts = PlanOpts(ctypes.sizeof(PlanOpts), int(cut), float(avg_degree))
+    _check(_lib.sg2v_template_plan(k, _ptr(par), int(root), int(num_colours or k),
+                                   ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
            "sg2v_template_plan")
     return h.value
 
@@ -322,12 +333,14 @@ class Graph:
 class Plan:
     """Owns a template plan handle."""
 
-    def __init__(self, parent: Sequence[int], root: int = 0, num_colours: Optional[int] = None):
+    def __init__(self, parent: Sequence[int], root: int = 0, num_colours: Optional[int] = None,
+                 cut: Optional[str] = None, avg_degree: float = 0.0):
         self.parent = tuple(int(x) for x in parent)
         self.k = len(self.parent)
         self.kc = int(num_colours or self.k)
         self.root = root
-        self.handle = sg2v_template_plan(self.parent, root, self.kc)
+        c = None if cut is None else {"last": SG2V_CUT_LAST, "min_work": SG2V_CUT_MIN_WORK}[cut]
+        self.handle = sg2v_template_plan(self.parent, root, self.kc, c, avg_degree)
         self.alpha, self.num_nodes, self.max_cols = sg2v_plan_info(self.handle)
         self.scale = sg2v_plan_estimate_scale(self.handle)
 

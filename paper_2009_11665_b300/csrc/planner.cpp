@@ -295,21 +295,29 @@ uint64_t automorphisms(const Tree &T) {
     return a1 * a2 * (f1 == f2 ? 2u : 1u);
 }
 
+// Sub-templates are (x, mask): x with the children of x whose bits are set
+// in mask (each with its whole subtree).  The plan cuts one kept child per
+// node: the last (highest vertex index) by default, or the choice that
+// minimises a work model (min_work).
 struct PlanBuilder {
     const Tree &T;
+    int kc = 0;
+    bool min_work = false;
+    double degree = 32.0;
     std::vector<sg2v::PlanNode> nodes;
     std::map<std::string, int> by_form;
-    std::map<std::string, int> size_of_form;
+    // form of a sub-template -> (least work, form of the child subtree to cut);
+    // isomorphic sub-templates share the entry, so the cut is kept as a form
+    std::map<std::string, std::pair<double, std::string>> best;
 
     explicit PlanBuilder(const Tree &t) : T(t) {}
 
-    std::string form_of(int x, int hi) {
-        // rooted sub-template: x with its first `hi` children (and their subtrees)
+    std::string form_of(int x, uint32_t mask) {
         std::vector<std::string> forms;
-        for (int i = 0; i < hi; ++i) {
+        for (size_t i = 0; i < T.children[x].size(); ++i) {
+            if (!(mask >> i & 1u)) continue;
             uint64_t unused;
-            int y = T.children[x][i];
-            forms.push_back(rooted_form(T, y, x, &unused));
+            forms.push_back(rooted_form(T, T.children[x][i], x, &unused));
         }
         std::sort(forms.begin(), forms.end());
         std::string s = "(";
@@ -317,23 +325,98 @@ struct PlanBuilder {
         return s + ")";
     }
 
-    // Returns the node id of sub-template (x, first hi children), kLeaf for a
-    // single vertex; *size receives its number of vertices.
-    int make(int x, int hi, int *size) {
-        if (hi == 0) {
+    int subtree_size(int y) const {
+        int n = 1;
+        for (int c : T.children[y]) n += subtree_size(c);
+        return n;
+    }
+
+    int size_of(int x, uint32_t mask) const {
+        int n = 1;
+        for (size_t i = 0; i < T.children[x].size(); ++i)
+            if (mask >> i & 1u) n += subtree_size(T.children[x][i]);
+        return n;
+    }
+
+    static uint32_t all_children(const Tree &T, int x) {
+        return T.children[x].size() >= 32 ? ~0u : (1u << T.children[x].size()) - 1u;
+    }
+
+    // Work of one node per vertex and colouring, in units of one gathered
+    // word of a compressed row (B300 measurements): an arc of a gathering
+    // node costs about 20 units plus its row's words, an arc of a histogram
+    // node about 2, a product of the eMA about 0.5, a written output word
+    // about 1.4.  A root whose two children are isomorphic gathers half the
+    // arcs.
+    double node_work(int t, int a, int p, bool root, bool twin) const {
+        const int u = kc - 1;
+        double gather = p >= 2 ? degree * (20.0 + (double)sg2v::binom(u, p - 1)) : degree * 2.0;
+        if (root && twin) gather *= 0.5;
+        const double ema = a >= 2 ? 0.5 * (double)sg2v::binom(u, t - 1) * (double)sg2v::binom(t - 1, a - 1) : 0.0;
+        const double write = root ? 0.0 : 1.4 * (double)sg2v::binom(u, t - 1);
+        return gather + ema + write;
+    }
+
+    std::string child_form(int x, int i) const {
+        uint64_t unused;
+        return rooted_form(T, T.children[x][i], x, &unused);
+    }
+
+    // Least modelled work of (x, mask) and the child to cut (index into children[x]).
+    double plan_work(int x, uint32_t mask, bool root, int *cut) {
+        *cut = -1;
+        if (mask == 0) return 0.0;
+        const std::string f = form_of(x, mask) + (root ? "r" : "");
+        auto it = best.find(f);
+        if (it != best.end()) {
+            for (size_t i = 0; i < T.children[x].size(); ++i)
+                if ((mask >> i & 1u) && child_form(x, (int)i) == it->second.second) {
+                    *cut = (int)i;
+                    break;
+                }
+            return it->second.first;
+        }
+        double w_best = 0.0;
+        int c_best = -1;
+        const int t = size_of(x, mask);
+        for (size_t i = 0; i < T.children[x].size(); ++i) {
+            if (!(mask >> i & 1u)) continue;
+            const int y = T.children[x][i];
+            const uint32_t rest = mask & ~(1u << i);
+            int unused;
+            const int p = subtree_size(y);
+            const bool twin = root && form_of(x, rest) == form_of(y, all_children(T, y));
+            const double w = node_work(t, t - p, p, root, twin) + plan_work(x, rest, false, &unused) +
+                             plan_work(y, all_children(T, y), false, &unused);
+            if (c_best < 0 || w < w_best) {
+                w_best = w;
+                c_best = (int)i;
+            }
+        }
+        best[f] = {w_best, child_form(x, c_best)};
+        *cut = c_best;
+        return w_best;
+    }
+
+    // Returns the node id of sub-template (x, mask), kLeaf for a single vertex;
+    // *size receives its number of vertices.
+    int make(int x, uint32_t mask, bool root, int *size) {
+        if (mask == 0) {
             *size = 1;
             return sg2v::kLeaf;
         }
-        std::string f = form_of(x, hi);
+        std::string f = form_of(x, mask);
         auto it = by_form.find(f);
-        if (it != by_form.end()) {
+        if (it != by_form.end() && !root) {
             *size = nodes[it->second].t;
             return it->second;
         }
-        int tau = T.children[x][hi - 1];  // cut the edge to the last kept child
+        int ci = 31 - __builtin_clz(mask);  // the last kept child
+        if (min_work) plan_work(x, mask, root, &ci);
+        const int tau = T.children[x][ci];
         int a, p;
-        int ia = make(x, hi - 1, &a);
-        int ip = make(tau, (int)T.children[tau].size(), &p);
+        int ia = make(x, mask & ~(1u << ci), false, &a);
+        int ip = make(tau, all_children(T, tau), false, &p);
         sg2v::PlanNode nd;
         nd.t = a + p;
         nd.a = a;
@@ -343,9 +426,19 @@ struct PlanBuilder {
         nd.canon = f;
         nodes.push_back(nd);
         int id = (int)nodes.size() - 1;
-        by_form[f] = id;
+        if (!root) by_form[f] = id;
         *size = nd.t;
         return id;
+    }
+
+    // Modelled work of the built plan, every distinct node counted once.
+    double built_work() const {
+        double w = 0.0;
+        for (const auto &nd : nodes) {
+            const bool twin = nd.is_root && nd.active == nd.passive && nd.active != sg2v::kLeaf;
+            w += node_work(nd.t, nd.a, nd.p, nd.is_root, twin);
+        }
+        return w;
     }
 };
 
@@ -355,7 +448,6 @@ extern "C" {
 
 sg2v_status sg2v_template_plan(int32_t k, const int32_t *parent, int32_t root, int32_t num_colours,
                                const void *opts, sg2v_plan **out) {
-    (void)opts;
     if (!out || !parent) {
         sg2v::set_error("null argument");
         return SG2V_ERR_INVALID_ARGUMENT;
@@ -383,11 +475,37 @@ sg2v_status sg2v_template_plan(int32_t k, const int32_t *parent, int32_t root, i
     plan->root = root;
     plan->parent.assign(parent, parent + k);
     plan->alpha = automorphisms(T);
+    if (T.children[root].size() > 31) {
+        sg2v::set_error("template root has too many children");
+        delete plan;
+        return SG2V_ERR_UNSUPPORTED;
+    }
+    const sg2v_plan_opts *o = static_cast<const sg2v_plan_opts *>(opts);
+    if (o && (o->size != sizeof(sg2v_plan_opts) || (o->cut != SG2V_CUT_LAST && o->cut != SG2V_CUT_MIN_WORK) ||
+              !(o->avg_degree >= 0.0f))) {
+        sg2v::set_error("invalid plan options");
+        delete plan;
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    auto build = [&](bool min_work, PlanBuilder *B) {
+        B->kc = num_colours;
+        B->min_work = min_work;
+        if (o && o->avg_degree > 0.0f) B->degree = o->avg_degree;
+        int size;
+        int rid = B->make(root, PlanBuilder::all_children(T, root), true, &size);
+        if (rid != sg2v::kLeaf) B->nodes[rid].is_root = true;
+    };
     PlanBuilder B(T);
-    int size;
-    int rid = B.make(root, (int)T.children[root].size(), &size);
+    build(false, &B);
+    if (o && o->cut == SG2V_CUT_MIN_WORK) {
+        // the work-minimising cuts when the model gains at least 1% over the
+        // default plan, sharing counted (smaller gains are within the
+        // model's error on B300)
+        PlanBuilder M(T);
+        build(true, &M);
+        if (M.built_work() < 0.99 * B.built_work()) B.nodes = std::move(M.nodes);
+    }
     plan->nodes = std::move(B.nodes);
-    if (rid != sg2v::kLeaf) plan->nodes[rid].is_root = true;
     plan->max_cols = sg2v::binom(num_colours, 1);
     for (auto &nd : plan->nodes) {
         plan->max_cols = std::max<int64_t>(plan->max_cols, sg2v::binom(num_colours, nd.t));

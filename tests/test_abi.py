@@ -166,6 +166,53 @@ def test_invalid_templates(lib):
     assert e.value.status == lib.SG2V_ERR_UNSUPPORTED
 
 
+def test_plan_options(lib):
+    """Plan options: a wrong struct size, cut rule or degree is rejected;
+    cut-last options give the default plan."""
+    import ctypes
+
+    par = np.ascontiguousarray(si.TREE10.parent, dtype=np.int32)
+    h = ctypes.c_void_p()
+    for size, cut, deg in ((4, 0, 0.0), (ctypes.sizeof(lib.PlanOpts), 7, 0.0),
+                           (ctypes.sizeof(lib.PlanOpts), 1, -1.0)):
+        o = lib.PlanOpts(size, cut, deg)
+        st = lib._lib.sg2v_template_plan(10, par.ctypes.data_as(ctypes.c_void_p), 0, 10, ctypes.byref(o),
+                                         ctypes.byref(h))
+        assert st == lib.SG2V_ERR_INVALID_ARGUMENT
+    assert lib.Plan(si.TREE10.parent, cut="last").nodes() == lib.Plan(si.TREE10.parent).nodes()
+
+
+def _check_decomposition(nodes, k):
+    """Every node splits t = a + p with children that exist and have those
+    sizes; the root covers the template."""
+    size = {-1: 1}
+    for i, (t, a, p, ia, ip, is_root) in enumerate(nodes):
+        assert t == a + p and a >= 1 and p >= 1
+        assert ia < i and ip < i
+        assert size[ia] == a and size[ip] == p
+        size[i] = t
+    assert nodes[-1][5] == 1 and nodes[-1][0] == k
+    assert sum(n[5] for n in nodes) == 1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_min_work_plans_are_decompositions(lib, seed):
+    """Work-minimising cut orders still give a valid partition of the
+    template (Sec. 2.3.2), with the same alpha and estimate scale; tree10
+    takes the alternative plan (a (4,2,2) node) at average degree 32."""
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(3, 13))
+    parent = [-1] + [int(rng.integers(0, i)) for i in range(1, k)]
+    for deg in (8.0, 32.0, 95.0):
+        a = lib.Plan(parent)
+        b = lib.Plan(parent, cut="min_work", avg_degree=deg)
+        _check_decomposition(b.nodes(), k)
+        assert (a.alpha, a.scale) == (b.alpha, b.scale)
+    t10 = lib.Plan(si.TREE10.parent, cut="min_work", avg_degree=32.0).nodes()
+    _check_decomposition(t10, 10)
+    assert [n[:3] for n in t10] == [(2, 1, 1), (4, 2, 2), (5, 1, 4), (10, 5, 5)]
+
+
 def test_sharing_of_isomorphic_subtemplates(lib):
     """tree10's two halves below the root are isomorphic rooted trees: the
     root node reads one shared table as both children."""

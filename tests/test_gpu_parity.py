@@ -295,3 +295,22 @@ def test_totals_with_symmetric_root(sg, parent, chunk, monkeypatch):
                     tol = FP64_RTOL if prec == "fp64" else FP32_RTOL
                     assert abs(tot[b] - ref.total) <= tol * ref.total
                     assert abs(tot_pv[b] - ref.total) <= tol * ref.total
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_min_work_plans_match_oracle(sg, seed):
+    """Counts do not depend on the cut order (Sec. 2.3.2): plans built with
+    the work-minimising cuts equal the oracle (FP64 bit-exact)."""
+    rng = np.random.default_rng(100 + seed)
+    k = int(rng.integers(4, 10))
+    parent = [-1] + [int(rng.integers(0, i)) for i in range(1, k)]
+    parents = [tuple(parent), si.TREE10.parent] if seed == 0 else [tuple(parent)]
+    g = si.rmat(11, 10000, seed=seed)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    for par in parents:
+        kk = len(par)
+        plan = sg.Plan(par, 0, kk, cut="min_work", avg_degree=16.0)
+        col = si.colouring(g.n, kk, seed)
+        ref = oracle.count(g.row_ptr, g.col_idx, par, 0, col)
+        pv, tot, _ = sg.count(graph, plan, _dev(col), "fp64")
+        _check_fp64(pv.cpu().numpy(), tot, ref, exact=ref.max_bits <= 53)

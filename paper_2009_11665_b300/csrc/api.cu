@@ -231,6 +231,9 @@ struct Workspace {
 }  // namespace
 }  // namespace sg2v
 
+// Rows of at most this many arcs may run one per lane group (narrow rows).
+constexpr int kShortTaskArcs = 64;
+
 struct sg2v_graph {
     int device = 0;
     int64_t n = 0, nnz = 0, max_degree = 0;
@@ -243,6 +246,7 @@ struct sg2v_graph {
     int32_t *heavy_chunks = nullptr;
     int64_t nheavy = 0;
     int chunk = 0;
+    int64_t short_begin = 0;  // first task of at most kShortTaskArcs arcs (the rest, sorted by work, are too)
     int32_t *rev = nullptr;  // reverse arc of every arc, built on the first backward call
 };
 
@@ -372,6 +376,9 @@ struct Shape {
     size_t smem;
     int blocks_per_sm;
     bool rows = false;  // histogram node run 32 rows per warp (hist_rows_kernel)
+    bool group = false; // narrow rows: short tasks one per lane group (node_group_kernel)
+    int wthreads = 0, wbps = 0;  // the one-warp-per-row launch of the longer tasks of a group node
+    size_t wsmem = 0;
     bool defer = false; // eMA in its own launch over blocks of rows (ema_rows_kernel)
     int64_t ldy = 0;    // Y' row stride of a deferred node
 };
@@ -504,6 +511,30 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.blocks_per_sm =
             P->scaled ? node_blocks_per_sm_scaled(hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem)
                       : node_blocks_per_sm(P->fp64, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
+        const char *group_env = std::getenv("SG2V_GROUP_ROWS");
+        if (!hist && sh.grp < 32 && sh.nv == 1 && !(group_env && std::atoi(group_env) == 0)) {
+            // narrow rows: every lane group takes its own row
+            const size_t per_warp =
+                (size_t)(32 / sh.grp) * (kc * sh.wz_pad + sh.ywords + sh.mwords + sh.owords) * P->esz;
+            const int threads = kNodeThreads;
+            const size_t smem = per_warp * (threads / 32);
+            const int bps = smem <= 200 * 1024 ? (P->scaled ? node_blocks_per_sm_scaled(false, sh.grp, 1,
+                                                                                        g->weights != nullptr,
+                                                                                        threads, smem, true)
+                                                            : node_blocks_per_sm(P->fp64, false, sh.grp, 1,
+                                                                                 g->weights != nullptr, threads, smem,
+                                                                                 true))
+                                               : 0;
+            if (bps >= 1) {
+                sh.group = true;
+                sh.wthreads = sh.threads;
+                sh.wsmem = sh.smem;
+                sh.wbps = sh.blocks_per_sm;
+                sh.threads = threads;
+                sh.smem = smem;
+                sh.blocks_per_sm = bps;
+            }
+        }
         const char *rows_env = std::getenv("SG2V_HIST_ROWS");
         if (hist && !g->weighted && !(rows_env && std::atoi(rows_env) == 0)) {
             // 32 rows per warp when the block's active rows fit shared memory
@@ -706,6 +737,7 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
         else
             A.root_out = rb;
     }
+    A.group_rows = sh.group;
     if (P.scaled) {
         A.scaled = 1;
         A.owords = sh.owords;
@@ -724,6 +756,24 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
     const Shape &sh = P.shape[i];
     const int grid_cap = P.info.sms * sh.blocks_per_sm;
     if (sh.rows) return launch_hist_rows(A, P.fp64, P.scaled, sh.threads, sh.smem, grid_cap, stream);
+    if (sh.group) {
+        // the longer tasks (the front of the work list) one per warp, the short
+        // ones one per lane group
+        const int64_t split = P.g->short_begin;
+        NodeArgs W = A;
+        W.group_rows = 0;
+        W.ntasks = split;
+        cudaError_t e = P.scaled ? launch_node_scaled(W, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
+                                                      stream)
+                                 : launch_node(W, P.fp64, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
+                                               stream);
+        if (e != cudaSuccess) return e;
+        NodeArgs S = A;
+        S.tasks = A.tasks + split;
+        S.ntasks = A.ntasks - split;
+        return P.scaled ? launch_node_scaled(S, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
+                        : launch_node(S, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
+    }
     if (P.scaled) return launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     return launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
 }
@@ -808,6 +858,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             }
             SG2V_CUDA(launch_forward_node(P, i, A, stream), "node kernel launch");
             timer.end();
+            if (sh.group) timer.count_extra(1);  // short and long tasks launch apart
             if (sh.defer) {
                 const double rows = (double)n * wb;
                 char name[64];
@@ -971,7 +1022,7 @@ int64_t count_launches(const Prepared &P, int wave) {
     int64_t per_wave = 1 + (int64_t)P.nodes.size();
     if (P.scaled)
         for (const CNode &c : P.nodes) per_wave += c.p != 1;
-    for (const Shape &sh : P.shape) per_wave += sh.defer;
+    for (const Shape &sh : P.shape) per_wave += sh.defer + sh.group;
     return 1 + waves * per_wave + 2 * (int64_t)P.plans.size() + 1;
 }
 
@@ -1031,6 +1082,16 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
     build_tasks(n, rp, g->chunk, &tasks, &hc);
     g->ntasks = (int64_t)tasks.size();
     g->nheavy = (int64_t)hc.size();
+    {
+        int64_t nchunks = 0;
+        for (int32_t c : hc) nchunks += c;
+        g->short_begin = g->ntasks;
+        for (int64_t i = nchunks; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kShortTaskArcs) {
+                g->short_begin = i;
+                break;
+            }
+    }
     cudaError_t e = cudaSuccess;
     auto up = [&](void **dst, const void *src, size_t bytes) {
         if (e != cudaSuccess) return;
@@ -1618,6 +1679,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             A.zwords = sh.zwords;
             A.ywords = sh.ywords;
             A.mwords = 0;
+            A.group_rows = 0;  // the transposed SpMM's shape is its own (one task per warp)
+            A.defer = 0;
             A.p = btab[ii].nterms;
             A.wy = btab[ii].wout;
             A.expand = d_bexp[ii];

@@ -162,6 +162,22 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Sum / maximum over an aligned group of G lanes (every lane of the warp
+// takes part; each group gets its own result).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_max(T v) {
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
 // Colour-compressed accumulation of one (row, colouring b) over arcs [e0, e1).
 //
 // Every table row u stores only the colour sets containing u's colour c_u
@@ -600,6 +616,214 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             __syncwarp();
         }
         task = next;
+    }
+}
+
+// Narrow rows (G = 4, 8 or 16 lanes cover a compressed row): every group of
+// G lanes of a warp takes its own work-list task, so a warp runs 32 / G rows
+// at once and the per-row chain (colour, arc batch, gathers, expansion,
+// epilogue) is paid once per 32 / G rows.  A group walks its row's sorted
+// arcs in batches of G, compacted to the arcs that add something; groups
+// step together (the warp runs to its longest row, shorter rows read the
+// zero row).  Shared memory per group: Z [kc][wz_pad], Y', the active row
+// and (scaled) the output row.
+template <typename T, int G, bool WEIGHTED, bool SCALED>
+__global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_group_kernel(const NodeArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = Vec16<T>;
+    using VT = typename V::type;
+    constexpr int NG = 32 / G;
+    constexpr int U = 4;                       // arcs in flight per group and step
+    constexpr bool FMA = WEIGHTED || SCALED;
+    constexpr bool SKIP_ZERO = sizeof(T) == 8;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G, g0 = grp * G;
+    const unsigned gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << g0;
+    const int kc = A.kc, wzp = A.wz_pad;       // wzp = G * V::n
+    const int per_group = kc * wzp + A.ywords + A.mwords + A.owords;
+    T *zg = reinterpret_cast<T *>(smem_raw) + (int64_t)(wib * NG + grp) * per_group;
+    T *ybuf = zg + kc * wzp;
+    T *mbuf = ybuf + A.ywords;
+    T *obuf = mbuf + A.mwords;
+    const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    const bool qok = gl < (A.Wz + V::n - 1) / V::n;
+    const int zero_row = (int)A.n;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t wglob = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
+    const int64_t nrounds = (A.ntasks + (int64_t)NG - 1) / NG;
+    for (int64_t rnd = wglob; rnd < nrounds; rnd += nwarps) {
+        const int64_t ti = rnd * NG + grp;
+        const bool have = ti < A.ntasks;
+        const int4 task = have ? A.tasks[ti] : make_int4(0, -1, 0, 0);
+        const int v = task.x, slot = task.y;
+        const int e0 = task.z, e1 = task.w;
+        // batches of G arcs of the longest row in the warp
+        const int nbat_w = __reduce_max_sync(kFull, (unsigned)((e1 - e0 + G - 1) / G));
+        for (int b = 0; b < A.nb; ++b) {
+            const int64_t rowb = (int64_t)v * A.nb + b;
+            const int cv = have ? (int)A.colours[(int64_t)b * A.n + v] : -1;
+            const bool cok = have && (unsigned)cv < (unsigned)kc;
+            const int eref = (SCALED && have) ? row_eref(A, rowb) : 0;
+            if (mchunks && cok) {
+                const char *src = static_cast<const char *>(A.Ma) + rowb * A.lda * sizeof(T);
+                for (int c = gl; c < mchunks; c += G) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(mbuf) + 16 * c);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * c) : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + gl;
+            const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;
+            const int32_t *scol = A.scol + (int64_t)b * A.nnz;
+            const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
+            const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+            const int16_t *Ep = SCALED ? A.Ep + b : nullptr;
+            VT run = V::zero();
+            int cur = -1;
+            uint32_t seen = 0;
+            auto flush = [&](int c) {
+                if (c != cv) {
+                    reinterpret_cast<VT *>(zg + c * wzp)[gl] = run;
+                    seen |= 1u << c;
+                }
+                run = V::zero();
+            };
+            for (int kb = 0; kb < nbat_w; ++kb) {
+                const int base = e0 + kb * G;
+                const bool in = base + gl < e1;
+                const int c_in = in ? (int)__ldg(sclr + base + gl) : -1;
+                bool t_in = c_in >= 0 && c_in != cv;
+                const int u_in = t_in ? __ldg(scol + base + gl) : zero_row;
+                if (A.half_arcs && u_in <= v) t_in = false;
+                const unsigned live = (__ballot_sync(kFull, t_in) & gbits) >> g0;
+                const int cnt = __popc(live);
+                const int cnt_w = __reduce_max_sync(kFull, (unsigned)cnt);
+                const bool t_l = gl < cnt;
+                const int src = g0 + (t_l ? (int)__fns(live, 0, gl + 1) : gl);
+                int u_l = __shfl_sync(kFull, u_in, src);
+                int c_l = __shfl_sync(kFull, c_in, src);
+                const int c_last = __shfl_sync(kFull, c_l, g0 + (cnt > 0 ? cnt - 1 : 0));
+                if (!t_l) {
+                    u_l = zero_row;
+                    c_l = cnt > 0 ? c_last : (cur >= 0 ? cur : 0);
+                }
+                T w_l = T(1);
+                if (WEIGHTED) w_l = t_l ? T(__ldg(sw + base + (src - g0))) : T(0);
+                int ep_l = eref;
+                if (SCALED && t_l) ep_l = (int)__ldg(Ep + (int64_t)u_l * A.nb);
+                for (int j0 = 0; j0 < cnt_w; j0 += U) {
+                    VT x[U];
+                    T w[U];
+                    int cr[U];
+                    bool lv[U];
+#pragma unroll
+                    for (int r = 0; r < U; ++r) {
+                        const int j = (j0 + r) & (G - 1);
+                        const bool inb = j0 + r < G;
+                        const int u = __shfl_sync(kFull, u_l, g0 + j);
+                        cr[r] = __shfl_sync(kFull, c_l, g0 + j);
+                        lv[r] = inb && j0 + r < cnt && (!SKIP_ZERO || u != zero_row);
+                        w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, g0 + j) : T(1);
+                        if (SCALED) {
+                            const int ep = __shfl_sync(kFull, ep_l, g0 + j);
+                            w[r] *= T(exp2_neg(ep - eref));
+                        }
+                        const VT *row = Mb + (int64_t)(lv[r] ? u : zero_row) * uvec;
+                        x[r] = (SKIP_ZERO ? (lv[r] && qok) : true) ? ldg_row(row) : V::zero();
+                    }
+#pragma unroll
+                    for (int r = 0; r < U; ++r) {
+                        if (!lv[r]) continue;
+                        if (cr[r] != cur) {
+                            if (cur >= 0) flush(cur);
+                            cur = cr[r];
+                        }
+                        if (FMA)
+                            V::fma(run, w[r], x[r]);
+                        else
+                            V::add(run, x[r]);
+                    }
+                }
+            }
+            if (cur >= 0) flush(cur);
+            for (int d = 0; d < kc; ++d)
+                if (!(seen >> d & 1u) && d != cv) reinterpret_cast<VT *>(zg + d * wzp)[gl] = V::zero();
+            __syncwarp();
+            // split rows: fold Z into the scratch row; the last chunk finishes
+            bool fin = have;
+            if (have && slot >= 0) {
+                T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
+                for (int j = gl; j < kc * wzp; j += G) atomicAdd(sc + j, zg[j]);
+                __threadfence();
+            }
+            __syncwarp();
+            int last = 1;
+            if (have && slot >= 0 && gl == 0) {
+                const unsigned done = atomicAdd(A.counters + (int64_t)slot * A.nb + b, 1u);
+                last = done + 1u == (unsigned)__ldg(A.heavy_chunks + slot);
+            }
+            last = __shfl_sync(kFull, last, g0);
+            if (have && slot >= 0) {
+                fin = last != 0;
+                if (fin) {
+                    __threadfence();
+                    T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
+                    for (int j = gl; j < kc * wzp; j += G) zg[j] = __ldcg(sc + j);
+                }
+            }
+            __syncwarp();
+            const bool ok = fin && cok && e0 < e1;
+            if (ok) {
+                const uint16_t *ex = A.expand + (int64_t)cv * A.wy * A.p;
+                for (int j = gl; j < A.wy; j += G) {
+                    T y = T(0);
+                    for (int k = 0; k < A.p; ++k) y += zg[__ldg(ex + j * A.p + k)];
+                    ybuf[j] = y;
+                }
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncwarp();
+            if (fin && (A.defer || (!SCALED && A.Yout))) {
+                T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
+                for (int j = gl; j < A.wy; j += G) yo[j] = ok ? ybuf[j] : T(0);
+            }
+            if (A.defer) {
+                __syncwarp();
+                continue;
+            }
+            // eMA epilogue of the group's row
+            const int base_e = SCALED ? (A.a_leaf ? 0 : (fin && have ? (int)A.Ea[rowb] : 0)) + eref : 0;
+            if (A.root) {
+                const T sum = group_sum<G>(ema_root_partial<T, G>(A, ok, ybuf, mbuf, gl));
+                if (fin && gl == 0) {
+                    if constexpr (SCALED)
+                        A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)sum, base_e + (A.half_arcs ? 1 : 0)) : 0.0;
+                    else
+                        static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? T(2) * sum : sum;
+                }
+            } else if constexpr (SCALED) {
+                T mx = T(0);
+                ema_rows<T, G>(A, ok, ybuf, mbuf, gl, [&](int S, T x) {
+                    obuf[S] = x;
+                    mx = fmax(mx, x);
+                });
+                mx = group_max<G>(mx);
+                const int em = mx > T(0) ? ilogb(mx) : 0;
+                __syncwarp();
+                if (fin) {
+                    T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+                    for (int j = gl; j < A.Ws; j += G) out[j] = ldexp(obuf[j], -em);
+                    if (gl == 0) A.Es[rowb] = mx > T(0) ? clamp_exp(base_e + em) : kEmptyRowExp;
+                }
+            } else {
+                T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+                const bool accumulate = A.accumulate != 0;
+                ema_rows<T, G>(A, ok, ybuf, mbuf, gl, [&](int S, T x) {
+                    if (fin) out[S] = accumulate ? out[S] + x : x;
+                });
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -1096,7 +1320,20 @@ void *pick_wide(int nv) {
     }
 }
 
-void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted) {
+template <typename T, bool W, bool SC>
+void *pick_group(int g) {
+    if (g == 4) return reinterpret_cast<void *>(&node_group_kernel<T, 4, W, SC>);
+    if (g == 8) return reinterpret_cast<void *>(&node_group_kernel<T, 8, W, SC>);
+    if (g == 16) return reinterpret_cast<void *>(&node_group_kernel<T, 16, W, SC>);
+    return nullptr;
+}
+
+void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted, bool group = false) {
+    if (group) {
+        if (hist || nv != 1) return nullptr;
+        if (fp64) return weighted ? pick_group<double, true, false>(g) : pick_group<double, false, false>(g);
+        return weighted ? pick_group<float, true, false>(g) : pick_group<float, false, false>(g);
+    }
     if (g == kWideLanes) {
         // wide rows: one CTA per task (nv vectors per lane, 8 warps)
         if (hist) return nullptr;
@@ -1107,7 +1344,11 @@ void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted) {
     return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
 }
 
-void *select_kernel_scaled(bool hist, int g, int nv, bool weighted) {
+void *select_kernel_scaled(bool hist, int g, int nv, bool weighted, bool group = false) {
+    if (group) {
+        if (hist || nv != 1) return nullptr;
+        return weighted ? pick_group<float, true, true>(g) : pick_group<float, false, true>(g);
+    }
     if (g == kWideLanes) {
         if (hist) return nullptr;
         return weighted ? pick_wide<float, true, true>(nv) : pick_wide<float, false, true>(nv);
@@ -1644,7 +1885,8 @@ cudaError_t launch_variant(void *k, const NodeArgs &args, int g, int threads, si
                            cudaStream_t stream) {
     if (!k) return cudaErrorInvalidValue;
     if (args.ntasks == 0) return cudaSuccess;
-    const int64_t warps_per_block = g == kWideLanes ? 1 : threads / 32;  // wide: one task per CTA
+    // tasks per block: wide rows one per CTA, group rows 32 / g per warp, else one per warp
+    const int64_t warps_per_block = g == kWideLanes ? 1 : (args.group_rows ? (threads / 32) * (32 / g) : threads / 32);
     int64_t grid = (args.ntasks + warps_per_block - 1) / warps_per_block;
     if (grid > grid_cap) grid = grid_cap;
     if (grid < 1) grid = 1;
@@ -1655,23 +1897,23 @@ cudaError_t launch_variant(void *k, const NodeArgs &args, int g, int threads, si
 
 }  // namespace
 
-int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
-    return blocks_per_sm(select_kernel(fp64, hist, g, nv, weighted), threads, smem);
+int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem, bool group) {
+    return blocks_per_sm(select_kernel(fp64, hist, g, nv, weighted, group), threads, smem);
 }
 
-int node_blocks_per_sm_scaled(bool hist, int g, int nv, bool weighted, int threads, size_t smem) {
-    return blocks_per_sm(select_kernel_scaled(hist, g, nv, weighted), threads, smem);
+int node_blocks_per_sm_scaled(bool hist, int g, int nv, bool weighted, int threads, size_t smem, bool group) {
+    return blocks_per_sm(select_kernel_scaled(hist, g, nv, weighted, group), threads, smem);
 }
 
 cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int threads, size_t smem, int grid_cap,
                         cudaStream_t stream) {
-    void *k = select_kernel(fp64, args.hist != 0, g, nv, args.weights != nullptr);
+    void *k = select_kernel(fp64, args.hist != 0, g, nv, args.weights != nullptr, args.group_rows != 0);
     return launch_variant(k, args, g, threads, smem, grid_cap, stream);
 }
 
 cudaError_t launch_node_scaled(const NodeArgs &args, int g, int nv, int threads, size_t smem, int grid_cap,
                                cudaStream_t stream) {
-    void *k = select_kernel_scaled(args.hist != 0, g, nv, args.weights != nullptr);
+    void *k = select_kernel_scaled(args.hist != 0, g, nv, args.weights != nullptr, args.group_rows != 0);
     return launch_variant(k, args, g, threads, smem, grid_cap, stream);
 }
 

@@ -79,6 +79,10 @@ struct NodeArgs {
     // large eMA: the gather kernel stores Y' rows in Yout (ldy) and skips the
     // eMA, which launch_ema_rows then runs over blocks of rows
     int defer;
+    // narrow rows: each group of lanes (lanes_per_group) takes its own task
+    // (node_group_kernel); shared memory per warp is then
+    // (32 / lanes) * (kc * wz_pad + ywords + mwords + owords) elements
+    int group_rows;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
@@ -157,7 +161,7 @@ constexpr unsigned kFlagNonFinite = 2u;
 
 // Resident blocks per SM / launch of the scaled FP32 variants (per-row exponents).
 int node_blocks_per_sm_scaled(bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
-                              size_t smem);
+                              size_t smem, bool group_rows = false);
 cudaError_t launch_node_scaled(const NodeArgs &args, int lanes_per_group, int vec_per_lane, int threads, size_t smem,
                                int grid_cap, cudaStream_t stream);
 
@@ -175,7 +179,7 @@ constexpr int kWideThreads = 256;
 // dynamic shared-memory size (0 if it cannot run); raises the kernel's
 // shared-memory limit when needed.
 int node_blocks_per_sm(bool fp64, bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
-                       size_t smem);
+                       size_t smem, bool group_rows = false);
 
 // Launches the fused SpMM/histogram + eMA kernel of one node.
 cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, int vec_per_lane, int threads,

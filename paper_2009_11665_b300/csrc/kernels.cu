@@ -40,9 +40,6 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef SG2V_PACKED
 #define SG2V_PACKED 1
 #endif
-#ifndef SG2V_LDG_MODE
-#define SG2V_LDG_MODE 0
-#endif
 constexpr int kMaxHistColours = 16;
 
 template <typename T>
@@ -112,28 +109,11 @@ struct Vec16<double> {
     }
 };
 
-// Load of one 16-byte vector of a gathered table row.  SG2V_LDG_MODE picks
-// the cache policy: 0 read-only path, 1 no L1 allocation, 2 with a 256-byte
-// L2 prefetch, 3 both.
-__device__ __forceinline__ float4 ldg_row(const float4 *p) {
-#if SG2V_LDG_MODE == 0
+// Load of one 16-byte vector of a gathered table row (read-only path).
+template <typename VT>
+__device__ __forceinline__ VT ldg_row(const VT *p) {
     return __ldg(p);
-#else
-    float4 v;
-#if SG2V_LDG_MODE == 1
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-#elif SG2V_LDG_MODE == 2
-    asm("ld.global.nc.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-#else
-    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-#endif
-    return v;
-#endif
 }
-
-__device__ __forceinline__ double2 ldg_row(const double2 *p) { return __ldg(p); }
 
 // 2^d as a float for an exponent difference d <= 0 (0 below the normal range).
 __device__ __forceinline__ float exp2_neg(int d) { return d < -126 ? 0.f : __int_as_float((d + 127) << 23); }

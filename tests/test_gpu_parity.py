@@ -314,3 +314,25 @@ def test_min_work_plans_match_oracle(sg, seed):
         ref = oracle.count(g.row_ptr, g.col_idx, par, 0, col)
         pv, tot, _ = sg.count(graph, plan, _dev(col), "fp64")
         _check_fp64(pv.cpu().numpy(), tot, ref, exact=ref.max_bits <= 53)
+
+
+@pytest.mark.parametrize("knob", ["SG2V_HIST_ROWS", "SG2V_GROUP_ROWS", "SG2V_HALF_ROOT"])
+def test_alternative_kernel_forms(sg, knob, monkeypatch):
+    """The one-row-per-warp forms that the 32-row histogram kernel, the
+    lane-group kernel and the half-arc root replace on unweighted graphs
+    (they still serve weighted graphs and long tasks) equal the oracle."""
+    monkeypatch.setenv(knob, "0")
+    g = _hub_graph(9)
+    for parent in (si.TREE10.parent, si.TREE7.parent, si.PATH7.parent, (-1, 0, 0, 2)):
+        k = len(parent)
+        col = si.colouring(g.n, k, 5)
+        ref, plan, r64, r32 = _run(sg, g, parent, 0, col)
+        _check_fp64(r64[0], r64[1], ref, exact=ref.max_bits <= 53)
+        _check_fp32(r32[0], r32[1], ref)
+        graph = sg.Graph(g.row_ptr, g.col_idx)
+        _, tot, _ = sg.count_batched(graph, [plan], _dev(col[None, :]), "fp64", per_vertex=False)
+        t = float(tot.cpu().numpy()[0, 0])
+        if ref.max_bits <= 52:
+            assert t == float(ref.total)
+        else:
+            assert abs(t - ref.total) <= FP64_RTOL * ref.total

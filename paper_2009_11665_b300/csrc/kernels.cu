@@ -815,6 +815,8 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
 // once per 32 rows.  Shared memory per warp: counts [kc][32], the active rows
 // of the block [32][mwords], Y' and (scaled) the output row.
 constexpr int kHistRows = 32;
+// rows with at most this many eMA products run their epilogue one per lane
+constexpr int kLaneRowProducts = 1024;
 
 template <typename T, bool WEIGHTED, bool SCALED>
 __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeArgs A) {
@@ -906,6 +908,57 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
             const unsigned fin = __ballot_sync(kFull, finish);
             if (mchunks) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
+            if ((int64_t)A.Ws * (A.a_leaf ? 1 : A.nsplit) <= kLaneRowProducts) {
+                // phase 2 for small rows: lane = row as well.  With a single-
+                // vertex passive child, Y'(j) is the count of the j-th colour
+                // other than v's own.
+                const bool mine = (fin >> lane & 1u) != 0;
+                const int cv = cv_l;
+                const bool ok = mine && (unsigned)cv < (unsigned)kc && task.w > task.z;
+                const int64_t rowb = (int64_t)task.x * A.nb + b;
+                auto y = [&](int j) -> T { return cnt[(j < cv ? j : j + 1) * kHistRows + lane]; };
+                const T *ma = mrows + lane * A.mwords;
+                if (mine && A.Yout && !SCALED) {
+                    T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
+                    for (int j = 0; j < A.wy; ++j) yo[j] = ok ? y(j) : T(0);
+                }
+                T sum = T(0), mx = T(0);
+                T *out = A.root ? nullptr : static_cast<T *>(A.Ms) + rowb * A.ldt;
+                for (int S = 0; S < A.Ws; ++S) {
+                    T acc = T(0);
+                    if (ok) {
+                        if (A.a_leaf) {
+                            acc = y(S);
+                        } else {
+                            const uint32_t *sp = A.splits + (int64_t)S * A.nsplit;
+                            for (int j = 0; j < A.nsplit; ++j) {
+                                const uint32_t x = __ldg(sp + j);
+                                acc = fma(ma[x & 0xffffu], y((int)(x >> 16)), acc);
+                            }
+                        }
+                    }
+                    sum += acc;
+                    mx = fmax(mx, acc);
+                    if (out && mine) out[S] = (!SCALED && A.accumulate) ? out[S] + acc : acc;
+                }
+                if (mine) {
+                    if constexpr (SCALED) {
+                        const int base = ea_l;
+                        if (A.root) {
+                            A.root_out_d[(int64_t)b * A.n + task.x] = ok ? ldexp((double)sum, base) : 0.0;
+                        } else {
+                            const int em = mx > T(0) ? ilogb(mx) : 0;
+                            if (em != 0)
+                                for (int S = 0; S < A.Ws; ++S) out[S] = ldexp(out[S], -em);
+                            A.Es[rowb] = mx > T(0) ? clamp_exp(base + em) : kEmptyRowExp;
+                        }
+                    } else if (A.root) {
+                        static_cast<T *>(A.root_out)[(int64_t)b * A.n + task.x] = sum;
+                    }
+                }
+                __syncwarp();
+                continue;
+            }
             // phase 2: warp = row, expansion and eMA epilogue
             for (int r = 0; r < kHistRows; ++r) {
                 if (!(fin >> r & 1u)) continue;

@@ -247,6 +247,7 @@ struct sg2v_graph {
     int64_t nheavy = 0;
     int chunk = 0;
     int64_t short_begin = 0;  // first task of at most kShortTaskArcs arcs (the rest, sorted by work, are too)
+    int64_t small_begin = 0;  // first task of at most kSortSmallArcs arcs
     int32_t *rev = nullptr;  // reverse arc of every arc, built on the first backward call
 };
 
@@ -799,10 +800,11 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
         const int8_t *wcol = d_col + (int64_t)b0 * n;
         timer.begin("colour_sort",
                     (double)wb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))));
-        SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->col_idx, g->weights, n, g->nnz, wcol, wb, kc, R.scol,
-                                     R.sclr, R.sw, P.info.sms, stream),
+        SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, g->nnz, wcol, wb,
+                                     kc, R.scol, R.sclr, R.sw, P.info.sms, stream),
                   "colour sort");
         timer.end();
+        if (g->small_begin > 0 && g->small_begin < g->ntasks) timer.count_extra(1);  // the small-task sort
         for (size_t i = 0; i < P.nodes.size(); ++i) {
             const CNode &c = P.nodes[i];
             const Shape &sh = P.shape[i];
@@ -1020,6 +1022,7 @@ sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bo
 int64_t count_launches(const Prepared &P, int wave) {
     const int64_t waves = (P.nb + wave - 1) / wave;
     int64_t per_wave = 1 + (int64_t)P.nodes.size();
+    if (P.g->small_begin > 0 && P.g->small_begin < P.g->ntasks) per_wave += 1;  // two sort launches
     if (P.scaled)
         for (const CNode &c : P.nodes) per_wave += c.p != 1;
     for (const Shape &sh : P.shape) per_wave += sh.defer + sh.group;
@@ -1089,6 +1092,12 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
         for (int64_t i = nchunks; i < g->ntasks; ++i)
             if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kShortTaskArcs) {
                 g->short_begin = i;
+                break;
+            }
+        g->small_begin = g->ntasks;
+        for (int64_t i = g->short_begin; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kSortSmallArcs) {
+                g->small_begin = i;
                 break;
             }
     }
@@ -1579,8 +1588,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     if ((st = alloc_run(Pw, 1, alloc, &R))) return st;
     SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
     SG2V_CUDA(launch_check_colours(d_col, n, kc, R.status, stream), "colour check");
-    SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->col_idx, g->weights, n, nnz, d_col, 1, kc, R.scol, R.sclr,
-                                 R.sw, P.info.sms, stream),
+    SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, nnz, d_col, 1, kc,
+                                 R.scol, R.sclr, R.sw, P.info.sms, stream),
               "colour sort");
     // forward, keeping every table and every node's Y'
     std::vector<void *> yt(nn, nullptr), gt(nn, nullptr);

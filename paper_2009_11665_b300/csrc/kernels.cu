@@ -1513,6 +1513,43 @@ __global__ void eref_kernel(const int4 *__restrict__ tasks, int64_t ntasks, cons
     }
 }
 
+// The same sort for tasks of at most G arcs, 32 / G tasks per warp: a lane's
+// arc goes to the number of the task's arcs with a smaller colour (or the
+// same colour and a lower index), counted over the group with shuffles.
+template <int G>
+__global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t ntasks,
+                                         const int32_t *__restrict__ col_idx, const float *__restrict__ weights,
+                                         int64_t n, int64_t nnz, const int8_t *__restrict__ colours, int nb, int kc,
+                                         int32_t *scol, int8_t *sclr, float *sw) {
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G, g0 = grp * G;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t rounds = (ntasks + NG - 1) / NG;
+    for (int64_t rd = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); rd < rounds; rd += nwarps) {
+        const int64_t t = rd * NG + grp;
+        const int4 task = t < ntasks ? tasks[t] : make_int4(0, -1, 0, 0);
+        const int m = task.w - task.z;  // at most G
+        const bool in = gl < m;
+        const int u = in ? __ldg(col_idx + task.z + gl) : 0;
+        for (int b = 0; b < nb; ++b) {
+            int c = in ? (int)__ldg(colours + (int64_t)b * n + u) : 0x7fff;
+            if (in && (unsigned)c >= (unsigned)kc) c = kc;  // invalid colours last
+            int rank = 0;
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int ck = __shfl_sync(kFull, c, g0 + k);
+                rank += (k < m) && (ck < c || (ck == c && k < gl));
+            }
+            if (in) {
+                const int64_t pos = (int64_t)b * nnz + task.z + rank;
+                scol[pos] = u;
+                sclr[pos] = (int8_t)(c == kc ? -1 : c);
+                if (sw) sw[pos] = __ldg(weights + task.z + gl);
+            }
+        }
+    }
+}
+
 // Stable counting sort by neighbour colour of the arcs of each work-list task
 // (a row, or a chunk of a split row), one warp per task for every colouring
 // of the wave; colours outside [0, kc) go last, tagged -1.  Each colour then
@@ -2035,14 +2072,23 @@ cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t *col_idx, const float *weights,
-                               int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc, int32_t *scol,
-                               int8_t *sclr, float *sw, int sms, cudaStream_t stream) {
-    int64_t blocks = (ntasks + 7) / 8;
-    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
-    if (blocks < 1) blocks = 1;
-    colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, col_idx, weights, n, nnz, colours, nb, kc,
-                                                             scol, sclr, sw);
+cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
+                               const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
+                               int32_t *scol, int8_t *sclr, float *sw, int sms, cudaStream_t stream) {
+    if (small_begin > 0) {
+        int64_t blocks = (small_begin + 7) / 8;
+        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, small_begin, col_idx, weights, n, nnz, colours,
+                                                                 nb, kc, scol, sclr, sw);
+    }
+    const int64_t rest = ntasks - small_begin;
+    if (rest > 0) {
+        constexpr int G = kSortSmallArcs;
+        int64_t blocks = ((rest + 32 / G - 1) / (32 / G) + 7) / 8;
+        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        colour_sort_small_kernel<G><<<(unsigned)blocks, 256, 0, stream>>>(
+            tasks + small_begin, rest, col_idx, weights, n, nnz, colours, nb, kc, scol, sclr, sw);
+    }
     return cudaGetLastError();
 }
 

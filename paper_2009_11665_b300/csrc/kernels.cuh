@@ -216,9 +216,12 @@ cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, 
 
 // Sorts the arcs of every work-list task by neighbour colour (stable) for
 // each of nb colourings: scol/sclr/sw [nb][nnz] (sw only when weights != null).
-cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, const int32_t *col_idx, const float *weights,
-                               int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc, int32_t *scol,
-                               int8_t *sclr, float *sw, int sms, cudaStream_t stream);
+// Tasks from small_begin on have at most kSortSmallArcs arcs (the work list
+// is sorted by work) and sort several per warp.
+constexpr int kSortSmallArcs = 8;
+cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
+                               const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
+                               int32_t *scol, int8_t *sclr, float *sw, int sms, cudaStream_t stream);
 
 // Totals and estimates of nseg segments from their root sums: the exact
 // 128-bit sum rounded once to double when every value was an integer, else

@@ -1452,10 +1452,27 @@ __global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, RootSu
     const int64_t lo = (int64_t)chunk * per;
     const int64_t hi = (lo + per < n) ? lo + per : n;
     RootSum acc = rs_from(0.0);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double v = (double)vals[(int64_t)seg * n + i];
-        if (pv) pv[(int64_t)seg * n + i] = v;
-        rs_combine(acc, rs_from(v));
+    if constexpr (sizeof(T) == 4) {
+        // FP32 tables: the exact integer path buys nothing; each thread sums
+        // in double (the per-thread sums are then combined compensated)
+        double sum = 0.0;
+        unsigned bad = 0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const T x = vals[(int64_t)seg * n + i];
+            if (pv) pv[(int64_t)seg * n + i] = (double)x;
+            if (isfinite(x))
+                sum += (double)x;
+            else
+                bad = 1;
+        }
+        acc.s = sum;
+        acc.flags = kFlagNotIntegral | (bad ? kFlagNonFinite : 0u);
+    } else {
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const double v = (double)vals[(int64_t)seg * n + i];
+            if (pv) pv[(int64_t)seg * n + i] = v;
+            rs_combine(acc, rs_from(v));
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

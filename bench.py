@@ -244,7 +244,7 @@ def main():
                     help="run exactly one count call (R-MAT scale 18 or 20 with avg degree 32 and tree10, or the "
                          "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
                          "summaries capture")
-    ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled", "u64"], default="fp32")
     args = ap.parse_args()
     if args.profile_call:
         profile_call(args)
@@ -363,6 +363,30 @@ def main():
                                       "k=8, one colouring", "forward_ms": ms_f, "forward_and_gradient_ms": ms_b,
                           "dtype": "f32"}
 
+    # exact integer tables: the same Chung-Lu graph unweighted, tree8, k = 8,
+    # one colouring per call; its table entries reach 2^61, past the 2^53 up
+    # to which FP64 tables are exact (the headline's reach 2^94: no fit)
+    exact = None
+    if not args.no_batched:
+        graph4u = sg.Graph(g4.row_ptr, g4.col_idx)
+
+        def one(prec):
+            return lambda: sg.sg2v_count_batched(graph4u.handle, [plan4.handle], col4, 1, prec, None, tot4, None,
+                                                 stream)
+
+        reps = max(3, args.steps // 2)
+        try:
+            ms_u = time_steps(torch, one(sg.SG2V_U64), reps, args.warmup, stream, dist)
+            exact_total = float(tot4.item())
+        except sg.Sg2vError as e:  # a colouring whose counts pass 2^64
+            ms_u, exact_total = None, str(e)
+        ms_d = time_steps(torch, one(sg.SG2V_FP64), reps, args.warmup, stream, dist)
+        ms_s = time_steps(torch, one(sg.SG2V_FP32), reps, args.warmup, stream, dist)
+        exact = {"workload": "chunglu200k unweighted (200k vertices, 2M edges, gamma 2.3), tree8, k=8, one "
+                             "colouring per call; table entries up to 2^61", "u64_ms": ms_u, "fp64_ms": ms_d,
+                 "fp32_ms": ms_s, "u64_total": exact_total, "dtype": "u64 (exact), f64, f32"}
+        del graph4u
+
     # large form: R-MAT scale 20 with 5e7 edges, tree15, k = 15, 8 colourings
     # per call.  Counts reach about 2^155, beyond FP32's range, so the tables
     # carry per-row exponents (plain FP32 would overflow and be rerun).
@@ -431,6 +455,7 @@ def main():
         "kernels": kernel_table,
         "batched_3_templates": batched,
         "differentiable": differentiable,
+        "exact_integer": exact,
         "large_form": large,
         "cpu_baseline": cpu,
         "e2e": {"value": ms_e2e * 1e-3 / total_colourings, "unit": UNIT, "h2d_bytes_per_step": int(B * g.n),

@@ -52,7 +52,7 @@ typedef enum {
     SG2V_ERR_COLOUR_OUT_OF_RANGE = 3,
     SG2V_ERR_GRAPH_NOT_SIMPLE = 4, /* self-loop, duplicate arc, unsorted row, asymmetric CSR or weights */
     SG2V_ERR_OUT_OF_MEMORY = 5,
-    SG2V_ERR_FP_OVERFLOW = 6,      /* a count left the range of the table type (inf/NaN) */
+    SG2V_ERR_FP_OVERFLOW = 6,      /* a count left the range of the table type (inf/NaN, or 2^64 for SG2V_U64) */
     SG2V_ERR_CUDA = 7,             /* a CUDA runtime call failed; see sg2v_last_error() */
     SG2V_ERR_TIMEOUT = 8,          /* a bounded device-side wait gave up */
     SG2V_ERR_UNSUPPORTED = 9       /* a valid request this build cannot run (e.g. too many columns) */
@@ -61,7 +61,7 @@ typedef enum {
 typedef enum {
     SG2V_FP64 = 0,       /* count tables and sums in FP64 */
     SG2V_FP32 = 1,       /* count tables in FP32, final reductions in FP64 */
-    SG2V_FP32_SCALED = 2 /* FP32 tables whose rows carry a power-of-two exponent
+    SG2V_FP32_SCALED = 2, /* FP32 tables whose rows carry a power-of-two exponent
                           * (int16): a row's values are its stored values times
                           * 2^E, its largest stored value lies in [1, 2), so
                           * counts far beyond FP32's 2^128 (k = 15 on large
@@ -69,6 +69,13 @@ typedef enum {
                           * 2^-126 of their row's largest, after the gather's
                           * alignment to the row's largest neighbour exponent,
                           * are flushed to zero.  Forward counts only. */
+    SG2V_U64 = 3         /* count tables in unsigned 64-bit integers: every
+                          * value of the DP on an unweighted graph is an integer
+                          * (Alg. 3 / 5), so counts are exact while every table
+                          * entry stays below 2^64, past FP64's 2^53; a sum or
+                          * product that wraps is detected and the call returns
+                          * SG2V_ERR_FP_OVERFLOW.  Unweighted graphs and forward
+                          * counts only (SG2V_ERR_UNSUPPORTED otherwise). */
 } sg2v_precision;
 
 /* ------------------------------------------------------------------ graph */
@@ -175,8 +182,8 @@ sg2v_status sg2v_plan_estimate_scale(const sg2v_plan *plan, double *scale);
  * SpMM + eMA per sub-template, then the root reduction and finalCount).
  *
  *   colours     [n] int8, host or device, values in [0, kc)
- *   precision   SG2V_FP64, SG2V_FP32 or SG2V_FP32_SCALED (table type); an
- *               SG2V_FP32 call that overflows is run again as
+ *   precision   SG2V_FP64, SG2V_FP32, SG2V_FP32_SCALED or SG2V_U64 (table
+ *               type); an SG2V_FP32 call that overflows is run again as
  *               SG2V_FP32_SCALED by sg2v_count and sg2v_count_batched
  *   per_vertex  [n] double, host or device, or NULL: per_vertex[v] is the
  *               number of colourful embeddings (labelled maps) with the

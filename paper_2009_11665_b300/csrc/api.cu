@@ -393,6 +393,7 @@ struct Prepared {
     int kc = 0, nb = 0, dev = 0;
     bool fp64 = false;
     bool scaled = false;          // FP32 tables with per-row power-of-two exponents
+    Elem elem = Elem::F32;        // table element type
     size_t esz = 4;
     int vecn = 4;
     int64_t n = 0;
@@ -407,12 +408,22 @@ struct Prepared {
     int64_t defer_words = 0;      // largest deferred node's Y' row stride (0: none)
 };
 
+const char *elem_name(const Prepared &P) {
+    if (P.scaled) return "fp32s";
+    return P.elem == Elem::F64 ? "fp64" : (P.elem == Elem::U64 ? "u64" : "fp32");
+}
+
 sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t num_plans, int32_t B,
                     sg2v_precision precision, Prepared *P) {
     if (!g || !plans || num_plans < 1 || B < 1 ||
-        (precision != SG2V_FP64 && precision != SG2V_FP32 && precision != SG2V_FP32_SCALED)) {
+        (precision != SG2V_FP64 && precision != SG2V_FP32 && precision != SG2V_FP32_SCALED &&
+         precision != SG2V_U64)) {
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (precision == SG2V_U64 && g->weights) {
+        set_error("integer tables count unweighted graphs only");
+        return SG2V_ERR_UNSUPPORTED;
     }
     const int kc = plans[0] ? plans[0]->kc : 0;
     for (int i = 0; i < num_plans; ++i)
@@ -433,8 +444,9 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
     P->nb = B;
     P->fp64 = precision == SG2V_FP64;
     P->scaled = precision == SG2V_FP32_SCALED;
-    P->esz = P->fp64 ? 8 : 4;
-    P->vecn = P->fp64 ? 2 : 4;
+    P->elem = P->fp64 ? Elem::F64 : (precision == SG2V_U64 ? Elem::U64 : Elem::F32);
+    P->esz = P->elem == Elem::F32 ? 4 : 8;
+    P->vecn = P->elem == Elem::F32 ? 4 : 2;
     P->n = g->n;
     P->plan_root.assign(num_plans, -1);
     std::map<std::string, int> shared;
@@ -477,7 +489,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.wz = hist ? 1 : (int)binom(kc - 1, c.p - 1);
         sh.grp = 32;
         sh.nv = 1;
-        if (!hist) node_shape(P->fp64, sh.wz, &sh.grp, &sh.nv);
+        if (!hist) node_shape(P->esz == 8, sh.wz, &sh.grp, &sh.nv);
         if (!hist && sh.grp != kWideLanes && sh.wz >= wide_min) {
             // rows at least SG2V_WIDE_MIN_WZ wide go to the CTA-per-row kernel
             sh.grp = kWideLanes;
@@ -511,7 +523,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         }
         sh.blocks_per_sm =
             P->scaled ? node_blocks_per_sm_scaled(hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem)
-                      : node_blocks_per_sm(P->fp64, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
+                      : node_blocks_per_sm(P->elem, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
         const char *group_env = std::getenv("SG2V_GROUP_ROWS");
         if (!hist && sh.grp < 32 && sh.nv == 1 && !(group_env && std::atoi(group_env) == 0)) {
             // narrow rows: every lane group takes its own row
@@ -522,7 +534,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             const int bps = smem <= 200 * 1024 ? (P->scaled ? node_blocks_per_sm_scaled(false, sh.grp, 1,
                                                                                         g->weights != nullptr,
                                                                                         threads, smem, true)
-                                                            : node_blocks_per_sm(P->fp64, false, sh.grp, 1,
+                                                            : node_blocks_per_sm(P->elem, false, sh.grp, 1,
                                                                                  g->weights != nullptr, threads, smem,
                                                                                  true))
                                                : 0;
@@ -545,7 +557,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             const int threads = kNodeThreads;
             const size_t smem = per_warp * (threads / 32);
             const int bps = smem <= 160 * 1024
-                                ? hist_rows_blocks_per_sm(P->fp64, P->scaled, g->weights != nullptr, threads, smem)
+                                ? hist_rows_blocks_per_sm(P->elem, P->scaled, g->weights != nullptr, threads, smem)
                                 : 0;
             if (bps >= 1) {
                 sh.rows = true;
@@ -570,8 +582,8 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             probe.wy = (int)binom(kc - 1, c.p);
             probe.Wa = (int)binom(kc - 1, c.a - 1);
             probe.Ws = (int)binom(kc - 1, c.t - 1);
-            const size_t smem = ema_rows_smem(probe, P->fp64, P->scaled);
-            if (ema_rows_blocks_per_sm(P->fp64, P->scaled, smem) >= 1) {
+            const size_t smem = ema_rows_smem(probe, P->elem, P->scaled);
+            if (ema_rows_blocks_per_sm(P->elem, P->scaled, smem) >= 1) {
                 sh.defer = true;
                 sh.ldy = (probe.wy + P->vecn - 1) / P->vecn * P->vecn;
                 P->defer_words = std::max<int64_t>(P->defer_words, sh.ldy);
@@ -749,6 +761,7 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     A.scratch = R.scratch;
     A.scratch_ld = P.scratch_ld;
     A.counters = R.counters;
+    A.status = R.status;
     return A;
 }
 
@@ -756,7 +769,7 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
 cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, cudaStream_t stream) {
     const Shape &sh = P.shape[i];
     const int grid_cap = P.info.sms * sh.blocks_per_sm;
-    if (sh.rows) return launch_hist_rows(A, P.fp64, P.scaled, sh.threads, sh.smem, grid_cap, stream);
+    if (sh.rows) return launch_hist_rows(A, P.elem, P.scaled, sh.threads, sh.smem, grid_cap, stream);
     if (sh.group) {
         // the longer tasks (the front of the work list) one per warp, the short
         // ones one per lane group
@@ -766,17 +779,17 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
         W.ntasks = split;
         cudaError_t e = P.scaled ? launch_node_scaled(W, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
                                                       stream)
-                                 : launch_node(W, P.fp64, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
+                                 : launch_node(W, P.elem, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
                                                stream);
         if (e != cudaSuccess) return e;
         NodeArgs S = A;
         S.tasks = A.tasks + split;
         S.ntasks = A.ntasks - split;
         return P.scaled ? launch_node_scaled(S, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
-                        : launch_node(S, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
+                        : launch_node(S, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     }
     if (P.scaled) return launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
-    return launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
+    return launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
 }
 
 // Enqueues the whole DP for colourings d_col ([nb][n], device) on `stream`:
@@ -820,6 +833,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             A.scratch = R.scratch;
             A.scratch_ld = P.scratch_ld;
             A.counters = R.counters;
+            A.status = R.status;
             // totals only and a root whose two children are one table: each
             // edge's contribution is counted once from its lower end, doubled
             A.half_arcs = c.is_root && c.active == c.passive && c.active != kLeaf && !pv && !A.hist &&
@@ -850,7 +864,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                 if (P.scaled) bytes += rows * (A.hist ? 2.0 : 6.0) + (A.a_leaf ? 0.0 : rows * 2.0);
                 char name[64];
                 std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p,
-                              P.fp64 ? "fp64" : (P.scaled ? "fp32s" : "fp32"));
+                              elem_name(P));
                 timer.begin(name, bytes);
             }
             if (sh.defer) {
@@ -865,9 +879,9 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                 const double rows = (double)n * wb;
                 char name[64];
                 std::snprintf(name, sizeof name, "ema t=%d a=%d p=%d %s", c.t, c.a, c.p,
-                              P.fp64 ? "fp64" : (P.scaled ? "fp32s" : "fp32"));
+                              elem_name(P));
                 timer.begin(name, rows * esz * (double)(sh.ldy + binom(kc - 1, c.a - 1) + A.Ws));
-                SG2V_CUDA(launch_ema_rows(A, P.fp64, P.scaled, P.info.sms, stream), "eMA launch");
+                SG2V_CUDA(launch_ema_rows(A, P.elem, P.scaled, P.info.sms, stream), "eMA launch");
                 timer.end();
             }
             if (c.active != kLeaf && P.nodes[c.active].last_use == (int)i) src.done(c.active);
@@ -878,10 +892,11 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     for (size_t pi = 0; pi < P.plans.size(); ++pi) {
         double *pvp = pv ? pv + pi * (size_t)nb * n : nullptr;
         const void *vals = P.plan_root[pi] >= 0 ? R.rootbuf[pi] : R.ones;
-        const bool vals_fp64 = P.plan_root[pi] >= 0 ? (P.fp64 || P.scaled) : true;
-        timer.begin("root_reduce", (double)nb * n * ((vals_fp64 ? 8 : 4) + (pvp ? 8 : 0)));
+        // root values: the table type, doubles for scaled tables and single-vertex plans
+        const Elem ve = P.plan_root[pi] >= 0 ? (P.scaled ? Elem::F64 : P.elem) : Elem::F64;
+        timer.begin("root_reduce", (double)nb * n * ((ve == Elem::F32 ? 4 : 8) + (pvp ? 8 : 0)));
         timer.count_extra(1);
-        SG2V_CUDA(launch_root_reduce(vals, vals_fp64, n, nb, pvp, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
+        SG2V_CUDA(launch_root_reduce(vals, ve, n, nb, pvp, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
                                      R.sums + pi * (size_t)nb, stream),
                   "root reduction");
         timer.end();
@@ -1197,12 +1212,12 @@ static sg2v_status count_batched_once(const sg2v_graph *g, const sg2v_plan *cons
                   "per-vertex copy");
     SG2V_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
     timer.collect();
-    if (status[0]) {
+    if (status[0] & 1u) {
         set_error("a colour is outside [0, num_colours)");
         return SG2V_ERR_COLOUR_OUT_OF_RANGE;
     }
     std::vector<double> tot(sums.size()), est(sums.size());
-    bool nonfinite = false;
+    bool nonfinite = (status[0] & 2u) != 0;  // an integer count wrapped past 2^64
     for (int pi = 0; pi < num_plans; ++pi) {
         for (int b = 0; b < nb; ++b) {
             const RootSum &r = sums[(size_t)pi * nb + b];
@@ -1467,7 +1482,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
-    if (precision == SG2V_FP32_SCALED) {
+    if (precision == SG2V_FP32_SCALED || precision == SG2V_U64) {
         set_error("the backward pass keeps plain FP64 or FP32 tables");
         return SG2V_ERR_UNSUPPORTED;
     }
@@ -1533,7 +1548,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         const CNode &c = P.nodes[i];
         Shape &sh = bshape[i];
         sh.wz = (int)binom(kc - 1, c.p);
-        node_shape(P.fp64, sh.wz, &sh.grp, &sh.nv);
+        node_shape(P.esz == 8, sh.wz, &sh.grp, &sh.nv);
         if (sh.nv == 0) {
             set_error("gradient rows wider than this build's register tile");
             return SG2V_ERR_UNSUPPORTED;
@@ -1553,7 +1568,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             sh.smem = (size_t)(sh.threads / 32) * per_warp;
         }
         if (c.p >= 2) {
-            sh.blocks_per_sm = node_blocks_per_sm(P.fp64, false, sh.grp, sh.nv, g->weights != nullptr, sh.threads,
+            sh.blocks_per_sm = node_blocks_per_sm(P.elem, false, sh.grp, sh.nv, g->weights != nullptr, sh.threads,
                                                   sh.smem);
             if (sh.blocks_per_sm < 1 || sh.smem > 227 * 1024) {
                 set_error("transposed SpMM does not fit shared memory");
@@ -1621,7 +1636,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     }
     if (total) {
         timer.count_extra(2);
-        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.fp64, n, 1, nullptr, R.partials, R.chunks, R.sums, stream),
+        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.elem, n, 1, nullptr, R.partials, R.chunks, R.sums, stream),
                   "root reduction");
     }
     // seed: gradient of the per-vertex counts
@@ -1709,7 +1724,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
                 SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
             }
             timer.begin("backward: transposed SpMM", 0.0);
-            SG2V_CUDA(launch_node(A, P.fp64, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
+            SG2V_CUDA(launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
                                   stream),
                       "transposed SpMM launch");
             timer.end();
@@ -1735,7 +1750,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         if (c.p >= 2) {
             // row-oriented form over the forward work list, gather shape of M_p' rows
             int lanes = 32, vecs = 1;
-            node_shape(P.fp64, D.wmp, &lanes, &vecs);
+            node_shape(P.esz == 8, D.wmp, &lanes, &vecs);
             if (lanes != kWideLanes && vecs >= 1) {
                 D.tasks = g->tasks;
                 D.ntasks = g->ntasks;

@@ -109,6 +109,104 @@ struct Vec16<double> {
     }
 };
 
+// Exact integer tables: unsigned 64-bit counts.  Every sum and product of
+// the DP is an integer (Alg. 3 / 5 on an unweighted graph), so these tables
+// are exact while each entry stays below 2^64; Ar<u64> reports every wrap.
+using u64 = unsigned long long;
+
+// Arithmetic of the table type with overflow accounting.  Floating-point
+// types round and leave ovf alone; for unsigned 64-bit counts a carry out of
+// bit 63 of a sum increments ovf and a product whose high 64 bits are not
+// zero sets it, so ovf != 0 exactly when some result wrapped (a thread makes
+// far fewer than 2^32 checked steps between two reports).
+template <typename T>
+struct Ar {
+    static constexpr bool exact = false;
+    __device__ static void add(T &a, T b, unsigned &) { a += b; }
+    __device__ static void mad(T &acc, T a, T b, unsigned &) { acc = fma(a, b, acc); }
+    __device__ static T twice(T a, unsigned &) { return T(2) * a; }
+};
+template <>
+struct Ar<u64> {
+    static constexpr bool exact = true;
+    __device__ static void add(u64 &a, u64 b, unsigned &ovf) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(a), "+r"(ovf) : "l"(b));
+    }
+    __device__ static void mad(u64 &acc, u64 a, u64 b, unsigned &ovf) {
+        ovf |= __umul64hi(a, b) != 0ull ? 1u : 0u;
+        add(acc, a * b, ovf);
+    }
+    __device__ static u64 twice(u64 a, unsigned &ovf) {
+        ovf |= (unsigned)(a >> 63);
+        return a << 1;
+    }
+};
+
+template <>
+struct Vec16<u64> {
+    using type = ulonglong2;
+    static constexpr int n = 2;
+    __device__ static ulonglong2 zero() { return make_ulonglong2(0ull, 0ull); }
+    __device__ static void add(ulonglong2 &a, const ulonglong2 &b) {
+        a.x += b.x;
+        a.y += b.y;
+    }
+    // integer tables count unweighted graphs only: w is 1
+    __device__ static void fma(ulonglong2 &a, u64 w, const ulonglong2 &b) {
+        a.x += w * b.x;
+        a.y += w * b.y;
+    }
+    __device__ static void store(u64 *p, const ulonglong2 &a) {
+        p[0] = a.x;
+        p[1] = a.y;
+    }
+    __device__ static ulonglong2 shfl_xor(const ulonglong2 &a, int o) {
+        return make_ulonglong2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+    }
+};
+
+// a += b for a 16-byte vector, with overflow accounting for integer tables.
+template <typename T>
+__device__ __forceinline__ void vadd(typename Vec16<T>::type &a, const typename Vec16<T>::type &b, unsigned &ovf) {
+    if constexpr (Ar<T>::exact) {
+        Ar<T>::add(a.x, b.x, ovf);
+        Ar<T>::add(a.y, b.y, ovf);
+    } else {
+        (void)ovf;
+        Vec16<T>::add(a, b);
+    }
+}
+
+// *p += x in global memory (partial rows of split rows), with overflow
+// accounting for integer tables.
+template <typename T>
+__device__ __forceinline__ void atomic_add(T *p, T x, unsigned &ovf) {
+    if constexpr (Ar<T>::exact) {
+        const T old = atomicAdd(p, x);
+        ovf |= old + x < old ? 1u : 0u;
+    } else {
+        (void)ovf;
+        atomicAdd(p, x);
+    }
+}
+
+// Bit 1 of status word 0: a count left the range of the table type.
+constexpr unsigned kStatusOverflow = 2u;
+
+// Integer tables: a thread that saw a wrap raises the overflow status.
+template <typename T>
+__device__ __forceinline__ void report_ovf(unsigned *status, unsigned &ovf) {
+    if constexpr (Ar<T>::exact) {
+        if (ovf) {
+            atomicOr(status, kStatusOverflow);
+            ovf = 0;
+        }
+    } else {
+        (void)status;
+        (void)ovf;
+    }
+}
+
 // Load of one 16-byte vector of a gathered table row (read-only path).
 template <typename VT>
 __device__ __forceinline__ VT ldg_row(const VT *p) {
@@ -152,6 +250,13 @@ __device__ __forceinline__ T group_sum(T v) {
 }
 
 template <int G, typename T>
+__device__ __forceinline__ T group_sum_chk(T v, unsigned &ovf) {
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) Ar<T>::add(v, __shfl_xor_sync(kFull, v, o), ovf);
+    return v;
+}
+
+template <int G, typename T>
 __device__ __forceinline__ T group_max(T v) {
 #pragma unroll
     for (int o = G >> 1; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
@@ -173,7 +278,7 @@ __device__ __forceinline__ T group_max(T v) {
 // still fill a warp-wide load).  Copies are folded into copy 0 at the end.
 template <typename T, int G, int NV, bool WEIGHTED, bool SCALED>
 __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int64_t e1, int b, int cv, int eref,
-                                       T *zbuf, int lane) {
+                                       T *zbuf, int lane, unsigned &ovf) {
     constexpr bool FMA = WEIGHTED || SCALED;
     using V = Vec16<T>;
     using VT = typename V::type;
@@ -196,6 +301,11 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
     bool qok[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) qok[q] = gl + G * q < nvec;
+    // integer tables of odd width: the last vector's second element is row
+    // padding that no kernel writes; it is cleared so that it adds no carry
+    bool tail[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && (A.Wz & 1) && gl + G * q == nvec - 1;
     const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;  // vectors between consecutive vertices' rows
     const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + gl;
     const int32_t *scol = A.scol + (int64_t)b * A.nnz;
@@ -270,8 +380,11 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
                 }
                 const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
-                for (int q = 0; q < NV; ++q)
+                for (int q = 0; q < NV; ++q) {
                     x[r][q] = (!SKIP_ZERO || (live[r] && qok[q])) ? ldg_row(row + G * q) : V::zero();
+                    if constexpr (Ar<T>::exact)
+                        if (tail[q]) x[r][q].y = 0;
+                }
             }
 #pragma unroll
             for (int r = 0; r < U; ++r) {
@@ -285,7 +398,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
                     if (FMA)
                         V::fma(run[q], w[r], x[r][q]);
                     else
-                        V::add(run[q], x[r][q]);
+                        vadd<T>(run[q], x[r][q], ovf);
                 }
             }
         }
@@ -300,10 +413,13 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
     }
     __syncwarp();
     if (NG > 1) {
+        // the copies' rows of v's own colour hold stale data: skipped
+        const int own0 = cv * (wzp / V::n), own1 = own0 + wzp / V::n;
         for (int i = lane; i < zlen / V::n; i += 32) {
+            if (i >= own0 && i < own1) continue;
             VT acc = zv[i];
 #pragma unroll
-            for (int g = 1; g < NG; ++g) V::add(acc, zv[g * zlen / V::n + i]);
+            for (int g = 1; g < NG; ++g) vadd<T>(acc, zv[g * zlen / V::n + i], ovf);
             zv[i] = acc;
         }
     }
@@ -364,12 +480,13 @@ __device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, i
 // Y'(j) for the p-sets j of the squeezed universe of colour cv (the colour
 // sets without cv the eMA needs), summed from Z.
 template <typename T>
-__device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbuf, T *ybuf, int lane) {
+__device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbuf, T *ybuf, int lane,
+                                         unsigned &ovf) {
     const int p = A.p, wy = A.wy;
     const uint16_t *ex = A.expand + (int64_t)cv * wy * p;
     for (int j = lane; j < wy; j += 32) {
         T s = T(0);
-        for (int k = 0; k < p; ++k) s += zbuf[__ldg(ex + j * p + k)];
+        for (int k = 0; k < p; ++k) Ar<T>::add(s, zbuf[__ldg(ex + j * p + k)], ovf);
         ybuf[j] = s;
     }
 }
@@ -381,17 +498,18 @@ __device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbu
 // thread that owns one output set of a non-root row walks its splits in
 // order, so the split table's cache lines serve 32 consecutive steps.
 template <typename T, int NT>
-__device__ __forceinline__ T ema_root_partial(const NodeArgs &A, bool ok, const T *ybuf, const T *ma, int tid) {
+__device__ __forceinline__ T ema_root_partial(const NodeArgs &A, bool ok, const T *ybuf, const T *ma, int tid,
+                                             unsigned &ovf) {
     T s = T(0);
     if (!ok) return s;
     if (A.a_leaf) {
-        for (int j = tid; j < A.Ws; j += NT) s += ybuf[j];
+        for (int j = tid; j < A.Ws; j += NT) Ar<T>::add(s, ybuf[j], ovf);
         return s;
     }
     const int total = A.Ws * A.nsplit;
     for (int p = tid; p < total; p += NT) {
         const uint32_t x = __ldg(A.splits + p);
-        s = fma(ma[x & 0xffffu], ybuf[x >> 16], s);
+        Ar<T>::mad(s, ma[x & 0xffffu], ybuf[x >> 16], ovf);
     }
     return s;
 }
@@ -402,7 +520,7 @@ __device__ __forceinline__ T ema_root_partial(const NodeArgs &A, bool ok, const 
 // sets L = 1.
 template <typename T, int NT, typename F>
 __device__ __forceinline__ void ema_rows(const NodeArgs &A, bool ok, const T *ybuf, const T *ma, int tid,
-                                         F &&put) {
+                                         unsigned &ovf, F &&put) {
     const int ws = A.Ws;
     if (A.a_leaf) {
         for (int S = tid; S < ws; S += NT) put(S, ok ? ybuf[S] : T(0));
@@ -418,7 +536,7 @@ __device__ __forceinline__ void ema_rows(const NodeArgs &A, bool ok, const T *yb
                 const uint32_t *sp = A.splits + (int64_t)S * ns;
                 for (int j = 0; j < ns; ++j) {
                     const uint32_t x = __ldg(sp + j);
-                    acc = fma(ma[x & 0xffffu], ybuf[x >> 16], acc);
+                    Ar<T>::mad(acc, ma[x & 0xffffu], ybuf[x >> 16], ovf);
                 }
             }
             put(S, acc);
@@ -433,10 +551,10 @@ __device__ __forceinline__ void ema_rows(const NodeArgs &A, bool ok, const T *yb
             const uint32_t *sp = A.splits + (int64_t)S * ns;
             for (int j = j0; j < ns; j += L) {
                 const uint32_t x = __ldg(sp + j);
-                acc = fma(ma[x & 0xffffu], ybuf[x >> 16], acc);
+                Ar<T>::mad(acc, ma[x & 0xffffu], ybuf[x >> 16], ovf);
             }
         }
-        for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        for (int o = L >> 1; o > 0; o >>= 1) Ar<T>::add(acc, __shfl_xor_sync(kFull, acc, o), ovf);
         if (j0 == 0 && S < ws) put(S, acc);
     }
 }
@@ -448,20 +566,23 @@ __device__ __forceinline__ void ema_rows(const NodeArgs &A, bool ok, const T *yb
 // [0, kc), reported by the host) writes zeros.
 template <typename T>
 __device__ __forceinline__ void epilogue(const NodeArgs &A, int v, int b, bool ok, const T *ybuf, const T *ma,
-                                         int lane) {
+                                         int lane, unsigned &ovf) {
     const int64_t rowb = (int64_t)v * A.nb + b;
     if (A.Yout) {
         T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
         for (int j = lane; j < A.wy; j += 32) yo[j] = ok ? ybuf[j] : T(0);
     }
     if (A.root) {
-        const T s = warp_sum(ema_root_partial<T, 32>(A, ok, ybuf, ma, lane));
-        if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? T(2) * s : s;
+        const T s = group_sum_chk<32>(ema_root_partial<T, 32>(A, ok, ybuf, ma, lane, ovf), ovf);
+        if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? Ar<T>::twice(s, ovf) : s;
         return;
     }
     T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
     const bool accumulate = A.accumulate != 0;
-    ema_rows<T, 32>(A, ok, ybuf, ma, lane, [&](int S, T x) { out[S] = accumulate ? out[S] + x : x; });
+    ema_rows<T, 32>(A, ok, ybuf, ma, lane, ovf, [&](int S, T x) {
+        if (accumulate) Ar<T>::add(x, out[S], ovf);
+        out[S] = x;
+    });
 }
 
 // Scaled FP32 eMA: outputs go to obuf first; the row is then normalised so
@@ -472,12 +593,14 @@ __device__ __forceinline__ void epilogue_scaled(const NodeArgs &A, int v, int b,
                                                 const float *ma, float *obuf, int base, int lane) {
     const int64_t rowb = (int64_t)v * A.nb + b;
     if (A.root) {
-        const float s = warp_sum(ema_root_partial<float, 32>(A, ok, ybuf, ma, lane));
+        unsigned ovf = 0;
+        const float s = warp_sum(ema_root_partial<float, 32>(A, ok, ybuf, ma, lane, ovf));
         if (lane == 0) A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)s, base + (A.half_arcs ? 1 : 0)) : 0.0;
         return;
     }
     float m = 0.f;
-    ema_rows<float, 32>(A, ok, ybuf, ma, lane, [&](int S, float x) {
+    unsigned ovf = 0;
+    ema_rows<float, 32>(A, ok, ybuf, ma, lane, ovf, [&](int S, float x) {
         obuf[S] = x;
         m = fmaxf(m, x);
     });
@@ -517,6 +640,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
     int4 task = ti < A.ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
+    unsigned ovf = 0;
     for (; ti < A.ntasks; ti += nwarps) {
         // the next task's descriptor is fetched while this one runs
         const int4 next = ti + nwarps < A.ntasks ? A.tasks[ti + nwarps] : task;
@@ -536,7 +660,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
                 if constexpr (SCALED)
                     epilogue_scaled(A, v, b, false, ybuf, mbuf, obuf, 0, lane);
                 else
-                    epilogue<T>(A, v, b, false, ybuf, mbuf, lane);
+                    epilogue<T>(A, v, b, false, ybuf, mbuf, lane, ovf);
                 continue;
             }
             int eref = 0;
@@ -553,13 +677,16 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
             if (HIST)
                 hist_z<T, WEIGHTED>(A, e0, e1, b, zbuf, lane);
             else
-                spmm_z<T, G, NV, WEIGHTED, SCALED>(A, v, e0, e1, b, cv, eref, zbuf, lane);
+                spmm_z<T, G, NV, WEIGHTED, SCALED>(A, v, e0, e1, b, cv, eref, zbuf, lane, ovf);
             __syncwarp();
             if (slot >= 0) {
                 // one chunk of a split row: fold Z into the scratch row; the
                 // last chunk to arrive finishes the row
                 T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
-                for (int j = lane; j < zlen; j += 32) atomicAdd(sc + j, zbuf[j]);
+                // (the row of v's own colour in Z is stale and read by nothing)
+                const int own0 = HIST ? zlen : cv * A.wz_pad, own1 = HIST ? zlen : own0 + A.wz_pad;
+                for (int j = lane; j < zlen; j += 32)
+                    if (j < own0 || j >= own1) atomic_add(sc + j, zbuf[j], ovf);
                 __threadfence();
                 __syncwarp();
                 int last = 0;
@@ -577,7 +704,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
                 for (int j = lane; j < zlen; j += 32) zbuf[j] = __ldcg(sc + j);
                 __syncwarp();
             }
-            if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane);
+            if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane, ovf);
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
             if (A.defer) {
@@ -591,10 +718,11 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
                 const int base = (A.a_leaf ? 0 : (int)A.Ea[(int64_t)v * A.nb + b]) + eref;
                 epilogue_scaled(A, v, b, cok, ybuf, mbuf, obuf, base, lane);
             } else {
-                epilogue<T>(A, v, b, cok, ybuf, mbuf, lane);
+                epilogue<T>(A, v, b, cok, ybuf, mbuf, lane, ovf);
             }
             __syncwarp();
         }
+        report_ovf<T>(A.status, ovf);
         task = next;
     }
 }
@@ -627,10 +755,13 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
     T *obuf = mbuf + A.mwords;
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const bool qok = gl < (A.Wz + V::n - 1) / V::n;
+    // integer tables of odd width: the last vector's padding element is cleared
+    const bool tail = Ar<T>::exact && (A.Wz & 1) && gl == (A.Wz + V::n - 1) / V::n - 1;
     const int zero_row = (int)A.n;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t wglob = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
     const int64_t nrounds = (A.ntasks + (int64_t)NG - 1) / NG;
+    unsigned ovf = 0;
     for (int64_t rnd = wglob; rnd < nrounds; rnd += nwarps) {
         const int64_t ti = rnd * NG + grp;
         const bool have = ti < A.ntasks;
@@ -710,6 +841,8 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
                         }
                         const VT *row = Mb + (int64_t)(lv[r] ? u : zero_row) * uvec;
                         x[r] = (SKIP_ZERO ? (lv[r] && qok) : true) ? ldg_row(row) : V::zero();
+                        if constexpr (Ar<T>::exact)
+                            if (tail) x[r].y = 0;
                     }
 #pragma unroll
                     for (int r = 0; r < U; ++r) {
@@ -721,7 +854,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
                         if (FMA)
                             V::fma(run, w[r], x[r]);
                         else
-                            V::add(run, x[r]);
+                            vadd<T>(run, x[r], ovf);
                     }
                 }
             }
@@ -733,7 +866,9 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             bool fin = have;
             if (have && slot >= 0) {
                 T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
-                for (int j = gl; j < kc * wzp; j += G) atomicAdd(sc + j, zg[j]);
+                // (the row of v's own colour in Z is stale and read by nothing)
+                for (int j = gl; j < kc * wzp; j += G)
+                    if (j / wzp != cv) atomic_add(sc + j, zg[j], ovf);
                 __threadfence();
             }
             __syncwarp();
@@ -757,7 +892,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
                 const uint16_t *ex = A.expand + (int64_t)cv * A.wy * A.p;
                 for (int j = gl; j < A.wy; j += G) {
                     T y = T(0);
-                    for (int k = 0; k < A.p; ++k) y += zg[__ldg(ex + j * A.p + k)];
+                    for (int k = 0; k < A.p; ++k) Ar<T>::add(y, zg[__ldg(ex + j * A.p + k)], ovf);
                     ybuf[j] = y;
                 }
             }
@@ -774,16 +909,16 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             // eMA epilogue of the group's row
             const int base_e = SCALED ? (A.a_leaf ? 0 : (fin && have ? (int)A.Ea[rowb] : 0)) + eref : 0;
             if (A.root) {
-                const T sum = group_sum<G>(ema_root_partial<T, G>(A, ok, ybuf, mbuf, gl));
+                const T sum = group_sum_chk<G>(ema_root_partial<T, G>(A, ok, ybuf, mbuf, gl, ovf), ovf);
                 if (fin && gl == 0) {
                     if constexpr (SCALED)
                         A.root_out_d[(int64_t)b * A.n + v] = ok ? ldexp((double)sum, base_e + (A.half_arcs ? 1 : 0)) : 0.0;
                     else
-                        static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? T(2) * sum : sum;
+                        static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? Ar<T>::twice(sum, ovf) : sum;
                 }
             } else if constexpr (SCALED) {
                 T mx = T(0);
-                ema_rows<T, G>(A, ok, ybuf, mbuf, gl, [&](int S, T x) {
+                ema_rows<T, G>(A, ok, ybuf, mbuf, gl, ovf, [&](int S, T x) {
                     obuf[S] = x;
                     mx = fmax(mx, x);
                 });
@@ -798,12 +933,15 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             } else {
                 T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
                 const bool accumulate = A.accumulate != 0;
-                ema_rows<T, G>(A, ok, ybuf, mbuf, gl, [&](int S, T x) {
-                    if (fin) out[S] = accumulate ? out[S] + x : x;
+                ema_rows<T, G>(A, ok, ybuf, mbuf, gl, ovf, [&](int S, T x) {
+                    if (!fin) return;
+                    if (accumulate) Ar<T>::add(x, out[S], ovf);
+                    out[S] = x;
                 });
             }
             __syncwarp();
         }
+        report_ovf<T>(A.status, ovf);
     }
 }
 
@@ -832,6 +970,7 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
     const int mchunks = A.a_leaf ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nblocks = (A.ntasks + kHistRows - 1) / kHistRows;
+    unsigned ovf = 0;
     for (int64_t blk = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; blk < nblocks; blk += nwarps) {
         const int64_t t = blk * kHistRows + lane;
         const bool have = t < A.ntasks;
@@ -933,13 +1072,16 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
                             const uint32_t *sp = A.splits + (int64_t)S * A.nsplit;
                             for (int j = 0; j < A.nsplit; ++j) {
                                 const uint32_t x = __ldg(sp + j);
-                                acc = fma(ma[x & 0xffffu], y((int)(x >> 16)), acc);
+                                Ar<T>::mad(acc, ma[x & 0xffffu], y((int)(x >> 16)), ovf);
                             }
                         }
                     }
-                    sum += acc;
-                    mx = fmax(mx, acc);
-                    if (out && mine) out[S] = (!SCALED && A.accumulate) ? out[S] + acc : acc;
+                    Ar<T>::add(sum, acc, ovf);
+                    if constexpr (SCALED) mx = fmax(mx, acc);
+                    if (out && mine) {
+                        if (!SCALED && A.accumulate) Ar<T>::add(acc, out[S], ovf);
+                        out[S] = acc;
+                    }
                 }
                 if (mine) {
                     if constexpr (SCALED) {
@@ -977,11 +1119,12 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
                     const int base = __shfl_sync(kFull, ea_l, r);
                     epilogue_scaled(A, v, b, ok, ybuf, ma, obuf, base, lane);
                 } else {
-                    epilogue<T>(A, v, b, ok, ybuf, ma, lane);
+                    epilogue<T>(A, v, b, ok, ybuf, ma, lane, ovf);
                 }
                 __syncwarp();
             }
         }
+        report_ovf<T>(A.status, ovf);
     }
 }
 
@@ -1012,6 +1155,16 @@ struct RowVec<double> {
         }
     }
 };
+template <>
+struct RowVec<u64> {
+    static __device__ void load(const u64 *p, u64 (&x)[kEmaRows]) {
+#pragma unroll
+        for (int i = 0; i < kEmaRows; i += 2) {
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(p + i);
+            x[i] = a.x; x[i + 1] = a.y;
+        }
+    }
+};
 static_assert(kEmaRows % 4 == 0, "RowVec loads rows four at a time");
 
 template <typename T, bool SCALED>
@@ -1025,6 +1178,7 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
     __shared__ T s_max[R][8];
     __shared__ int s_ok[R];
     const int64_t rows = A.n * A.nb;
+    unsigned ovf = 0;
     for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < rows; r0 += (int64_t)gridDim.x * R) {
         if (tid < R) {
             const int64_t row = r0 + tid;
@@ -1060,12 +1214,12 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
                 RowVec<T>::load(mas + (x & 0xffffu) * R, m);
                 RowVec<T>::load(ys + (x >> 16) * R, y);
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] = fma(m[r], y[r], acc[r]);
+                for (int r = 0; r < R; ++r) Ar<T>::mad(acc[r], m[r], y[r], ovf);
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const T val = s_ok[r] ? acc[r] : T(0);
-                if (SCALED) mx[r] = fmax(mx[r], val);
+                if constexpr (SCALED) mx[r] = fmax(mx[r], val);
                 if (r0 + r < rows) static_cast<T *>(A.Ms)[(r0 + r) * A.ldt + S] = val;
             }
         }
@@ -1094,6 +1248,7 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
             }
         }
         __syncthreads();
+        report_ovf<T>(A.status, ovf);
     }
 }
 
@@ -1129,6 +1284,11 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     bool qok[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) qok[q] = vbase + 32 * q < nvec;
+    // integer tables of odd width: the last vector's padding element is cleared
+    bool tail[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && (A.Wz & 1) && vbase + 32 * q == nvec - 1;
+    unsigned ovf = 0;
     for (int64_t ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
         const int4 task = A.tasks[ti];
         const int v = task.x, slot = task.y;
@@ -1212,8 +1372,11 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                             }
                             const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
-                            for (int q = 0; q < NV; ++q)
+                            for (int q = 0; q < NV; ++q) {
                                 x[r][q] = (sizeof(T) == 4 || qok[q]) ? ldg_row(row + 32 * q) : V::zero();
+                                if constexpr (Ar<T>::exact)
+                                    if (tail[q]) x[r][q].y = 0;
+                            }
                         }
 #pragma unroll
                         for (int r = 0; r < U; ++r) {
@@ -1226,7 +1389,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                                 if (FMA)
                                     V::fma(run[q], wr[r], x[r][q]);
                                 else
-                                    V::add(run[q], x[r][q]);
+                                    vadd<T>(run[q], x[r][q], ovf);
                             }
                         }
                     }
@@ -1243,7 +1406,9 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             __syncthreads();
             if (slot >= 0 && cok) {
                 T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
-                for (int j = tid; j < zlen; j += blockDim.x) atomicAdd(sc + j, zbuf[j]);
+                // (the row of v's own colour in Z is stale and read by nothing)
+                for (int j = tid; j < zlen; j += blockDim.x)
+                    if (j < cv * wzp || j >= (cv + 1) * wzp) atomic_add(sc + j, zbuf[j], ovf);
                 __threadfence();
                 __syncthreads();
                 if (tid == 0) {
@@ -1266,7 +1431,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                 const uint16_t *ex = A.expand + (int64_t)cv * wy * p;
                 for (int j = tid; j < wy; j += blockDim.x) {
                     T s = T(0);
-                    for (int k = 0; k < p; ++k) s += zbuf[__ldg(ex + j * p + k)];
+                    for (int k = 0; k < p; ++k) Ar<T>::add(s, zbuf[__ldg(ex + j * p + k)], ovf);
                     ybuf[j] = s;
                 }
             }
@@ -1284,12 +1449,12 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             // eMA in squeezed coordinates over the whole CTA
             const int base = SCALED ? (A.a_leaf ? 0 : (int)A.Ea[rowb]) + eref : 0;
             if (A.root) {
-                T sum = warp_sum(ema_root_partial<T, kWideThreads>(A, cok, ybuf, mbuf, tid));
+                T sum = group_sum_chk<32>(ema_root_partial<T, kWideThreads>(A, cok, ybuf, mbuf, tid, ovf), ovf);
                 if (lane == 0) s_red[w] = sum;
                 __syncthreads();
                 if (tid == 0) {
                     T t = T(0);
-                    for (int i = 0; i < kWideWarps; ++i) t += s_red[i];
+                    for (int i = 0; i < kWideWarps; ++i) Ar<T>::add(t, s_red[i], ovf);
                     if constexpr (SCALED)
                         A.root_out_d[(int64_t)b * A.n + v] = cok ? ldexp((double)t, base) : 0.0;
                     else
@@ -1298,7 +1463,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             } else if constexpr (SCALED) {
                 // outputs to obuf, then the row is normalised by its largest value
                 T mx = T(0);
-                ema_rows<T, kWideThreads>(A, cok, ybuf, mbuf, tid, [&](int S, T x) {
+                ema_rows<T, kWideThreads>(A, cok, ybuf, mbuf, tid, ovf, [&](int S, T x) {
                     obuf[S] = x;
                     mx = fmax(mx, x);
                 });
@@ -1314,11 +1479,14 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             } else {
                 T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
                 const bool accumulate = A.accumulate != 0;
-                ema_rows<T, kWideThreads>(A, cok, ybuf, mbuf, tid,
-                                          [&](int S, T x) { out[S] = accumulate ? out[S] + x : x; });
+                ema_rows<T, kWideThreads>(A, cok, ybuf, mbuf, tid, ovf, [&](int S, T x) {
+                    if (accumulate) Ar<T>::add(x, out[S], ovf);
+                    out[S] = x;
+                });
             }
             __syncthreads();
         }
+        report_ovf<T>(A.status, ovf);
     }
 }
 
@@ -1361,19 +1529,24 @@ void *pick_group(int g) {
     return nullptr;
 }
 
-void *select_kernel(bool fp64, bool hist, int g, int nv, bool weighted, bool group = false) {
+void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group = false) {
+    // integer tables count unweighted graphs only
+    if (e == Elem::U64 && weighted) return nullptr;
     if (group) {
         if (hist || nv != 1) return nullptr;
-        if (fp64) return weighted ? pick_group<double, true, false>(g) : pick_group<double, false, false>(g);
+        if (e == Elem::U64) return pick_group<u64, false, false>(g);
+        if (e == Elem::F64) return weighted ? pick_group<double, true, false>(g) : pick_group<double, false, false>(g);
         return weighted ? pick_group<float, true, false>(g) : pick_group<float, false, false>(g);
     }
     if (g == kWideLanes) {
         // wide rows: one CTA per task (nv vectors per lane, 8 warps)
         if (hist) return nullptr;
-        if (fp64) return weighted ? pick_wide<double, true>(nv) : pick_wide<double, false>(nv);
+        if (e == Elem::U64) return pick_wide<u64, false>(nv);
+        if (e == Elem::F64) return weighted ? pick_wide<double, true>(nv) : pick_wide<double, false>(nv);
         return weighted ? pick_wide<float, true>(nv) : pick_wide<float, false>(nv);
     }
-    if (fp64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
+    if (e == Elem::U64) return pick<u64, false>(hist, g, nv);
+    if (e == Elem::F64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
     return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
 }
 
@@ -1467,6 +1640,17 @@ __global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, RootSu
         }
         acc.s = sum;
         acc.flags = kFlagNotIntegral | (bad ? kFlagNonFinite : 0u);
+    } else if constexpr (Ar<T>::exact) {
+        // integer tables: the 128-bit sum directly (and a double sum beside it)
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const u64 x = vals[(int64_t)seg * n + i];
+            const double d = __ull2double_rn(x);
+            if (pv) pv[(int64_t)seg * n + i] = d;
+            RootSum r = rs_from(0.0);
+            r.lo = x;
+            r.s = d;
+            rs_combine(acc, r);
+        }
     } else {
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const double v = (double)vals[(int64_t)seg * n + i];
@@ -1921,8 +2105,8 @@ __global__ void check_colours_kernel(const int8_t *colours, int64_t count, int k
 
 }  // namespace
 
-void node_shape(bool fp64, int wz, int *g, int *nv) {
-    const int vecn = fp64 ? 2 : 4;
+void node_shape(bool eight_byte, int wz, int *g, int *nv) {
+    const int vecn = eight_byte ? 2 : 4;
     const int nvec = (wz + vecn - 1) / vecn;
     *nv = 1;
     if (nvec <= 4)
@@ -1984,17 +2168,18 @@ cudaError_t launch_variant(void *k, const NodeArgs &args, int g, int threads, si
 
 }  // namespace
 
-int node_blocks_per_sm(bool fp64, bool hist, int g, int nv, bool weighted, int threads, size_t smem, bool group) {
-    return blocks_per_sm(select_kernel(fp64, hist, g, nv, weighted, group), threads, smem);
+int node_blocks_per_sm(Elem e, bool hist, int g, int nv, bool weighted, int threads, size_t smem, bool group) {
+    return blocks_per_sm(select_kernel(e, hist, g, nv, weighted, group), threads, smem);
 }
 
 int node_blocks_per_sm_scaled(bool hist, int g, int nv, bool weighted, int threads, size_t smem, bool group) {
     return blocks_per_sm(select_kernel_scaled(hist, g, nv, weighted, group), threads, smem);
 }
 
-cudaError_t launch_node(const NodeArgs &args, bool fp64, int g, int nv, int threads, size_t smem, int grid_cap,
+cudaError_t launch_node(const NodeArgs &args, Elem e, int g, int nv, int threads, size_t smem, int grid_cap,
                         cudaStream_t stream) {
-    void *k = select_kernel(fp64, args.hist != 0, g, nv, args.weights != nullptr, args.group_rows != 0);
+    void *k = select_kernel(e, args.hist != 0, g, nv, args.weights != nullptr, args.group_rows != 0);
+    if (!k) return cudaErrorInvalidValue;
     return launch_variant(k, args, g, threads, smem, grid_cap, stream);
 }
 
@@ -2005,23 +2190,25 @@ cudaError_t launch_node_scaled(const NodeArgs &args, int g, int nv, int threads,
 }
 
 namespace {
-void *select_hist_rows(bool fp64, bool scaled, bool weighted) {
+void *select_hist_rows(Elem e, bool scaled, bool weighted) {
     if (scaled) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<float, true, true>)
                                 : reinterpret_cast<void *>(&hist_rows_kernel<float, false, true>);
-    if (fp64) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<double, true, false>)
+    if (e == Elem::U64) return weighted ? nullptr : reinterpret_cast<void *>(&hist_rows_kernel<u64, false, false>);
+    if (e == Elem::F64) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<double, true, false>)
                               : reinterpret_cast<void *>(&hist_rows_kernel<double, false, false>);
     return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<float, true, false>)
                     : reinterpret_cast<void *>(&hist_rows_kernel<float, false, false>);
 }
 }  // namespace
 
-int hist_rows_blocks_per_sm(bool fp64, bool scaled, bool weighted, int threads, size_t smem) {
-    return blocks_per_sm(select_hist_rows(fp64, scaled, weighted), threads, smem);
+int hist_rows_blocks_per_sm(Elem e, bool scaled, bool weighted, int threads, size_t smem) {
+    return blocks_per_sm(select_hist_rows(e, scaled, weighted), threads, smem);
 }
 
-cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int threads, size_t smem, int grid_cap,
+cudaError_t launch_hist_rows(const NodeArgs &args, Elem e, bool scaled, int threads, size_t smem, int grid_cap,
                              cudaStream_t stream) {
-    void *k = select_hist_rows(fp64, scaled, args.weights != nullptr);
+    void *k = select_hist_rows(e, scaled, args.weights != nullptr);
+    if (!k) return cudaErrorInvalidValue;
     if (args.ntasks == 0) return cudaSuccess;
     const int64_t warps = (args.ntasks + kHistRows - 1) / kHistRows;
     int64_t grid = (warps + threads / 32 - 1) / (threads / 32);
@@ -2032,40 +2219,43 @@ cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int t
     return cudaLaunchKernel(k, dim3((unsigned)grid), dim3((unsigned)threads), params, smem, stream);
 }
 
-size_t ema_rows_smem(const NodeArgs &a, bool fp64, bool scaled) {
+size_t ema_rows_smem(const NodeArgs &a, Elem e, bool scaled) {
     (void)scaled;
     const size_t words = (size_t)kEmaRows * (a.wy + a.Wa);
-    return words * (fp64 ? 8 : 4);
+    return words * (e == Elem::F32 ? 4 : 8);
 }
 
 namespace {
-void *select_ema_rows(bool fp64, bool scaled) {
+void *select_ema_rows(Elem e, bool scaled) {
     if (scaled) return reinterpret_cast<void *>(&ema_rows_kernel<float, true>);
-    return fp64 ? reinterpret_cast<void *>(&ema_rows_kernel<double, false>)
-                : reinterpret_cast<void *>(&ema_rows_kernel<float, false>);
+    if (e == Elem::U64) return reinterpret_cast<void *>(&ema_rows_kernel<u64, false>);
+    return e == Elem::F64 ? reinterpret_cast<void *>(&ema_rows_kernel<double, false>)
+                          : reinterpret_cast<void *>(&ema_rows_kernel<float, false>);
 }
 }  // namespace
 
-int ema_rows_blocks_per_sm(bool fp64, bool scaled, size_t smem) {
-    return blocks_per_sm(select_ema_rows(fp64, scaled), 256, smem);
+int ema_rows_blocks_per_sm(Elem e, bool scaled, size_t smem) {
+    return blocks_per_sm(select_ema_rows(e, scaled), 256, smem);
 }
 
-cudaError_t launch_ema_rows(const NodeArgs &args, bool fp64, bool scaled, int sms, cudaStream_t stream) {
-    const size_t smem = ema_rows_smem(args, fp64, scaled);
-    const int per_sm = ema_rows_blocks_per_sm(fp64, scaled, smem);
+cudaError_t launch_ema_rows(const NodeArgs &args, Elem e, bool scaled, int sms, cudaStream_t stream) {
+    const size_t smem = ema_rows_smem(args, e, scaled);
+    const int per_sm = ema_rows_blocks_per_sm(e, scaled, smem);
     if (per_sm < 1) return cudaErrorInvalidValue;
     const int64_t rows = args.n * args.nb;
     const int64_t blocks = std::min<int64_t>((rows + kEmaRows - 1) / kEmaRows, (int64_t)sms * per_sm);
     NodeArgs a = args;
     void *params[] = {&a};
-    return cudaLaunchKernel(select_ema_rows(fp64, scaled), dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256),
+    return cudaLaunchKernel(select_ema_rows(e, scaled), dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256),
                             params, smem, stream);
 }
 
-cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,
+cudaError_t launch_root_reduce(const void *vals, Elem ve, int64_t n, int nseg, double *pv, RootSum *partials,
                                int chunks, RootSum *out, cudaStream_t stream) {
     dim3 grid((unsigned)chunks, (unsigned)nseg);
-    if (fp64)
+    if (ve == Elem::U64)
+        root_partial_kernel<u64><<<grid, 256, 0, stream>>>(static_cast<const u64 *>(vals), n, pv, partials, chunks);
+    else if (ve == Elem::F64)
         root_partial_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double *>(vals), n, pv, partials,
                                                                 chunks);
     else

@@ -7,6 +7,10 @@
 
 namespace sg2v {
 
+// Element type of the count tables: FP32, FP64 or unsigned 64-bit integers
+// (exact counts; every wrap past 2^64 is reported).
+enum class Elem : int { F32 = 0, F64 = 1, U64 = 2 };
+
 // Arguments of one DP node over a batch of nb colourings.  Tables are
 // colour-compressed: row v*nb + b holds, for colouring b of vertex v, only the
 // colour sets containing v's colour, indexed by the colex rank of the other
@@ -87,6 +91,9 @@ struct NodeArgs {
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
     unsigned *counters;           // [slots][nb], zero on entry
+    // status word 0 of the call: integer tables set bit 1 when a count
+    // wrapped past 2^64
+    unsigned *status;
 };
 
 // Backward of the eMA of one node for one colouring (one warp per row):
@@ -168,7 +175,7 @@ cudaError_t launch_node_scaled(const NodeArgs &args, int lanes_per_group, int ve
 // Shape of the gather of compressed rows of wz elements: lanes per neighbour
 // group (4, 8, 16 or 32; kWideLanes when a whole CTA shares one row) and
 // 16-byte vectors per lane (1..4; 0 if too wide).
-void node_shape(bool fp64, int wz, int *lanes_per_group, int *vec_per_lane);
+void node_shape(bool eight_byte, int wz, int *lanes_per_group, int *vec_per_lane);
 
 constexpr int kNodeThreads = 256;
 // node_shape's lanes-per-group value for rows handled by a whole CTA (wide rows)
@@ -178,11 +185,11 @@ constexpr int kWideThreads = 256;
 // Resident blocks per SM of one node-kernel variant at a block size and
 // dynamic shared-memory size (0 if it cannot run); raises the kernel's
 // shared-memory limit when needed.
-int node_blocks_per_sm(bool fp64, bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
+int node_blocks_per_sm(Elem e, bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
                        size_t smem, bool group_rows = false);
 
 // Launches the fused SpMM/histogram + eMA kernel of one node.
-cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, int vec_per_lane, int threads,
+cudaError_t launch_node(const NodeArgs &args, Elem e, int lanes_per_group, int vec_per_lane, int threads,
                         size_t smem, int grid_cap, cudaStream_t stream);
 
 // Deferred eMA of a non-root node (a >= 2) over blocks of kEmaRows rows: Y'
@@ -191,20 +198,21 @@ cudaError_t launch_node(const NodeArgs &args, bool fp64, int lanes_per_group, in
 // split-table word serves kEmaRows rows.  0 blocks per SM if the rows of a
 // block do not fit shared memory.
 constexpr int kEmaRows = 8;
-size_t ema_rows_smem(const NodeArgs &args, bool fp64, bool scaled);
-int ema_rows_blocks_per_sm(bool fp64, bool scaled, size_t smem);
-cudaError_t launch_ema_rows(const NodeArgs &args, bool fp64, bool scaled, int sms, cudaStream_t stream);
+size_t ema_rows_smem(const NodeArgs &args, Elem e, bool scaled);
+int ema_rows_blocks_per_sm(Elem e, bool scaled, size_t smem);
+cudaError_t launch_ema_rows(const NodeArgs &args, Elem e, bool scaled, int sms, cudaStream_t stream);
 
 // Histogram nodes in blocks of 32 rows per warp (counts with one lane per
 // row, then the eMA epilogue row by row).  Shared memory per warp:
 // (kc * 32 + 32 * mwords + ywords + owords) elements.
-int hist_rows_blocks_per_sm(bool fp64, bool scaled, bool weighted, int threads, size_t smem);
-cudaError_t launch_hist_rows(const NodeArgs &args, bool fp64, bool scaled, int threads, size_t smem, int grid_cap,
+int hist_rows_blocks_per_sm(Elem e, bool scaled, bool weighted, int threads, size_t smem);
+cudaError_t launch_hist_rows(const NodeArgs &args, Elem e, bool scaled, int threads, size_t smem, int grid_cap,
                              cudaStream_t stream);
 
-// Root reduction: vals is [nseg][n] of float/double; writes per-vertex doubles
-// when pv != null and one RootSum per segment.
-cudaError_t launch_root_reduce(const void *vals, bool fp64, int64_t n, int nseg, double *pv, RootSum *partials,
+// Root reduction: vals is [nseg][n] of float, double or unsigned 64-bit
+// counts; writes per-vertex doubles when pv != null and one RootSum per
+// segment.
+cudaError_t launch_root_reduce(const void *vals, Elem e, int64_t n, int nseg, double *pv, RootSum *partials,
                                int chunks, RootSum *out, cudaStream_t stream);
 
 // Eref[row] = max over the row's arcs to neighbours of another valid colour

@@ -244,7 +244,7 @@ def main():
                     help="run exactly one count call (R-MAT scale 18 or 20 with avg degree 32 and tree10, or the "
                          "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
                          "summaries capture")
-    ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled", "u64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled", "u64", "u128"], default="fp32")
     args = ap.parse_args()
     if args.profile_call:
         profile_call(args)
@@ -382,9 +382,15 @@ def main():
             ms_u, exact_total = None, str(e)
         ms_d = time_steps(torch, one(sg.SG2V_FP64), reps, args.warmup, stream, dist)
         ms_s = time_steps(torch, one(sg.SG2V_FP32), reps, args.warmup, stream, dist)
+        # the headline workload (entries up to 2^94) in 128-bit integers, beside its plain FP64 form
+        ms_h = time_steps(torch, lambda: sg.sg2v_count_batched(graph.handle, [plan.handle], d_cols[0:1], 1,
+                                                               sg.SG2V_U128, None, tot64, None, stream),
+                          max(3, args.steps // 2), args.warmup, stream, dist)
         exact = {"workload": "chunglu200k unweighted (200k vertices, 2M edges, gamma 2.3), tree8, k=8, one "
                              "colouring per call; table entries up to 2^61", "u64_ms": ms_u, "fp64_ms": ms_d,
-                 "fp32_ms": ms_s, "u64_total": exact_total, "dtype": "u64 (exact), f64, f32"}
+                 "fp32_ms": ms_s, "u64_total": exact_total, "dtype": "u64 (exact), f64, f32",
+                 "headline_u128": {"workload": WORKLOAD + ", one colouring per call (entries up to 2^94)",
+                                   "ms_per_colouring": ms_h, "fp64_ms_per_colouring": ms64, "dtype": "u128 (exact)"}}
         del graph4u
 
     # large form: R-MAT scale 20 with 5e7 edges, tree15, k = 15, 8 colourings

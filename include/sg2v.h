@@ -52,7 +52,7 @@ typedef enum {
     SG2V_ERR_COLOUR_OUT_OF_RANGE = 3,
     SG2V_ERR_GRAPH_NOT_SIMPLE = 4, /* self-loop, duplicate arc, unsorted row, asymmetric CSR or weights */
     SG2V_ERR_OUT_OF_MEMORY = 5,
-    SG2V_ERR_FP_OVERFLOW = 6,      /* a count left the range of the table type (inf/NaN, or 2^64 for SG2V_U64) */
+    SG2V_ERR_FP_OVERFLOW = 6,      /* a count left the range of the table type (inf/NaN; 2^64 or 2^128 for integers) */
     SG2V_ERR_CUDA = 7,             /* a CUDA runtime call failed; see sg2v_last_error() */
     SG2V_ERR_TIMEOUT = 8,          /* a bounded device-side wait gave up */
     SG2V_ERR_UNSUPPORTED = 9       /* a valid request this build cannot run (e.g. too many columns) */
@@ -69,13 +69,16 @@ typedef enum {
                           * 2^-126 of their row's largest, after the gather's
                           * alignment to the row's largest neighbour exponent,
                           * are flushed to zero.  Forward counts only. */
-    SG2V_U64 = 3         /* count tables in unsigned 64-bit integers: every
+    SG2V_U64 = 3,        /* count tables in unsigned 64-bit integers: every
                           * value of the DP on an unweighted graph is an integer
                           * (Alg. 3 / 5), so counts are exact while every table
                           * entry stays below 2^64, past FP64's 2^53; a sum or
                           * product that wraps is detected and the call returns
                           * SG2V_ERR_FP_OVERFLOW.  Unweighted graphs and forward
                           * counts only (SG2V_ERR_UNSUPPORTED otherwise). */
+    SG2V_U128 = 4        /* as SG2V_U64 with unsigned 128-bit counts (two 64-bit
+                          * words, 16 bytes per entry): exact to 2^128.  Rows of
+                          * more than 1,024 colour sets are SG2V_ERR_UNSUPPORTED. */
 } sg2v_precision;
 
 /* ------------------------------------------------------------------ graph */
@@ -182,9 +185,10 @@ sg2v_status sg2v_plan_estimate_scale(const sg2v_plan *plan, double *scale);
  * SpMM + eMA per sub-template, then the root reduction and finalCount).
  *
  *   colours     [n] int8, host or device, values in [0, kc)
- *   precision   SG2V_FP64, SG2V_FP32, SG2V_FP32_SCALED or SG2V_U64 (table
- *               type); an SG2V_FP32 call that overflows is run again as
- *               SG2V_FP32_SCALED by sg2v_count and sg2v_count_batched
+ *   precision   SG2V_FP64, SG2V_FP32, SG2V_FP32_SCALED, SG2V_U64 or
+ *               SG2V_U128 (table type); an SG2V_FP32 call that overflows is
+ *               run again as SG2V_FP32_SCALED by sg2v_count and
+ *               sg2v_count_batched
  *   per_vertex  [n] double, host or device, or NULL: per_vertex[v] is the
  *               number of colourful embeddings (labelled maps) with the
  *               root rho at v, i.e. sum over colour sets C of M_0(v, I_C)

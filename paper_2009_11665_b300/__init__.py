@@ -35,6 +35,7 @@ SG2V_FP64 = 0
 SG2V_FP32 = 1
 SG2V_FP32_SCALED = 2
 SG2V_U64 = 3
+SG2V_U128 = 4
 SG2V_GRAPH_SKIP_VALIDATION = 0x1
 SG2V_CUT_LAST = 0
 SG2V_CUT_MIN_WORK = 1
@@ -42,7 +43,7 @@ SG2V_SESSION_PER_VERTEX = 0x1
 SG2V_SESSION_NO_GRAPH = 0x2
 SG2V_SESSION_AUTOTUNE = 0x4
 
-PRECISIONS = {"fp64": SG2V_FP64, "fp32": SG2V_FP32, "fp32_scaled": SG2V_FP32_SCALED, "u64": SG2V_U64}
+PRECISIONS = {"fp64": SG2V_FP64, "fp32": SG2V_FP32, "fp32_scaled": SG2V_FP32_SCALED, "u64": SG2V_U64, "u128": SG2V_U128}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2009_11665_b300.build`")

@@ -410,6 +410,7 @@ struct Prepared {
 
 const char *elem_name(const Prepared &P) {
     if (P.scaled) return "fp32s";
+    if (P.elem == Elem::U128) return "u128";
     return P.elem == Elem::F64 ? "fp64" : (P.elem == Elem::U64 ? "u64" : "fp32");
 }
 
@@ -417,11 +418,11 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
                     sg2v_precision precision, Prepared *P) {
     if (!g || !plans || num_plans < 1 || B < 1 ||
         (precision != SG2V_FP64 && precision != SG2V_FP32 && precision != SG2V_FP32_SCALED &&
-         precision != SG2V_U64)) {
+         precision != SG2V_U64 && precision != SG2V_U128)) {
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
-    if (precision == SG2V_U64 && g->weights) {
+    if ((precision == SG2V_U64 || precision == SG2V_U128) && g->weights) {
         set_error("integer tables count unweighted graphs only");
         return SG2V_ERR_UNSUPPORTED;
     }
@@ -444,9 +445,10 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
     P->nb = B;
     P->fp64 = precision == SG2V_FP64;
     P->scaled = precision == SG2V_FP32_SCALED;
-    P->elem = P->fp64 ? Elem::F64 : (precision == SG2V_U64 ? Elem::U64 : Elem::F32);
-    P->esz = P->elem == Elem::F32 ? 4 : 8;
-    P->vecn = P->elem == Elem::F32 ? 4 : 2;
+    P->elem = P->fp64 ? Elem::F64
+                      : (precision == SG2V_U64 ? Elem::U64 : (precision == SG2V_U128 ? Elem::U128 : Elem::F32));
+    P->esz = P->elem == Elem::F32 ? 4 : (P->elem == Elem::U128 ? 16 : 8);
+    P->vecn = (int)(16 / P->esz);
     P->n = g->n;
     P->plan_root.assign(num_plans, -1);
     std::map<std::string, int> shared;
@@ -489,7 +491,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.wz = hist ? 1 : (int)binom(kc - 1, c.p - 1);
         sh.grp = 32;
         sh.nv = 1;
-        if (!hist) node_shape(P->esz == 8, sh.wz, &sh.grp, &sh.nv);
+        if (!hist) node_shape(P->vecn, sh.wz, &sh.grp, &sh.nv);
         if (!hist && sh.grp != kWideLanes && sh.wz >= wide_min) {
             // rows at least SG2V_WIDE_MIN_WZ wide go to the CTA-per-row kernel
             sh.grp = kWideLanes;
@@ -894,7 +896,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
         const void *vals = P.plan_root[pi] >= 0 ? R.rootbuf[pi] : R.ones;
         // root values: the table type, doubles for scaled tables and single-vertex plans
         const Elem ve = P.plan_root[pi] >= 0 ? (P.scaled ? Elem::F64 : P.elem) : Elem::F64;
-        timer.begin("root_reduce", (double)nb * n * ((ve == Elem::F32 ? 4 : 8) + (pvp ? 8 : 0)));
+        timer.begin("root_reduce", (double)nb * n * ((ve == Elem::F32 ? 4 : (ve == Elem::U128 ? 16 : 8)) + (pvp ? 8 : 0)));
         timer.count_extra(1);
         SG2V_CUDA(launch_root_reduce(vals, ve, n, nb, pvp, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
                                      R.sums + pi * (size_t)nb, stream),
@@ -1482,7 +1484,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
-    if (precision == SG2V_FP32_SCALED || precision == SG2V_U64) {
+    if (precision == SG2V_FP32_SCALED || precision == SG2V_U64 || precision == SG2V_U128) {
         set_error("the backward pass keeps plain FP64 or FP32 tables");
         return SG2V_ERR_UNSUPPORTED;
     }
@@ -1548,7 +1550,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         const CNode &c = P.nodes[i];
         Shape &sh = bshape[i];
         sh.wz = (int)binom(kc - 1, c.p);
-        node_shape(P.esz == 8, sh.wz, &sh.grp, &sh.nv);
+        node_shape(P.vecn, sh.wz, &sh.grp, &sh.nv);
         if (sh.nv == 0) {
             set_error("gradient rows wider than this build's register tile");
             return SG2V_ERR_UNSUPPORTED;
@@ -1750,7 +1752,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         if (c.p >= 2) {
             // row-oriented form over the forward work list, gather shape of M_p' rows
             int lanes = 32, vecs = 1;
-            node_shape(P.esz == 8, D.wmp, &lanes, &vecs);
+            node_shape(P.vecn, D.wmp, &lanes, &vecs);
             if (lanes != kWideLanes && vecs >= 1) {
                 D.tasks = g->tasks;
                 D.ntasks = g->ntasks;

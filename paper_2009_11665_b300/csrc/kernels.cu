@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -165,10 +166,98 @@ struct Vec16<u64> {
     }
 };
 
+// Unsigned 128-bit counts (two 64-bit words): exact to 2^128, for counts
+// that pass 2^64 (tree10 on a graph of 2^24 edges reaches about 2^94).
+struct alignas(16) u128 {
+    u64 lo, hi;
+    u128() = default;
+    __host__ __device__ constexpr u128(u64 l, u64 h) : lo(l), hi(h) {}
+    __host__ __device__ constexpr u128(int x) : lo((u64)(long long)x), hi(0) {}
+    __host__ __device__ constexpr u128(unsigned x) : lo(x), hi(0) {}
+    // (weights and exponent factors are 1 on the integer path)
+    __host__ __device__ explicit u128(float x) : lo((u64)x), hi(0) {}
+    __device__ u128 &operator+=(const u128 &b) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(b.lo), "l"(b.hi));
+        return *this;
+    }
+    __device__ u128 &operator*=(const u128 &b) {
+        const u64 h = __umul64hi(lo, b.lo) + lo * b.hi + hi * b.lo;
+        lo *= b.lo;
+        hi = h;
+        return *this;
+    }
+};
+__device__ __forceinline__ u128 operator+(u128 a, const u128 &b) { return a += b; }
+__device__ __forceinline__ u128 operator*(u128 a, const u128 &b) { return a *= b; }
+
+// Shuffles, cache-global loads and atomic adds of 128-bit counts (the
+// built-in overloads stay visible beside them).
+using ::__shfl_sync;
+using ::__shfl_xor_sync;
+using ::__ldcg;
+__device__ __forceinline__ u128 __shfl_sync(unsigned mask, const u128 &v, int src, int width = 32) {
+    return u128(__shfl_sync(mask, v.lo, src, width), __shfl_sync(mask, v.hi, src, width));
+}
+__device__ __forceinline__ u128 __shfl_xor_sync(unsigned mask, const u128 &v, int o, int width = 32) {
+    return u128(__shfl_xor_sync(mask, v.lo, o, width), __shfl_xor_sync(mask, v.hi, o, width));
+}
+__device__ __forceinline__ u128 __ldcg(const u128 *p) {
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
+    return u128(v.x, v.y);
+}
+
+__device__ __forceinline__ double u128_to_double(unsigned long long hi, unsigned long long lo) {
+    if (hi == 0) return __ull2double_rn(lo);
+    const int shift = 64 - __clzll((long long)hi);  // 1..64
+    const unsigned long long top = shift == 64 ? hi : (hi << (64 - shift)) | (lo >> shift);
+    const unsigned long long sticky = (shift == 64 ? lo : (lo << (64 - shift))) != 0ull ? 1ull : 0ull;
+    return ldexp(__ull2double_rn(top | sticky), shift);
+}
+
+template <>
+struct Ar<u128> {
+    static constexpr bool exact = true;
+    // a += b; a carry out of bit 127 increments ovf
+    __device__ static void add(u128 &a, const u128 &b, unsigned &ovf) {
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u32 %2, %2, 0;"
+            : "+l"(a.lo), "+l"(a.hi), "+r"(ovf)
+            : "l"(b.lo), "l"(b.hi));
+    }
+    // acc += a * b; a product of 128 bits or more sets ovf
+    __device__ static void mad(u128 &acc, const u128 &a, const u128 &b, unsigned &ovf) {
+        const u64 c1 = a.lo * b.hi, c2 = a.hi * b.lo;
+        const bool big = (a.hi != 0ull && b.hi != 0ull) || __umul64hi(a.lo, b.hi) != 0ull ||
+                         __umul64hi(a.hi, b.lo) != 0ull;
+        u128 p(a.lo * b.lo, __umul64hi(a.lo, b.lo));
+        unsigned c = big ? 1u : 0u;
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(p.hi), "+r"(c) : "l"(c1));
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(p.hi), "+r"(c) : "l"(c2));
+        ovf |= c;
+        add(acc, p, ovf);
+    }
+    __device__ static u128 twice(const u128 &a, unsigned &ovf) {
+        ovf |= (unsigned)(a.hi >> 63);
+        return u128(a.lo << 1, (a.hi << 1) | (a.lo >> 63));
+    }
+};
+
+template <>
+struct Vec16<u128> {
+    using type = u128;
+    static constexpr int n = 1;
+    __device__ static u128 zero() { return u128(0ull, 0ull); }
+    __device__ static void add(u128 &a, const u128 &b) { a += b; }
+    __device__ static void fma(u128 &a, const u128 &w, const u128 &b) { a += w * b; }
+    __device__ static void store(u128 *p, const u128 &a) { *p = a; }
+    __device__ static u128 shfl_xor(const u128 &a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+};
+
 // a += b for a 16-byte vector, with overflow accounting for integer tables.
 template <typename T>
 __device__ __forceinline__ void vadd(typename Vec16<T>::type &a, const typename Vec16<T>::type &b, unsigned &ovf) {
-    if constexpr (Ar<T>::exact) {
+    if constexpr (Ar<T>::exact && Vec16<T>::n == 1) {
+        Ar<T>::add(a, b, ovf);
+    } else if constexpr (Ar<T>::exact) {
         Ar<T>::add(a.x, b.x, ovf);
         Ar<T>::add(a.y, b.y, ovf);
     } else {
@@ -181,7 +270,16 @@ __device__ __forceinline__ void vadd(typename Vec16<T>::type &a, const typename 
 // accounting for integer tables.
 template <typename T>
 __device__ __forceinline__ void atomic_add(T *p, T x, unsigned &ovf) {
-    if constexpr (Ar<T>::exact) {
+    if constexpr (std::is_same<T, u128>::value) {
+        // low word first; its carry goes into the high word's add, so the
+        // 128-bit sum of all adds is exact in any order
+        const u64 old_lo = atomicAdd(&p->lo, x.lo);
+        const u64 c = old_lo + x.lo < old_lo ? 1ull : 0ull;
+        const u64 add_hi = x.hi + c;
+        if (add_hi < c) ovf |= 1u;
+        const u64 old_hi = atomicAdd(&p->hi, add_hi);
+        ovf |= old_hi + add_hi < old_hi ? 1u : 0u;
+    } else if constexpr (Ar<T>::exact) {
         const T old = atomicAdd(p, x);
         ovf |= old + x < old ? 1u : 0u;
     } else {
@@ -211,6 +309,11 @@ __device__ __forceinline__ void report_ovf(unsigned *status, unsigned &ovf) {
 template <typename VT>
 __device__ __forceinline__ VT ldg_row(const VT *p) {
     return __ldg(p);
+}
+template <>
+__device__ __forceinline__ u128 ldg_row<u128>(const u128 *p) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+    return u128(v.x, v.y);
 }
 
 // 2^d as a float for an exponent difference d <= 0 (0 below the normal range).
@@ -296,7 +399,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
     // nothing.  FP32 loads stay unpredicated (measured faster): lanes past
     // the last vector read the next row or the table's padding into Z
     // columns that nothing reads.
-    constexpr bool SKIP_ZERO = sizeof(T) == 8;
+    constexpr bool SKIP_ZERO = sizeof(T) >= 8;
     const int nvec = (A.Wz + V::n - 1) / V::n;
     bool qok[NV];
 #pragma unroll
@@ -305,7 +408,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
     // padding that no kernel writes; it is cleared so that it adds no carry
     bool tail[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && (A.Wz & 1) && gl + G * q == nvec - 1;
+    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && V::n == 2 && (A.Wz & 1) && gl + G * q == nvec - 1;
     const int64_t uvec = (int64_t)A.nb * A.ldp / V::n;  // vectors between consecutive vertices' rows
     const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp) + gl;
     const int32_t *scol = A.scol + (int64_t)b * A.nnz;
@@ -382,7 +485,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     x[r][q] = (!SKIP_ZERO || (live[r] && qok[q])) ? ldg_row(row + G * q) : V::zero();
-                    if constexpr (Ar<T>::exact)
+                    if constexpr (Ar<T>::exact && V::n == 2)
                         if (tail[q]) x[r][q].y = 0;
                 }
             }
@@ -743,7 +846,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
     constexpr int NG = 32 / G;
     constexpr int U = 4;                       // arcs in flight per group and step
     constexpr bool FMA = WEIGHTED || SCALED;
-    constexpr bool SKIP_ZERO = sizeof(T) == 8;
+    constexpr bool SKIP_ZERO = sizeof(T) >= 8;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G, g0 = grp * G;
     const unsigned gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << g0;
@@ -756,7 +859,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const bool qok = gl < (A.Wz + V::n - 1) / V::n;
     // integer tables of odd width: the last vector's padding element is cleared
-    const bool tail = Ar<T>::exact && (A.Wz & 1) && gl == (A.Wz + V::n - 1) / V::n - 1;
+    const bool tail = Ar<T>::exact && V::n == 2 && (A.Wz & 1) && gl == (A.Wz + V::n - 1) / V::n - 1;
     const int zero_row = (int)A.n;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t wglob = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
@@ -841,7 +944,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
                         }
                         const VT *row = Mb + (int64_t)(lv[r] ? u : zero_row) * uvec;
                         x[r] = (SKIP_ZERO ? (lv[r] && qok) : true) ? ldg_row(row) : V::zero();
-                        if constexpr (Ar<T>::exact)
+                        if constexpr (Ar<T>::exact && V::n == 2)
                             if (tail) x[r].y = 0;
                     }
 #pragma unroll
@@ -1035,7 +1138,7 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
             bool finish = have;
             if (have && task.y >= 0) {
                 T *sc = static_cast<T *>(A.scratch) + ((int64_t)task.y * A.nb + b) * A.scratch_ld;
-                for (int d = 0; d < kc; ++d) atomicAdd(sc + d, cnt[d * kHistRows + lane]);
+                for (int d = 0; d < kc; ++d) atomic_add(sc + d, cnt[d * kHistRows + lane], ovf);
                 __threadfence();
                 const unsigned done = atomicAdd(A.counters + (int64_t)task.y * A.nb + b, 1u);
                 finish = done + 1u == (unsigned)__ldg(A.heavy_chunks + task.y);
@@ -1153,6 +1256,13 @@ struct RowVec<double> {
             const double2 a = *reinterpret_cast<const double2 *>(p + i);
             x[i] = a.x; x[i + 1] = a.y;
         }
+    }
+};
+template <>
+struct RowVec<u128> {
+    static __device__ void load(const u128 *p, u128 (&x)[kEmaRows]) {
+#pragma unroll
+        for (int i = 0; i < kEmaRows; ++i) x[i] = p[i];
     }
 };
 template <>
@@ -1287,7 +1397,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     // integer tables of odd width: the last vector's padding element is cleared
     bool tail[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && (A.Wz & 1) && vbase + 32 * q == nvec - 1;
+    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && V::n == 2 && (A.Wz & 1) && vbase + 32 * q == nvec - 1;
     unsigned ovf = 0;
     for (int64_t ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
         const int4 task = A.tasks[ti];
@@ -1374,7 +1484,7 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
 #pragma unroll
                             for (int q = 0; q < NV; ++q) {
                                 x[r][q] = (sizeof(T) == 4 || qok[q]) ? ldg_row(row + 32 * q) : V::zero();
-                                if constexpr (Ar<T>::exact)
+                                if constexpr (Ar<T>::exact && V::n == 2)
                                     if (tail[q]) x[r][q].y = 0;
                             }
                         }
@@ -1531,10 +1641,11 @@ void *pick_group(int g) {
 
 void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group = false) {
     // integer tables count unweighted graphs only
-    if (e == Elem::U64 && weighted) return nullptr;
+    if ((e == Elem::U64 || e == Elem::U128) && weighted) return nullptr;
     if (group) {
         if (hist || nv != 1) return nullptr;
         if (e == Elem::U64) return pick_group<u64, false, false>(g);
+        if (e == Elem::U128) return pick_group<u128, false, false>(g);
         if (e == Elem::F64) return weighted ? pick_group<double, true, false>(g) : pick_group<double, false, false>(g);
         return weighted ? pick_group<float, true, false>(g) : pick_group<float, false, false>(g);
     }
@@ -1542,10 +1653,12 @@ void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group 
         // wide rows: one CTA per task (nv vectors per lane, 8 warps)
         if (hist) return nullptr;
         if (e == Elem::U64) return pick_wide<u64, false>(nv);
+        if (e == Elem::U128) return pick_wide<u128, false>(nv);
         if (e == Elem::F64) return weighted ? pick_wide<double, true>(nv) : pick_wide<double, false>(nv);
         return weighted ? pick_wide<float, true>(nv) : pick_wide<float, false>(nv);
     }
     if (e == Elem::U64) return pick<u64, false>(hist, g, nv);
+    if (e == Elem::U128) return pick<u128, false>(hist, g, nv);
     if (e == Elem::F64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
     return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
 }
@@ -1643,12 +1756,17 @@ __global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, RootSu
     } else if constexpr (Ar<T>::exact) {
         // integer tables: the 128-bit sum directly (and a double sum beside it)
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const u64 x = vals[(int64_t)seg * n + i];
-            const double d = __ull2double_rn(x);
-            if (pv) pv[(int64_t)seg * n + i] = d;
+            const T x = vals[(int64_t)seg * n + i];
             RootSum r = rs_from(0.0);
-            r.lo = x;
-            r.s = d;
+            if constexpr (std::is_same<T, u128>::value) {
+                r.lo = x.lo;
+                r.hi = x.hi;
+                r.s = u128_to_double(x.hi, x.lo);
+            } else {
+                r.lo = x;
+                r.s = __ull2double_rn(x);
+            }
+            if (pv) pv[(int64_t)seg * n + i] = r.s;
             rs_combine(acc, r);
         }
     } else {
@@ -2044,14 +2162,6 @@ __global__ void symmetrize_kernel(const double *part, const int32_t *rev, int64_
 // 128-bit unsigned integer to the nearest double (ties to even): the top 64
 // significant bits keep a sticky bit for everything below them, so the one
 // rounding of the 64-bit conversion is the correct rounding of the whole.
-__device__ __forceinline__ double u128_to_double(unsigned long long hi, unsigned long long lo) {
-    if (hi == 0) return __ull2double_rn(lo);
-    const int shift = 64 - __clzll((long long)hi);  // 1..64
-    const unsigned long long top = shift == 64 ? hi : (hi << (64 - shift)) | (lo >> shift);
-    const unsigned long long sticky = (shift == 64 ? lo : (lo << (64 - shift))) != 0ull ? 1ull : 0ull;
-    return ldexp(__ull2double_rn(top | sticky), shift);
-}
-
 __global__ void finalize_kernel(const RootSum *sums, int nseg, int nb, const double *scale_hi,
                                 const double *scale_lo, double *totals, double *estimates, unsigned *status) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2105,8 +2215,7 @@ __global__ void check_colours_kernel(const int8_t *colours, int64_t count, int k
 
 }  // namespace
 
-void node_shape(bool eight_byte, int wz, int *g, int *nv) {
-    const int vecn = eight_byte ? 2 : 4;
+void node_shape(int vecn, int wz, int *g, int *nv) {
     const int nvec = (wz + vecn - 1) / vecn;
     *nv = 1;
     if (nvec <= 4)
@@ -2194,6 +2303,7 @@ void *select_hist_rows(Elem e, bool scaled, bool weighted) {
     if (scaled) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<float, true, true>)
                                 : reinterpret_cast<void *>(&hist_rows_kernel<float, false, true>);
     if (e == Elem::U64) return weighted ? nullptr : reinterpret_cast<void *>(&hist_rows_kernel<u64, false, false>);
+    if (e == Elem::U128) return weighted ? nullptr : reinterpret_cast<void *>(&hist_rows_kernel<u128, false, false>);
     if (e == Elem::F64) return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<double, true, false>)
                               : reinterpret_cast<void *>(&hist_rows_kernel<double, false, false>);
     return weighted ? reinterpret_cast<void *>(&hist_rows_kernel<float, true, false>)
@@ -2222,13 +2332,14 @@ cudaError_t launch_hist_rows(const NodeArgs &args, Elem e, bool scaled, int thre
 size_t ema_rows_smem(const NodeArgs &a, Elem e, bool scaled) {
     (void)scaled;
     const size_t words = (size_t)kEmaRows * (a.wy + a.Wa);
-    return words * (e == Elem::F32 ? 4 : 8);
+    return words * (e == Elem::F32 ? 4 : (e == Elem::U128 ? 16 : 8));
 }
 
 namespace {
 void *select_ema_rows(Elem e, bool scaled) {
     if (scaled) return reinterpret_cast<void *>(&ema_rows_kernel<float, true>);
     if (e == Elem::U64) return reinterpret_cast<void *>(&ema_rows_kernel<u64, false>);
+    if (e == Elem::U128) return reinterpret_cast<void *>(&ema_rows_kernel<u128, false>);
     return e == Elem::F64 ? reinterpret_cast<void *>(&ema_rows_kernel<double, false>)
                           : reinterpret_cast<void *>(&ema_rows_kernel<float, false>);
 }
@@ -2255,6 +2366,9 @@ cudaError_t launch_root_reduce(const void *vals, Elem ve, int64_t n, int nseg, d
     dim3 grid((unsigned)chunks, (unsigned)nseg);
     if (ve == Elem::U64)
         root_partial_kernel<u64><<<grid, 256, 0, stream>>>(static_cast<const u64 *>(vals), n, pv, partials, chunks);
+    else if (ve == Elem::U128)
+        root_partial_kernel<u128><<<grid, 256, 0, stream>>>(static_cast<const u128 *>(vals), n, pv, partials,
+                                                              chunks);
     else if (ve == Elem::F64)
         root_partial_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double *>(vals), n, pv, partials,
                                                                 chunks);

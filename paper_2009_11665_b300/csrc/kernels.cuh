@@ -7,9 +7,9 @@
 
 namespace sg2v {
 
-// Element type of the count tables: FP32, FP64 or unsigned 64-bit integers
-// (exact counts; every wrap past 2^64 is reported).
-enum class Elem : int { F32 = 0, F64 = 1, U64 = 2 };
+// Element type of the count tables: FP32, FP64, or unsigned 64-bit or
+// 128-bit integers (exact counts; every wrap past 2^64 / 2^128 is reported).
+enum class Elem : int { F32 = 0, F64 = 1, U64 = 2, U128 = 3 };
 
 // Arguments of one DP node over a batch of nb colourings.  Tables are
 // colour-compressed: row v*nb + b holds, for colouring b of vertex v, only the
@@ -92,7 +92,7 @@ struct NodeArgs {
     int64_t scratch_ld;
     unsigned *counters;           // [slots][nb], zero on entry
     // status word 0 of the call: integer tables set bit 1 when a count
-    // wrapped past 2^64
+    // wrapped past their width
     unsigned *status;
 };
 
@@ -175,7 +175,7 @@ cudaError_t launch_node_scaled(const NodeArgs &args, int lanes_per_group, int ve
 // Shape of the gather of compressed rows of wz elements: lanes per neighbour
 // group (4, 8, 16 or 32; kWideLanes when a whole CTA shares one row) and
 // 16-byte vectors per lane (1..4; 0 if too wide).
-void node_shape(bool eight_byte, int wz, int *lanes_per_group, int *vec_per_lane);
+void node_shape(int elems_per_vector, int wz, int *lanes_per_group, int *vec_per_lane);
 
 constexpr int kNodeThreads = 256;
 // node_shape's lanes-per-group value for rows handled by a whole CTA (wide rows)

@@ -94,10 +94,15 @@ sg2v_status device_info(int dev, DeviceInfo *out) {
 // Device copies of the colour-compressed expansion and split tables of node
 // (t, a) for kc colours with Z rows of wz_pad elements (built once, kept).
 struct DeviceTables {
-    const uint16_t *expand = nullptr;
+    const uint16_t *expand = nullptr;  // [kc][wy][pstride]
     const uint32_t *splits = nullptr;
-    int wy = 0, nsplit = 0;
+    const uint16_t *rootpair = nullptr;  // t = kc, a >= 2: rank(P') -> rank(A') of its one split
+    int wy = 0, nsplit = 0, pstride = 1;
 };
+
+// Entries between consecutive sets of the device expansion table: for
+// 2 <= p <= 4 the offsets are padded to 4 (one 8-byte load per set).
+int expand_stride(int p) { return (p >= 2 && p <= 4) ? 4 : p; }
 std::map<std::tuple<int, int, int, int, int>, DeviceTables> g_ctables;
 
 sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTables *out) {
@@ -113,16 +118,35 @@ sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTable
     DeviceTables d;
     d.wy = tab.wy;
     d.nsplit = tab.nsplit;
-    void *pe = nullptr, *ps = nullptr;
-    const size_t be = tab.expand.size() * sizeof(uint16_t), bs = tab.splits.size() * sizeof(uint32_t);
+    const int p = t - a, ps = expand_stride(p);
+    d.pstride = ps;
+    std::vector<uint16_t> packed((size_t)kc * tab.wy * ps, 0);
+    for (size_t set = 0; set < (size_t)kc * tab.wy; ++set)
+        for (int k = 0; k < p; ++k) packed[set * ps + k] = tab.expand[set * p + k];
+    void *pe = nullptr, *ps_ = nullptr;
+    const size_t be = packed.size() * sizeof(uint16_t), bs = tab.splits.size() * sizeof(uint32_t);
     SG2V_CUDA(cudaMalloc(&pe, std::max<size_t>(be, 16)), "table upload");
-    SG2V_CUDA(cudaMemcpy(pe, tab.expand.data(), be, cudaMemcpyHostToDevice), "table upload");
+    SG2V_CUDA(cudaMemcpy(pe, packed.data(), be, cudaMemcpyHostToDevice), "table upload");
     if (bs) {
-        SG2V_CUDA(cudaMalloc(&ps, bs), "table upload");
-        SG2V_CUDA(cudaMemcpy(ps, tab.splits.data(), bs, cudaMemcpyHostToDevice), "table upload");
+        SG2V_CUDA(cudaMalloc(&ps_, bs), "table upload");
+        SG2V_CUDA(cudaMemcpy(ps_, tab.splits.data(), bs, cudaMemcpyHostToDevice), "table upload");
     }
     d.expand = static_cast<const uint16_t *>(pe);
-    d.splits = static_cast<const uint32_t *>(ps);
+    d.splits = static_cast<const uint32_t *>(ps_);
+    if (t == kc && a >= 2 && tab.nsplit == tab.wy && (int)tab.splits.size() == tab.nsplit) {
+        // one output set: every p-set appears in exactly one split
+        std::vector<uint16_t> pair((size_t)tab.wy, 0xffffu);
+        for (uint32_t x : tab.splits) pair[x >> 16] = (uint16_t)(x & 0xffffu);
+        bool perm = true;
+        for (uint16_t q : pair) perm = perm && q != 0xffffu;
+        if (perm) {
+            void *pr = nullptr;
+            SG2V_CUDA(cudaMalloc(&pr, pair.size() * sizeof(uint16_t)), "table upload");
+            SG2V_CUDA(cudaMemcpy(pr, pair.data(), pair.size() * sizeof(uint16_t), cudaMemcpyHostToDevice),
+                      "table upload");
+            d.rootpair = static_cast<const uint16_t *>(pr);
+        }
+    }
     g_ctables[key] = d;
     *out = d;
     return SG2V_OK;
@@ -741,9 +765,15 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     }
     A.Ws = (int)binom(kc - 1, c.t - 1);
     A.expand = P.tabs[i].expand;
+    A.pstride = P.tabs[i].pstride;
     A.wy = P.tabs[i].wy;
     A.splits = P.tabs[i].splits;
     A.nsplit = P.tabs[i].nsplit;
+    // the root's pairing form (warp-per-row kernel, plain tables)
+    const char *pair_env = std::getenv("SG2V_ROOT_PAIRS");
+    if (c.is_root && !P.scaled && !A.hist && sh.grp == 32 && !sh.group && !sh.defer && P.tabs[i].wy <= 128 &&
+        !(pair_env && std::atoi(pair_env) == 0))
+        A.rootpair = P.tabs[i].rootpair;
     A.root = c.is_root;
     if (c.is_root) {
         char *rb = static_cast<char *>(R.rootbuf[P.root_plan[i]]) + (size_t)b0 * P.n * root_esz(P);
@@ -1708,6 +1738,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             A.group_rows = 0;  // the transposed SpMM's shape is its own (one task per warp)
             A.defer = 0;
             A.p = btab[ii].nterms;
+            A.pstride = btab[ii].nterms;
             A.wy = btab[ii].wout;
             A.expand = d_bexp[ii];
             A.a_leaf = 1;

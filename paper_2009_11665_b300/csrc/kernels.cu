@@ -23,7 +23,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "kernels.cuh"
 
@@ -173,7 +175,6 @@ struct alignas(16) u128 {
     u128() = default;
     __host__ __device__ constexpr u128(u64 l, u64 h) : lo(l), hi(h) {}
     __host__ __device__ constexpr u128(int x) : lo((u64)(long long)x), hi(0) {}
-    __host__ __device__ constexpr u128(unsigned x) : lo(x), hi(0) {}
     // (weights and exponent factors are 1 on the integer path)
     __host__ __device__ explicit u128(float x) : lo((u64)x), hi(0) {}
     __device__ u128 &operator+=(const u128 &b) {
@@ -187,7 +188,6 @@ struct alignas(16) u128 {
         return *this;
     }
 };
-__device__ __forceinline__ u128 operator+(u128 a, const u128 &b) { return a += b; }
 __device__ __forceinline__ u128 operator*(u128 a, const u128 &b) { return a *= b; }
 
 // Shuffles, cache-global loads and atomic adds of 128-bit counts (the
@@ -580,18 +580,34 @@ __device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, i
     }
 }
 
-// Y'(j) for the p-sets j of the squeezed universe of colour cv (the colour
-// sets without cv the eMA needs), summed from Z.
+// Y'(j) = sum over the p offsets of set j of Z[offset] (ex: the table of the
+// row's colour).  With stride 4 (2 <= p <= 4) the offsets of a set are one
+// 8-byte load, else they are read one by one (measured: 16-byte loads for
+// p = 5 made the tree10 root slower).
 template <typename T>
-__device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbuf, T *ybuf, int lane,
-                                         unsigned &ovf) {
-    const int p = A.p, wy = A.wy;
-    const uint16_t *ex = A.expand + (int64_t)cv * wy * p;
-    for (int j = lane; j < wy; j += 32) {
-        T s = T(0);
-        for (int k = 0; k < p; ++k) Ar<T>::add(s, zbuf[__ldg(ex + j * p + k)], ovf);
-        ybuf[j] = s;
+__device__ __forceinline__ T expand_set(const uint16_t *ex, int ps, int p, int j, const T *z, unsigned &ovf) {
+    T s = T(0);
+    const uint16_t *e = ex + (int64_t)j * ps;
+    if (ps == 4) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(e));
+        const uint32_t wd[2] = {w.x, w.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < p) Ar<T>::add(s, z[(wd[k >> 1] >> (16 * (k & 1))) & 0xffffu], ovf);
+    } else {
+        for (int k = 0; k < p; ++k) Ar<T>::add(s, z[__ldg(e + k)], ovf);
     }
+    return s;
+}
+
+// Y'(j) for the p-sets j of the squeezed universe of colour cv (the colour
+// sets without cv the eMA needs), summed from Z into dst.
+template <typename T>
+__device__ __forceinline__ void expand_y(const NodeArgs &A, int cv, const T *zbuf, T *dst, int lane,
+                                         unsigned &ovf) {
+    const int p = A.p, wy = A.wy, ps = A.pstride;
+    const uint16_t *ex = A.expand + (int64_t)cv * wy * ps;
+    for (int j = lane; j < wy; j += 32) dst[j] = expand_set(ex, ps, p, j, zbuf, ovf);
 }
 
 // eMA (Eq. 1 in squeezed coordinates) of one row by NT threads (tid in
@@ -729,7 +745,12 @@ struct MinBlocks {
         sizeof(T) == 4 ? (NV == 1 ? SG2V_MINB_F32_NV1 : NV == 2 ? SG2V_MINB_F32_NV2 : 2) : (NV == 1 ? 3 : 2);
 };
 
-template <typename T, int G, int NV, bool HIST, bool WEIGHTED, bool SCALED>
+// FORM selects a specialised epilogue (chosen on the host by node_form):
+// 0 generic; 1 single-vertex active child with a plain output row (the
+// expansion writes M_s' = Y' straight to the table); 2 a root with one
+// output set (rootpair: each lane pairs its p-sets with their active sets,
+// no Y' in shared memory).
+template <typename T, int G, int NV, bool HIST, bool WEIGHTED, bool SCALED, int FORM>
 __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_kernel(const NodeArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -740,6 +761,16 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
     T *obuf = mbuf + A.mwords;  // this row's outputs before normalisation (scaled)
     const int zlen = HIST ? A.kc : A.kc * A.wz_pad;
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    constexpr bool direct = FORM == 1 && !SCALED;
+    constexpr bool pairs = FORM == 2 && !SCALED && !HIST;
+    uint16_t pr[4] = {0, 0, 0, 0};
+    if constexpr (pairs) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = lane + 32 * q;
+            pr[q] = j < A.wy ? __ldg(A.rootpair + j) : (uint16_t)0;
+        }
+    }
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
     int4 task = ti < A.ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
@@ -806,6 +837,35 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
                 __threadfence();
                 for (int j = lane; j < zlen; j += 32) zbuf[j] = __ldcg(sc + j);
                 __syncwarp();
+            }
+            if constexpr (pairs) {
+                // row sum = sum over p-sets P' of M_a'(S' - P') * Y'(P')
+                if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
+                __syncwarp();
+                T s = T(0);
+                if (cok) {
+                    const uint16_t *ex = A.expand + (int64_t)cv * A.wy * A.pstride;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < A.wy) Ar<T>::mad(s, mbuf[pr[q]], expand_set(ex, A.pstride, A.p, j, zbuf, ovf), ovf);
+                    }
+                }
+                s = group_sum_chk<32>(s, ovf);
+                if (lane == 0)
+                    static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = A.half_arcs ? Ar<T>::twice(s, ovf) : s;
+                __syncwarp();
+                continue;
+            }
+            if constexpr (direct) {
+                // M_s' = Y': straight from the expansion to the output row
+                T *out = static_cast<T *>(A.Ms) + ((int64_t)v * A.nb + b) * A.ldt;
+                if (cok)
+                    expand_y<T>(A, cv, zbuf, out, lane, ovf);
+                else
+                    for (int j = lane; j < A.Ws; j += 32) out[j] = T(0);
+                __syncwarp();
+                continue;
             }
             if (cok) expand_y<T>(A, cv, zbuf, ybuf, lane, ovf);
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -992,12 +1052,8 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             __syncwarp();
             const bool ok = fin && cok && e0 < e1;
             if (ok) {
-                const uint16_t *ex = A.expand + (int64_t)cv * A.wy * A.p;
-                for (int j = gl; j < A.wy; j += G) {
-                    T y = T(0);
-                    for (int k = 0; k < A.p; ++k) Ar<T>::add(y, zg[__ldg(ex + j * A.p + k)], ovf);
-                    ybuf[j] = y;
-                }
+                const uint16_t *ex = A.expand + (int64_t)cv * A.wy * A.pstride;
+                for (int j = gl; j < A.wy; j += G) ybuf[j] = expand_set(ex, A.pstride, A.p, j, zg, ovf);
             }
             asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
@@ -1538,12 +1594,8 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             // Y' = expansion of Z over the p-sets without v's colour
             if (cok) {
                 const int p = A.p, wy = A.wy;
-                const uint16_t *ex = A.expand + (int64_t)cv * wy * p;
-                for (int j = tid; j < wy; j += blockDim.x) {
-                    T s = T(0);
-                    for (int k = 0; k < p; ++k) Ar<T>::add(s, zbuf[__ldg(ex + j * p + k)], ovf);
-                    ybuf[j] = s;
-                }
+                const uint16_t *ex = A.expand + (int64_t)cv * wy * A.pstride;
+                for (int j = tid; j < wy; j += blockDim.x) ybuf[j] = expand_set(ex, A.pstride, p, j, zbuf, ovf);
             }
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncthreads();
@@ -1600,14 +1652,20 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     }
 }
 
-template <typename T, int G, int NV, bool HIST, bool WEIGHTED, bool SC>
+template <typename T, int G, int NV, bool HIST, bool WEIGHTED, bool SC, int FORM = 0>
 void *kernel_ptr() {
-    return reinterpret_cast<void *>(&node_kernel<T, G, NV, HIST, WEIGHTED, SC>);
+    return reinterpret_cast<void *>(&node_kernel<T, G, NV, HIST, WEIGHTED, SC, FORM>);
 }
 
 template <typename T, bool W, bool SC = false>
-void *pick(bool hist, int g, int nv) {
+void *pick(bool hist, int g, int nv, int form = 0) {
     if (hist) return kernel_ptr<T, 32, 1, true, W, SC>();
+    if constexpr (!SC && !std::is_same<T, u128>::value) {
+        if (g == 32 && form == 1) return nv == 1 ? kernel_ptr<T, 32, 1, false, W, SC, 1>()
+                                                 : kernel_ptr<T, 32, 2, false, W, SC, 1>();
+        if (g == 32 && form == 2) return nv == 1 ? kernel_ptr<T, 32, 1, false, W, SC, 2>()
+                                                 : kernel_ptr<T, 32, 2, false, W, SC, 2>();
+    }
     if (g == 4) return kernel_ptr<T, 4, 1, false, W, SC>();
     if (g == 8) return kernel_ptr<T, 8, 1, false, W, SC>();
     if (g == 16) return kernel_ptr<T, 16, 1, false, W, SC>();
@@ -1639,7 +1697,7 @@ void *pick_group(int g) {
     return nullptr;
 }
 
-void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group = false) {
+void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group = false, int form = 0) {
     // integer tables count unweighted graphs only
     if ((e == Elem::U64 || e == Elem::U128) && weighted) return nullptr;
     if (group) {
@@ -1657,10 +1715,10 @@ void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group 
         if (e == Elem::F64) return weighted ? pick_wide<double, true>(nv) : pick_wide<double, false>(nv);
         return weighted ? pick_wide<float, true>(nv) : pick_wide<float, false>(nv);
     }
-    if (e == Elem::U64) return pick<u64, false>(hist, g, nv);
+    if (e == Elem::U64) return pick<u64, false>(hist, g, nv, form);
     if (e == Elem::U128) return pick<u128, false>(hist, g, nv);
-    if (e == Elem::F64) return weighted ? pick<double, true>(hist, g, nv) : pick<double, false>(hist, g, nv);
-    return weighted ? pick<float, true>(hist, g, nv) : pick<float, false>(hist, g, nv);
+    if (e == Elem::F64) return weighted ? pick<double, true>(hist, g, nv, form) : pick<double, false>(hist, g, nv, form);
+    return weighted ? pick<float, true>(hist, g, nv, form) : pick<float, false>(hist, g, nv, form);
 }
 
 void *select_kernel_scaled(bool hist, int g, int nv, bool weighted, bool group = false) {
@@ -2285,10 +2343,40 @@ int node_blocks_per_sm_scaled(bool hist, int g, int nv, bool weighted, int threa
     return blocks_per_sm(select_kernel_scaled(hist, g, nv, weighted, group), threads, smem);
 }
 
+// The specialised epilogue a node launch can use (node_kernel's FORM).
+int node_form(const NodeArgs &a, Elem e, int g, int nv) {
+    if (a.hist || a.group_rows || g != 32 || nv > 2 || e == Elem::U128) return 0;
+    if (a.a_leaf && !a.root && !a.defer && !a.Yout && !a.accumulate) return 1;
+    if (a.root && a.rootpair && !a.Yout && !a.defer && a.wy <= 128) return 2;
+    return 0;
+}
+
+namespace {
+// The occupancy queries of a request configure its FORM 0 kernels; a
+// specialised form chosen at launch gets its shared-memory limit raised
+// here, once per kernel.
+cudaError_t ensure_smem(void *k, int threads, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::unordered_map<void *, size_t> raised;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = raised.find(k);
+    if (it != raised.end() && it->second >= smem) return cudaSuccess;
+    if (blocks_per_sm(k, threads, smem) < 1) return cudaErrorInvalidValue;
+    raised[k] = smem;
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_node(const NodeArgs &args, Elem e, int g, int nv, int threads, size_t smem, int grid_cap,
                         cudaStream_t stream) {
-    void *k = select_kernel(e, args.hist != 0, g, nv, args.weights != nullptr, args.group_rows != 0);
+    const int form = node_form(args, e, g, nv);
+    void *k = select_kernel(e, args.hist != 0, g, nv, args.weights != nullptr, args.group_rows != 0, form);
     if (!k) return cudaErrorInvalidValue;
+    if (form != 0) {
+        const cudaError_t err = ensure_smem(k, threads, smem);
+        if (err != cudaSuccess) return err;
+    }
     return launch_variant(k, args, g, threads, smem, grid_cap, stream);
 }
 

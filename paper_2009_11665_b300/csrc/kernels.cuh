@@ -44,7 +44,8 @@ struct NodeArgs {
     // Y' (p-sets without v's colour) from Z
     int p;
     int wy;                       // C(kc-1, p)
-    const uint16_t *expand;       // [kc][wy][p] offsets into Z
+    const uint16_t *expand;       // [kc][wy][pstride] offsets into Z (the first p of each set)
+    int pstride;                  // p, or 4 when 2 <= p <= 4 (one 8-byte load per set)
     // shared memory per warp, in elements: Z copies, Y', the active row
     int zwords, ywords, mwords;
     // active side
@@ -60,6 +61,10 @@ struct NodeArgs {
     void *root_out;               // [nb][n]
     const uint32_t *splits;       // [Ws][nsplit] rank(A') | rank(S' - A') << 16 (a >= 2)
     int nsplit;
+    // root with t = kc (one output set S', so each p-set P' of Y' pairs with
+    // exactly one A' = S' - P'): rootpair[rank(P')] = rank(A'), [wy], wy <= 128;
+    // null otherwise.  The row sum is then sum over P' of M_a'(A') * Y'(P').
+    const uint16_t *rootpair;
     // FP32 range: per-row power-of-two exponents (scaled != 0).  A row's true
     // values are its stored values times 2^E[row]; Eref[row] is the largest
     // exponent among the neighbours the row gathers (colour != own colour).

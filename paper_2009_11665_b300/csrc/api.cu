@@ -526,7 +526,10 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             return SG2V_ERR_UNSUPPORTED;
         }
         if (!hist) widest = std::max<int64_t>(widest, (sh.wz + P->vecn - 1) / P->vecn * P->vecn);
-        sh.wz_pad = hist ? 1 : sh.grp * sh.nv * P->vecn;
+        // Z rows: narrow rows (lane groups) hold the row's vectors only,
+        // warp- and CTA-wide rows the whole tile of their lanes
+        sh.wz_pad = hist ? 1
+                         : (sh.grp < 32 ? (sh.wz + P->vecn - 1) / P->vecn * P->vecn : sh.grp * sh.nv * P->vecn);
         sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
         sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
         sh.owords = P->scaled ? ((int)binom(kc - 1, c.t - 1) + 3) / 4 * 4 : 0;

@@ -428,11 +428,18 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
     for (int q = 0; q < NV; ++q) run[q] = V::zero();
     int cur = -1;
     uint32_t seen = 0;  // colours whose Z row this group has written
+    // narrow rows (G < 32): Z rows hold the row's vectors only (wzp / V::n
+    // of them) and lanes past them write nothing; warp-wide rows keep the
+    // warp's whole tile (measured faster without the guards)
+    bool zok[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) zok[q] = G == 32 || gl + G * q < wzp / V::n;
     auto flush = [&](int c) {
         if (c != cv) {
             VT *zr = reinterpret_cast<VT *>(zg + c * wzp) + gl;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) zr[G * q] = run[q];
+            for (int q = 0; q < NV; ++q)
+                if (zok[q]) zr[G * q] = run[q];
             seen |= 1u << c;
         }
 #pragma unroll
@@ -511,7 +518,8 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
         if (!(seen >> d & 1u) && d != cv) {
             VT *zr = reinterpret_cast<VT *>(zg + d * wzp) + gl;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) zr[G * q] = V::zero();
+            for (int q = 0; q < NV; ++q)
+                if (zok[q]) zr[G * q] = V::zero();
         }
     }
     __syncwarp();
@@ -918,6 +926,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
     T *obuf = mbuf + A.mwords;
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const bool qok = gl < (A.Wz + V::n - 1) / V::n;
+    const bool zok = gl < wzp / V::n;  // Z rows hold wzp / V::n vectors
     // integer tables of odd width: the last vector's padding element is cleared
     const bool tail = Ar<T>::exact && V::n == 2 && (A.Wz & 1) && gl == (A.Wz + V::n - 1) / V::n - 1;
     const int zero_row = (int)A.n;
@@ -957,7 +966,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             uint32_t seen = 0;
             auto flush = [&](int c) {
                 if (c != cv) {
-                    reinterpret_cast<VT *>(zg + c * wzp)[gl] = run;
+                    if (zok) reinterpret_cast<VT *>(zg + c * wzp)[gl] = run;
                     seen |= 1u << c;
                 }
                 run = V::zero();
@@ -1023,7 +1032,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             }
             if (cur >= 0) flush(cur);
             for (int d = 0; d < kc; ++d)
-                if (!(seen >> d & 1u) && d != cv) reinterpret_cast<VT *>(zg + d * wzp)[gl] = V::zero();
+                if (!(seen >> d & 1u) && d != cv && zok) reinterpret_cast<VT *>(zg + d * wzp)[gl] = V::zero();
             __syncwarp();
             // split rows: fold Z into the scratch row; the last chunk finishes
             bool fin = have;

@@ -39,7 +39,8 @@ struct NodeArgs {
     const void *Mp;
     int64_t ldp;
     int Wz;
-    int wz_pad;                   // Z row stride (lanes per group * vectors per lane * elements per vector)
+    int wz_pad;                   // Z row stride in elements: narrow rows (lane groups) the row's
+                                  // 16-byte vectors, warp- and CTA-wide rows their lanes' whole tile
     int hist;
     // Y' (p-sets without v's colour) from Z
     int p;

@@ -100,9 +100,10 @@ struct DeviceTables {
     int wy = 0, nsplit = 0, pstride = 1;
 };
 
-// Entries between consecutive sets of the device expansion table: for
-// 2 <= p <= 4 the offsets are padded to 4 (one 8-byte load per set).
-int expand_stride(int p) { return (p >= 2 && p <= 4) ? 4 : p; }
+// Entries between consecutive sets of the device expansion table: the p
+// offsets padded to 4 (2 <= p <= 4: one 8-byte load per set) or to 8
+// (5 <= p <= 8: two).
+int expand_stride(int p) { return (p >= 2 && p <= 4) ? 4 : ((p >= 5 && p <= 8) ? 8 : p); }
 std::map<std::tuple<int, int, int, int, int>, DeviceTables> g_ctables;
 
 sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTables *out) {

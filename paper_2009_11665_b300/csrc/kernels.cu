@@ -590,8 +590,8 @@ __device__ __forceinline__ void hist_z_weighted(const NodeArgs &A, int64_t e0, i
 
 // Y'(j) = sum over the p offsets of set j of Z[offset] (ex: the table of the
 // row's colour).  With stride 4 (2 <= p <= 4) the offsets of a set are one
-// 8-byte load, else they are read one by one (measured: 16-byte loads for
-// p = 5 made the tree10 root slower).
+// 8-byte load, with stride 8 (5 <= p <= 8) two, else they are read one by
+// one (measured: one 16-byte load for p = 5 made the tree10 root slower).
 template <typename T>
 __device__ __forceinline__ T expand_set(const uint16_t *ex, int ps, int p, int j, const T *z, unsigned &ovf) {
     T s = T(0);
@@ -601,6 +601,13 @@ __device__ __forceinline__ T expand_set(const uint16_t *ex, int ps, int p, int j
         const uint32_t wd[2] = {w.x, w.y};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
+            if (k < p) Ar<T>::add(s, z[(wd[k >> 1] >> (16 * (k & 1))) & 0xffffu], ovf);
+    } else if (ps == 8) {
+        const uint2 w0 = __ldg(reinterpret_cast<const uint2 *>(e));
+        const uint2 w1 = __ldg(reinterpret_cast<const uint2 *>(e + 4));
+        const uint32_t wd[4] = {w0.x, w0.y, w1.x, w1.y};
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
             if (k < p) Ar<T>::add(s, z[(wd[k >> 1] >> (16 * (k & 1))) & 0xffffu], ovf);
     } else {
         for (int k = 0; k < p; ++k) Ar<T>::add(s, z[__ldg(e + k)], ovf);

@@ -46,7 +46,7 @@ struct NodeArgs {
     int p;
     int wy;                       // C(kc-1, p)
     const uint16_t *expand;       // [kc][wy][pstride] offsets into Z (the first p of each set)
-    int pstride;                  // p, or 4 when 2 <= p <= 4 (one 8-byte load per set)
+    int pstride;                  // p, 4 when 2 <= p <= 4, 8 when 5 <= p <= 8 (8-byte loads)
     // shared memory per warp, in elements: Z copies, Y', the active row
     int zwords, ywords, mwords;
     // active side

@@ -1948,13 +1948,21 @@ __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t
 // of the wave; colours outside [0, kc) go last, tagged -1.  Each colour then
 // forms one run per task.  Tasks of at most 32 arcs sort in one pass from
 // registers; longer ones count buckets first, then place.
+constexpr int kSortStage = 1024;
+
 __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntasks, const int32_t *__restrict__ col_idx,
                                    const float *__restrict__ weights, int64_t n, int64_t nnz,
                                    const int8_t *__restrict__ colours, int nb, int kc, int32_t *scol, int8_t *sclr,
                                    float *sw) {
     __shared__ int base_s[8][kMaxHistColours + 1];
+    // tasks of up to kSortStage arcs keep their neighbours and colours here
+    // between the counting pass and the placing pass
+    __shared__ int32_t ubuf_s[8][kSortStage];
+    __shared__ int8_t cbuf_s[8][kSortStage];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *start = base_s[wib];
+    int32_t *ubuf = ubuf_s[wib];
+    int8_t *cbuf = cbuf_s[wib];
     const unsigned lt = (1u << lane) - 1u;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // software pipeline over the warp's tasks: the descriptor two tasks ahead
@@ -2010,6 +2018,61 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
             // pass 1: arcs per colour (bucket kc holds invalid colours)
             if (lane <= kc) start[lane] = 0;
             __syncwarp();
+            if (e1 - e0 <= kSortStage) {
+                // four batches of neighbours, then their colours, load together;
+                // both are staged for the placing pass
+                for (int64_t e = e0 + lane; e - lane < e1; e += 128) {
+                    int uu[4], cc[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) uu[k] = e + 32 * k < e1 ? __ldg(col_idx + e + 32 * k) : 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool ok = e + 32 * k < e1;
+                        cc[k] = ok ? (int)__ldg(col + uu[k]) : -2;
+                        if (ok && (unsigned)cc[k] >= (unsigned)kc) cc[k] = kc;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int64_t ek = e + 32 * k;
+                        if (ek - lane >= e1) break;  // warp-uniform: no such batch
+                        const bool ok = ek < e1;
+                        const unsigned same = __match_any_sync(kFull, cc[k]);
+                        if (ok) {
+                            ubuf[ek - e0] = uu[k];
+                            cbuf[ek - e0] = (int8_t)cc[k];
+                            if ((same & lt) == 0) start[cc[k]] += __popc(same);
+                        }
+                        __syncwarp();
+                    }
+                }
+                const int cnt = lane <= kc ? start[lane] : 0;
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                __syncwarp();
+                if (lane <= kc) start[lane] = incl - cnt;
+                __syncwarp();
+                // pass 2 from the staged copies
+                for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
+                    const bool ok = e < e1;
+                    const int u = ok ? ubuf[e - e0] : 0;
+                    const int c = ok ? (int)cbuf[e - e0] : -2;
+                    const unsigned same = __match_any_sync(kFull, c);
+                    if (ok) {
+                        const int pos = start[c] + __popc(same & lt);
+                        so[pos] = u;
+                        co[pos] = (int8_t)(c == kc ? -1 : c);
+                        if (wo) wo[pos] = __ldg(weights + e);
+                    }
+                    __syncwarp();
+                    if (ok && (same & lt) == 0) start[c] += __popc(same);
+                    __syncwarp();
+                }
+                continue;
+            }
             for (int64_t e = e0 + lane; e - lane < e1; e += 32) {
                 const bool ok = e < e1;
                 int c = ok ? (int)__ldg(col + __ldg(col_idx + e)) : -2;
@@ -2501,8 +2564,10 @@ cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
                                int32_t *scol, int8_t *sclr, float *sw, int sms, cudaStream_t stream) {
     if (small_begin > 0) {
+        // one wave of resident blocks (the staging buffers limit residency)
+        static const int per_sm = std::max(1, blocks_per_sm(reinterpret_cast<void *>(&colour_sort_kernel), 256, 0));
         int64_t blocks = (small_begin + 7) / 8;
-        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        if (blocks > (int64_t)sms * per_sm) blocks = (int64_t)sms * per_sm;
         colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, small_begin, col_idx, weights, n, nnz, colours,
                                                                  nb, kc, scol, sclr, sw);
     }

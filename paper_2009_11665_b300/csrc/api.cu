@@ -832,6 +832,20 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
 // colour check, per wave the colour sort and one launch per node, then the
 // root reductions into R.sums (and per-vertex doubles when pv != null).
 // Nothing here synchronises, so the sequence can be captured in a CUDA graph.
+// The node whose table the colour sort writes from its bucket counts: a
+// non-root histogram node with two single-vertex children (t = 2) on an
+// unweighted graph with plain tables (-1: none; SG2V_SORT_HIST=0 turns the
+// fusion off).  Its children are leaves, so it is the first node to run.
+int sort_hist_node(const Prepared &P) {
+    const char *env = std::getenv("SG2V_SORT_HIST");
+    if ((env && std::atoi(env) == 0) || P.scaled || P.g->weights) return -1;
+    for (size_t i = 0; i < P.nodes.size(); ++i) {
+        const CNode &c = P.nodes[i];
+        if (c.t == 2 && c.a == 1 && c.p == 1 && !c.is_root) return (int)i;
+    }
+    return -1;
+}
+
 sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, double *pv, TableSource &src,
                     cudaStream_t stream, CallTimer &timer) {
     const sg2v_graph *g = P.g;
@@ -844,19 +858,35 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, R.status, stream), "colour check");
     const char *half_env = std::getenv("SG2V_HALF_ROOT");
     const bool half_root = !(half_env && std::atoi(half_env) == 0);
+    const int fused = sort_hist_node(P);
     for (int b0 = 0; b0 < nb; b0 += wave) {
         const int wb = std::min(wave, nb - b0);
         const int8_t *wcol = d_col + (int64_t)b0 * n;
+        SortHist hist{nullptr, 0, P.elem};
+        double hist_bytes = 0.0;
+        if (fused >= 0) {
+            // the (2, 1, 1) node's table comes from the sort's bucket counts
+            const CNode &c = P.nodes[(size_t)fused];
+            R.ld[(size_t)fused] = table_ld(P, c);
+            if ((st = src.get((size_t)fused, table_bytes(P, c, wb), &R.table[(size_t)fused]))) return st;
+            if ((st = zero_gather_row(R.table[(size_t)fused], n, wb, R.ld[(size_t)fused], esz, stream))) return st;
+            if (g->nheavy)  // chunks of split rows add into zeroed rows
+                SG2V_CUDA(cudaMemsetAsync(R.table[(size_t)fused], 0, (size_t)n * wb * R.ld[(size_t)fused] * esz, stream),
+                          "memset");
+            hist = SortHist{R.table[(size_t)fused], R.ld[(size_t)fused], P.elem};
+            hist_bytes = (double)n * wb * (kc - 1) * esz;
+        }
         timer.begin("colour_sort",
-                    (double)wb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))));
+                    (double)wb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))) + hist_bytes);
         SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, g->nnz, wcol, wb,
-                                     kc, R.scol, R.sclr, R.sw, P.info.sms, stream),
+                                     kc, R.scol, R.sclr, R.sw, hist, P.info.sms, stream),
                   "colour sort");
         timer.end();
         if (g->small_begin > 0 && g->small_begin < g->ntasks) timer.count_extra(1);  // the small-task sort
         for (size_t i = 0; i < P.nodes.size(); ++i) {
             const CNode &c = P.nodes[i];
             const Shape &sh = P.shape[i];
+            if ((int)i == fused) continue;  // written by the sort
             NodeArgs A = node_args(P, R, i, b0, wb, wcol);
             if (!c.is_root) {
                 R.ld[i] = table_ld(P, c);
@@ -1072,7 +1102,7 @@ sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bo
 
 int64_t count_launches(const Prepared &P, int wave) {
     const int64_t waves = (P.nb + wave - 1) / wave;
-    int64_t per_wave = 1 + (int64_t)P.nodes.size();
+    int64_t per_wave = 1 + (int64_t)P.nodes.size() - (sort_hist_node(P) >= 0 ? 1 : 0);
     if (P.g->small_begin > 0 && P.g->small_begin < P.g->ntasks) per_wave += 1;  // two sort launches
     if (P.scaled)
         for (const CNode &c : P.nodes) per_wave += c.p != 1;
@@ -1085,12 +1115,6 @@ sg2v_status copy_out(double *dst, const double *src, size_t count, cudaStream_t 
     SG2V_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, stream), "result copy");
     return SG2V_OK;
 }
-
-}  // namespace
-}  // namespace sg2v
-
-namespace sg2v {
-namespace {
 
 }  // namespace
 }  // namespace sg2v
@@ -1639,8 +1663,9 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     if ((st = alloc_run(Pw, 1, alloc, &R))) return st;
     SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
     SG2V_CUDA(launch_check_colours(d_col, n, kc, R.status, stream), "colour check");
+    const SortHist no_hist{nullptr, 0, Elem::F32};
     SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, nnz, d_col, 1, kc,
-                                 R.scol, R.sclr, R.sw, P.info.sms, stream),
+                                 R.scol, R.sclr, R.sw, no_hist, P.info.sms, stream),
               "colour sort");
     // forward, keeping every table and every node's Y'
     std::vector<void *> yt(nn, nullptr), gt(nn, nullptr);

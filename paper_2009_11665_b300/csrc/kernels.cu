@@ -1906,6 +1906,57 @@ __global__ void eref_kernel(const int4 *__restrict__ tasks, int64_t ntasks, cons
     }
 }
 
+// Entry j of row `row` of a fused histogram table: cnt neighbours (added
+// atomically for chunks of split rows).
+__device__ __forceinline__ void hist_put(const SortHist &H, int64_t row, int j, unsigned cnt, bool atomic) {
+    const int64_t at = row * H.ld + j;
+    switch (H.elem) {
+        case Elem::F32: {
+            float *p = static_cast<float *>(H.out) + at;
+            if (!atomic)
+                *p = (float)cnt;
+            else if (cnt)
+                atomicAdd(p, (float)cnt);
+            break;
+        }
+        case Elem::F64: {
+            double *p = static_cast<double *>(H.out) + at;
+            if (!atomic)
+                *p = (double)cnt;
+            else if (cnt)
+                atomicAdd(p, (double)cnt);
+            break;
+        }
+        case Elem::U64: {
+            u64 *p = static_cast<u64 *>(H.out) + at;
+            if (!atomic)
+                *p = cnt;
+            else if (cnt)
+                atomicAdd(p, (u64)cnt);
+            break;
+        }
+        default: {
+            u128 *p = static_cast<u128 *>(H.out) + at;
+            if (!atomic)
+                *p = u128((u64)cnt, 0ull);
+            else if (cnt)
+                atomicAdd(&p->lo, (u64)cnt);  // counts stay far below 2^64
+            break;
+        }
+    }
+}
+
+// The fused histogram row of (task, b) from per-colour counts cnt(x) (x in
+// [0, kc)): lane j < kc - 1 writes the count of the j-th colour other than cv.
+template <typename F>
+__device__ __forceinline__ void hist_row(const SortHist &H, const int4 &task, int b, int nb, int cv, int kc, int j,
+                                         F &&cnt) {
+    if (j >= kc - 1) return;
+    const bool ok = (unsigned)cv < (unsigned)kc;
+    const int x = j < cv ? j : j + 1;
+    hist_put(H, (int64_t)task.x * nb + b, j, ok ? (unsigned)cnt(x) : 0u, task.y >= 0);
+}
+
 // The same sort for tasks of at most G arcs, 32 / G tasks per warp: a lane's
 // arc goes to the number of the task's arcs with a smaller colour (or the
 // same colour and a lower index), counted over the group with shuffles.
@@ -1913,7 +1964,7 @@ template <int G>
 __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t ntasks,
                                          const int32_t *__restrict__ col_idx, const float *__restrict__ weights,
                                          int64_t n, int64_t nnz, const int8_t *__restrict__ colours, int nb, int kc,
-                                         int32_t *scol, int8_t *sclr, float *sw) {
+                                         int32_t *scol, int8_t *sclr, float *sw, const SortHist H) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G, g0 = grp * G;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1939,6 +1990,27 @@ __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t
                 sclr[pos] = (int8_t)(c == kc ? -1 : c);
                 if (sw) sw[pos] = __ldg(weights + task.z + gl);
             }
+            if (H.out) {
+                // lane gl counts colours gl and gl + G of its task's arcs
+                unsigned n0 = 0, n1 = 0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const int ck = __shfl_sync(kFull, c, g0 + k);
+                    n0 += (k < m) && ck == gl;
+                    n1 += (k < m) && ck == gl + G;
+                }
+                const bool have = t < ntasks;
+                const int cv = have ? (int)__ldg(colours + (int64_t)b * n + task.x) : -1;
+                // the count of colour x lives on lane x % G of the group (n0 or n1)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = gl + G * h;  // output entry j: colour j or j + 1
+                    const int x = j < cv ? j : j + 1;
+                    const unsigned c0 = __shfl_sync(kFull, n0, g0 + (x % G));
+                    const unsigned c1 = __shfl_sync(kFull, n1, g0 + (x % G));
+                    if (have) hist_row(H, task, b, nb, cv, kc, j, [&](int) { return x < G ? c0 : c1; });
+                }
+            }
         }
     }
 }
@@ -1953,7 +2025,7 @@ constexpr int kSortStage = 1024;
 __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntasks, const int32_t *__restrict__ col_idx,
                                    const float *__restrict__ weights, int64_t n, int64_t nnz,
                                    const int8_t *__restrict__ colours, int nb, int kc, int32_t *scol, int8_t *sclr,
-                                   float *sw) {
+                                   float *sw, const SortHist H) {
     __shared__ int base_s[8][kMaxHistColours + 1];
     // tasks of up to kSortStage arcs keep their neighbours and colours here
     // between the counting pass and the placing pass
@@ -1996,6 +2068,8 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 __syncwarp();
                 if (ok && (same & lt) == 0) start[c] = __popc(same);
                 __syncwarp();
+                if (H.out)
+                    hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
                 const int cnt = lane <= kc ? start[lane] : 0;
                 int incl = cnt;
 #pragma unroll
@@ -2045,6 +2119,8 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                         __syncwarp();
                     }
                 }
+                if (H.out)
+                    hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
                 const int cnt = lane <= kc ? start[lane] : 0;
                 int incl = cnt;
 #pragma unroll
@@ -2081,6 +2157,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 if (ok && (same & lt) == 0) start[c] += __popc(same);
                 __syncwarp();
             }
+            if (H.out) hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
             // exclusive prefix over buckets
             const int cnt = lane <= kc ? start[lane] : 0;
             int incl = cnt;
@@ -2562,14 +2639,15 @@ cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, 
 
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
-                               int32_t *scol, int8_t *sclr, float *sw, int sms, cudaStream_t stream) {
+                               int32_t *scol, int8_t *sclr, float *sw, const SortHist &hist, int sms,
+                               cudaStream_t stream) {
     if (small_begin > 0) {
         // one wave of resident blocks (the staging buffers limit residency)
         static const int per_sm = std::max(1, blocks_per_sm(reinterpret_cast<void *>(&colour_sort_kernel), 256, 0));
         int64_t blocks = (small_begin + 7) / 8;
         if (blocks > (int64_t)sms * per_sm) blocks = (int64_t)sms * per_sm;
         colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, small_begin, col_idx, weights, n, nnz, colours,
-                                                                 nb, kc, scol, sclr, sw);
+                                                                 nb, kc, scol, sclr, sw, hist);
     }
     const int64_t rest = ntasks - small_begin;
     if (rest > 0) {
@@ -2577,7 +2655,7 @@ cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_
         int64_t blocks = ((rest + 32 / G - 1) / (32 / G) + 7) / 8;
         if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
         colour_sort_small_kernel<G><<<(unsigned)blocks, 256, 0, stream>>>(
-            tasks + small_begin, rest, col_idx, weights, n, nnz, colours, nb, kc, scol, sclr, sw);
+            tasks + small_begin, rest, col_idx, weights, n, nnz, colours, nb, kc, scol, sclr, sw, hist);
     }
     return cudaGetLastError();
 }

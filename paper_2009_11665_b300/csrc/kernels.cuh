@@ -233,9 +233,21 @@ cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, 
 // Tasks from small_begin on have at most kSortSmallArcs arcs (the work list
 // is sorted by work) and sort several per warp.
 constexpr int kSortSmallArcs = 8;
+// The table of a histogram node whose children are both single vertices
+// (t = 2), written by the sort from its bucket counts: row v * nb + b gets,
+// for each colour x != col(v) in squeezed order, the number of v's
+// neighbours of colour x (a row of zeros when col(v) is invalid).  Chunks of
+// split rows add their counts atomically, so the table must be zero on entry
+// when the graph has split rows.  out == null: no histogram.
+struct SortHist {
+    void *out;
+    int64_t ld;                   // elements between rows
+    Elem elem;
+};
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
-                               int32_t *scol, int8_t *sclr, float *sw, int sms, cudaStream_t stream);
+                               int32_t *scol, int8_t *sclr, float *sw, const SortHist &hist, int sms,
+                               cudaStream_t stream);
 
 // Totals and estimates of nseg segments from their root sums: the exact
 // 128-bit sum rounded once to double when every value was an integer, else

@@ -316,12 +316,13 @@ def test_min_work_plans_match_oracle(sg, seed):
         _check_fp64(pv.cpu().numpy(), tot, ref, exact=ref.max_bits <= 53)
 
 
-@pytest.mark.parametrize("knob", ["SG2V_HIST_ROWS", "SG2V_GROUP_ROWS", "SG2V_HALF_ROOT", "SG2V_ROOT_PAIRS"])
+@pytest.mark.parametrize("knob", ["SG2V_HIST_ROWS", "SG2V_GROUP_ROWS", "SG2V_HALF_ROOT", "SG2V_ROOT_PAIRS",
+                                  "SG2V_SORT_HIST"])
 def test_alternative_kernel_forms(sg, knob, monkeypatch):
-    """The one-row-per-warp forms that the 32-row histogram kernel, the
-    lane-group kernel, the half-arc root and the paired root sum replace on
-    unweighted graphs (they still serve weighted graphs, long tasks and
-    roots with several output sets) equal the oracle."""
+    """The forms that the 32-row histogram kernel, the lane-group kernel, the
+    half-arc root, the paired root sum and the sort-written (2, 1, 1) table
+    replace on unweighted graphs (they still serve weighted graphs, long
+    tasks and roots with several output sets) equal the oracle."""
     monkeypatch.setenv(knob, "0")
     g = _hub_graph(9)
     for parent in (si.TREE10.parent, si.TREE7.parent, si.PATH7.parent, (-1, 0, 0, 2)):

@@ -176,6 +176,25 @@ def physical_gpu_index(local: int) -> int:
     return local
 
 
+def rank_colourings(n: int, kc: int, batch: int, rank: int, seed: int) -> np.ndarray:
+    """Colourings of `rank` (replicas over colourings, Alg. 1's independent
+    draws): indices rank*batch .. rank*batch+batch-1 of one seeded stream, so
+    the ranks' colourings are disjoint and together the stream's first
+    world*batch."""
+    return si.colourings(n, kc, batch * (rank + 1), seed=seed)[rank * batch:(rank + 1) * batch]
+
+
+def max_over_ranks(torch, value: float, dist=None) -> float:
+    """The largest of every rank's value (the whole job's step time); the
+    reduction runs on the GPU under NCCL and on the host under gloo."""
+    if not dist:
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_steps(torch, fn, steps, warmup, stream, dist=None):
     for _ in range(warmup):
         fn()
@@ -189,11 +208,8 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
         fn()
     stop.record(stream)
     torch.cuda.synchronize()
-    ms = start.elapsed_time(stop)
+    ms = max_over_ranks(torch, start.elapsed_time(stop), dist)
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     return ms / steps
 
@@ -282,7 +298,7 @@ def main():
     graph = sg.Graph(g.row_ptr, g.col_idx)
     plan = sg.Plan(TEMPLATE.parent, 0, K_COLOURS, cut=PLAN_CUT, avg_degree=32.0)
     # colourings of this rank: indices rank*B .. rank*B+B-1 (replicas over colourings)
-    cols = si.colourings(g.n, K_COLOURS, B * (rank + 1), seed=0)[rank * B:(rank + 1) * B]
+    cols = rank_colourings(g.n, K_COLOURS, B, rank, seed=0)
     d_cols = torch.from_numpy(cols).cuda()
     stream = torch.cuda.current_stream()
     tot32 = torch.empty((1, B), dtype=torch.float64, device="cuda")
@@ -331,7 +347,7 @@ def main():
         plans3 = [sg.Plan(t.parent, 0, 7) for t in (si.PATH7, si.STAR7, si.TREE7)]
         B3 = 64
         ses = sg.Session(graph3, plans3, B3, "fp32", autotune=True)
-        cols3 = torch.from_numpy(si.colourings(g3.n, 7, B3 * (rank + 1), seed=1)[rank * B3:(rank + 1) * B3]).cuda()
+        cols3 = torch.from_numpy(rank_colourings(g3.n, 7, B3, rank, seed=1)).cuda()
         tot3 = torch.empty((3, B3), dtype=torch.float64, device="cuda")
         ms3 = time_steps(torch, lambda: ses.run(cols3, tot3, None, None, stream), args.steps, args.warmup, stream,
                          dist)
@@ -402,7 +418,7 @@ def main():
         graph5 = sg.Graph(g5.row_ptr, g5.col_idx)
         plan5 = sg.Plan(si.TREE15.parent, 0, 15)
         B5 = 8
-        cols5 = torch.from_numpy(si.colourings(g5.n, 15, B5 * (rank + 1), seed=0)[rank * B5:(rank + 1) * B5]).cuda()
+        cols5 = torch.from_numpy(rank_colourings(g5.n, 15, B5, rank, seed=0)).cuda()
         tot5 = torch.empty((1, B5), dtype=torch.float64, device="cuda")
         ms5 = time_steps(torch, lambda: sg.sg2v_count_batched(graph5.handle, [plan5.handle], cols5, B5,
                                                               sg.SG2V_FP32_SCALED, None, tot5, None, stream),

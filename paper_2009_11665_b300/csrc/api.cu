@@ -402,6 +402,8 @@ struct Shape {
     size_t smem;
     int blocks_per_sm;
     bool rows = false;  // histogram node run 32 rows per warp (hist_rows_kernel)
+    int npass = 1;      // CTA-wide rows: column tiles per row
+    bool zglobal = false;  // CTA-wide rows: Z in global memory (too wide for shared memory)
     bool group = false; // narrow rows: short tasks one per lane group (node_group_kernel)
     int wthreads = 0, wbps = 0;  // the one-warp-per-row launch of the longer tasks of a group node
     size_t wsmem = 0;
@@ -431,6 +433,7 @@ struct Prepared {
     int64_t scratch_ld = 1;
     int auto_wave = 1;            // widest wave whose gathered table fits half of L2
     int64_t defer_words = 0;      // largest deferred node's Y' row stride (0: none)
+    size_t zglobal_bytes = 0;     // global Z of CTA-wide rows that do not fit shared memory
 };
 
 const char *elem_name(const Prepared &P) {
@@ -522,24 +525,39 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             sh.grp = kWideLanes;
             sh.nv = (sh.wz + kWideThreads * P->vecn - 1) / (kWideThreads * P->vecn);
         }
+        if (sh.grp == kWideLanes) {
+            // rows wider than the CTA's tile walk their arcs once per column tile
+            const int nvec = (sh.wz + P->vecn - 1) / P->vecn;
+            if (sh.nv == 0) sh.nv = 4;
+            sh.npass = (nvec + kWideThreads * sh.nv - 1) / (kWideThreads * sh.nv);
+        }
         if (sh.nv == 0) {
-            set_error("passive table wider than this build's register tile (column tiling not built)");
+            set_error("passive table wider than this build's register tile");
             return SG2V_ERR_UNSUPPORTED;
         }
         if (!hist) widest = std::max<int64_t>(widest, (sh.wz + P->vecn - 1) / P->vecn * P->vecn);
-        // Z rows: narrow rows (lane groups) hold the row's vectors only,
-        // warp- and CTA-wide rows the whole tile of their lanes
+        // Z rows: narrow rows (lane groups) and CTA-wide rows hold the row's
+        // vectors only, warp-wide rows the whole tile of their lanes
         sh.wz_pad = hist ? 1
-                         : (sh.grp < 32 ? (sh.wz + P->vecn - 1) / P->vecn * P->vecn : sh.grp * sh.nv * P->vecn);
+                         : (sh.grp != 32 ? (sh.wz + P->vecn - 1) / P->vecn * P->vecn : sh.grp * sh.nv * P->vecn);
+        if ((int64_t)kc * sh.wz_pad > 65536) {
+            set_error("per-colour accumulators wider than 16-bit expansion offsets (more than 65,536 elements)");
+            return SG2V_ERR_UNSUPPORTED;
+        }
         sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
         sh.mwords = c.a == 1 ? 0 : ((int)binom(kc - 1, c.a - 1) + 3) / 4 * 4;
         sh.owords = P->scaled ? ((int)binom(kc - 1, c.t - 1) + 3) / 4 * 4 : 0;
         P->scratch_ld = std::max<int64_t>(P->scratch_ld, hist ? kc : (int64_t)kc * sh.wz_pad);
         if (sh.grp == kWideLanes) {
-            // one CTA per row: Z, Y' and the active row once per CTA
+            // one CTA per row: Z, Y' and the active row once per CTA; Z goes to
+            // global memory (one slot per resident CTA) when it does not fit
             sh.zwords = kc * sh.wz_pad;
             sh.threads = kWideThreads;
             sh.smem = (size_t)(sh.zwords + sh.ywords + sh.mwords + sh.owords) * P->esz;
+            if (sh.smem > 220 * 1024) {
+                sh.zglobal = true;
+                sh.smem = (size_t)(sh.ywords + sh.mwords + sh.owords) * P->esz;
+            }
         } else {
             sh.zwords = hist ? (kc + 3) / 4 * 4 : (32 / sh.grp) * kc * sh.wz_pad;
             sh.threads = kNodeThreads;
@@ -554,6 +572,9 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         sh.blocks_per_sm =
             P->scaled ? node_blocks_per_sm_scaled(hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem)
                       : node_blocks_per_sm(P->elem, hist, sh.grp, sh.nv, g->weights != nullptr, sh.threads, sh.smem);
+        if (sh.zglobal)
+            P->zglobal_bytes = std::max(P->zglobal_bytes, (size_t)P->info.sms * std::max(sh.blocks_per_sm, 1) *
+                                                              (size_t)sh.zwords * P->esz);
         const char *group_env = std::getenv("SG2V_GROUP_ROWS");
         if (!hist && sh.grp < 32 && sh.nv == 1 && !(group_env && std::atoi(group_env) == 0)) {
             // narrow rows: every lane group takes its own row
@@ -642,6 +663,7 @@ struct RunBuffers {
     std::vector<int64_t> ld;
     int32_t *eref = nullptr;      // scaled: [n][wave] reference exponents
     void *defer_y = nullptr;      // Y' rows of a deferred-eMA node: [n][wave][defer_words]
+    void *zglobal = nullptr;      // global Z of CTA-wide rows: [resident CTAs][kc][wz_pad]
     unsigned *status = nullptr;   // [4]: bit 0 colour out of range
     double *ones = nullptr;       // [nb][n] ones for single-vertex templates
     int chunks = 1;
@@ -715,6 +737,7 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     }
     if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R->eref))) return st;
     if (P.defer_words && (st = alloc((size_t)P.n * wave * P.defer_words * P.esz, &R->defer_y))) return st;
+    if (P.zglobal_bytes && (st = alloc(P.zglobal_bytes, &R->zglobal))) return st;
     R->rootbuf.assign(P.plans.size(), nullptr);
     for (size_t pi = 0; pi < P.plans.size(); ++pi)
         if (P.plan_root[pi] >= 0 && (st = alloc((size_t)P.nb * P.n * root_esz(P), &R->rootbuf[pi]))) return st;
@@ -798,6 +821,8 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     A.scratch_ld = P.scratch_ld;
     A.counters = R.counters;
     A.status = R.status;
+    A.npass = sh.npass;
+    A.zglobal = sh.zglobal ? R.zglobal : nullptr;
     return A;
 }
 
@@ -1766,6 +1791,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             A.mwords = 0;
             A.group_rows = 0;  // the transposed SpMM's shape is its own (one task per warp)
             A.defer = 0;
+            A.npass = 1;
+            A.zglobal = nullptr;
             A.p = btab[ii].nterms;
             A.pstride = btab[ii].nterms;
             A.wy = btab[ii].wout;

@@ -1454,22 +1454,20 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
     __shared__ T s_red[kWideWarps];
     __shared__ T s_max[kWideWarps];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int kc = A.kc, wzp = A.wz_pad;  // wzp = kWideWarps * 32 * NV * V::n
-    T *zbuf = reinterpret_cast<T *>(smem_raw);
-    T *ybuf = zbuf + A.zwords;
+    const int kc = A.kc, wzp = A.wz_pad;  // wzp = the row's vectors * V::n
+    // Z in shared memory, or (rows too wide for it) in this CTA's slot of a
+    // global scratch that stays in L2
+    T *zbuf = A.zglobal ? static_cast<T *>(A.zglobal) + (int64_t)blockIdx.x * kc * wzp
+                        : reinterpret_cast<T *>(smem_raw);
+    T *ybuf = reinterpret_cast<T *>(smem_raw) + (A.zglobal ? 0 : A.zwords);
     T *mbuf = ybuf + A.ywords;
     T *obuf = mbuf + A.mwords;  // outputs before normalisation (scaled)
     const int zlen = kc * wzp;
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int nvec = (A.Wz + V::n - 1) / V::n;
-    const int vbase = w * 32 * NV + lane;  // this lane's first vector of the row
-    bool qok[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) qok[q] = vbase + 32 * q < nvec;
-    // integer tables of odd width: the last vector's padding element is cleared
-    bool tail[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) tail[q] = Ar<T>::exact && V::n == 2 && (A.Wz & 1) && vbase + 32 * q == nvec - 1;
+    // column passes: the CTA's tile covers kWideThreads * NV vectors of the
+    // row; wider rows walk their arcs once per tile
+    const int npass = A.npass > 0 ? A.npass : 1;
     unsigned ovf = 0;
     for (int64_t ti = blockIdx.x; ti < A.ntasks; ti += gridDim.x) {
         const int4 task = A.tasks[ti];
@@ -1488,7 +1486,16 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
-            if (cok) {
+            for (int pass = 0; cok && pass < npass; ++pass) {
+                const int vbase = pass * kWideThreads * NV + w * 32 * NV + lane;  // this lane's first vector
+                bool qok[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) qok[q] = vbase + 32 * q < nvec;
+                // integer tables of odd width: the last vector's padding element is cleared
+                bool tail[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q)
+                    tail[q] = Ar<T>::exact && V::n == 2 && (A.Wz & 1) && vbase + 32 * q == nvec - 1;
                 // sum colour runs of the arcs into this warp's slice of Z: each
                 // colour's slice is written once; colours without arcs are
                 // zeroed after the walk (v's own colour is read by nothing)
@@ -1507,15 +1514,14 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                     if (c != cv) {
                         VT *zr = reinterpret_cast<VT *>(zbuf + c * wzp) + vbase;
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) zr[32 * q] = run[q];
+                        for (int q = 0; q < NV; ++q)
+                            if (qok[q]) zr[32 * q] = run[q];
                         seen |= 1u << c;
                     }
 #pragma unroll
                     for (int q = 0; q < NV; ++q) run[q] = V::zero();
                 };
-                // slots past the live arcs read the zero row (vertex n); FP32
-                // loads are unpredicated (the table padding covers a whole CTA
-                // tile past the last row)
+                // slots past the live arcs read the zero row (vertex n)
                 const int zero_row = (int)A.n;
                 for (int64_t base = e0; base < e1; base += 32) {
                     const int cnt_in = (int)(e1 - base < 32 ? e1 - base : 32);
@@ -1555,7 +1561,10 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                             const VT *row = Mb + (int64_t)u * uvec;
 #pragma unroll
                             for (int q = 0; q < NV; ++q) {
-                                x[r][q] = (sizeof(T) == 4 || qok[q]) ? ldg_row(row + 32 * q) : V::zero();
+                                // FP32 loads of the first tile are unpredicated (the
+                                // table's padding covers a tile past its last row)
+                                x[r][q] = ((sizeof(T) == 4 && pass == 0) || qok[q]) ? ldg_row(row + 32 * q)
+                                                                                    : V::zero();
                                 if constexpr (Ar<T>::exact && V::n == 2)
                                     if (tail[q]) x[r][q].y = 0;
                             }
@@ -1581,7 +1590,8 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
                     if (!(seen >> d & 1u) && d != cv) {
                         VT *zr = reinterpret_cast<VT *>(zbuf + d * wzp) + vbase;
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) zr[32 * q] = V::zero();
+                        for (int q = 0; q < NV; ++q)
+                            if (qok[q]) zr[32 * q] = V::zero();
                     }
                 }
             }

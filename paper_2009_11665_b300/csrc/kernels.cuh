@@ -93,6 +93,11 @@ struct NodeArgs {
     // (node_group_kernel); shared memory per warp is then
     // (32 / lanes) * (kc * wz_pad + ywords + mwords + owords) elements
     int group_rows;
+    // CTA-wide rows: column tiles walked per row (npass >= 1), and Z in
+    // global memory ([grid][kc][wz_pad], this CTA's slot at blockIdx.x) when
+    // it does not fit shared memory (null: Z in shared memory)
+    int npass;
+    void *zglobal;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;

@@ -115,3 +115,42 @@ def test_deferred_ema_on_small_cases(sg, parent, wide, monkeypatch):
                     assert np.all(pv[0, b][~nz] == 0)
                     tol = 1e-12 if prec == "fp64" else 1e-4
                     assert (np.abs(pv[0, b][nz] - want[nz]) / want[nz]).max() <= tol
+
+
+PATH15 = tuple([-1] + list(range(14)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "u64", "u128"])
+def test_widest_rows_column_tiles(sg, prec, monkeypatch):
+    """A 15-vertex path, k = 15: its (9, 1, 8) node gathers compressed rows of
+    C(14, 7) = 3,432 columns, the widest any 15-vertex tree has.  FP32 keeps
+    Z in shared memory; FP64 and the integer tables walk the arcs once per
+    column tile of the CTA (2 and 4 tiles) with Z in global memory.  Split
+    rows too (chunks of 40 arcs)."""
+    import torch
+
+    g = si.erdos_renyi(150, 450, seed=1)
+    edges = {(int(u), int(v)) for u, v in g.edges} | {(0, v) for v in range(1, 120)}
+    g = si.from_edges(150, sorted(edges))
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(PATH15, 0, 15)
+    assert max(int(n[2]) for n in plan.nodes()) == 14
+    for chunk in ("1024", "40"):
+        monkeypatch.setenv("SG2V_CHUNK", chunk)
+        graph = sg.Graph(g.row_ptr, g.col_idx)
+        for b in range(2):
+            col = si.colouring(g.n, 15, 2, b)
+            ref = oracle.count(g.row_ptr, g.col_idx, PATH15, 0, col, 15)
+            pv, tot, _ = sg.count(graph, plan, torch.from_numpy(col).cuda(), prec)
+            pv = pv.cpu().numpy()
+            want = np.array([float(int(x)) for x in ref.per_vertex])
+            if prec == "fp32":
+                nz = want != 0
+                assert np.all(pv[~nz] == 0)
+                if nz.any():
+                    assert (np.abs(pv[nz] - want[nz]) / want[nz]).max() <= 1e-4
+                assert abs(tot - float(int(ref.total))) <= 1e-4 * float(int(ref.total))
+            else:
+                assert ref.max_bits <= 53
+                assert np.array_equal(pv, want)
+                assert tot == float(int(ref.total))

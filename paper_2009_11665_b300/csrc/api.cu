@@ -95,6 +95,7 @@ sg2v_status device_info(int dev, DeviceInfo *out) {
 // (t, a) for kc colours with Z rows of wz_pad elements (built once, kept).
 struct DeviceTables {
     const uint16_t *expand = nullptr;  // [kc][wy][pstride]
+    const uint32_t *expand32 = nullptr;  // [kc][wy][p] when offsets pass 16 bits (expand is then null)
     const uint32_t *splits = nullptr;
     const uint16_t *rootpair = nullptr;  // t = kc, a >= 2: rank(P') -> rank(A') of its one split
     int wy = 0, nsplit = 0, pstride = 1;
@@ -121,18 +122,28 @@ sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTable
     d.nsplit = tab.nsplit;
     const int p = t - a, ps = expand_stride(p);
     d.pstride = ps;
-    std::vector<uint16_t> packed((size_t)kc * tab.wy * ps, 0);
-    for (size_t set = 0; set < (size_t)kc * tab.wy; ++set)
-        for (int k = 0; k < p; ++k) packed[set * ps + k] = tab.expand[set * p + k];
     void *pe = nullptr, *ps_ = nullptr;
-    const size_t be = packed.size() * sizeof(uint16_t), bs = tab.splits.size() * sizeof(uint32_t);
-    SG2V_CUDA(cudaMalloc(&pe, std::max<size_t>(be, 16)), "table upload");
-    SG2V_CUDA(cudaMemcpy(pe, packed.data(), be, cudaMemcpyHostToDevice), "table upload");
+    const size_t bs = tab.splits.size() * sizeof(uint32_t);
+    if ((int64_t)kc * wz_pad > 65536) {
+        // Z offsets pass 16 bits: 32-bit offsets, one set after another
+        const size_t be = tab.expand.size() * sizeof(uint32_t);
+        SG2V_CUDA(cudaMalloc(&pe, std::max<size_t>(be, 16)), "table upload");
+        SG2V_CUDA(cudaMemcpy(pe, tab.expand.data(), be, cudaMemcpyHostToDevice), "table upload");
+        d.expand32 = static_cast<const uint32_t *>(pe);
+        d.pstride = p;
+    } else {
+        std::vector<uint16_t> packed((size_t)kc * tab.wy * ps, 0);
+        for (size_t set = 0; set < (size_t)kc * tab.wy; ++set)
+            for (int k = 0; k < p; ++k) packed[set * ps + k] = (uint16_t)tab.expand[set * p + k];
+        const size_t be = packed.size() * sizeof(uint16_t);
+        SG2V_CUDA(cudaMalloc(&pe, std::max<size_t>(be, 16)), "table upload");
+        SG2V_CUDA(cudaMemcpy(pe, packed.data(), be, cudaMemcpyHostToDevice), "table upload");
+        d.expand = static_cast<const uint16_t *>(pe);
+    }
     if (bs) {
         SG2V_CUDA(cudaMalloc(&ps_, bs), "table upload");
         SG2V_CUDA(cudaMemcpy(ps_, tab.splits.data(), bs, cudaMemcpyHostToDevice), "table upload");
     }
-    d.expand = static_cast<const uint16_t *>(pe);
     d.splits = static_cast<const uint32_t *>(ps_);
     if (t == kc && a >= 2 && tab.nsplit == tab.wy && (int)tab.splits.size() == tab.nsplit) {
         // one output set: every p-set appears in exactly one split
@@ -540,8 +551,8 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         // vectors only, warp-wide rows the whole tile of their lanes
         sh.wz_pad = hist ? 1
                          : (sh.grp != 32 ? (sh.wz + P->vecn - 1) / P->vecn * P->vecn : sh.grp * sh.nv * P->vecn);
-        if ((int64_t)kc * sh.wz_pad > 65536) {
-            set_error("per-colour accumulators wider than 16-bit expansion offsets (more than 65,536 elements)");
+        if ((int64_t)kc * sh.wz_pad > 65536 && sh.grp != kWideLanes) {
+            set_error("per-colour accumulators of more than 65,536 elements outside the CTA-wide kernel");
             return SG2V_ERR_UNSUPPORTED;
         }
         sh.ywords = ((int)binom(kc - 1, c.p) + 3) / 4 * 4;
@@ -792,6 +803,7 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     }
     A.Ws = (int)binom(kc - 1, c.t - 1);
     A.expand = P.tabs[i].expand;
+    A.expand32 = P.tabs[i].expand32;
     A.pstride = P.tabs[i].pstride;
     A.wy = P.tabs[i].wy;
     A.splits = P.tabs[i].splits;

@@ -1620,8 +1620,18 @@ __global__ void __launch_bounds__(kWideWarps * 32, 1) node_wide_kernel(const Nod
             // Y' = expansion of Z over the p-sets without v's colour
             if (cok) {
                 const int p = A.p, wy = A.wy;
-                const uint16_t *ex = A.expand + (int64_t)cv * wy * A.pstride;
-                for (int j = tid; j < wy; j += blockDim.x) ybuf[j] = expand_set(ex, A.pstride, p, j, zbuf, ovf);
+                if (A.expand32) {
+                    // 32-bit offsets (Z of more than 65,536 elements)
+                    const uint32_t *ex = A.expand32 + (int64_t)cv * wy * p;
+                    for (int j = tid; j < wy; j += blockDim.x) {
+                        T s = T(0);
+                        for (int k = 0; k < p; ++k) Ar<T>::add(s, zbuf[__ldg(ex + (int64_t)j * p + k)], ovf);
+                        ybuf[j] = s;
+                    }
+                } else {
+                    const uint16_t *ex = A.expand + (int64_t)cv * wy * A.pstride;
+                    for (int j = tid; j < wy; j += blockDim.x) ybuf[j] = expand_set(ex, A.pstride, p, j, zbuf, ovf);
+                }
             }
             if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncthreads();

@@ -46,6 +46,8 @@ struct NodeArgs {
     int p;
     int wy;                       // C(kc-1, p)
     const uint16_t *expand;       // [kc][wy][pstride] offsets into Z (the first p of each set)
+    const uint32_t *expand32;     // [kc][wy][p] 32-bit offsets instead (Z of more than 65,536
+                                  // elements: CTA-wide rows only), else null
     int pstride;                  // p, 4 when 2 <= p <= 4, 8 when 5 <= p <= 8 (8-byte loads)
     // shared memory per warp, in elements: Z copies, Y', the active row
     int zwords, ywords, mwords;

@@ -83,7 +83,7 @@ void build_compressed_tables(int kc, int t, int a, int wz_pad, CompressedTables 
             for (uint32_t rest = P; rest; rest &= rest - 1, ++k) {
                 const int d = __builtin_ctz(rest);
                 const uint32_t idx = p == 1 ? 0u : colex_rank(squeeze_colour(P ^ (1u << d), d));
-                out->expand[((size_t)c * wy + j) * p + k] = (uint16_t)(d * wz_pad + (int)idx);
+                out->expand[((size_t)c * wy + j) * p + k] = (uint32_t)d * (uint32_t)wz_pad + idx;
             }
         }
     }

@@ -42,7 +42,7 @@ struct CompressedTables {
     // the sum over k < p of Z[expand[(c * wy + j) * p + k]], where Z(d, i)
     // (offset d * wz_pad + i) accumulates the compressed rows of neighbours of
     // colour d; for p = 1, Z(d) is the colour histogram (wz_pad = 1).
-    std::vector<uint16_t> expand;
+    std::vector<uint32_t> expand;
     int wy = 0;
     // eMA splits in squeezed coordinates (a >= 2): for each (t-1)-set S',
     // nsplit pairs rank(A') | rank(S' - A') << 16 over the (a-1)-subsets A'

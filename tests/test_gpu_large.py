@@ -154,3 +154,35 @@ def test_widest_rows_column_tiles(sg, prec, monkeypatch):
                 assert ref.max_bits <= 53
                 assert np.array_equal(pv, want)
                 assert tot == float(int(ref.total))
+
+
+PATH16 = tuple([-1] + list(range(15)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "u128"])
+def test_sixteen_colours_widest_rows(sg, prec):
+    """A 16-vertex path, k = 16: its (9, 1, 8) node gathers rows of
+    C(15, 7) = 6,435 columns, so Z holds 16 x 6,436 elements (beyond 16-bit
+    expansion offsets and shared memory): two column tiles even in FP32,
+    32-bit offsets, Z in global memory."""
+    import torch
+
+    g = si.erdos_renyi(120, 360, seed=1)
+    edges = {(int(u), int(v)) for u, v in g.edges} | {(0, v) for v in range(1, 100)}
+    g = si.from_edges(120, sorted(edges))
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(PATH16, 0, 16)
+    col = si.colouring(g.n, 16, 2, 0)
+    ref = oracle.count(g.row_ptr, g.col_idx, PATH16, 0, col, 16)
+    pv, tot, _ = sg.count(graph, plan, torch.from_numpy(col).cuda(), prec)
+    pv = pv.cpu().numpy()
+    want = np.array([float(int(x)) for x in ref.per_vertex])
+    if prec == "fp32":
+        nz = want != 0
+        assert np.all(pv[~nz] == 0)
+        assert (np.abs(pv[nz] - want[nz]) / want[nz]).max() <= 1e-4
+        assert abs(tot - float(int(ref.total))) <= 1e-4 * float(int(ref.total))
+    else:
+        assert ref.max_bits <= 53
+        assert np.array_equal(pv, want)
+        assert tot == float(int(ref.total))

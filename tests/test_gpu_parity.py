@@ -338,3 +338,28 @@ def test_alternative_kernel_forms(sg, knob, monkeypatch):
             assert t == float(ref.total)
         else:
             assert abs(t - ref.total) <= FP64_RTOL * ref.total
+
+
+def test_split_rows_in_waves(sg, monkeypatch):
+    """Split rows (chunks of 64 arcs) with two colourings per wave: every
+    chunk adds its partial counts, for each colouring of the wave, into the
+    same table rows (the sort-written (2,1,1) table and the scratch rows of
+    the gathering nodes)."""
+    monkeypatch.setenv("SG2V_CHUNK", "64")
+    monkeypatch.setenv("SG2V_WAVE", "2")
+    g = _hub_graph(3)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    B = 3
+    cols = si.colourings(g.n, 7, B, seed=8)
+    plans = [sg.Plan(t.parent) for t in (si.TREE7, si.PATH7)]
+    for prec in ("fp64", "u64"):
+        pv, tot, _ = sg.count_batched(graph, plans, _dev(cols), prec, per_vertex=True)
+        pv, tot = pv.cpu().numpy(), tot.cpu().numpy()
+        for i, t in enumerate((si.TREE7, si.PATH7)):
+            for b in range(B):
+                ref = oracle.count(g.row_ptr, g.col_idx, t.parent, 0, cols[b])
+                if prec == "u64" or ref.max_bits <= 53:
+                    assert np.array_equal(pv[i, b], np.array([float(int(x)) for x in ref.per_vertex]))
+                    assert tot[i, b] == float(int(ref.total))
+                else:
+                    _check_fp64(pv[i, b], tot[i, b], ref, exact=False)

@@ -675,6 +675,8 @@ struct RunBuffers {
     int32_t *eref = nullptr;      // scaled: [n][wave] reference exponents
     void *defer_y = nullptr;      // Y' rows of a deferred-eMA node: [n][wave][defer_words]
     void *zglobal = nullptr;      // global Z of CTA-wide rows: [resident CTAs][kc][wz_pad]
+    int32_t *hcount = nullptr;    // neighbour counts per colour from the sort: [n][wave][hld]
+    int hld = 0;
     unsigned *status = nullptr;   // [4]: bit 0 colour out of range
     double *ones = nullptr;       // [nb][n] ones for single-vertex templates
     int chunks = 1;
@@ -730,6 +732,9 @@ int16_t *table_exps(const Prepared &P, const RunBuffers &R, int node, int wb) {
 size_t root_esz(const Prepared &P) { return P.scaled ? sizeof(double) : P.esz; }
 
 // Allocates the non-table buffers of a run from `alloc(bytes, &ptr)`.
+bool sort_counts_used(const Prepared &P);
+int sort_hist_node(const Prepared &P);
+
 template <typename Alloc>
 sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     const sg2v_graph *g = P.g;
@@ -749,6 +754,10 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R->eref))) return st;
     if (P.defer_words && (st = alloc((size_t)P.n * wave * P.defer_words * P.esz, &R->defer_y))) return st;
     if (P.zglobal_bytes && (st = alloc(P.zglobal_bytes, &R->zglobal))) return st;
+    if (sort_counts_used(P)) {
+        R->hld = (P.kc + 3) / 4 * 4;
+        if ((st = alloc((size_t)P.n * wave * R->hld * sizeof(int32_t), (void **)&R->hcount))) return st;
+    }
     R->rootbuf.assign(P.plans.size(), nullptr);
     for (size_t pi = 0; pi < P.plans.size(); ++pi)
         if (P.plan_root[pi] >= 0 && (st = alloc((size_t)P.nb * P.n * root_esz(P), &R->rootbuf[pi]))) return st;
@@ -835,6 +844,10 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     A.status = R.status;
     A.npass = sh.npass;
     A.zglobal = sh.zglobal ? R.zglobal : nullptr;
+    if (sh.rows && R.hcount) {
+        A.hcount = R.hcount;
+        A.hld = R.hld;
+    }
     return A;
 }
 
@@ -873,6 +886,18 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
 // non-root histogram node with two single-vertex children (t = 2) on an
 // unweighted graph with plain tables (-1: none; SG2V_SORT_HIST=0 turns the
 // fusion off).  Its children are leaves, so it is the first node to run.
+// Whether the colour sort also writes the per-colour neighbour counts of
+// every row for the histogram nodes that run 32 rows per warp (unweighted
+// graphs; SG2V_SORT_COUNTS=0 keeps their own counting).
+bool sort_counts_used(const Prepared &P) {
+    const char *env = std::getenv("SG2V_SORT_COUNTS");
+    if ((env && std::atoi(env) == 0) || P.g->weights) return false;
+    const int fused = sort_hist_node(P);
+    for (size_t i = 0; i < P.nodes.size(); ++i)
+        if (P.shape[i].rows && (int)i != fused) return true;
+    return false;
+}
+
 int sort_hist_node(const Prepared &P) {
     const char *env = std::getenv("SG2V_SORT_HIST");
     if ((env && std::atoi(env) == 0) || P.scaled || P.g->weights) return -1;
@@ -899,8 +924,16 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     for (int b0 = 0; b0 < nb; b0 += wave) {
         const int wb = std::min(wave, nb - b0);
         const int8_t *wcol = d_col + (int64_t)b0 * n;
-        SortHist hist{nullptr, 0, P.elem};
+        SortHist hist{nullptr, 0, P.elem, nullptr, 0};
         double hist_bytes = 0.0;
+        if (R.hcount) {
+            // neighbour counts per colour for the histogram nodes
+            if (g->nheavy)  // chunks of split rows add into zeroed rows
+                SG2V_CUDA(cudaMemsetAsync(R.hcount, 0, (size_t)n * wb * R.hld * sizeof(int32_t), stream), "memset");
+            hist.hcount = R.hcount;
+            hist.hld = R.hld;
+            hist_bytes += (double)n * wb * kc * sizeof(int32_t);
+        }
         if (fused >= 0) {
             // the (2, 1, 1) node's table comes from the sort's bucket counts
             const CNode &c = P.nodes[(size_t)fused];
@@ -910,8 +943,9 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             if (g->nheavy)  // chunks of split rows add into zeroed rows
                 SG2V_CUDA(cudaMemsetAsync(R.table[(size_t)fused], 0, (size_t)n * wb * R.ld[(size_t)fused] * esz, stream),
                           "memset");
-            hist = SortHist{R.table[(size_t)fused], R.ld[(size_t)fused], P.elem};
-            hist_bytes = (double)n * wb * (kc - 1) * esz;
+            hist.out = R.table[(size_t)fused];
+            hist.ld = R.ld[(size_t)fused];
+            hist_bytes += (double)n * wb * (kc - 1) * esz;
         }
         timer.begin("colour_sort",
                     (double)wb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))) + hist_bytes);
@@ -1063,7 +1097,7 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     };
     // wave-dependent: sorted arcs, split-row scratch, tables
     for (void *p : {(void *)S->R.scol, (void *)S->R.sclr_base, (void *)S->R.sw, S->R.scratch, (void *)S->R.counters,
-                    (void *)S->R.eref, S->R.defer_y}) {
+                    (void *)S->R.eref, S->R.defer_y, (void *)S->R.hcount}) {
         if (!p) continue;
         auto it = std::find(S->owned.begin(), S->owned.end(), p);
         if (it != S->owned.end()) {
@@ -1082,7 +1116,12 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     R.counters = nullptr;
     R.eref = nullptr;
     R.defer_y = nullptr;
+    R.hcount = nullptr;
     if ((st = alloc((size_t)wave * g->nnz * sizeof(int32_t), (void **)&R.scol))) return st;
+    if (sort_counts_used(P)) {
+        R.hld = (P.kc + 3) / 4 * 4;
+        if ((st = alloc((size_t)P.n * wave * R.hld * sizeof(int32_t), (void **)&R.hcount))) return st;
+    }
     if (P.scaled && (st = alloc((size_t)P.n * wave * sizeof(int32_t), (void **)&R.eref))) return st;
     if (P.defer_words && (st = alloc((size_t)P.n * wave * P.defer_words * P.esz, &R.defer_y))) return st;
     if ((st = alloc((size_t)wave * g->nnz + 32, (void **)&R.sclr_base))) return st;
@@ -1700,7 +1739,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     if ((st = alloc_run(Pw, 1, alloc, &R))) return st;
     SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
     SG2V_CUDA(launch_check_colours(d_col, n, kc, R.status, stream), "colour check");
-    const SortHist no_hist{nullptr, 0, Elem::F32};
+    const SortHist no_hist{nullptr, 0, Elem::F32, nullptr, 0};
     SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, nnz, d_col, 1, kc,
                                  R.scol, R.sclr, R.sw, no_hist, P.info.sms, stream),
               "colour sort");

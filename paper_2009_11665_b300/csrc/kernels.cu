@@ -1172,10 +1172,20 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
             // own colour and active-row exponent, for phase 2)
             const int cv_l = have ? (int)A.colours[(int64_t)b * A.n + task.x] : -1;
             const int ea_l = (SCALED && have && !A.a_leaf) ? (int)A.Ea[(int64_t)task.x * A.nb + b] : 0;
-            for (int d = 0; d < kc; ++d) cnt[d * kHistRows + lane] = T(0);
             const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
             const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
-            if (WEIGHTED) {
+            // counts written by the colour sort (the whole row's, also for
+            // split rows, whose first chunk then finishes the row alone)
+            const bool sorted_counts = !WEIGHTED && A.hcount != nullptr;
+            if (sorted_counts) {
+                const int32_t *hr = A.hcount + ((int64_t)task.x * A.nb + b) * A.hld;
+                for (int d = 0; d < kc; ++d) cnt[d * kHistRows + lane] = have ? T(__ldg(hr + d)) : T(0);
+            } else {
+                for (int d = 0; d < kc; ++d) cnt[d * kHistRows + lane] = T(0);
+            }
+            if (sorted_counts) {
+                // loaded above
+            } else if (WEIGHTED) {
                 // eight arcs per step: their loads issue together
                 for (int64_t e = task.z; e < task.w; e += 8) {
                     int c[8];
@@ -1208,7 +1218,9 @@ __global__ void __launch_bounds__(kNodeThreads, 4) hist_rows_kernel(const NodeAr
             }
             // split rows: fold the chunk's counts; the last chunk finishes the row
             bool finish = have;
-            if (have && task.y >= 0) {
+            if (sorted_counts) {
+                if (have && task.y >= 0) finish = (int64_t)task.z == __ldg(A.row_ptr + task.x);
+            } else if (have && task.y >= 0) {
                 T *sc = static_cast<T *>(A.scratch) + ((int64_t)task.y * A.nb + b) * A.scratch_ld;
                 for (int d = 0; d < kc; ++d) atomic_add(sc + d, cnt[d * kHistRows + lane], ovf);
                 __threadfence();
@@ -1971,10 +1983,20 @@ __device__ __forceinline__ void hist_put(const SortHist &H, int64_t row, int j, 
 template <typename F>
 __device__ __forceinline__ void hist_row(const SortHist &H, const int4 &task, int b, int nb, int cv, int kc, int j,
                                          F &&cnt) {
-    if (j >= kc - 1) return;
+    const int64_t row = (int64_t)task.x * nb + b;
+    if (H.hcount && j < kc) {
+        // the full count row (invalid colours of v included: the nodes check it)
+        int32_t *p = H.hcount + row * H.hld + j;
+        const int c = (int)cnt(j);
+        if (task.y < 0)
+            *p = c;
+        else if (c)
+            atomicAdd(p, c);
+    }
+    if (!H.out || j >= kc - 1) return;
     const bool ok = (unsigned)cv < (unsigned)kc;
     const int x = j < cv ? j : j + 1;
-    hist_put(H, (int64_t)task.x * nb + b, j, ok ? (unsigned)cnt(x) : 0u, task.y >= 0);
+    hist_put(H, row, j, ok ? (unsigned)cnt(x) : 0u, task.y >= 0);
 }
 
 // The same sort for tasks of at most G arcs, 32 / G tasks per warp: a lane's
@@ -2010,7 +2032,7 @@ __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t
                 sclr[pos] = (int8_t)(c == kc ? -1 : c);
                 if (sw) sw[pos] = __ldg(weights + task.z + gl);
             }
-            if (H.out) {
+            if (H.out || H.hcount) {
                 // lane gl counts colours gl and gl + G of its task's arcs
                 unsigned n0 = 0, n1 = 0;
 #pragma unroll
@@ -2028,7 +2050,20 @@ __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t
                     const int x = j < cv ? j : j + 1;
                     const unsigned c0 = __shfl_sync(kFull, n0, g0 + (x % G));
                     const unsigned c1 = __shfl_sync(kFull, n1, g0 + (x % G));
-                    if (have) hist_row(H, task, b, nb, cv, kc, j, [&](int) { return x < G ? c0 : c1; });
+                    if (have && H.out) {
+                        SortHist Ho = H;
+                        Ho.hcount = nullptr;
+                        hist_row(Ho, task, b, nb, cv, kc, j, [&](int) { return x < G ? c0 : c1; });
+                    }
+                    // the full count row: colour j is this lane's own count
+                    if (have && H.hcount && j < kc) {
+                        int32_t *p = H.hcount + ((int64_t)task.x * nb + b) * H.hld + j;
+                        const int cj = (int)(h == 0 ? n0 : n1);
+                        if (task.y < 0)
+                            *p = cj;
+                        else if (cj)
+                            atomicAdd(p, cj);
+                    }
                 }
             }
         }
@@ -2088,7 +2123,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 __syncwarp();
                 if (ok && (same & lt) == 0) start[c] = __popc(same);
                 __syncwarp();
-                if (H.out)
+                if (H.out || H.hcount)
                     hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
                 const int cnt = lane <= kc ? start[lane] : 0;
                 int incl = cnt;
@@ -2139,7 +2174,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                         __syncwarp();
                     }
                 }
-                if (H.out)
+                if (H.out || H.hcount)
                     hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
                 const int cnt = lane <= kc ? start[lane] : 0;
                 int incl = cnt;
@@ -2177,7 +2212,8 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 if (ok && (same & lt) == 0) start[c] += __popc(same);
                 __syncwarp();
             }
-            if (H.out) hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
+            if (H.out || H.hcount)
+                hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
             // exclusive prefix over buckets
             const int cnt = lane <= kc ? start[lane] : 0;
             int incl = cnt;

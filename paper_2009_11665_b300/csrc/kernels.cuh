@@ -49,6 +49,10 @@ struct NodeArgs {
     const uint32_t *expand32;     // [kc][wy][p] 32-bit offsets instead (Z of more than 65,536
                                   // elements: CTA-wide rows only), else null
     int pstride;                  // p, 4 when 2 <= p <= 4, 8 when 5 <= p <= 8 (8-byte loads)
+    // histogram nodes: neighbour counts per colour written by the colour sort
+    // ([n * nb][hld] int32, the full row's counts even for split rows), or null
+    const int32_t *hcount;
+    int hld;
     // shared memory per warp, in elements: Z copies, Y', the active row
     int zwords, ywords, mwords;
     // active side
@@ -250,6 +254,11 @@ struct SortHist {
     void *out;
     int64_t ld;                   // elements between rows
     Elem elem;
+    // per-row neighbour counts of every colour for the other histogram nodes:
+    // row v * nb + b holds hld int32 (entry c: neighbours of colour c, c < kc;
+    // split rows add atomically into a zeroed buffer); null: none
+    int32_t *hcount;
+    int hld;
 };
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,

@@ -317,7 +317,7 @@ def test_min_work_plans_match_oracle(sg, seed):
 
 
 @pytest.mark.parametrize("knob", ["SG2V_HIST_ROWS", "SG2V_GROUP_ROWS", "SG2V_HALF_ROOT", "SG2V_ROOT_PAIRS",
-                                  "SG2V_SORT_HIST"])
+                                  "SG2V_SORT_HIST", "SG2V_SORT_COUNTS"])
 def test_alternative_kernel_forms(sg, knob, monkeypatch):
     """The forms that the 32-row histogram kernel, the lane-group kernel, the
     half-arc root, the paired root sum and the sort-written (2, 1, 1) table

@@ -912,8 +912,9 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
 // arcs in batches of G, compacted to the arcs that add something; groups
 // step together (the warp runs to its longest row, shorter rows read the
 // zero row).  Shared memory per group: Z [kc][wz_pad], Y', the active row
-// and (scaled) the output row.
-template <typename T, int G, bool WEIGHTED, bool SCALED>
+// and (scaled) the output row.  FORM 1 (single-vertex active child, plain
+// output): the expansion writes M_s' = Y' straight to the output row.
+template <typename T, int G, bool WEIGHTED, bool SCALED, int FORM = 0>
 __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_group_kernel(const NodeArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = Vec16<T>;
@@ -1067,6 +1068,16 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
             }
             __syncwarp();
             const bool ok = fin && cok && e0 < e1;
+            if constexpr (FORM == 1 && !SCALED) {
+                if (fin) {
+                    T *out = static_cast<T *>(A.Ms) + rowb * A.ldt;
+                    const uint16_t *ex = A.expand + (int64_t)(ok ? cv : 0) * A.wy * A.pstride;
+                    for (int j = gl; j < A.wy; j += G)
+                        out[j] = ok ? expand_set(ex, A.pstride, A.p, j, zg, ovf) : T(0);
+                }
+                __syncwarp();
+                continue;
+            }
             if (ok) {
                 const uint16_t *ex = A.expand + (int64_t)cv * A.wy * A.pstride;
                 for (int j = gl; j < A.wy; j += G) ybuf[j] = expand_set(ex, A.pstride, A.p, j, zg, ovf);
@@ -1738,7 +1749,15 @@ void *pick_wide(int nv) {
 }
 
 template <typename T, bool W, bool SC>
-void *pick_group(int g) {
+void *pick_group(int g, int form = 0) {
+    if constexpr (!SC && !std::is_same<T, u128>::value) {
+        if (form == 1) {
+            if (g == 4) return reinterpret_cast<void *>(&node_group_kernel<T, 4, W, SC, 1>);
+            if (g == 8) return reinterpret_cast<void *>(&node_group_kernel<T, 8, W, SC, 1>);
+            if (g == 16) return reinterpret_cast<void *>(&node_group_kernel<T, 16, W, SC, 1>);
+            return nullptr;
+        }
+    }
     if (g == 4) return reinterpret_cast<void *>(&node_group_kernel<T, 4, W, SC>);
     if (g == 8) return reinterpret_cast<void *>(&node_group_kernel<T, 8, W, SC>);
     if (g == 16) return reinterpret_cast<void *>(&node_group_kernel<T, 16, W, SC>);
@@ -1750,10 +1769,11 @@ void *select_kernel(Elem e, bool hist, int g, int nv, bool weighted, bool group 
     if ((e == Elem::U64 || e == Elem::U128) && weighted) return nullptr;
     if (group) {
         if (hist || nv != 1) return nullptr;
-        if (e == Elem::U64) return pick_group<u64, false, false>(g);
+        if (e == Elem::U64) return pick_group<u64, false, false>(g, form);
         if (e == Elem::U128) return pick_group<u128, false, false>(g);
-        if (e == Elem::F64) return weighted ? pick_group<double, true, false>(g) : pick_group<double, false, false>(g);
-        return weighted ? pick_group<float, true, false>(g) : pick_group<float, false, false>(g);
+        if (e == Elem::F64)
+            return weighted ? pick_group<double, true, false>(g, form) : pick_group<double, false, false>(g, form);
+        return weighted ? pick_group<float, true, false>(g, form) : pick_group<float, false, false>(g, form);
     }
     if (g == kWideLanes) {
         // wide rows: one CTA per task (nv vectors per lane, 8 warps)
@@ -2557,6 +2577,8 @@ int node_blocks_per_sm_scaled(bool hist, int g, int nv, bool weighted, int threa
 
 // The specialised epilogue a node launch can use (node_kernel's FORM).
 int node_form(const NodeArgs &a, Elem e, int g, int nv) {
+    if (a.group_rows && !a.hist && e != Elem::U128)
+        return (a.a_leaf && !a.root && !a.defer && !a.Yout && !a.accumulate) ? 1 : 0;
     if (a.hist || a.group_rows || g != 32 || nv > 2 || e == Elem::U128) return 0;
     if (a.a_leaf && !a.root && !a.defer && !a.Yout && !a.accumulate) return 1;
     if (a.root && a.rootpair && !a.Yout && !a.defer && a.wy <= 128) return 2;

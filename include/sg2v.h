@@ -55,7 +55,7 @@ typedef enum {
     SG2V_ERR_FP_OVERFLOW = 6,      /* a count left the range of the table type (inf/NaN; 2^64 or 2^128 for integers) */
     SG2V_ERR_CUDA = 7,             /* a CUDA runtime call failed; see sg2v_last_error() */
     SG2V_ERR_TIMEOUT = 8,          /* a bounded device-side wait gave up */
-    SG2V_ERR_UNSUPPORTED = 9       /* a valid request this build cannot run (e.g. too many columns) */
+    SG2V_ERR_UNSUPPORTED = 9       /* a valid request this build cannot run (e.g. integer tables on a weighted graph) */
 } sg2v_status;
 
 typedef enum {
@@ -77,8 +77,7 @@ typedef enum {
                           * SG2V_ERR_FP_OVERFLOW.  Unweighted graphs and forward
                           * counts only (SG2V_ERR_UNSUPPORTED otherwise). */
     SG2V_U128 = 4        /* as SG2V_U64 with unsigned 128-bit counts (two 64-bit
-                          * words, 16 bytes per entry): exact to 2^128.  Rows of
-                          * more than 1,024 colour sets are SG2V_ERR_UNSUPPORTED. */
+                          * words, 16 bytes per entry): exact to 2^128. */
 } sg2v_precision;
 
 /* ------------------------------------------------------------------ graph */

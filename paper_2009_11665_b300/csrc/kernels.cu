@@ -2097,6 +2097,9 @@ __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t
 // registers; longer ones count buckets first, then place.
 constexpr int kSortStage = 1024;
 
+// HIST: some histogram output is requested (H.out or H.hcount); without it
+// the kernel carries none of that code.
+template <bool HIST>
 __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntasks, const int32_t *__restrict__ col_idx,
                                    const float *__restrict__ weights, int64_t n, int64_t nnz,
                                    const int8_t *__restrict__ colours, int nb, int kc, int32_t *scol, int8_t *sclr,
@@ -2143,7 +2146,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 __syncwarp();
                 if (ok && (same & lt) == 0) start[c] = __popc(same);
                 __syncwarp();
-                if (H.out || H.hcount)
+                if (HIST)
                     hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
                 const int cnt = lane <= kc ? start[lane] : 0;
                 int incl = cnt;
@@ -2194,7 +2197,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                         __syncwarp();
                     }
                 }
-                if (H.out || H.hcount)
+                if (HIST)
                     hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
                 const int cnt = lane <= kc ? start[lane] : 0;
                 int incl = cnt;
@@ -2232,7 +2235,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                 if (ok && (same & lt) == 0) start[c] += __popc(same);
                 __syncwarp();
             }
-            if (H.out || H.hcount)
+            if (HIST)
                 hist_row(H, task, b, nb, (int)__ldg(col + task.x), kc, lane, [&](int x) { return start[x]; });
             // exclusive prefix over buckets
             const int cnt = lane <= kc ? start[lane] : 0;
@@ -2721,11 +2724,17 @@ cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_
                                cudaStream_t stream) {
     if (small_begin > 0) {
         // one wave of resident blocks (the staging buffers limit residency)
-        static const int per_sm = std::max(1, blocks_per_sm(reinterpret_cast<void *>(&colour_sort_kernel), 256, 0));
+        const bool with_hist = hist.out || hist.hcount;
+        // (both variants use the same staging buffers: one residency figure)
+        static const int per_sm = std::max(1, blocks_per_sm(reinterpret_cast<void *>(&colour_sort_kernel<true>), 256, 0));
         int64_t blocks = (small_begin + 7) / 8;
         if (blocks > (int64_t)sms * per_sm) blocks = (int64_t)sms * per_sm;
-        colour_sort_kernel<<<(unsigned)blocks, 256, 0, stream>>>(tasks, small_begin, col_idx, weights, n, nnz, colours,
-                                                                 nb, kc, scol, sclr, sw, hist);
+        if (with_hist)
+            colour_sort_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(tasks, small_begin, col_idx, weights, n, nnz,
+                                                                           colours, nb, kc, scol, sclr, sw, hist);
+        else
+            colour_sort_kernel<false><<<(unsigned)blocks, 256, 0, stream>>>(tasks, small_begin, col_idx, weights, n, nnz,
+                                                                            colours, nb, kc, scol, sclr, sw, hist);
     }
     const int64_t rest = ntasks - small_begin;
     if (rest > 0) {

@@ -164,6 +164,53 @@ sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTable
     return SG2V_OK;
 }
 
+// Run map of node (t, a, p) for the run-scatter kernel: for the row's colour
+// cv, a neighbour colour d and entry e of the neighbour's compressed row
+// (the e-th (p-1)-subset Q' of d's squeezed universe, i.e. the p-set
+// S = unsqueeze(Q', d) + {d}), the destination of that entry:
+//   form 0 / 1: the colex rank of S in cv's squeezed p-sets (Y'),
+//   form 2 (t = kc): the rank of the active set S' - S that completes S,
+// or `sink` when S holds cv (and for d = cv, e >= C(kc-1, p-1)).
+// [kc][kc][wmap] 16-bit entries, cached per device.
+std::map<std::tuple<int, int, int, int, int, int, int>, const uint16_t *> g_runmaps;
+
+sg2v_status run_map(int dev, int kc, int t, int a, int form, int wmap, int sink, const uint16_t **out) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    const auto key = std::make_tuple(dev, kc, t, a, form, wmap, sink);
+    auto it = g_runmaps.find(key);
+    if (it != g_runmaps.end()) {
+        *out = it->second;
+        return SG2V_OK;
+    }
+    const int p = t - a;
+    const int wz = (int)binom(kc - 1, p - 1);
+    const uint32_t full = (1u << (kc - 1)) - 1u;  // every colour of a squeezed universe
+    std::vector<uint16_t> m((size_t)kc * kc * wmap, (uint16_t)sink);
+    for (int d = 0; d < kc; ++d) {
+        // the gathered row's sets in colex order: (p-1)-subsets by increasing mask
+        std::vector<uint32_t> sets;
+        sets.reserve((size_t)wz);
+        for (uint32_t q = 0; q <= full; ++q)
+            if (__builtin_popcount(q) == p - 1) sets.push_back(unsqueeze_colour(q, d) | (1u << d));
+        for (int cv = 0; cv < kc; ++cv) {
+            if (cv == d) continue;
+            uint16_t *row = m.data() + ((size_t)cv * kc + d) * wmap;
+            for (int e = 0; e < wz && e < wmap; ++e) {
+                const uint32_t S = sets[(size_t)e];
+                if (S >> cv & 1u) continue;
+                const uint32_t Sq = squeeze_colour(S, cv);
+                row[e] = (uint16_t)(form == 2 ? colex_rank(full ^ Sq) : colex_rank(Sq));
+            }
+        }
+    }
+    void *dptr = nullptr;
+    SG2V_CUDA(cudaMalloc(&dptr, m.size() * sizeof(uint16_t)), "table upload");
+    SG2V_CUDA(cudaMemcpy(dptr, m.data(), m.size() * sizeof(uint16_t), cudaMemcpyHostToDevice), "table upload");
+    g_runmaps[key] = static_cast<const uint16_t *>(dptr);
+    *out = static_cast<const uint16_t *>(dptr);
+    return SG2V_OK;
+}
+
 // ---- kernel timing records (measurement support)
 struct ProfRecord {
     int64_t launches = 0;
@@ -419,6 +466,10 @@ struct Shape {
     int wthreads = 0, wbps = 0;  // the one-warp-per-row launch of the longer tasks of a group node
     size_t wsmem = 0;
     bool defer = false; // eMA in its own launch over blocks of rows (ema_rows_kernel)
+    bool run = false;   // run-scatter kernel (warp-wide rows, plain FP32 / FP64 tables)
+    const uint16_t *runmap_y = nullptr;  // its run map into Y' (forms 0 and 1)
+    const uint16_t *runmap_m = nullptr;  // into the active row (form 2: root with t = kc)
+    int wmap = 0, mzero = 0;
     int64_t ldy = 0;    // Y' row stride of a deferred node
 };
 
@@ -633,6 +684,36 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             return SG2V_ERR_UNSUPPORTED;
         }
         if ((st = device_tables(P->dev, kc, c.t, c.a, sh.wz_pad, &P->tabs[i]))) return st;
+        // warp-wide gathering rows of plain FP32 / FP64 tables: the run-scatter
+        // kernel (SG2V_RUN_KERNEL=0 keeps the per-colour accumulators of node_kernel)
+        const char *run_env = std::getenv("SG2V_RUN_KERNEL");
+        if (!(run_env && std::atoi(run_env) == 0) && !hist && sh.grp == 32 && !sh.group && !sh.rows &&
+            (sh.nv == 1 || sh.nv == 2) && !P->scaled && (P->elem == Elem::F32 || P->elem == Elem::F64)) {
+            const int E = P->vecn;
+            const int wy = (int)binom(kc - 1, c.p);
+            const int wa = c.a == 1 ? 1 : (int)binom(kc - 1, c.a - 1);
+            const int ybase = (wy + E - 1) / E * E, mbase = (wa + E - 1) / E * E;
+            const int ywords = ybase + E;
+            const int mwords = (c.a >= 2 || c.is_root) ? mbase + E : 0;
+            const int threads = kNodeThreads;
+            const size_t smem = (size_t)(threads / 32) * ((size_t)(ywords + mwords) * P->esz + kRunCompactBytes);
+            const int form = (c.is_root && c.t == kc) ? 2 : ((c.a == 1 && !c.is_root) ? 1 : 0);
+            const int bps = node_run_blocks_per_sm(P->elem, sh.nv, g->weights != nullptr, form, threads, smem);
+            if (bps >= 1) {
+                sh.run = true;
+                sh.wmap = 32 * sh.nv * E;
+                sh.mzero = mbase;
+                if ((st = run_map(P->dev, kc, c.t, c.a, 0, sh.wmap, ybase, &sh.runmap_y))) return st;
+                if (form == 2 && (st = run_map(P->dev, kc, c.t, c.a, 2, sh.wmap, mbase, &sh.runmap_m))) return st;
+                sh.zwords = 0;
+                sh.ywords = ywords;
+                sh.mwords = mwords;
+                sh.owords = 0;
+                sh.threads = threads;
+                sh.smem = smem;
+                sh.blocks_per_sm = bps;
+            }
+        }
         // large eMA (many sets times many splits per row, root excepted): its own launch over
         // blocks of rows, so each split-table word serves several rows
         const char *defer_env = std::getenv("SG2V_DEFER_EMA");  // 0: never; else the least products per row
@@ -831,6 +912,11 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
             A.root_out = rb;
     }
     A.group_rows = sh.group;
+    {
+        // FP32 gathers load only lanes inside the row (SG2V_PRED_LANES=0: every lane)
+        const char *pl = std::getenv("SG2V_PRED_LANES");
+        A.pred_lanes = (pl && std::atoi(pl) == 0) ? 0 : 1;
+    }
     if (P.scaled) {
         A.scaled = 1;
         A.owords = sh.owords;
@@ -873,6 +959,19 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
         S.ntasks = A.ntasks - split;
         return P.scaled ? launch_node_scaled(S, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
                         : launch_node(S, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
+    }
+    if (sh.run) {
+        const CNode &c = P.nodes[i];
+        NodeArgs R = A;
+        int form = 0;
+        if (A.root && c.t == P.kc && !A.Yout && !A.defer && sh.runmap_m)
+            form = 2;
+        else if (A.a_leaf && !A.root && !A.defer && !A.Yout && !A.accumulate)
+            form = 1;
+        R.runmap = form == 2 ? sh.runmap_m : sh.runmap_y;
+        R.wmap = sh.wmap;
+        R.mzero = sh.mzero;
+        return launch_node_run(R, P.elem, sh.nv, form, sh.threads, sh.smem, grid_cap, stream);
     }
     if (P.scaled) return launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     return launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);

@@ -104,6 +104,17 @@ struct NodeArgs {
     // it does not fit shared memory (null: Z in shared memory)
     int npass;
     void *zglobal;
+    // FP32 gathers: lanes past the row's last 16-byte vector load nothing
+    // (else they read the next row into Z columns nothing reads)
+    int pred_lanes;
+    // run-scatter kernel: for the row's colour cv and a neighbour colour d,
+    // runmap[(cv * kc + d) * wmap + e] is where entry e of a gathered row
+    // goes: a Y' index (a sink index past Y' when the entry's set holds cv)
+    // or, at a root with one output set, the index of the active-row entry it
+    // pairs with (mzero, a zero, when the set holds cv)
+    const uint16_t *runmap;
+    int wmap;
+    int mzero;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
@@ -204,6 +215,15 @@ constexpr int kWideThreads = 256;
 // shared-memory limit when needed.
 int node_blocks_per_sm(Elem e, bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
                        size_t smem, bool group_rows = false);
+
+// Run-scatter node kernel (plain FP32 / FP64 tables, warp-wide rows of up
+// to 32 * nv vectors, nv <= 2): form 0 generic eMA epilogue, 1 single-vertex
+// active child (M_s' = Y'), 2 root with one output set (row sum of pairs).
+// Shared memory per warp: (ywords + mwords) elements plus kRunCompactBytes.
+constexpr int kRunCompactBytes = 384;
+int node_run_blocks_per_sm(Elem e, int nv, bool weighted, int form, int threads, size_t smem);
+cudaError_t launch_node_run(const NodeArgs &args, Elem e, int nv, int form, int threads, size_t smem, int grid_cap,
+                            cudaStream_t stream);
 
 // Launches the fused SpMM/histogram + eMA kernel of one node.
 cudaError_t launch_node(const NodeArgs &args, Elem e, int lanes_per_group, int vec_per_lane, int threads,

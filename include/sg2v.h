@@ -83,6 +83,7 @@ typedef enum {
 /* ------------------------------------------------------------------ graph */
 
 #define SG2V_GRAPH_SKIP_VALIDATION 0x1u /* trust the CSR (no simplicity/symmetry check) */
+#define SG2V_GRAPH_KEEP_ORDER 0x2u      /* keep the caller's vertex order on the device */
 
 /*
  * sg2v_graph_create -- the input network as a sparse adjacency matrix A_G in
@@ -96,15 +97,20 @@ typedef enum {
  *            weighted form uses A_G.val of Alg. 4 (each embedding then
  *            contributes the product of its edge weights); weights[e] must
  *            equal the weight of the reverse arc and be finite and >= 0
- *   flags    0 or SG2V_GRAPH_SKIP_VALIDATION
+ *   flags    0 or a combination of SG2V_GRAPH_SKIP_VALIDATION and
+ *            SG2V_GRAPH_KEEP_ORDER
  *   out      receives the handle
  *
  * The graph must be simple and undirected: the CSR must be symmetric, with no
  * self-loops and no repeated arcs (Sec. 2.2.1: simple graph); violations give
  * SG2V_ERR_GRAPH_NOT_SIMPLE unless validation is skipped.  The library copies
  * the arrays onto the current device (the caller may free its copies) and
- * derives its load-balanced work list there.  Errors: INVALID_ARGUMENT,
- * GRAPH_NOT_SIMPLE, OUT_OF_MEMORY, CUDA.
+ * derives its load-balanced work list there.  Unless SG2V_GRAPH_KEEP_ORDER is
+ * given, the device copy numbers the vertices by decreasing degree (the rows
+ * most arcs gather share cache lines); this is invisible to the caller:
+ * colourings, per-vertex counts, per-vertex gradient seeds, weights and
+ * per-arc gradients are always in the caller's vertex and arc order.
+ * Errors: INVALID_ARGUMENT, GRAPH_NOT_SIMPLE, OUT_OF_MEMORY, CUDA.
  */
 sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col_idx,
                               const float *weights, uint32_t flags, sg2v_graph **out);

@@ -37,6 +37,7 @@ SG2V_FP32_SCALED = 2
 SG2V_U64 = 3
 SG2V_U128 = 4
 SG2V_GRAPH_SKIP_VALIDATION = 0x1
+SG2V_GRAPH_KEEP_ORDER = 0x2
 SG2V_CUT_LAST = 0
 SG2V_CUT_MIN_WORK = 1
 SG2V_SESSION_PER_VERTEX = 0x1
@@ -307,7 +308,7 @@ def sg2v_launch_count() -> int:
 class Graph:
     """Owns a library graph handle (CSR copied onto the current device)."""
 
-    def __init__(self, row_ptr, col_idx, weights=None, validate: bool = True):
+    def __init__(self, row_ptr, col_idx, weights=None, validate: bool = True, keep_order: bool = False):
         rp = row_ptr if hasattr(row_ptr, "data_ptr") else np.ascontiguousarray(row_ptr, dtype=np.int64)
         ci = col_idx if hasattr(col_idx, "data_ptr") else np.ascontiguousarray(col_idx, dtype=np.int32)
         w = None
@@ -315,7 +316,8 @@ class Graph:
             w = weights if hasattr(weights, "data_ptr") else np.ascontiguousarray(weights, dtype=np.float32)
         self.n = int(rp.shape[0]) - 1
         self.nnz = int(ci.shape[0])
-        self.handle = sg2v_graph_create(self.n, self.nnz, rp, ci, w, 0 if validate else SG2V_GRAPH_SKIP_VALIDATION)
+        flags = (0 if validate else SG2V_GRAPH_SKIP_VALIDATION) | (SG2V_GRAPH_KEEP_ORDER if keep_order else 0)
+        self.handle = sg2v_graph_create(self.n, self.nnz, rp, ci, w, flags)
 
     def info(self):
         return sg2v_graph_info(self.handle)

@@ -332,6 +332,11 @@ struct sg2v_graph {
     int64_t short_begin = 0;  // first task of at most kShortTaskArcs arcs (the rest, sorted by work, are too)
     int64_t small_begin = 0;  // first task of at most kSortSmallArcs arcs
     int32_t *rev = nullptr;  // reverse arc of every arc, built on the first backward call
+    // vertices relabelled by decreasing degree (unless SG2V_GRAPH_KEEP_ORDER):
+    // the device CSR is in the new order; iperm[new] = the caller's vertex,
+    // arcmap[new arc] = the caller's arc (null when the caller's order is kept)
+    int32_t *iperm = nullptr;
+    int32_t *arcmap = nullptr;
 };
 
 namespace sg2v {
@@ -345,6 +350,8 @@ void free_graph(sg2v_graph *g) {
     cudaFree(g->tasks);
     cudaFree(g->heavy_chunks);
     cudaFree(g->rev);
+    cudaFree(g->iperm);
+    cudaFree(g->arcmap);
     delete g;
 }
 
@@ -445,6 +452,53 @@ void build_tasks(int64_t n, const std::vector<int64_t> &rp, int chunk, std::vect
         }
     }
     tasks->insert(tasks->end(), light.begin(), light.end());
+}
+
+// Relabels the vertices by decreasing degree (ties keep the caller's order):
+// the rows of the hubs, which most arcs gather, share cache lines and sit
+// together in L2, and the work list (by decreasing work) walks the tables in
+// address order.  Rows keep increasing column order.  iperm[new] = old;
+// arcmap[new arc] = old arc; the weights follow their arcs.
+void relabel_by_degree(int64_t n, std::vector<int64_t> &rp, std::vector<int32_t> &ci, std::vector<float> *w,
+                       std::vector<int32_t> *iperm, std::vector<int32_t> *arcmap) {
+    const int64_t nnz = rp[(size_t)n];
+    iperm->resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) (*iperm)[(size_t)i] = (int32_t)i;
+    std::stable_sort(iperm->begin(), iperm->end(),
+                     [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+    std::vector<int32_t> newid((size_t)n);
+    for (int64_t i = 0; i < n; ++i) newid[(size_t)(*iperm)[(size_t)i]] = (int32_t)i;
+    std::vector<int64_t> rp2((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t o = (*iperm)[(size_t)i];
+        rp2[(size_t)i + 1] = rp2[(size_t)i] + (rp[o + 1] - rp[o]);
+    }
+    std::vector<int32_t> ci2((size_t)nnz);
+    arcmap->resize((size_t)nnz);
+#pragma omp parallel
+    {
+        std::vector<std::pair<int32_t, int32_t>> row;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t o = (*iperm)[(size_t)i];
+            row.clear();
+            for (int64_t e = rp[o]; e < rp[o + 1]; ++e) row.emplace_back(newid[(size_t)ci[(size_t)e]], (int32_t)e);
+            std::sort(row.begin(), row.end());
+            int64_t k = rp2[(size_t)i];
+            for (const auto &x : row) {
+                ci2[(size_t)k] = x.first;
+                (*arcmap)[(size_t)k] = x.second;
+                ++k;
+            }
+        }
+    }
+    if (w) {
+        std::vector<float> w2((size_t)nnz);
+        for (int64_t e = 0; e < nnz; ++e) w2[(size_t)e] = (*w)[(size_t)(*arcmap)[(size_t)e]];
+        w->swap(w2);
+    }
+    rp.swap(rp2);
+    ci.swap(ci2);
 }
 
 struct CNode {
@@ -759,6 +813,7 @@ struct RunBuffers {
     int32_t *hcount = nullptr;    // neighbour counts per colour from the sort: [n][wave][hld]
     int hld = 0;
     unsigned *status = nullptr;   // [4]: bit 0 colour out of range
+    int8_t *colp = nullptr;       // colourings in the graph's vertex order (relabelled graphs)
     double *ones = nullptr;       // [nb][n] ones for single-vertex templates
     int chunks = 1;
     RootSum *partials = nullptr;  // [plans][nb][chunks]
@@ -845,6 +900,7 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     R->table.assign(P.nodes.size(), nullptr);
     R->ld.assign(P.nodes.size(), 0);
     if ((st = alloc(16, (void **)&R->status))) return st;
+    if (g->iperm && (st = alloc((size_t)P.nb * P.n, (void **)&R->colp))) return st;
     R->chunks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (P.n + 65535) / 65536 * 4));
     const size_t segs = P.plans.size() * (size_t)P.nb;
     if ((st = alloc(sizeof(RootSum) * segs * R->chunks, (void **)&R->partials))) return st;
@@ -1015,6 +1071,12 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     const size_t esz = P.esz;
     sg2v_status st;
     SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
+    if (g->iperm) {
+        // the caller's colourings into the graph's vertex order
+        timer.count_extra(1);
+        SG2V_CUDA(launch_gather_i8(d_col, R.colp, g->iperm, n, nb, stream), "colour permutation");
+        d_col = R.colp;
+    }
     timer.count_extra(1);
     SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, R.status, stream), "colour check");
     const char *half_env = std::getenv("SG2V_HALF_ROOT");
@@ -1132,7 +1194,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
         const Elem ve = P.plan_root[pi] >= 0 ? (P.scaled ? Elem::F64 : P.elem) : Elem::F64;
         timer.begin("root_reduce", (double)nb * n * ((ve == Elem::F32 ? 4 : (ve == Elem::U128 ? 16 : 8)) + (pvp ? 8 : 0)));
         timer.count_extra(1);
-        SG2V_CUDA(launch_root_reduce(vals, ve, n, nb, pvp, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
+        SG2V_CUDA(launch_root_reduce(vals, ve, n, nb, pvp, g->iperm, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
                                      R.sums + pi * (size_t)nb, stream),
                   "root reduction");
         timer.end();
@@ -1306,7 +1368,7 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
     }
     *out = nullptr;
     if (n < 1 || n >= (int64_t(1) << 31) || nnz < 0 || nnz >= (int64_t(1) << 31) || !row_ptr ||
-        (nnz > 0 && !col_idx) || (flags & ~SG2V_GRAPH_SKIP_VALIDATION)) {
+        (nnz > 0 && !col_idx) || (flags & ~(SG2V_GRAPH_SKIP_VALIDATION | SG2V_GRAPH_KEEP_ORDER))) {
         set_error("invalid graph size, pointer or flag");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
@@ -1319,6 +1381,9 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
     if (weights && (st = host_copy(weights, nnz, &w))) return st;
     st = validate_csr(n, nnz, rp, ci, weights ? &w : nullptr, !(flags & SG2V_GRAPH_SKIP_VALIDATION));
     if (st) return st;
+    std::vector<int32_t> iperm, arcmap;
+    const bool relabel = !(flags & SG2V_GRAPH_KEEP_ORDER);
+    if (relabel) relabel_by_degree(n, rp, ci, weights ? &w : nullptr, &iperm, &arcmap);
 
     int dev = 0;
     SG2V_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -1362,6 +1427,10 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
     if (weights) up((void **)&g->weights, w.data(), w.size() * sizeof(float));
     up((void **)&g->tasks, tasks.data(), tasks.size() * sizeof(int4));
     up((void **)&g->heavy_chunks, hc.data(), hc.size() * sizeof(int32_t));
+    if (relabel) {
+        up((void **)&g->iperm, iperm.data(), iperm.size() * sizeof(int32_t));
+        up((void **)&g->arcmap, arcmap.data(), arcmap.size() * sizeof(int32_t));
+    }
     if (e != cudaSuccess) {
         free_graph(g);
         return cuda_fail(e, "graph upload");
@@ -1704,8 +1773,19 @@ sg2v_status sg2v_graph_set_weights(sg2v_graph *g, const float *weights, sg2v_str
         return SG2V_ERR_INVALID_ARGUMENT;
     }
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    SG2V_CUDA(cudaMemcpyAsync(g->weights, weights, (size_t)g->nnz * sizeof(float), cudaMemcpyDefault, stream),
-              "weight copy");
+    if (!g->arcmap) {
+        SG2V_CUDA(cudaMemcpyAsync(g->weights, weights, (size_t)g->nnz * sizeof(float), cudaMemcpyDefault, stream),
+                  "weight copy");
+        return SG2V_OK;
+    }
+    // the caller's arc order: staged, then gathered into the graph's order
+    void *tmp = nullptr;
+    SG2V_CUDA(cudaMallocAsync(&tmp, std::max<size_t>((size_t)g->nnz * sizeof(float), 16), stream), "allocation");
+    cudaError_t e = cudaMemcpyAsync(tmp, weights, (size_t)g->nnz * sizeof(float), cudaMemcpyDefault, stream);
+    if (e == cudaSuccess)
+        e = launch_gather_f32(static_cast<const float *>(tmp), g->weights, g->arcmap, g->nnz, stream);
+    cudaFreeAsync(tmp, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "weight copy");
     return SG2V_OK;
 }
 
@@ -1761,6 +1841,13 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         void *p;
         if ((st = ws.alloc(&p, (size_t)n))) return st;
         SG2V_CUDA(cudaMemcpyAsync(p, colours, (size_t)n, cudaMemcpyHostToDevice, stream), "colour upload");
+        d_col = static_cast<const int8_t *>(p);
+    }
+    if (g->iperm) {
+        // the caller's colouring into the graph's vertex order
+        void *p;
+        if ((st = ws.alloc(&p, (size_t)n))) return st;
+        SG2V_CUDA(launch_gather_i8(d_col, static_cast<int8_t *>(p), g->iperm, n, 1, stream), "colour permutation");
         d_col = static_cast<const int8_t *>(p);
     }
     double *gradw;
@@ -1872,7 +1959,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     }
     if (total) {
         timer.count_extra(2);
-        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.elem, n, 1, nullptr, R.partials, R.chunks, R.sums, stream),
+        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.elem, n, 1, nullptr, nullptr, R.partials, R.chunks, R.sums, stream),
                   "root reduction");
     }
     // seed: gradient of the per-vertex counts
@@ -1881,6 +1968,13 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     if (grad_per_vertex) {
         SG2V_CUDA(cudaMemcpyAsync(seed, grad_per_vertex, (size_t)n * sizeof(double), cudaMemcpyDefault, stream),
                   "seed copy");
+        if (g->iperm) {
+            // into the graph's vertex order
+            double *seed2;
+            if ((st = alloc((size_t)n * sizeof(double), (void **)&seed2))) return st;
+            SG2V_CUDA(launch_gather_f64(seed, seed2, g->iperm, n, stream), "seed permutation");
+            seed = seed2;
+        }
     } else {
         std::vector<double> ones((size_t)n, 1.0);
         SG2V_CUDA(cudaMemcpyAsync(seed, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, stream),
@@ -2004,7 +2098,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         ws.release(ybar);
     }
     timer.count_extra(1);
-    SG2V_CUDA(launch_symmetrize(part, g->rev, nnz, gradw, stream), "symmetrize");
+    SG2V_CUDA(launch_symmetrize(part, g->rev, g->arcmap, nnz, gradw, stream), "symmetrize");
     SG2V_CUDA(cudaMemcpyAsync(grad_weights, gradw, (size_t)nnz * sizeof(double), cudaMemcpyDefault, stream),
               "gradient copy");
     RootSum sum;

@@ -2172,7 +2172,8 @@ __device__ __forceinline__ RootSum rs_from(double v) {
 }
 
 template <typename T>
-__global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, RootSum *partials, int chunks) {
+__global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, const int32_t *pvmap, RootSum *partials,
+                                    int chunks) {
     __shared__ RootSum red[32];
     const int seg = blockIdx.y;
     const int chunk = blockIdx.x;
@@ -2187,7 +2188,7 @@ __global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, RootSu
         unsigned bad = 0;
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const T x = vals[(int64_t)seg * n + i];
-            if (pv) pv[(int64_t)seg * n + i] = (double)x;
+            if (pv) pv[(int64_t)seg * n + (pvmap ? (int64_t)pvmap[i] : i)] = (double)x;
             if (isfinite(x))
                 sum += (double)x;
             else
@@ -2208,13 +2209,13 @@ __global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, RootSu
                 r.lo = x;
                 r.s = __ull2double_rn(x);
             }
-            if (pv) pv[(int64_t)seg * n + i] = r.s;
+            if (pv) pv[(int64_t)seg * n + (pvmap ? (int64_t)pvmap[i] : i)] = r.s;
             rs_combine(acc, r);
         }
     } else {
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const double v = (double)vals[(int64_t)seg * n + i];
-            if (pv) pv[(int64_t)seg * n + i] = v;
+            if (pv) pv[(int64_t)seg * n + (pvmap ? (int64_t)pvmap[i] : i)] = v;
             rs_combine(acc, rs_from(v));
         }
     }
@@ -2763,9 +2764,21 @@ __global__ void __launch_bounds__(256) sddmm_rows_kernel(const SddmmArgs A) {
     }
 }
 
-__global__ void symmetrize_kernel(const double *part, const int32_t *rev, int64_t nnz, double *grad_w) {
+__global__ void symmetrize_kernel(const double *part, const int32_t *rev, const int32_t *arcmap, int64_t nnz,
+                                  double *grad_w) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-        grad_w[e] = part[e] + part[rev[e]];
+        grad_w[arcmap ? (int64_t)arcmap[e] : e] = part[e] + part[rev[e]];
+}
+
+// dst[b * n + i] = src[b * n + idx[i]] for nb rows of n elements
+template <typename T>
+__global__ void gather_rows_kernel(const T *src, T *dst, const int32_t *idx, int64_t n, int nb) {
+    const int64_t total = n * nb;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = k / n, i = k - b * n;
+        dst[k] = src[b * n + idx[i]];
+    }
 }
 
 // 128-bit unsigned integer to the nearest double (ties to even): the top 64
@@ -3037,20 +3050,21 @@ cudaError_t launch_ema_rows(const NodeArgs &args, Elem e, bool scaled, int sms, 
                             params, smem, stream);
 }
 
-cudaError_t launch_root_reduce(const void *vals, Elem ve, int64_t n, int nseg, double *pv, RootSum *partials,
-                               int chunks, RootSum *out, cudaStream_t stream) {
+cudaError_t launch_root_reduce(const void *vals, Elem ve, int64_t n, int nseg, double *pv, const int32_t *pvmap,
+                               RootSum *partials, int chunks, RootSum *out, cudaStream_t stream) {
     dim3 grid((unsigned)chunks, (unsigned)nseg);
     if (ve == Elem::U64)
-        root_partial_kernel<u64><<<grid, 256, 0, stream>>>(static_cast<const u64 *>(vals), n, pv, partials, chunks);
+        root_partial_kernel<u64><<<grid, 256, 0, stream>>>(static_cast<const u64 *>(vals), n, pv, pvmap, partials,
+                                                             chunks);
     else if (ve == Elem::U128)
-        root_partial_kernel<u128><<<grid, 256, 0, stream>>>(static_cast<const u128 *>(vals), n, pv, partials,
+        root_partial_kernel<u128><<<grid, 256, 0, stream>>>(static_cast<const u128 *>(vals), n, pv, pvmap, partials,
                                                               chunks);
     else if (ve == Elem::F64)
-        root_partial_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double *>(vals), n, pv, partials,
-                                                                chunks);
+        root_partial_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double *>(vals), n, pv, pvmap,
+                                                                partials, chunks);
     else
-        root_partial_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float *>(vals), n, pv, partials,
-                                                               chunks);
+        root_partial_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float *>(vals), n, pv, pvmap,
+                                                               partials, chunks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     root_final_kernel<<<(nseg + 127) / 128, 128, 0, stream>>>(partials, chunks, nseg, out);
@@ -3166,11 +3180,31 @@ cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_symmetrize(const double *part, const int32_t *rev, int64_t nnz, double *grad_w,
-                              cudaStream_t stream) {
+template <typename T>
+cudaError_t gather_rows(const T *src, T *dst, const int32_t *idx, int64_t n, int nb, cudaStream_t stream) {
+    if (n == 0 || nb == 0) return cudaSuccess;
+    int64_t blocks = (n * nb + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    gather_rows_kernel<T><<<(unsigned)blocks, 256, 0, stream>>>(src, dst, idx, n, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_i8(const int8_t *src, int8_t *dst, const int32_t *idx, int64_t n, int nb,
+                             cudaStream_t stream) {
+    return gather_rows<int8_t>(src, dst, idx, n, nb, stream);
+}
+cudaError_t launch_gather_f32(const float *src, float *dst, const int32_t *idx, int64_t n, cudaStream_t stream) {
+    return gather_rows<float>(src, dst, idx, n, 1, stream);
+}
+cudaError_t launch_gather_f64(const double *src, double *dst, const int32_t *idx, int64_t n, cudaStream_t stream) {
+    return gather_rows<double>(src, dst, idx, n, 1, stream);
+}
+
+cudaError_t launch_symmetrize(const double *part, const int32_t *rev, const int32_t *arcmap, int64_t nnz,
+                              double *grad_w, cudaStream_t stream) {
     if (nnz == 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 4096);
-    symmetrize_kernel<<<(unsigned)blocks, 256, 0, stream>>>(part, rev, nnz, grad_w);
+    symmetrize_kernel<<<(unsigned)blocks, 256, 0, stream>>>(part, rev, arcmap, nnz, grad_w);
     return cudaGetLastError();
 }
 

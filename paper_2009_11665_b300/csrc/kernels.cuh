@@ -176,9 +176,15 @@ struct SddmmArgs {
 
 cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStream_t stream);
 cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream);
-// grad_w[e] = part[e] + part[rev[e]]
-cudaError_t launch_symmetrize(const double *part, const int32_t *rev, int64_t nnz, double *grad_w,
-                              cudaStream_t stream);
+// grad_w[arcmap[e]] = part[e] + part[rev[e]] (arcmap null: grad_w[e])
+cudaError_t launch_symmetrize(const double *part, const int32_t *rev, const int32_t *arcmap, int64_t nnz,
+                              double *grad_w, cudaStream_t stream);
+// dst[b * n + i] = src[b * n + idx[i]] (colourings into the graph's vertex
+// order, weights into its arc order, per-vertex seeds)
+cudaError_t launch_gather_i8(const int8_t *src, int8_t *dst, const int32_t *idx, int64_t n, int nb,
+                             cudaStream_t stream);
+cudaError_t launch_gather_f32(const float *src, float *dst, const int32_t *idx, int64_t n, cudaStream_t stream);
+cudaError_t launch_gather_f64(const double *src, double *dst, const int32_t *idx, int64_t n, cudaStream_t stream);
 
 // Per-segment (template x colouring) result of the root reduction.
 struct RootSum {
@@ -247,10 +253,11 @@ cudaError_t launch_hist_rows(const NodeArgs &args, Elem e, bool scaled, int thre
                              cudaStream_t stream);
 
 // Root reduction: vals is [nseg][n] of float, double or unsigned 64-bit
-// counts; writes per-vertex doubles when pv != null and one RootSum per
+// counts; writes per-vertex doubles when pv != null (value of vertex i at
+// pv[seg * n + pvmap[i]], or at i when pvmap is null) and one RootSum per
 // segment.
-cudaError_t launch_root_reduce(const void *vals, Elem e, int64_t n, int nseg, double *pv, RootSum *partials,
-                               int chunks, RootSum *out, cudaStream_t stream);
+cudaError_t launch_root_reduce(const void *vals, Elem e, int64_t n, int nseg, double *pv, const int32_t *pvmap,
+                               RootSum *partials, int chunks, RootSum *out, cudaStream_t stream);
 
 // Eref[row] = max over the row's arcs to neighbours of another valid colour
 // of Ep[neighbour row] (Eref pre-filled below kEmptyRowExp, e.g. bytes 0x80; split rows combine

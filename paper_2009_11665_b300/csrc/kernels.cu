@@ -933,7 +933,10 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, NV>::value) node_ke
 // step of U arcs that stays in the current colour run skips the per-arc
 // colour test.
 #ifndef SG2V_RUN_MINB_F32
-#define SG2V_RUN_MINB_F32 4
+#define SG2V_RUN_MINB_F32 5
+#endif
+#ifndef SG2V_RUN_U_F32
+#define SG2V_RUN_U_F32 4
 #endif
 template <typename T, int NV>
 struct RunMinBlocks {
@@ -945,7 +948,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     using V = Vec16<T>;
     using VT = typename V::type;
     constexpr int E = V::n;  // entries per 16-byte vector
-    constexpr int U = (NV == 1 && sizeof(T) == 4) ? 8 : 4;  // arcs in flight per step
+    constexpr int U = (NV == 1 && sizeof(T) == 4) ? SG2V_RUN_U_F32 : 4;  // arcs in flight per step
     // FP64 adds are scarce on this part: slots past a batch's live arcs skip
     // their load and adds; FP32 slots read the zero row instead
     constexpr bool SKIP_ZERO = sizeof(T) >= 8;

@@ -1,4 +1,6 @@
-"""Builds libsg2v.so (CUDA kernels + C ABI) in-tree for sm_103a with nvcc."""
+"""Builds libsg2v.so (CUDA kernels + C ABI) in-tree for sm_103a with nvcc.
+
+Each source compiles to an object of its own (in parallel), then one link."""
 import os
 import shutil
 import subprocess
@@ -6,10 +8,12 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsg2v.so")
-SOURCES = ["api.cu", "kernels.cu", "planner.cpp", "noalloc.cu"]
-HEADERS = ["kernels.cuh", "sg2v_internal.h"]
+SOURCES = ["api.cu", "kernels.cu", "run_kernel.cu", "planner.cpp", "noalloc.cu"]
+HEADERS = ["kernels.cuh", "device_common.cuh", "sg2v_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-O3"]
 
 
 def nvcc() -> str:
@@ -32,12 +36,21 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC,-fopenmp,-O3",
-           "-o", LIB + ".tmp"]
-    if ptxas_verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += [os.path.join(CSRC, s) for s in SOURCES]
-    cmd += ["-lgomp"]
+    os.makedirs(OBJ, exist_ok=True)
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc(), *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        if ptxas_verbose:
+            cmd += ["-Xptxas", "-v"]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((src, subprocess.Popen(cmd)))
+        objs.append(obj)
+    failed = [src for src, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {', '.join(failed)}")
+    cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC,-fopenmp", "-o", LIB + ".tmp", *objs, "-lgomp"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -520,10 +520,15 @@ struct Shape {
     int wthreads = 0, wbps = 0;  // the one-warp-per-row launch of the longer tasks of a group node
     size_t wsmem = 0;
     bool defer = false; // eMA in its own launch over blocks of rows (ema_rows_kernel)
-    bool run = false;   // run-scatter kernel (warp-wide rows, plain FP32 / FP64 tables)
-    const uint16_t *runmap_y = nullptr;  // its run map into Y' (forms 0 and 1)
-    const uint16_t *runmap_m = nullptr;  // into the active row (form 2: root with t = kc)
+    // run-scatter kernel (plain FP32 / FP64 tables) for the one-task-per-warp
+    // launch: its run maps into Y' (forms 0 and 1) and into the active row
+    // (form 2: root with t = kc), and its own launch shape
+    bool run = false;
+    const uint16_t *runmap_y = nullptr;
+    const uint16_t *runmap_m = nullptr;
     int wmap = 0, mzero = 0;
+    int run_ywords = 0, run_mwords = 0, run_threads = 0, run_bps = 0;
+    size_t run_smem = 0;
     int64_t ldy = 0;    // Y' row stride of a deferred node
 };
 
@@ -738,11 +743,14 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             return SG2V_ERR_UNSUPPORTED;
         }
         if ((st = device_tables(P->dev, kc, c.t, c.a, sh.wz_pad, &P->tabs[i]))) return st;
-        // warp-wide gathering rows of plain FP32 / FP64 tables: the run-scatter
-        // kernel (SG2V_RUN_KERNEL=0 keeps the per-colour accumulators of node_kernel)
+        // gathering nodes of plain FP32 / FP64 tables: the one-task-per-warp
+        // launch uses the run-scatter kernel (SG2V_RUN_KERNEL=0 keeps the
+        // per-colour accumulators of node_kernel); short tasks of narrow rows
+        // stay one per lane group (node_group_kernel)
         const char *run_env = std::getenv("SG2V_RUN_KERNEL");
-        if (!(run_env && std::atoi(run_env) == 0) && !hist && sh.grp == 32 && !sh.group && !sh.rows &&
-            (sh.nv == 1 || sh.nv == 2) && !P->scaled && (P->elem == Elem::F32 || P->elem == Elem::F64)) {
+        if (!(run_env && std::atoi(run_env) == 0) && !hist && sh.grp != kWideLanes && !sh.rows &&
+            (sh.nv == 1 || (sh.nv == 2 && sh.grp == 32)) && !P->scaled &&
+            (P->elem == Elem::F32 || P->elem == Elem::F64)) {
             const int E = P->vecn;
             const int wy = (int)binom(kc - 1, c.p);
             const int wa = c.a == 1 ? 1 : (int)binom(kc - 1, c.a - 1);
@@ -752,20 +760,19 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             const int threads = kNodeThreads;
             const size_t smem = (size_t)(threads / 32) * ((size_t)(ywords + mwords) * P->esz + kRunCompactBytes);
             const int form = (c.is_root && c.t == kc) ? 2 : ((c.a == 1 && !c.is_root) ? 1 : 0);
-            const int bps = node_run_blocks_per_sm(P->elem, sh.nv, g->weights != nullptr, form, threads, smem);
+            const int bps =
+                node_run_blocks_per_sm(P->elem, sh.grp, sh.nv, g->weights != nullptr, form, threads, smem);
             if (bps >= 1) {
                 sh.run = true;
-                sh.wmap = 32 * sh.nv * E;
+                sh.wmap = sh.grp * sh.nv * E;
                 sh.mzero = mbase;
                 if ((st = run_map(P->dev, kc, c.t, c.a, 0, sh.wmap, ybase, &sh.runmap_y))) return st;
                 if (form == 2 && (st = run_map(P->dev, kc, c.t, c.a, 2, sh.wmap, mbase, &sh.runmap_m))) return st;
-                sh.zwords = 0;
-                sh.ywords = ywords;
-                sh.mwords = mwords;
-                sh.owords = 0;
-                sh.threads = threads;
-                sh.smem = smem;
-                sh.blocks_per_sm = bps;
+                sh.run_ywords = ywords;
+                sh.run_mwords = mwords;
+                sh.run_threads = threads;
+                sh.run_smem = smem;
+                sh.run_bps = bps;
             }
         }
         // large eMA (many sets times many splits per row, root excepted): its own launch over
@@ -993,6 +1000,25 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     return A;
 }
 
+// Launches node i's one-task-per-warp work on the run-scatter kernel.
+cudaError_t launch_run_node(const Prepared &P, size_t i, const NodeArgs &A, cudaStream_t stream) {
+    const CNode &c = P.nodes[i];
+    const Shape &sh = P.shape[i];
+    NodeArgs R = A;
+    int form = 0;
+    if (A.root && c.t == P.kc && !A.Yout && !A.defer && sh.runmap_m)
+        form = 2;
+    else if (A.a_leaf && !A.root && !A.defer && !A.Yout && !A.accumulate)
+        form = 1;
+    R.runmap = form == 2 ? sh.runmap_m : sh.runmap_y;
+    R.wmap = sh.wmap;
+    R.mzero = sh.mzero;
+    R.ywords = sh.run_ywords;
+    R.mwords = sh.run_mwords;
+    return launch_node_run(R, P.elem, sh.grp, sh.nv, form, sh.run_threads, sh.run_smem, P.info.sms * sh.run_bps,
+                           stream);
+}
+
 // Launches the forward kernel of node i with the prepared shape.
 cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, cudaStream_t stream) {
     const Shape &sh = P.shape[i];
@@ -1005,10 +1031,11 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
         NodeArgs W = A;
         W.group_rows = 0;
         W.ntasks = split;
-        cudaError_t e = P.scaled ? launch_node_scaled(W, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
-                                                      stream)
-                                 : launch_node(W, P.elem, sh.grp, sh.nv, sh.wthreads, sh.wsmem, P.info.sms * sh.wbps,
-                                               stream);
+        cudaError_t e = sh.run ? launch_run_node(P, i, W, stream)
+                        : P.scaled ? launch_node_scaled(W, sh.grp, sh.nv, sh.wthreads, sh.wsmem,
+                                                        P.info.sms * sh.wbps, stream)
+                                   : launch_node(W, P.elem, sh.grp, sh.nv, sh.wthreads, sh.wsmem,
+                                                 P.info.sms * sh.wbps, stream);
         if (e != cudaSuccess) return e;
         NodeArgs S = A;
         S.tasks = A.tasks + split;
@@ -1016,19 +1043,7 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
         return P.scaled ? launch_node_scaled(S, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
                         : launch_node(S, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     }
-    if (sh.run) {
-        const CNode &c = P.nodes[i];
-        NodeArgs R = A;
-        int form = 0;
-        if (A.root && c.t == P.kc && !A.Yout && !A.defer && sh.runmap_m)
-            form = 2;
-        else if (A.a_leaf && !A.root && !A.defer && !A.Yout && !A.accumulate)
-            form = 1;
-        R.runmap = form == 2 ? sh.runmap_m : sh.runmap_y;
-        R.wmap = sh.wmap;
-        R.mzero = sh.mzero;
-        return launch_node_run(R, P.elem, sh.nv, form, sh.threads, sh.smem, grid_cap, stream);
-    }
+    if (sh.run) return launch_run_node(P, i, A, stream);
     if (P.scaled) return launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     return launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
 }

@@ -222,14 +222,27 @@ constexpr int kWideThreads = 256;
 int node_blocks_per_sm(Elem e, bool hist, int lanes_per_group, int vec_per_lane, bool weighted, int threads,
                        size_t smem, bool group_rows = false);
 
-// Run-scatter node kernel (plain FP32 / FP64 tables, warp-wide rows of up
-// to 32 * nv vectors, nv <= 2): form 0 generic eMA epilogue, 1 single-vertex
-// active child (M_s' = Y'), 2 root with one output set (row sum of pairs).
-// Shared memory per warp: (ywords + mwords) elements plus kRunCompactBytes.
+// Run-scatter node kernel (run_kernel.cu; plain FP32 tables, FP64 without
+// weights): one task per warp, lane groups of g (4, 8, 16 or 32) covering a
+// gathered row of g * nv vectors (nv = 2 only with g = 32); form 0 generic
+// eMA epilogue, 1 single-vertex active child (M_s' = Y'), 2 root with one
+// output set (row sum of pairs).  Shared memory per warp: (ywords + mwords)
+// elements plus kRunCompactBytes.  0 blocks per SM when the variant does not
+// exist.
 constexpr int kRunCompactBytes = 384;
-int node_run_blocks_per_sm(Elem e, int nv, bool weighted, int form, int threads, size_t smem);
-cudaError_t launch_node_run(const NodeArgs &args, Elem e, int nv, int form, int threads, size_t smem, int grid_cap,
-                            cudaStream_t stream);
+int node_run_blocks_per_sm(Elem e, int g, int nv, bool weighted, int form, int threads, size_t smem);
+cudaError_t launch_node_run(const NodeArgs &args, Elem e, int g, int nv, int form, int threads, size_t smem,
+                            int grid_cap, cudaStream_t stream);
+
+// Launch helpers shared by the kernel files: resident blocks per SM of a
+// kernel at a block size and dynamic shared memory (raising the kernel's
+// shared-memory limit when needed; 0 if it cannot run), the same check made
+// once per kernel at launch, and a node launch over the work list (grid
+// capped at grid_cap; g lanes per task group, kWideLanes for one CTA per task).
+int blocks_per_sm(void *kernel, int threads, size_t smem);
+cudaError_t ensure_smem(void *kernel, int threads, size_t smem);
+cudaError_t launch_variant(void *kernel, const NodeArgs &args, int g, int threads, size_t smem, int grid_cap,
+                           cudaStream_t stream);
 
 // Launches the fused SpMM/histogram + eMA kernel of one node.
 cudaError_t launch_node(const NodeArgs &args, Elem e, int lanes_per_group, int vec_per_lane, int threads,

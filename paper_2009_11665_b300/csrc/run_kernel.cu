@@ -1,0 +1,399 @@
+// Run-scatter node kernel: one launch per DP node (Alg. 5) for the gathering
+// nodes of plain FP32 / FP64 tables.
+//
+// A warp owns one work-list task (a row v, or a chunk of a long row) and
+// computes, for the node s = (T_s, T_a, T_p),
+//   Y'(v, P)   = sum over arcs (v, u) of w_vu * M_p'(u, P - {col(u)})   (Alg. 4 / 6)
+//   M_s'(v, S) = sum over splits of M_a'(v, A) * Y'(v, S - A)           (Eq. 1)
+// in the colour-compressed layout (row v keeps only the sets holding
+// col(v)).  The arcs of a task come sorted by neighbour colour, so each colour
+// d is one run (per lane group), summed in registers; when the run ends, its
+// sum Z(d, .) goes straight to where the eMA needs it, through the node's run
+// map for the pair (col(v), d):
+//   FORM 0 / 1: Y'(P) += Z(d, P - {d}) for the p-sets P without col(v)
+//               (Y' in shared memory; FORM 1, a single-vertex active child,
+//               stores Y' as the output row, FORM 0 runs the eMA epilogue);
+//   FORM 2:     a root with one output set: the row sum gains
+//               Z(d, Q) * M_a'(v, S' - Q - {d}) for every (p-1)-set Q
+//               without col(v) (the active row in shared memory).
+// Entries of Z(d) whose set holds col(v) map to a sink (a Y' slot nothing
+// reads, or a zero of the active row), so the scatter has no branches.  No
+// per-colour accumulators are kept, so rows with few colours pay only for the
+// colours they have.
+//
+// Lanes form groups of G that cover one neighbour row (G * NV 16-byte
+// vectors), so a warp instruction gathers 32 / G arcs; only G = 32 is
+// instantiated (see pick_run).  The gather
+// loop is kept short because these launches are bound by issue slots: each
+// batch of 32 sorted arcs is compacted (through shared memory) to the arcs
+// that add something, each as one word u << 4 | colour, so an arc costs one
+// shuffle, one address, one 16-byte load and the adds; lanes past the row's
+// last vector load that vector again (no predicate), and a step that stays
+// in every group's current run skips the per-arc colour test.  Groups scatter
+// with shared-memory atomic adds (their runs end at different times).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "kernels.cuh"
+
+namespace sg2v {
+
+namespace {
+
+#ifndef SG2V_RUN_MINB_F32
+#define SG2V_RUN_MINB_F32 5
+#endif
+#ifndef SG2V_RUN_U_F32
+#define SG2V_RUN_U_F32 4
+#endif
+// warp-wide groups scatter with plain read-modify-writes (1) or atomics (0)
+#ifndef SG2V_RUN_RMW32
+#define SG2V_RUN_RMW32 1
+#endif
+
+// Resident blocks per SM requested from the compiler (the register cap);
+// tuned on B300 (occupancy matters more than a few spills).
+template <typename T, int NV>
+struct RunMinBlocks {
+    static constexpr int value = sizeof(T) == 4 ? SG2V_RUN_MINB_F32 : (NV == 1 ? 3 : 2);
+};
+
+template <typename T, int G, int NV, bool WEIGHTED, int FORM>
+__global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node_run_kernel(const NodeArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = Vec16<T>;
+    using VT = typename V::type;
+    constexpr int E = V::n;    // entries per 16-byte vector
+    constexpr int NG = 32 / G; // arcs per warp instruction
+    constexpr int U = (NV == 1 && sizeof(T) == 4) ? SG2V_RUN_U_F32 : 4;  // arcs in flight per group and step
+    // FP64 adds are scarce on this part: slots past a batch's live arcs skip
+    // their load and adds; FP32 slots read the zero row instead
+    constexpr bool SKIP_ZERO = sizeof(T) >= 8;
+    constexpr bool RMW = G == 32 && SG2V_RUN_RMW32;
+    static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G;
+    // per warp: Y' with its sink (FORM 0 / 1), the active row with its zero
+    // (a >= 2 or FORM 2), and the batch's compacted arcs
+    T *ybuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.ywords + A.mwords);
+    T *mbuf = ybuf + A.ywords;
+    unsigned *cbuf = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(smem_raw) +
+                                                  (size_t)(blockDim.x >> 5) * (A.ywords + A.mwords) * sizeof(T) +
+                                                  (size_t)wib * kRunCompactBytes);
+    float *wbuf = reinterpret_cast<float *>(cbuf + 32);
+    const int kc = A.kc;
+    const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
+    const int nvec = (A.Wz + E - 1) / E;
+    // the vector each lane loads (lanes past the row's end repeat the last
+    // one: same line, no extra traffic) and which of its entries are real
+    int lv_[NV];
+    unsigned emask = 0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        lv_[q] = min(gl + G * q, nvec - 1);
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+            if ((gl + G * q) * E + k < A.Wz) emask |= 1u << (q * E + k);
+    }
+    if (FORM == 2) {
+        // the active row's zero (the sink of the dot products); a single-vertex
+        // active child is the one-entry row {1}
+        if (lane < E) mbuf[A.mzero + lane] = T(0);
+        if (A.a_leaf && lane == 0) mbuf[0] = T(1);
+    }
+    const unsigned uvec = (unsigned)((int64_t)A.nb * A.ldp / E);  // vectors between vertex rows
+    const unsigned zero_word = (unsigned)A.n << 4;                 // the zero row
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
+    int4 task = ti < A.ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
+    unsigned ovf = 0;
+    for (; ti < A.ntasks; ti += nwarps) {
+        const int4 next = ti + nwarps < A.ntasks ? A.tasks[ti + nwarps] : task;
+        const int v = task.x;
+        const int slot = task.y;
+        const int64_t e0 = task.z, e1 = task.w;
+        for (int b = 0; b < A.nb; ++b) {
+            const int64_t rowb = (int64_t)v * A.nb + b;
+            const int cv = A.colours[(int64_t)b * A.n + v];
+            const bool cok = (unsigned)cv < (unsigned)kc;
+            if (slot < 0 && (e0 == e1 || !cok)) {
+                // no arcs (or no valid colour): every output of the row is zero
+                if (A.defer) {
+                    T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
+                    for (int j = lane; j < A.wy; j += 32) yo[j] = T(0);
+                } else if constexpr (FORM == 2) {
+                    if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = T(0);
+                } else if constexpr (FORM == 1) {
+                    VT *out = reinterpret_cast<VT *>(static_cast<T *>(A.Ms) + rowb * A.ldt);
+                    for (int j = lane; j < (int)(A.ldt / E); j += 32) out[j] = V::zero();
+                } else {
+                    epilogue<T>(A, v, b, false, ybuf, mbuf, lane, ovf);
+                }
+                __syncwarp();
+                continue;
+            }
+            if (mchunks && cok) {
+                // the active row, needed by the eMA (and by FORM 2's runs)
+                const char *src = static_cast<const char *>(A.Ma) + rowb * A.lda * sizeof(T);
+                for (int c = lane; c < mchunks; c += 32) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(mbuf) + 16 * c);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * c) : "memory");
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
+            if (FORM != 2)
+                for (int j = lane; j < A.ywords; j += 32) ybuf[j] = T(0);
+            bool mready = mchunks == 0 || !cok;
+            T acc = T(0);  // FORM 2: this lane's part of the row sum
+            const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp);
+            const VT *lrow[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) lrow[q] = Mb + lv_[q];
+            const int32_t *scol = A.scol + (int64_t)b * A.nnz;
+            const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
+            const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
+            const uint16_t *rmap = A.runmap + (int64_t)(cok ? cv : 0) * kc * A.wmap + gl * E;
+            VT run[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) run[q] = V::zero();
+            int cur = -1;
+            // the end of a colour run of this lane's group (called by the
+            // group's lanes only; warp-wide groups call it uniformly)
+            auto flush = [&](int c) {
+                const uint16_t *mp = rmap + (int64_t)c * A.wmap;
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    uint32_t ix[E];
+                    if constexpr (E == 4) {
+                        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(mp + G * E * q));
+                        ix[0] = w.x & 0xffffu;
+                        ix[1] = w.x >> 16;
+                        ix[2] = w.y & 0xffffu;
+                        ix[3] = w.y >> 16;
+                    } else {
+                        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(mp + G * E * q));
+                        ix[0] = w & 0xffffu;
+                        ix[1] = w >> 16;
+                    }
+                    const T *rv = reinterpret_cast<const T *>(&run[q]);
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        if constexpr (FORM == 2) {
+                            // entries past the row (padding) may hold anything
+                            const T x = (emask >> (q * E + k) & 1u) ? rv[k] : T(0);
+                            acc = fma(x, mbuf[ix[k]], acc);
+                        } else if constexpr (RMW) {
+                            ybuf[ix[k]] += rv[k];
+                        } else {
+                            atomicAdd(ybuf + ix[k], rv[k]);
+                        }
+                    }
+                    run[q] = V::zero();
+                }
+                // the next run may add to the same entries of Y'
+                if (FORM != 2 && RMW) __syncwarp();
+            };
+            for (int64_t base = e0; base < e1; base += 32) {
+                const int cnt_in = (int)(e1 - base < 32 ? e1 - base : 32);
+                const bool in = lane < cnt_in;
+                const int c_in = in ? (int)__ldg(sclr + base + lane) : -1;
+                const int u_in = in ? __ldg(scol + base + lane) : 0;
+                const bool t_in = cok && c_in >= 0 && c_in != cv && (!A.half_arcs || u_in > v);
+                // compact the batch to the arcs that add something (order kept,
+                // so colour runs stay contiguous) through the warp's slots
+                const unsigned live = __ballot_sync(kFull, t_in);
+                const int cnt = __popc(live);
+                if (cnt == 0) continue;
+                if (t_in) {
+                    const int r = __popc(live & ((1u << lane) - 1u));
+                    cbuf[r] = ((unsigned)u_in << 4) | (unsigned)c_in;
+                    if (WEIGHTED) wbuf[r] = __ldg(sw + base + lane);
+                }
+                __syncwarp();
+                // slots past the live arcs read the zero row into the batch's
+                // last run, so a run that continues in the next batch is not cut
+                const unsigned wl = cbuf[lane < cnt ? lane : cnt - 1];
+                const unsigned pk = lane < cnt ? wl : (zero_word | (wl & 15u));
+                T w_l = T(1);
+                if (WEIGHTED) w_l = lane < cnt ? T(wbuf[lane]) : T(0);
+                __syncwarp();
+                if (FORM == 2 && !mready) {
+                    // the active row is read from the first run end on
+                    asm volatile("cp.async.wait_all;\n" ::: "memory");
+                    __syncwarp();
+                    mready = true;
+                }
+                for (int j0 = 0; j0 < cnt; j0 += NG * U) {
+                    VT x[U][NV];
+                    T w[U];
+                    int cr[U];
+#pragma unroll
+                    for (int r = 0; r < U; ++r) {
+                        const int j = j0 + r * NG + grp;
+                        const unsigned pw = __shfl_sync(kFull, pk, j);
+                        const unsigned u = pw >> 4;
+                        cr[r] = (int)(pw & 15u);
+                        w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
+#pragma unroll
+                        for (int q = 0; q < NV; ++q)
+                            x[r][q] = (!SKIP_ZERO || j < cnt) ? ldg_row(lrow[q] + (size_t)u * uvec) : V::zero();
+                    }
+                    const bool same = G == 32 ? cr[U - 1] == cur : __all_sync(kFull, cr[U - 1] == cur);
+                    if (same) {
+                        // the whole step continues every group's current run
+#pragma unroll
+                        for (int r = 0; r < U; ++r) {
+                            if (SKIP_ZERO && j0 + r * NG + grp >= cnt) continue;
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) {
+                                if (WEIGHTED)
+                                    V::fma(run[q], w[r], x[r][q]);
+                                else
+                                    V::add(run[q], x[r][q]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < U; ++r) {
+                            if (SKIP_ZERO && j0 + r * NG + grp >= cnt) continue;
+                            if (cr[r] != cur) {
+                                if (cur >= 0) flush(cur);
+                                cur = cr[r];
+                            }
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) {
+                                if (WEIGHTED)
+                                    V::fma(run[q], w[r], x[r][q]);
+                                else
+                                    V::add(run[q], x[r][q]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (cur >= 0) flush(cur);
+            if (FORM == 2 && !mready) asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncwarp();
+            if constexpr (FORM == 2) {
+                T s = warp_sum(acc);
+                if (slot >= 0) {
+                    // one chunk of a split row: its part of the row sum goes to
+                    // the scratch row; the last chunk to arrive writes the sum
+                    T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
+                    int last = 0;
+                    if (lane == 0) {
+                        atomicAdd(sc, s);
+                        __threadfence();
+                        const unsigned done = atomicAdd(A.counters + (int64_t)slot * A.nb + b, 1u);
+                        last = (done + 1u == (unsigned)__ldg(A.heavy_chunks + slot));
+                        if (last) {
+                            __threadfence();
+                            s = __ldcg(sc);
+                        }
+                    }
+                    last = __shfl_sync(kFull, last, 0);
+                    if (!last) {
+                        __syncwarp();
+                        continue;
+                    }
+                }
+                if (lane == 0)
+                    static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = cok ? (A.half_arcs ? T(2) * s : s) : T(0);
+                __syncwarp();
+                continue;
+            }
+            if (slot >= 0) {
+                // one chunk of a split row: fold Y' into the scratch row; the
+                // last chunk to arrive finishes the row
+                T *sc = static_cast<T *>(A.scratch) + ((int64_t)slot * A.nb + b) * A.scratch_ld;
+                if (cok)
+                    for (int j = lane; j < A.wy; j += 32) atomicAdd(sc + j, ybuf[j]);
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) {
+                    const unsigned done = atomicAdd(A.counters + (int64_t)slot * A.nb + b, 1u);
+                    last = (done + 1u == (unsigned)__ldg(A.heavy_chunks + slot));
+                }
+                last = __shfl_sync(kFull, last, 0);
+                if (!last) {
+                    if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
+                    __syncwarp();
+                    continue;
+                }
+                __threadfence();
+                for (int j = lane; j < A.wy; j += 32) ybuf[j] = __ldcg(sc + j);
+                __syncwarp();
+            }
+            if constexpr (FORM == 1) {
+                // M_s' = Y' (the row's padding gets Y's zeros)
+                VT *out = reinterpret_cast<VT *>(static_cast<T *>(A.Ms) + rowb * A.ldt);
+                const VT *yv = reinterpret_cast<const VT *>(ybuf);
+                for (int j = lane; j < (int)(A.ldt / E); j += 32) out[j] = cok ? yv[j] : V::zero();
+                __syncwarp();
+                continue;
+            }
+            if (mchunks && cok) asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncwarp();
+            if (A.defer) {
+                // the eMA runs in its own launch over blocks of rows
+                T *yo = static_cast<T *>(A.Yout) + rowb * A.ldy;
+                for (int j = lane; j < A.wy; j += 32) yo[j] = cok ? ybuf[j] : T(0);
+                __syncwarp();
+                continue;
+            }
+            epilogue<T>(A, v, b, cok, ybuf, mbuf, lane, ovf);
+            __syncwarp();
+        }
+        task = next;
+    }
+}
+
+template <typename T, int G, int NV, bool W>
+void *pick_form(int form) {
+    if (form == 1) return reinterpret_cast<void *>(&node_run_kernel<T, G, NV, W, 1>);
+    if (form == 2) return reinterpret_cast<void *>(&node_run_kernel<T, G, NV, W, 2>);
+    return reinterpret_cast<void *>(&node_run_kernel<T, G, NV, W, 0>);
+}
+
+// Warp-wide rows only: for narrow rows (g < 32) the lane groups see their
+// colour runs cut into pieces (each group takes every (32/g)-th arc), and
+// the per-colour accumulators of node_kernel / node_group_kernel measured
+// faster ((4,2,2) on the 1M-vertex R-MAT graph: 0.76 ms there, 1.06 ms here).
+template <typename T, bool W>
+void *pick_run(int g, int nv, int form) {
+    if (g != 32) return nullptr;
+    if (nv == 2) return pick_form<T, 32, 2, W>(form);
+    if (nv == 1) return pick_form<T, 32, 1, W>(form);
+    return nullptr;
+}
+
+// FP32 weighted and unweighted, FP64 unweighted (the weighted FP64 form stays
+// on node_kernel: it serves the finite-difference reference only)
+void *select_run(Elem e, int g, int nv, bool weighted, int form) {
+    if (e == Elem::F64) return weighted ? nullptr : pick_run<double, false>(g, nv, form);
+    if (e == Elem::F32) return weighted ? pick_run<float, true>(g, nv, form) : pick_run<float, false>(g, nv, form);
+    return nullptr;
+}
+
+}  // namespace
+
+int node_run_blocks_per_sm(Elem e, int g, int nv, bool weighted, int form, int threads, size_t smem) {
+    return blocks_per_sm(select_run(e, g, nv, weighted, form), threads, smem);
+}
+
+cudaError_t launch_node_run(const NodeArgs &args, Elem e, int g, int nv, int form, int threads, size_t smem,
+                            int grid_cap, cudaStream_t stream) {
+    void *k = select_run(e, g, nv, args.weights != nullptr, form);
+    if (!k || !args.runmap) return cudaErrorInvalidValue;
+    const cudaError_t err = ensure_smem(k, threads, smem);
+    if (err != cudaSuccess) return err;
+    NodeArgs a = args;
+    a.group_rows = 0;  // one task per warp
+    return launch_variant(k, a, 32, threads, smem, grid_cap, stream);
+}
+
+}  // namespace sg2v

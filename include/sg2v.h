@@ -347,10 +347,11 @@ int64_t sg2v_launch_count(void);
 /*
  * sg2v_sum_counts_noalloc -- sums per-vertex counts into totals without
  * allocating anything.  The paper has no counterpart; this is a service for
- * callers that cannot allocate device memory where they need a total: code
- * being recorded into a CUDA graph, serving loops whose device memory is
- * reserved up front by their own allocator, and code that must not stall
- * other streams (cudaMalloc and cudaFree synchronise the device).
+ * callers that cannot allocate device memory where they need a total:
+ * serving loops whose device memory is reserved up front by their own
+ * allocator (where a further allocation may fail or be forbidden), and code
+ * that must not stall other streams (cudaMalloc and cudaFree synchronise the
+ * device).
  *
  *   values  [nseg][n] double, device memory: e.g. the per_vertex output of
  *           sg2v_count / sg2v_count_batched
@@ -371,7 +372,9 @@ int64_t sg2v_launch_count(void);
  * first call before any stream capture.  Each call overwrites the records it
  * reads, so nothing carries over between calls, but all calls share the
  * array: calls whose kernels overlap on the GPU (different streams without
- * ordering) race and give wrong totals.
+ * ordering) race and give wrong totals.  The looked-up address is kept for
+ * the life of the process: do not call this entry point on a device after
+ * cudaDeviceReset on it.
  * Errors: INVALID_ARGUMENT (null, sizes, host pointers), CUDA.
  */
 sg2v_status sg2v_sum_counts_noalloc(const double *values, int64_t n, int32_t nseg, double *totals,

@@ -235,7 +235,26 @@ def sg2v_count_batched(graph, plans: Sequence[int], colours, B: int, precision: 
 
 def sg2v_sum_counts_noalloc(values, n: int, nseg: int, totals, stream=None) -> None:
     """Sums device values [nseg][n] into device totals [nseg] without
-    allocating (see include/sg2v.h); stream-ordered, no synchronisation."""
+    allocating (see include/sg2v.h); stream-ordered, no synchronisation.
+    Torch tensors are checked first (float64, at least nseg * n values and
+    nseg totals, on a CUDA device): the C entry point cannot see sizes, and a
+    short or float32 buffer would be read past its end on the device."""
+    tensors = [(name, t, need) for name, t, need in (("values", values, int(nseg) * int(n)),
+                                                      ("totals", totals, int(nseg)))
+               if hasattr(t, "dtype") and hasattr(t, "numel")]
+    if tensors:
+        import torch
+
+        for name, t, need in tensors:
+            if t.dtype != torch.float64:
+                raise ValueError(f"sg2v_sum_counts_noalloc: {name} must be float64, got {t.dtype}")
+            if t.numel() < need:
+                raise ValueError(f"sg2v_sum_counts_noalloc: {name} holds {t.numel()} values, needs {need}")
+        for name, t, _ in tensors:
+            if not t.is_cuda:
+                raise ValueError(f"sg2v_sum_counts_noalloc: {name} must be a CUDA tensor")
+            if not t.is_contiguous():
+                raise ValueError(f"sg2v_sum_counts_noalloc: {name} must be contiguous")
     _check(_lib.sg2v_sum_counts_noalloc(_ptr(values), int(n), int(nseg), _ptr(totals), _stream(stream)),
            "sg2v_sum_counts_noalloc")
 

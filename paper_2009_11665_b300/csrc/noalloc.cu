@@ -1,15 +1,13 @@
 // Allocation-free summation of per-vertex counts (sg2v_sum_counts_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need a
-// total: code recorded into a CUDA graph (stream capture forbids the implicit
-// synchronisation of cudaMalloc and the library's own pool would add
-// allocation nodes the caller does not control), serving loops whose device
-// memory is reserved up front by their own allocator, and code that must not
-// stall other streams (cudaMalloc/cudaFree synchronise the device).  This
-// entry point sums per-vertex counts the caller already holds on the device
-// into per-segment totals without any allocation: its scratch is a fixed
-// file-scope device array that every GPU loading the library keeps until the
-// process exits.
+// total: serving loops whose device memory is reserved up front by their own
+// allocator (a further allocation may fail or be forbidden there), and code
+// that must not stall other streams (cudaMalloc and cudaFree synchronise the
+// device).  This entry point sums per-vertex counts the caller already holds
+// on the device into per-segment totals without any allocation: its scratch
+// is a fixed file-scope device array that every GPU loading the library keeps
+// until the process exits.
 //
 // The arithmetic is that of the library's root reduction: each value that is
 // a non-negative integer below 2^128 is added exactly in 128-bit integers and
@@ -46,9 +44,15 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
 }
 
 __device__ __forceinline__ void combine(Partial &x, const Partial &y) {
+    // 128-bit add with the carry out of each step kept apart: the high word
+    // takes y.hi plus the low word's carry (which itself wraps when y.hi is
+    // 2^64 - 1), then x.hi; a carry out of either step means the sum reached
+    // 2^128
     const unsigned long long lo = x.lo + y.lo;
-    const unsigned long long hi = x.hi + y.hi + (lo < x.lo ? 1ull : 0ull);
-    if (hi < x.hi || (hi == x.hi && y.hi + (lo < x.lo ? 1ull : 0ull) != 0ull)) x.flags |= 1u;  // sum reached 2^128
+    const unsigned long long c0 = lo < x.lo ? 1ull : 0ull;
+    const unsigned long long t = y.hi + c0;
+    const unsigned long long hi = x.hi + t;
+    if ((t < c0) | (hi < x.hi)) x.flags |= 1u;
     x.hi = hi;
     x.lo = lo;
     double s, e;
@@ -168,7 +172,9 @@ extern "C" sg2v_status sg2v_sum_counts_noalloc(const double *values, int64_t n, 
     Partial *scratch;
     {
         // once per device, with that device current: the host-side name of
-        // the array is not a device address, so ask the runtime for it
+        // the array is not a device address, so ask the runtime for it (the
+        // address is kept for the life of the process: a device reset, which
+        // recreates the module, invalidates it)
         std::lock_guard<std::mutex> lock(g_setup_mutex);
         if (!g_scratch_address[dev]) {
             void *p = nullptr;

@@ -1,9 +1,8 @@
 """sg2v_sum_counts_noalloc: totals without any device allocation.
 
 The entry point serves callers that cannot allocate device memory where they
-need a total (code recorded into a CUDA graph, serving loops whose memory is
-reserved up front by their own allocator, code that must not stall other
-streams).  It sums per-vertex counts the caller already holds, with its
+need a total (serving loops whose memory is reserved up front by their own
+allocator, code that must not stall other streams).  It sums per-vertex counts the caller already holds, with its
 scratch in a fixed device array inside the library.  These tests compare its
 totals with those of sg2v_count / sg2v_count_batched on the same counts, on
 two calls in a row (the shared scratch must not carry anything over).  This
@@ -100,3 +99,32 @@ def test_noalloc_rejects_oversized_and_host_requests(sg):
     sg.sg2v_sum_counts_noalloc(vals, 3, 1024, out)
     torch.cuda.synchronize()
     assert torch.equal(out[:1024], vals.sum(dim=1))
+
+
+def test_noalloc_sum_past_2_128_takes_the_compensated_sum(sg):
+    """Values whose exact 128-bit sum passes 2^128 must not come back wrapped.
+    With n = 192 each of the 64 blocks sums three consecutive values; block 1
+    holds 2^128 - 2^75, 2^75 - 2^64 and 2^64 - 2^11 (its partial has the high
+    word 2^64 - 1 and the low word 2^64 - 2^11), block 0 holds 4096, so the
+    final combination carries out of the low word into a high word of
+    2^64 - 1: the sum 2^128 + 2^11 must be reported as the compensated FP64
+    sum (2^128 after rounding), not as 2^11."""
+    import torch
+
+    vals = np.zeros(192)
+    vals[0] = 4096.0
+    vals[3] = 2.0 ** 128 - 2.0 ** 75
+    vals[4] = 2.0 ** 75 - 2.0 ** 64
+    vals[5] = 2.0 ** 64 - 2.0 ** 11
+    dv = torch.from_numpy(vals).cuda()
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.fill_(-1.0)
+        sg.sg2v_sum_counts_noalloc(dv, 192, 1, out)
+        torch.cuda.synchronize()
+        assert out.item() == 2.0 ** 128
+    # below 2^128 the same values stay exact: drop the 4096
+    dv[0] = 0.0
+    sg.sg2v_sum_counts_noalloc(dv, 192, 1, out)
+    torch.cuda.synchronize()
+    assert out.item() == 2.0 ** 128 - 2.0 ** 11

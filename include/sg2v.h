@@ -380,6 +380,38 @@ int64_t sg2v_launch_count(void);
 sg2v_status sg2v_sum_counts_noalloc(const double *values, int64_t n, int32_t nseg, double *totals,
                                     sg2v_stream stream);
 
+/* -------------------------------------------------------------- allocator */
+
+/*
+ * sg2v_set_allocator -- where per-call device workspaces come from.  The
+ * paper has no counterpart (its CPU code allocates its tables itself); the
+ * hook lets a caller that manages device memory (e.g. PyTorch's caching
+ * allocator) serve the library's temporary buffers.
+ *
+ *   alloc  alloc(bytes, stream, user) returns device memory of at least
+ *          `bytes` usable in stream order on `stream`, 16-byte aligned, or
+ *          NULL when it has none (the call then fails with
+ *          SG2V_ERR_OUT_OF_MEMORY after returning what it already took)
+ *   free   free(ptr, stream, user) takes back a block of alloc; the library
+ *          calls it in stream order after the block's last use on `stream`
+ *   user   passed through
+ *
+ * Both NULL restores the default: the library's stream-ordered pool of the
+ * current device.  Covered: the per-call buffers of sg2v_count,
+ * sg2v_count_batched and sg2v_count_backward (colour-sorted arcs, tables,
+ * scratch), and the buffers of sessions created while the hook is set (taken
+ * at sg2v_session_create on the default stream, given back at
+ * sg2v_session_destroy after a device synchronisation; a session keeps the
+ * hook it was created with, so alloc, free and user must stay valid until
+ * every such session is destroyed).  Graph and plan handles are not covered (they
+ * live until their destroy call).  The setting is process-wide: change it
+ * only while no call is running.  Errors: INVALID_ARGUMENT (exactly one of
+ * alloc / free given).
+ */
+typedef void *(*sg2v_alloc_fn)(size_t bytes, sg2v_stream stream, void *user);
+typedef void (*sg2v_free_fn)(void *ptr, sg2v_stream stream, void *user);
+sg2v_status sg2v_set_allocator(sg2v_alloc_fn alloc, sg2v_free_fn free, void *user);
+
 /* ---------------------------------------------------------------- status */
 
 /* Static English name of a status code. */

@@ -269,6 +269,58 @@ def sg2v_count_backward(graph, plan, colours, precision: int, grad_weights, grad
     return t.value
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+# every callback pair ever installed stays alive: sessions keep the functions
+# they were created with until they are destroyed, after any later change
+_allocator_refs = []
+_lib.sg2v_set_allocator.argtypes = [ALLOC_FN, FREE_FN, _p]
+_lib.sg2v_set_allocator.restype = ctypes.c_int
+
+
+def sg2v_set_allocator(alloc=None, free=None) -> None:
+    """Routes the library's per-call workspaces (and new sessions' buffers)
+    through Python callables alloc(bytes, stream) -> int device pointer (0 when
+    out of memory) and free(ptr, stream); both None restores the library's
+    pool.  See include/sg2v.h."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        _check(_lib.sg2v_set_allocator(ALLOC_FN(), FREE_FN(), None), "sg2v_set_allocator")
+        return
+
+    def _a(nbytes, stream, user):
+        try:
+            return int(alloc(int(nbytes), stream)) or None
+        except Exception:  # an exception must not cross the C ABI
+            return None
+
+    def _f(ptr, stream, user):
+        try:
+            free(ptr, stream)
+        except Exception:
+            pass
+
+    refs = (ALLOC_FN(_a), FREE_FN(_f))
+    _allocator_refs.append(refs)
+    _check(_lib.sg2v_set_allocator(refs[0], refs[1], None), "sg2v_set_allocator")
+
+
+def use_torch_allocator(device: Optional[int] = None) -> None:
+    """Serves the library's workspaces from PyTorch's caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, dev, stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    sg2v_set_allocator(alloc, free)
+
+
 def sg2v_graph_set_weights(graph, weights, stream=None) -> None:
     _check(_lib.sg2v_graph_set_weights(graph, _ptr(weights), _stream(stream)), "sg2v_graph_set_weights")
 

@@ -286,26 +286,57 @@ int env_int(const char *name, int dflt) {
     return v > 0 ? v : dflt;
 }
 
-// Allocations of one call, returned to the pool on every exit path.
+// The caller's allocator (sg2v_set_allocator), or none: the library's pool.
+struct AllocHook {
+    sg2v_alloc_fn alloc = nullptr;
+    sg2v_free_fn free = nullptr;
+    void *user = nullptr;
+};
+std::mutex g_hook_mutex;
+AllocHook g_hook;
+
+AllocHook current_hook() {
+    std::lock_guard<std::mutex> lock(g_hook_mutex);
+    return g_hook;
+}
+
+// Allocations of one call, returned on every exit path: from the caller's
+// allocator when one is set (taken once, at the call's start), else from the
+// library's stream-ordered pool.
 struct Workspace {
     cudaStream_t stream;
     cudaMemPool_t pool;
     std::vector<void *> live;
+    AllocHook hook = current_hook();
     ~Workspace() {
-        for (void *p : live) cudaFreeAsync(p, stream);
+        for (void *p : live) give_back(p);
+    }
+    void give_back(void *p) {
+        if (hook.alloc)
+            hook.free(p, reinterpret_cast<sg2v_stream>(stream), hook.user);
+        else
+            cudaFreeAsync(p, stream);
     }
     sg2v_status alloc(void **p, size_t bytes) {
         *p = nullptr;
         if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+        if (hook.alloc) {
+            *p = hook.alloc(bytes, reinterpret_cast<sg2v_stream>(stream), hook.user);
+            if (!*p) {
+                set_error("workspace allocation: the caller's allocator returned no memory");
+                return SG2V_ERR_OUT_OF_MEMORY;
+            }
+        } else {
+            cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+        }
         live.push_back(*p);
         return SG2V_OK;
     }
     void release(void *p) {
         auto it = std::find(live.begin(), live.end(), p);
         if (it != live.end()) {
-            cudaFreeAsync(p, stream);
+            give_back(p);
             live.erase(it);
         }
     }
@@ -378,16 +409,21 @@ sg2v_status validate_csr(int64_t n, int64_t nnz, const std::vector<int64_t> &rp,
             set_error("row_ptr is not monotone");
             return SG2V_ERR_INVALID_ARGUMENT;
         }
-    int bad = 0;  // 1: out of range, 2: not simple, 3: asymmetric, 4: bad weight
+    // every column index in range first: the symmetry lookups below index
+    // rows by column
+    bool in_range = true;
+#pragma omp parallel for schedule(static) reduction(&& : in_range)
+    for (int64_t e = 0; e < nnz; ++e) in_range = in_range && ci[e] >= 0 && ci[e] < n;
+    if (!in_range) {
+        set_error("col_idx entry out of range");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    if (!full) return SG2V_OK;
+    int bad = 0;  // 2: not simple, 3: asymmetric, 4: bad weight
 #pragma omp parallel for schedule(dynamic, 4096) reduction(max : bad)
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
             int32_t j = ci[e];
-            if (j < 0 || j >= n) {
-                bad = std::max(bad, 1);
-                break;
-            }
-            if (!full) continue;
             if (j == i || (e > rp[i] && ci[e - 1] >= j)) {
                 bad = std::max(bad, 2);
                 break;
@@ -408,9 +444,6 @@ sg2v_status validate_csr(int64_t n, int64_t nnz, const std::vector<int64_t> &rp,
         }
     }
     switch (bad) {
-        case 1:
-            set_error("col_idx entry out of range");
-            return SG2V_ERR_INVALID_ARGUMENT;
         case 2:
             set_error("graph has a self-loop, a repeated arc or an unsorted row");
             return SG2V_ERR_GRAPH_NOT_SIMPLE;
@@ -1230,7 +1263,8 @@ struct sg2v_session {
     sg2v::Prepared P;
     sg2v::RunBuffers R;
     uint32_t flags = 0;
-    std::vector<void *> owned;  // everything cudaMalloc'd here
+    sg2v::AllocHook hook;       // the caller's allocator at creation (or none)
+    std::vector<void *> owned;  // everything allocated here
     std::vector<void *> owned_tables;
     int8_t *colours = nullptr;  // [nb][n] staging
     double *pv = nullptr;       // [plans][nb][n]
@@ -1245,8 +1279,34 @@ struct sg2v_session {
 namespace sg2v {
 namespace {
 
+// Session buffers come from the caller's allocator when one was set at
+// creation (on the legacy default stream, synchronised), else cudaMalloc.
+sg2v_status session_malloc(sg2v_session *S, size_t bytes, void **p) {
+    bytes = std::max<size_t>(bytes, 16);
+    if (S->hook.alloc) {
+        *p = S->hook.alloc(bytes, nullptr, S->hook.user);
+        if (!*p) {
+            set_error("session allocation: the caller's allocator returned no memory");
+            return SG2V_ERR_OUT_OF_MEMORY;
+        }
+        return SG2V_OK;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "session allocation");
+    return SG2V_OK;
+}
+
+void session_mfree(sg2v_session *S, void *p) {
+    if (S->hook.alloc) {
+        cudaDeviceSynchronize();  // no replay may still use it
+        S->hook.free(p, nullptr, S->hook.user);
+    } else {
+        cudaFree(p);
+    }
+}
+
 void session_free_tables(sg2v_session *S) {
-    for (void *p : S->owned_tables) cudaFree(p);
+    for (void *p : S->owned_tables) session_mfree(S, p);
     S->owned_tables.clear();
     S->R.table.assign(S->P.nodes.size(), nullptr);
 }
@@ -1256,7 +1316,7 @@ void session_free(sg2v_session *S) {
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->capture) cudaStreamDestroy(S->capture);
     session_free_tables(S);
-    for (void *p : S->owned) cudaFree(p);
+    for (void *p : S->owned) session_mfree(S, p);
     delete S;
 }
 
@@ -1266,8 +1326,8 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
     // wave-independent buffers (root outputs, reductions) are reused when present
     sg2v_status st;
     auto alloc = [&](size_t bytes, void **p) -> sg2v_status {
-        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-        if (e != cudaSuccess) return cuda_fail(e, "session allocation");
+        sg2v_status s2 = session_malloc(S, bytes, p);
+        if (s2) return s2;
         S->owned.push_back(*p);
         return SG2V_OK;
     };
@@ -1277,7 +1337,7 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
         if (!p) continue;
         auto it = std::find(S->owned.begin(), S->owned.end(), p);
         if (it != S->owned.end()) {
-            cudaFree(p);
+            session_mfree(S, p);
             S->owned.erase(it);
         }
     }
@@ -1314,8 +1374,7 @@ sg2v_status session_alloc_wave(sg2v_session *S, int wave) {
         if (P.nodes[i].is_root) continue;
         R.ld[i] = table_ld(P, P.nodes[i]);
         void *t = nullptr;
-        cudaError_t e = cudaMalloc(&t, std::max<size_t>(table_bytes(P, P.nodes[i], wave), 16));
-        if (e != cudaSuccess) return cuda_fail(e, "session table allocation");
+        if ((st = session_malloc(S, table_bytes(P, P.nodes[i], wave), &t))) return st;
         S->owned_tables.push_back(t);
         R.table[i] = t;
     }
@@ -1612,6 +1671,7 @@ sg2v_status sg2v_session_create(const sg2v_graph *graph, const sg2v_plan *const 
     sg2v_session *S = new (std::nothrow) sg2v_session();
     if (!S) return SG2V_ERR_OUT_OF_MEMORY;
     S->flags = flags;
+    S->hook = current_hook();
     sg2v_status st = prepare(graph, plans, num_plans, B, precision, &S->P);
     if (st) {
         session_free(S);
@@ -1619,8 +1679,8 @@ sg2v_status sg2v_session_create(const sg2v_graph *graph, const sg2v_plan *const 
     }
     const Prepared &P = S->P;
     auto alloc = [&](size_t bytes, void **p) -> sg2v_status {
-        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-        if (e != cudaSuccess) return cuda_fail(e, "session allocation");
+        sg2v_status s2 = session_malloc(S, bytes, p);
+        if (s2) return s2;
         S->owned.push_back(*p);
         return SG2V_OK;
     };
@@ -2132,6 +2192,18 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         else
             *total = sum.s + sum.c;
     }
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_set_allocator(sg2v_alloc_fn alloc, sg2v_free_fn free_fn, void *user) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("sg2v_set_allocator: give both functions or neither");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    std::lock_guard<std::mutex> lock(g_hook_mutex);
+    g_hook.alloc = alloc;
+    g_hook.free = free_fn;
+    g_hook.user = alloc ? user : nullptr;
     return SG2V_OK;
 }
 

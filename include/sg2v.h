@@ -249,11 +249,24 @@ sg2v_status sg2v_count_batched(const sg2v_graph *graph, const sg2v_plan *const *
  *                    same value); unweighted graphs give the derivative at
  *                    w = 1 (the colourful maps through each edge)
  *   total            host double or NULL: the forward total sum_v per_vertex[v]
- *   flags            0
- * Memory: every node's table, Y' and gradient table of the colouring stay
- * allocated during the call.  Errors as sg2v_count; SG2V_FP32_SCALED is
- * UNSUPPORTED here.
+ *   flags            0 (choose the form by memory), SG2V_BACKWARD_STORE or
+ *                    SG2V_BACKWARD_RECOMPUTE (not both)
+ * Memory: the stored form keeps every node's table, Y' and gradient table
+ * of the colouring during the call.  The recompute form keeps only what the
+ * current reverse step reads: the tables of the node's children are rebuilt
+ * by replaying the forward of their sub-templates (the storage discipline of
+ * Sec. 5.3 / Alg. 5 applied to the reverse walk), the node's Y' by replaying
+ * its gather, and all of it is freed after the step; it costs more launches
+ * and gives the same gradients (bit for bit when no row is split into
+ * chunks: the same kernels produce each value; split rows fold their chunks
+ * with atomic adds, whose order can change the last bits).  With flags = 0
+ * the stored form is used
+ * when it fits 80% of the device's free memory, else the recompute form.
+ * sg2v_last_call_peak_bytes reports the call's peak workspace.  Errors as
+ * sg2v_count; SG2V_FP32_SCALED is UNSUPPORTED here.
  */
+#define SG2V_BACKWARD_RECOMPUTE 0x1u
+#define SG2V_BACKWARD_STORE 0x2u
 sg2v_status sg2v_count_backward(const sg2v_graph *graph, const sg2v_plan *plan, const int8_t *colours,
                                 sg2v_precision precision, const double *grad_per_vertex, double *grad_weights,
                                 double *total, uint32_t flags, sg2v_stream stream);
@@ -411,6 +424,15 @@ sg2v_status sg2v_sum_counts_noalloc(const double *values, int64_t n, int32_t nse
 typedef void *(*sg2v_alloc_fn)(size_t bytes, sg2v_stream stream, void *user);
 typedef void (*sg2v_free_fn)(void *ptr, sg2v_stream stream, void *user);
 sg2v_status sg2v_set_allocator(sg2v_alloc_fn alloc, sg2v_free_fn free, void *user);
+
+/*
+ * sg2v_last_call_peak_bytes -- the largest amount of per-call device
+ * workspace (tables, sorted arcs, scratch) that the last sg2v_count,
+ * sg2v_count_batched or sg2v_count_backward call of the calling thread held
+ * at once, in bytes (0 before any call).  Graph, plan and session memory is
+ * not included.
+ */
+int64_t sg2v_last_call_peak_bytes(void);
 
 /* ---------------------------------------------------------------- status */
 

@@ -40,6 +40,8 @@ SG2V_GRAPH_SKIP_VALIDATION = 0x1
 SG2V_GRAPH_KEEP_ORDER = 0x2
 SG2V_CUT_LAST = 0
 SG2V_CUT_MIN_WORK = 1
+SG2V_BACKWARD_RECOMPUTE = 0x1
+SG2V_BACKWARD_STORE = 0x2
 SG2V_SESSION_PER_VERTEX = 0x1
 SG2V_SESSION_NO_GRAPH = 0x2
 SG2V_SESSION_AUTOTUNE = 0x4
@@ -86,6 +88,8 @@ _lib.sg2v_version.argtypes = []
 _lib.sg2v_version.restype = ctypes.c_int32
 _lib.sg2v_launch_count.argtypes = []
 _lib.sg2v_launch_count.restype = ctypes.c_int64
+_lib.sg2v_last_call_peak_bytes.restype = ctypes.c_int64
+_lib.sg2v_last_call_peak_bytes.argtypes = []
 
 
 class PlanOpts(ctypes.Structure):
@@ -260,13 +264,20 @@ def sg2v_sum_counts_noalloc(values, n: int, nseg: int, totals, stream=None) -> N
 
 
 def sg2v_count_backward(graph, plan, colours, precision: int, grad_weights, grad_per_vertex=None,
-                        stream=None) -> float:
+                        stream=None, flags: int = 0) -> float:
     """Fills grad_weights ([nnz] float64) with dF/dw_e per arc; returns the
-    forward total."""
+    forward total.  flags: 0 (form chosen by memory), SG2V_BACKWARD_STORE or
+    SG2V_BACKWARD_RECOMPUTE."""
     t = ctypes.c_double()
     _check(_lib.sg2v_count_backward(graph, plan, _ptr(colours), int(precision), _ptr(grad_per_vertex),
-                                    _ptr(grad_weights), ctypes.byref(t), 0, _stream(stream)), "sg2v_count_backward")
+                                    _ptr(grad_weights), ctypes.byref(t), int(flags), _stream(stream)),
+           "sg2v_count_backward")
     return t.value
+
+
+def sg2v_last_call_peak_bytes() -> int:
+    """Peak per-call device workspace of this thread's last count call."""
+    return int(_lib.sg2v_last_call_peak_bytes())
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

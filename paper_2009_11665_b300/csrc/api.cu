@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -303,13 +304,18 @@ AllocHook current_hook() {
 // Allocations of one call, returned on every exit path: from the caller's
 // allocator when one is set (taken once, at the call's start), else from the
 // library's stream-ordered pool.
+thread_local int64_t g_last_peak_bytes = 0;
+
 struct Workspace {
     cudaStream_t stream;
     cudaMemPool_t pool;
     std::vector<void *> live;
     AllocHook hook = current_hook();
+    std::vector<size_t> sizes;  // of live blocks
+    int64_t in_use = 0, peak = 0;
     ~Workspace() {
         for (void *p : live) give_back(p);
+        g_last_peak_bytes = peak;
     }
     void give_back(void *p) {
         if (hook.alloc)
@@ -331,12 +337,18 @@ struct Workspace {
             if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
         }
         live.push_back(*p);
+        sizes.push_back(bytes);
+        in_use += (int64_t)bytes;
+        peak = std::max(peak, in_use);
         return SG2V_OK;
     }
     void release(void *p) {
         auto it = std::find(live.begin(), live.end(), p);
         if (it != live.end()) {
             give_back(p);
+            const size_t k = (size_t)(it - live.begin());
+            in_use -= (int64_t)sizes[k];
+            sizes.erase(sizes.begin() + (int64_t)k);
             live.erase(it);
         }
     }
@@ -1868,7 +1880,9 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
                                 sg2v_precision precision, const double *grad_per_vertex, double *grad_weights,
                                 double *total, uint32_t flags, sg2v_stream stream_) {
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    if (!g || !plan || !colours || !grad_weights || flags != 0) {
+    if (!g || !plan || !colours || !grad_weights ||
+        (flags & ~(SG2V_BACKWARD_RECOMPUTE | SG2V_BACKWARD_STORE)) ||
+        ((flags & SG2V_BACKWARD_RECOMPUTE) && (flags & SG2V_BACKWARD_STORE))) {
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
@@ -2004,33 +2018,102 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, nnz, d_col, 1, kc,
                                  R.scol, R.sclr, R.sw, no_hist, P.info.sms, stream),
               "colour sort");
-    // forward, keeping every table and every node's Y'
     std::vector<void *> yt(nn, nullptr), gt(nn, nullptr);
     std::vector<int64_t> ldy(nn, 0);
     for (size_t i = 0; i < nn; ++i) {
-        const CNode &c = P.nodes[i];
-        const Shape &sh = P.shape[i];
-        NodeArgs A = node_args(Pw, R, i, 0, 1, d_col);
-        if (!c.is_root) {
-            R.ld[i] = table_ld(P, c);
-            if ((st = alloc(gather_table_bytes(n, 1, R.ld[i], esz), &R.table[i]))) return st;
-            if ((st = zero_gather_row(R.table[i], n, 1, R.ld[i], esz, stream))) return st;
-            if ((st = alloc((size_t)n * R.ld[i] * esz, &gt[i]))) return st;
-            SG2V_CUDA(cudaMemsetAsync(gt[i], 0, (size_t)n * R.ld[i] * esz, stream), "memset");
-            A.Ms = R.table[i];
-            A.ldt = R.ld[i];
+        ldy[i] = (binom(kc - 1, P.nodes[i].p) + vecn - 1) / vecn * vecn;
+        if (!P.nodes[i].is_root) R.ld[i] = table_ld(P, P.nodes[i]);
+    }
+    // Stored form: the forward keeps every table, Y' and gradient table.
+    // Recompute form (SG2V_BACKWARD_RECOMPUTE, or automatically when the
+    // stored form would not fit 80% of free device memory): the forward
+    // frees each table after its last consumer; the reverse walk brings back
+    // the tables of the current node's children by replaying the forward of
+    // their sub-templates (Alg. 5's bottom-up order, from the leaves), and
+    // the node's Y' by replaying its gather, and frees all of it again.
+    bool recompute = (flags & SG2V_BACKWARD_RECOMPUTE) != 0;
+    if (!recompute && !(flags & SG2V_BACKWARD_STORE)) {
+        double stored = 0.0;
+        for (size_t i = 0; i < nn; ++i) {
+            stored += (double)n * ldy[i] * esz;
+            if (!P.nodes[i].is_root) stored += 2.0 * gather_table_bytes(n, 1, R.ld[i], esz);
         }
-        ldy[i] = (binom(kc - 1, c.p) + vecn - 1) / vecn * vecn;
-        if ((st = alloc((size_t)n * ldy[i] * esz, &yt[i]))) return st;
-        A.Yout = yt[i];
-        A.ldy = ldy[i];
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) recompute = stored > 0.8 * (double)free_b;
+        else cudaGetLastError();
+    }
+    // a node's children (distinct, not leaves)
+    auto children = [&](size_t j) {
+        std::vector<int> ch;
+        const CNode &cj = P.nodes[j];
+        if (cj.active != kLeaf) ch.push_back(cj.active);
+        if (cj.passive != kLeaf && cj.passive != cj.active) ch.push_back(cj.passive);
+        return ch;
+    };
+    // one forward node launch writing table j (Yout: also its Y')
+    auto run_node = [&](size_t j, void *Yout) -> sg2v_status {
+        NodeArgs A = node_args(Pw, R, j, 0, 1, d_col);
+        if (!P.nodes[j].is_root) {
+            if (!R.table[j]) {
+                sg2v_status s2 = alloc(gather_table_bytes(n, 1, R.ld[j], esz), &R.table[j]);
+                if (s2) return s2;
+                if ((s2 = zero_gather_row(R.table[j], n, 1, R.ld[j], esz, stream))) return s2;
+            }
+            A.Ms = R.table[j];
+            A.ldt = R.ld[j];
+        }
+        if (Yout) {
+            A.Yout = Yout;
+            A.ldy = ldy[j];
+        }
         if (g->nheavy) {
             SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
             SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
         }
-        timer.begin("backward: forward node", 0.0);
-        SG2V_CUDA(launch_forward_node(P, i, A, stream), "node kernel launch");
+        timer.begin(recompute ? "backward: recomputed forward node" : "backward: forward node", 0.0);
+        SG2V_CUDA(launch_forward_node(P, j, A, stream), "node kernel launch");
         timer.end();
+        return SG2V_OK;
+    };
+    auto drop_table = [&](int j) {
+        if (j != kLeaf && R.table[(size_t)j]) {
+            ws.release(R.table[(size_t)j]);
+            R.table[(size_t)j] = nullptr;
+        }
+    };
+    // recompute form: table j from its sub-template's leaves; tables of j's
+    // children that `keep` does not hold are dropped again afterwards
+    std::vector<char> keep(nn, 0);
+    std::function<sg2v_status(int)> materialize = [&](int j) -> sg2v_status {
+        if (j == kLeaf || R.table[(size_t)j]) return SG2V_OK;
+        const std::vector<int> ch = children((size_t)j);
+        for (int x : ch) {
+            sg2v_status s2 = materialize(x);
+            if (s2) return s2;
+        }
+        sg2v_status s2 = run_node((size_t)j, nullptr);
+        if (s2) return s2;
+        for (int x : ch)
+            if (!keep[(size_t)x]) drop_table(x);
+        return SG2V_OK;
+    };
+    if (!recompute) {
+        // forward, keeping every table and every node's Y'
+        for (size_t i = 0; i < nn; ++i) {
+            if (!P.nodes[i].is_root) {
+                if ((st = alloc((size_t)n * R.ld[i] * esz, &gt[i]))) return st;
+                SG2V_CUDA(cudaMemsetAsync(gt[i], 0, (size_t)n * R.ld[i] * esz, stream), "memset");
+            }
+            if ((st = alloc((size_t)n * ldy[i] * esz, &yt[i]))) return st;
+            if ((st = run_node(i, yt[i]))) return st;
+        }
+    } else {
+        // forward for the total, each table dropped after its last consumer
+        for (size_t i = 0; i < nn; ++i) {
+            if ((st = run_node(i, nullptr))) return st;
+            for (int x : children(i))
+                if (P.nodes[(size_t)x].last_use == (int)i) drop_table(x);
+        }
     }
     if (total) {
         timer.count_extra(2);
@@ -2063,6 +2146,24 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     for (size_t ii = nn; ii-- > 0;) {
         const CNode &c = P.nodes[ii];
         const int wy = (int)binom(kc - 1, c.p), wa = (int)binom(kc - 1, c.a - 1), ws_ = (int)binom(kc - 1, c.t - 1);
+        if (recompute) {
+            // the children's tables, this node's Y' (its table is rewritten
+            // with the same values; the root's per-vertex values likewise),
+            // and zeroed gradient tables for the children
+            const std::vector<int> ch = children(ii);
+            for (int x : ch) keep[(size_t)x] = 1;
+            for (int x : ch)
+                if ((st = materialize(x))) return st;
+            if ((st = alloc((size_t)n * ldy[ii] * esz, &yt[ii]))) return st;
+            if ((st = run_node(ii, yt[ii]))) return st;
+            if (!c.is_root) drop_table((int)ii);
+            for (int x : ch)
+                if (!gt[(size_t)x]) {
+                    if ((st = alloc((size_t)n * R.ld[(size_t)x] * esz, &gt[(size_t)x]))) return st;
+                    SG2V_CUDA(cudaMemsetAsync(gt[(size_t)x], 0, (size_t)n * R.ld[(size_t)x] * esz, stream),
+                              "memset");
+                }
+        }
         void *ybar;
         const int64_t ldyb = ldy[ii];
         if ((st = alloc(gather_table_bytes(n, 1, ldyb, esz), &ybar))) return st;
@@ -2171,6 +2272,18 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         SG2V_CUDA(launch_sddmm(D, P.fp64, P.info.sms, stream), "SDDMM");
         timer.end();
         ws.release(ybar);
+        if (recompute) {
+            // this node is done: its Y', its gradient table and its children's
+            // tables go (a table another parent reads is brought back there)
+            ws.release(yt[ii]);
+            yt[ii] = nullptr;
+            if (gt[ii]) ws.release(gt[ii]);
+            gt[ii] = nullptr;
+            for (int x : children(ii)) {
+                keep[(size_t)x] = 0;
+                drop_table(x);
+            }
+        }
     }
     timer.count_extra(1);
     SG2V_CUDA(launch_symmetrize(part, g->rev, g->arcmap, nnz, gradw, stream), "symmetrize");
@@ -2194,6 +2307,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     }
     return SG2V_OK;
 }
+
+int64_t sg2v_last_call_peak_bytes(void) { return g_last_peak_bytes; }
 
 sg2v_status sg2v_set_allocator(sg2v_alloc_fn alloc, sg2v_free_fn free_fn, void *user) {
     if ((alloc == nullptr) != (free_fn == nullptr)) {

@@ -168,3 +168,71 @@ def test_chunglu200k_tree8_finite_differences(sg):
     sg.sg2v_graph_set_weights(graph.handle, wt)
     euler = float(np.sum(w.astype(np.float64) * grad)) / 2.0
     assert euler == pytest.approx(7 * F64, rel=1e-4)
+
+
+@pytest.mark.parametrize("parent", [si.TREE8.parent, si.TREE10.parent, (-1, 0, 1, 2, 3), (-1, 0, 0, 0, 0),
+                                    (-1, 0, 1, 1, 0, 4, 5)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_recompute_form_matches_stored_form(sg, parent, prec, monkeypatch):
+    """The recompute form (tables rebuilt from the leaves during the reverse
+    walk, Y' replayed) gives the stored form's gradients: bit for bit when no
+    row is split (the chunk size here exceeds every degree), and holds less
+    device memory at its peak."""
+    import torch
+
+    monkeypatch.setenv("SG2V_CHUNK", "100000")
+    k = len(parent)
+    g = si.chung_lu(2000, 12000, 2.3, seed=9)
+    w = si.arc_weights(g, si.edge_weights(g, seed=4))
+    col = torch.from_numpy(si.colouring(g.n, k, 2)).cuda()
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(parent)
+    seedv = torch.from_numpy(np.linspace(0.25, 2.0, g.n)).cuda()
+    out, peak = {}, {}
+    for name, flag in (("store", sg.SG2V_BACKWARD_STORE), ("recompute", sg.SG2V_BACKWARD_RECOMPUTE)):
+        gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        t = sg.sg2v_count_backward(graph.handle, plan.handle, col, sg.PRECISIONS[prec], gw, seedv, flags=flag)
+        peak[name] = sg.sg2v_last_call_peak_bytes()
+        out[name] = (t, gw.cpu().numpy())
+    if prec == "fp64":
+        assert out["store"][0] == out["recompute"][0]
+        assert np.array_equal(out["store"][1], out["recompute"][1])
+    else:
+        # FP32: the recompute form's forward total may use a root kernel form
+        # with another summation order than the stored form's Y'-keeping one
+        assert abs(out["store"][0] - out["recompute"][0]) <= 1e-4 * abs(out["store"][0])
+        np.testing.assert_allclose(out["recompute"][1], out["store"][1], rtol=1e-4,
+                                   atol=1e-4 * np.abs(out["store"][1]).max())
+    assert 0 < peak["recompute"] < peak["store"]
+    # flags = 0 picks a form; its gradients are the same
+    gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+    sg.sg2v_count_backward(graph.handle, plan.handle, col, sg.PRECISIONS[prec], gw, seedv)
+    assert np.array_equal(gw.cpu().numpy(), out["store"][1]) or prec == "fp32"
+
+
+def test_recompute_form_with_split_rows(sg, monkeypatch):
+    """With rows split into chunks of 64 arcs (folded by atomic adds) the two
+    forms agree to the FP64 bar, and both match exact differences of the
+    oracle."""
+    import torch
+
+    monkeypatch.setenv("SG2V_CHUNK", "64")
+    g = si.chung_lu(2000, 12000, 2.3, seed=5)
+    w = si.arc_weights(g, si.edge_weights(g, seed=3))
+    parent = si.TREE8.parent
+    col = si.colouring(g.n, 8, 1)
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(parent)
+    assert int(np.diff(g.row_ptr).max()) > 64
+    res = {}
+    for name, flag in (("store", sg.SG2V_BACKWARD_STORE), ("recompute", sg.SG2V_BACKWARD_RECOMPUTE)):
+        gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        sg.sg2v_count_backward(graph.handle, plan.handle, torch.from_numpy(col).cuda(), sg.SG2V_FP64, gw, flags=flag)
+        res[name] = gw.cpu().numpy()
+    np.testing.assert_allclose(res["recompute"], res["store"], rtol=1e-12, atol=0)
+    ids = si.arc_edge_ids(g)
+    edges = [int(e) for e in si.sample_indices(12, g.m, seed=2)]
+    _, exact = _exact_grad(g, w, parent, col, edges)
+    for e in edges:
+        for a in np.nonzero(ids == e)[0]:
+            assert abs(res["recompute"][a] - float(exact[e])) <= 1e-12 * abs(float(exact[e])) + 1e-300

@@ -15,7 +15,8 @@ seeds, checks the graph fingerprint, and compares:
   totals and 4,000+ sampled per-vertex counts;
 * the differentiable form (Chung-Lu, 200k vertices, FP32 weights, tree8):
   the exact weighted forward and the exact per-edge gradient
-  (F - F(w_e = 0)) / w_e of 64 sampled edges;
+  (F - F(w_e = 0)) / w_e of 64 sampled edges, from both backward forms
+  (tables kept, and tables rebuilt during the reverse walk);
 * the large form (R-MAT scale 20 with 5e7 edges, tree15, k = 15) on two
   colourings: FP32 with per-row exponents against the FP64 tables, which are
   themselves oracle-checked on the scale-12 and scale-16 siblings (the exact
@@ -174,15 +175,17 @@ def test_differentiable_form_matches_oracle(sg):
         assert np.all(got[~nz] == 0), prec
         assert (np.abs(got[nz] - want[nz]) / want[nz]).max() <= tol, prec
         assert abs(tot - float(F)) <= tol * float(F), prec
-        gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
-        t2 = sg.sg2v_count_backward(graph.handle, plan.handle, _dev(col), sg.PRECISIONS[prec], gw)
-        assert abs(t2 - float(F)) <= tol * float(F), prec
-        gw = gw.cpu().numpy()
-        for e, gref in zip(edges, grads):
-            arcs = np.nonzero(ids == e)[0]
-            assert len(arcs) == 2
-            for a in arcs:
-                assert abs(gw[a] - gref) <= tol * abs(gref) + 1e-300, (prec, int(e))
+        # both backward forms: every table kept, or rebuilt during the reverse walk
+        for flag in (sg.SG2V_BACKWARD_STORE, sg.SG2V_BACKWARD_RECOMPUTE):
+            gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+            t2 = sg.sg2v_count_backward(graph.handle, plan.handle, _dev(col), sg.PRECISIONS[prec], gw, flags=flag)
+            assert abs(t2 - float(F)) <= tol * float(F), prec
+            gw = gw.cpu().numpy()
+            for e, gref in zip(edges, grads):
+                arcs = np.nonzero(ids == e)[0]
+                assert len(arcs) == 2
+                for a in arcs:
+                    assert abs(gw[a] - gref) <= tol * abs(gref) + 1e-300, (prec, flag, int(e))
 
 
 def test_large_form_fp32_matches_fp64(sg):

@@ -48,6 +48,99 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def fp64_peak_ops(torch):
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (4096^3, best of 5,
+    CUDA events), in FP64 operations per second counting one fused
+    multiply-add as one operation (the unit of the FP64 node kernels' adds
+    and FMAs)."""
+    nsz = 4096
+    a = torch.randn(nsz, nsz, dtype=torch.float64, device="cuda")
+    b = torch.randn(nsz, nsz, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return float(nsz) ** 3 / (best * 1e-3)
+
+
+def fp32_alu_peak_flops(peaks):
+    """FP32 FMA throughput from unit counts and clocks: 148 SMs x 128 FP32
+    lanes x 2 FLOP per FMA x the maximum SM clock."""
+    return 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6
+
+
+def node_fp64_ops(t, a, p, kc, n, nnz, half_root):
+    """FP64 adds and FMAs of one node launch over n rows (one colouring):
+    the gather adds one compressed row of C(kc-1, p-1) entries per arc to a
+    neighbour of another colour (a colour count for p = 1), Y' sums p
+    per-colour terms for each of its C(kc-1, p) sets, and the eMA does
+    C(t-1, a-1) products per output set (one per p-set at a one-set root)."""
+    from math import comb
+
+    arcs = nnz * (kc - 1) / kc * (0.5 if half_root else 1.0)
+    ops = arcs * (1 if p == 1 else comb(kc - 1, p - 1))
+    ops += n * comb(kc - 1, p) * p
+    if a >= 2:
+        ops += n * (comb(kc - 1, p) if t == kc else comb(kc - 1, t - 1) * comb(t - 1, a - 1))
+    return ops
+
+
+def parse_node(name):
+    """(t, a, p) from a kernel record name 'node t=T a=A p=P ...'."""
+    parts = dict(x.split("=") for x in name.split() if "=" in x)
+    return int(parts["t"]), int(parts["a"]), int(parts["p"])
+
+
+def records_block(records, steps, units):
+    """Per-kernel table and step totals of one block's kernel records."""
+    table = {}
+    step_bytes = step_ms = 0.0
+    for r in records:
+        per = r["total_ms"] / r["launches"]
+        table[r["name"]] = {"launches_per_step": r["launches"] / steps, "ms_per_launch": round(per, 4),
+                            "algorithmic_GB_per_launch": round(r["bytes_per_launch"] / 1e9, 4),
+                            "GBps": round(r["bytes_per_launch"] / (per * 1e-3) / 1e9, 1) if per > 0 else None}
+        step_bytes += r["bytes_per_launch"] * r["launches"] / steps
+        step_ms += r["total_ms"] / steps
+    return table, step_bytes, step_ms
+
+
+def hbm_roofline(name, bytes_per_launch, ms_per_launch, peak, peak_kind):
+    achieved = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind}
+
+
+def gather_rate(rec, g, kc, ms):
+    """Bytes the dominant node kernel gathers per launch (one compressed row
+    of C(kc-1, p-1) FP32 entries per arc to a neighbour of another colour;
+    half the arcs at a root whose children are one table) over its time,
+    against the L2 bandwidth ncu reports as the GPU's peak (profiles/l2_peak.json)."""
+    from math import comb
+
+    t, a, p = parse_node(rec["name"])
+    if p < 2:
+        return None
+    arcs = g.nnz * (kc - 1) / kc * (0.5 if (t == kc and a == p) else 1.0)
+    gathered = arcs * comb(kc - 1, p - 1) * 4
+    out = {"bytes_per_launch": gathered, "GBps": gathered / (ms * 1e-3) / 1e9}
+    try:
+        l2 = json.load(open(os.path.join(ROOT, "profiles", "l2_peak.json")))
+        out.update({"l2_peak_GBps": l2["l2_peak_GBps"], "frac_of_l2_peak": out["GBps"] / l2["l2_peak_GBps"],
+                    "l2_peak_source": l2["source"]})
+    except (OSError, KeyError, ValueError):
+        pass
+    return out
+
+
 def source_digest() -> str:
     """Digest of the sources that decide what a node launch does (kernels and
     the executor that sets its launch configuration)."""
@@ -217,7 +310,7 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
 def profile_call(args):
     """One sg2v_count_batched call (B = --batch colourings): tree10 on an
     R-MAT graph with the workload's parameters and average degree 32
-    (rmat18, rmat20), or tree15 with k = 15 on the large form's scale-17
+    (rmat18, rmat19, rmat20), or tree15 with k = 15 on the large form's scale-17
     sibling (large17: 6.25e6 edges, average degree about 95)."""
     import torch
 
@@ -231,7 +324,7 @@ def profile_call(args):
         g = si.rmat(17, 50_000_000 >> 3, seed=0)
         template, kc = si.TREE15, 15
     else:
-        scale = 18 if args.profile_call == "rmat18" else 20
+        scale = {"rmat18": 18, "rmat19": 19, "rmat20": 20}[args.profile_call]
         g = si.rmat(scale, (1 << scale) * 16, seed=0)
         template, kc = TEMPLATE, K_COLOURS
     graph = sg.Graph(g.row_ptr, g.col_idx)
@@ -256,8 +349,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3-template x 64-colouring session block")
     ap.add_argument("--no-large", action="store_true", help="skip the tree15 (k = 15) large-form block")
-    ap.add_argument("--profile-call", choices=["rmat18", "rmat20", "large17"], default=None,
-                    help="run exactly one count call (R-MAT scale 18 or 20 with avg degree 32 and tree10, or the "
+    ap.add_argument("--profile-call", choices=["rmat18", "rmat19", "rmat20", "large17"], default=None,
+                    help="run exactly one count call (R-MAT scale 18, 19 or 20 with avg degree 32 and tree10, or the "
                          "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
                          "summaries capture")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled", "u64", "u128"], default="fp32")
@@ -311,11 +404,28 @@ def main():
     def step_fp64():
         sg.sg2v_count_batched(graph.handle, [plan.handle], d_cols[0:1], 1, sg.SG2V_FP64, None, tot64, None, stream)
 
-    # plain FP64 form
-    ms64 = time_steps(torch, step_fp64, max(3, args.steps // 2), args.warmup, stream, dist)
+    # plain FP64 form: event records of its kernels over the timed steps, and
+    # the FP64 operation rate of its node kernels against measured DGEMM
+    peaks, peak_kind = measured_peaks()
+    steps64 = max(3, args.steps // 2)
+    for _ in range(args.warmup):
+        step_fp64()
+    torch.cuda.synchronize()
+    sg.sg2v_profile_reset()
+    sg.sg2v_profile_enable(True)
+    ms64 = time_steps(torch, step_fp64, steps64, 0, stream, dist)
+    sg.sg2v_profile_enable(False)
+    rec64 = sg.sg2v_profile_read()
+    fp64_ops_peak = fp64_peak_ops(torch)
+    ops64 = ms_nodes64 = 0.0
+    for r in rec64:
+        if r["name"].startswith("node"):
+            t, a, p = parse_node(r["name"])
+            ops64 += node_fp64_ops(t, a, p, K_COLOURS, g.n, g.nnz, half_root=(t == len(TEMPLATE.parent) and a == p)) \
+                * r["launches"] / steps64
+            ms_nodes64 += r["total_ms"] / steps64
 
     # FP32-batched form (the headline): kernel records collected over the timed region
-    peaks, peak_kind = measured_peaks()
     for _ in range(args.warmup):
         step_fp32()
     torch.cuda.synchronize()
@@ -360,9 +470,23 @@ def main():
                          dist)
         ses.sync(stream)
         wave3, graph_on = ses.info()
+        # kernel records of separate (profiled) steps: algorithmic bytes per step over the step time
+        sg.sg2v_profile_reset()
+        sg.sg2v_profile_enable(True)
+        for _ in range(3):
+            ses.run(cols3, tot3, None, None, stream)
+        ses.sync(stream)
+        torch.cuda.synchronize()
+        sg.sg2v_profile_enable(False)
+        tab3, bytes3, kms3 = records_block(sg.sg2v_profile_read(), 3, 1)
+        dom3 = max(tab3.items(), key=lambda kv: kv[1]["ms_per_launch"] * kv[1]["launches_per_step"])
         batched = {"workload": "rmat18_d16 (R-MAT scale 18, avg degree 16), path7+star7+tree7, k=7, 64 colourings",
                    "ms_per_step": ms3, "s_per_colouring_template": ms3 * 1e-3 / (B3 * 3 * world),
-                   "wave": wave3, "cuda_graph": graph_on, "dtype": "f32"}
+                   "wave": wave3, "cuda_graph": graph_on, "dtype": "f32",
+                   "kernel_ms_per_step": kms3, "algorithmic_GB_per_step": bytes3 / 1e9,
+                   "roofline": dict(hbm_roofline("whole step", bytes3, ms3, float(peaks["hbm_gbs"]), peak_kind),
+                                    dominant_kernel=dom3[0], dominant_GBps=dom3[1]["GBps"]),
+                   "kernels": tab3}
         ses.close()
 
     # differentiable form: Chung-Lu 200k (avg degree 20, gamma 2.3), FP32 weights
@@ -376,15 +500,43 @@ def main():
         col4 = torch.from_numpy(si.colouring(g4.n, 8, rank)).cuda()
         grad4 = torch.empty(g4.nnz, dtype=torch.float64, device="cuda")
         tot4 = torch.empty((1, 1), dtype=torch.float64, device="cuda")
-        ms_f = time_steps(torch, lambda: sg.sg2v_count_batched(graph4.handle, [plan4.handle], col4, 1, sg.SG2V_FP32,
-                                                               None, tot4, None, stream),
-                          max(3, args.steps // 2), args.warmup, stream, dist)
-        ms_b = time_steps(torch, lambda: sg.sg2v_count_backward(graph4.handle, plan4.handle, col4, sg.SG2V_FP32,
-                                                                grad4, None, stream),
-                          max(3, args.steps // 2), args.warmup, stream, dist)
+        reps4 = max(3, args.steps // 2)
+
+        def fwd4():
+            sg.sg2v_count_batched(graph4.handle, [plan4.handle], col4, 1, sg.SG2V_FP32, None, tot4, None, stream)
+
+        def bwd4(flag):
+            return lambda: sg.sg2v_count_backward(graph4.handle, plan4.handle, col4, sg.SG2V_FP32, grad4, None, stream,
+                                                  flags=flag)
+
+        def profiled(fn, reps):
+            sg.sg2v_profile_reset()
+            sg.sg2v_profile_enable(True)
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            sg.sg2v_profile_enable(False)
+            return records_block(sg.sg2v_profile_read(), reps, 1)
+
+        ms_f = time_steps(torch, fwd4, reps4, args.warmup, stream, dist)
+        ms_b = time_steps(torch, bwd4(sg.SG2V_BACKWARD_STORE), reps4, args.warmup, stream, dist)
+        peak_store = sg.sg2v_last_call_peak_bytes()
+        ms_r = time_steps(torch, bwd4(sg.SG2V_BACKWARD_RECOMPUTE), reps4, args.warmup, stream, dist)
+        peak_rec = sg.sg2v_last_call_peak_bytes()
+        tab_f, bytes_f, _ = profiled(fwd4, 3)
+        tab_b, bytes_b, _ = profiled(bwd4(sg.SG2V_BACKWARD_STORE), 3)
+        tab_r, bytes_r, _ = profiled(bwd4(sg.SG2V_BACKWARD_RECOMPUTE), 3)
+        hbm = float(peaks["hbm_gbs"])
         differentiable = {"workload": "chunglu200k (200k vertices, 2M edges, gamma 2.3, weights [0.5,1.5)), tree8, "
                                       "k=8, one colouring", "forward_ms": ms_f, "forward_and_gradient_ms": ms_b,
-                          "dtype": "f32"}
+                          "forward_and_gradient_recompute_ms": ms_r, "peak_workspace_bytes": peak_store,
+                          "peak_workspace_bytes_recompute": peak_rec, "dtype": "f32",
+                          "roofline_forward": hbm_roofline("forward step", bytes_f, ms_f, hbm, peak_kind),
+                          "roofline_forward_and_gradient": hbm_roofline("forward+gradient step", bytes_b, ms_b, hbm,
+                                                                        peak_kind),
+                          "roofline_forward_and_gradient_recompute": hbm_roofline("forward+gradient step (recompute)",
+                                                                                  bytes_r, ms_r, hbm, peak_kind),
+                          "kernels_forward": tab_f, "kernels_forward_and_gradient": tab_b}
 
     # exact integer tables: the same Chung-Lu graph unweighted, tree8, k = 8,
     # one colouring per call; its table entries reach 2^61, past the 2^53 up
@@ -427,12 +579,34 @@ def main():
         B5 = 8
         cols5 = torch.from_numpy(rank_colourings(g5.n, 15, B5, rank, seed=0)).cuda()
         tot5 = torch.empty((1, B5), dtype=torch.float64, device="cuda")
-        ms5 = time_steps(torch, lambda: sg.sg2v_count_batched(graph5.handle, [plan5.handle], cols5, B5,
-                                                              sg.SG2V_FP32_SCALED, None, tot5, None, stream),
-                         2, 1, stream, dist)
+        def step5():
+            sg.sg2v_count_batched(graph5.handle, [plan5.handle], cols5, B5, sg.SG2V_FP32_SCALED, None, tot5, None,
+                                  stream)
+
+        ms5 = time_steps(torch, step5, 2, 1, stream, dist)
+        sg.sg2v_profile_reset()
+        sg.sg2v_profile_enable(True)
+        step5()
+        torch.cuda.synchronize()
+        sg.sg2v_profile_enable(False)
+        tab5, bytes5, _ = records_block(sg.sg2v_profile_read(), 1, 1)
+        from math import comb
+
+        # the deferred eMA of the (10,5,5) node: 2 FLOP per product, C(14,9) sets x C(9,4) splits per row
+        ema5 = [(k, v) for k, v in tab5.items() if k.startswith("ema t=10 a=5 p=5")]
+        ema_roof = None
+        if ema5:
+            k5, v5 = ema5[0]
+            flops = 2.0 * comb(14, 9) * comb(9, 4) * g5.n * B5 / v5["launches_per_step"]
+            achieved = flops / (v5["ms_per_launch"] * 1e-3) / 1e12
+            alu = fp32_alu_peak_flops(peaks) / 1e12
+            ema_roof = {"kernel": k5, "bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                        "frac": achieved / alu, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock"}
         large = {"workload": "rmat20_50m (R-MAT scale 20, 5e7 edges), tree15, k=15, 8 colourings per call",
                  "ms_per_call": ms5, "s_per_colouring": ms5 * 1e-3 / B5, "dtype": "f32 with per-row exponents",
-                 "max_total": float(tot5.max().item()), "steps": 2, "warmup": 1}
+                 "max_total": float(tot5.max().item()), "steps": 2, "warmup": 1,
+                 "roofline": hbm_roofline("whole step", bytes5, ms5, float(peaks["hbm_gbs"]), peak_kind),
+                 "roofline_deferred_ema": ema_roof, "kernels": tab5}
         del graph5, g5
 
     if rank != 0:
@@ -473,14 +647,22 @@ def main():
                    "plan": f"cut {PLAN_CUT} (avg degree 32): nodes {[n[:3] for n in plan.nodes()]}",
                    "parallelism": f"replicas over colourings x{world}",
                    "l2": "inputs larger than L2: count tables of 1-8 GB per step"},
-        "fp64_plain": {"s_per_colouring": fp64_s, "ms_per_step": ms64, "dtype": "f64"},
+        "fp64_plain": {"s_per_colouring": fp64_s, "ms_per_step": ms64, "dtype": "f64",
+                       "roofline": {"kernel": "node kernels of one colouring", "bound": "fp64",
+                                    "achieved": ops64 / (ms_nodes64 * 1e-3) / 1e12,
+                                    "peak": fp64_ops_peak / 1e12, "unit": "TOP/s (FP64 add or FMA)",
+                                    "frac": ops64 / (ms_nodes64 * 1e-3) / fp64_ops_peak,
+                                    "peak_kind": "measured: cuBLAS DGEMM 4096^3 on this GPU, FMA = 1 op",
+                                    "ops_per_colouring": ops64, "node_ms_per_colouring": ms_nodes64},
+                       "kernels": records_block(rec64, steps64, 1)[0]},
         "fp32_batched": {"s_per_colouring": value, "ms_per_step": ms32, "B": B},
         "speedup_fp32_batched_vs_fp64_plain": fp64_s / value,
         "hbm": {"algorithmic_GB_per_step": step_bytes / 1e9, "GBps_step": step_bytes / (ms32 * 1e-3) / 1e9,
                 "frac_of_measured_peak": step_bytes / (ms32 * 1e-3) / 1e9 / peak,
                 "frac_of_nameplate_8TBps": step_bytes / (ms32 * 1e-3) / 1e9 / 8000.0},
         "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic},
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "gather": gather_rate(dom, g, K_COLOURS, dom_ms)},
         "kernels": kernel_table,
         "batched_3_templates": batched,
         "differentiable": differentiable,

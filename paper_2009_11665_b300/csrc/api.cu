@@ -216,7 +216,7 @@ sg2v_status run_map(int dev, int kc, int t, int a, int form, int wmap, int sink,
 struct ProfRecord {
     int64_t launches = 0;
     double total_ms = 0.0;
-    double bytes = 0.0;
+    double bytes = 0.0;  // summed over the launches
 };
 std::mutex g_prof_mutex;
 bool g_prof_enabled = false;
@@ -267,7 +267,7 @@ struct CallTimer {
                 ProfRecord &r = g_prof[it.name];
                 r.launches += 1;
                 r.total_ms += ms;
-                r.bytes = it.bytes;
+                r.bytes += it.bytes;
             }
         }
         cudaGetLastError();
@@ -2070,7 +2070,16 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
             SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
         }
-        timer.begin(recompute ? "backward: recomputed forward node" : "backward: forward node", 0.0);
+        {
+            const CNode &cj = P.nodes[j];
+            const double rows = (double)n;
+            double b = 8.0 * (n + 1) + (double)nnz * (5.0 + (g->weighted ? 4.0 : 0.0)) + rows;
+            if (cj.p >= 2) b += rows * binom(kc - 1, cj.p - 1) * (double)esz;
+            if (cj.a >= 2 && cj.active != cj.passive) b += rows * binom(kc - 1, cj.a - 1) * (double)esz;
+            b += cj.is_root ? rows * (double)esz : rows * binom(kc - 1, cj.t - 1) * (double)esz;
+            if (Yout) b += rows * binom(kc - 1, cj.p) * (double)esz;
+            timer.begin(recompute ? "backward: recomputed forward node" : "backward: forward node", b);
+        }
         SG2V_CUDA(launch_forward_node(P, j, A, stream), "node kernel launch");
         timer.end();
         return SG2V_OK;
@@ -2194,7 +2203,14 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         E.nybar = btab[ii].nybar;
         E.mabar = d_mabar[ii];
         E.nmabar = btab[ii].nmabar;
-        timer.begin("backward: eMA", 0.0);
+        {
+            // algorithmic bytes: G (or the seed), M_a and Y' read, Ybar written,
+            // the active child's gradient read and written
+            const double rows = (double)n;
+            double b = rows * ((c.is_root ? 8.0 : ws_ * (double)esz) + wy * (double)esz * 2.0);
+            if (c.a >= 2) b += rows * wa * (double)esz * 3.0;
+            timer.begin("backward: eMA", b);
+        }
         SG2V_CUDA(launch_bwd_ema(E, P.fp64, P.info.sms, stream), "backward eMA");
         timer.end();
         if (c.p >= 2) {
@@ -2232,7 +2248,11 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
                 SG2V_CUDA(cudaMemsetAsync(R.scratch, 0, R.scratch_bytes, stream), "memset");
                 SG2V_CUDA(cudaMemsetAsync(R.counters, 0, R.counter_bytes, stream), "memset");
             }
-            timer.begin("backward: transposed SpMM", 0.0);
+            // algorithmic bytes: the sorted arcs and row pointers, Ybar read once,
+            // the passive child's gradient read and written
+            timer.begin("backward: transposed SpMM",
+                        (double)nnz * (5.0 + (g->weighted ? 4.0 : 0.0)) + 8.0 * (n + 1) +
+                            (double)n * (wy + 2.0 * binom(kc - 1, c.p - 1)) * (double)esz);
             SG2V_CUDA(launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
                                   stream),
                       "transposed SpMM launch");
@@ -2268,7 +2288,10 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
                 D.wz_pad = lanes * vecs * vecn;
             }
         }
-        timer.begin("backward: SDDMM", 0.0);
+        // algorithmic bytes: the CSR, the colouring, Ybar and M_p read once,
+        // the per-arc partial gradient read and written
+        timer.begin("backward: SDDMM", (double)nnz * (4.0 + 16.0) + 8.0 * (n + 1) + (double)n +
+                                           (double)n * (wy + (c.p >= 2 ? binom(kc - 1, c.p - 1) : 0)) * (double)esz);
         SG2V_CUDA(launch_sddmm(D, P.fp64, P.info.sms, stream), "SDDMM");
         timer.end();
         ws.release(ybar);
@@ -2366,7 +2389,7 @@ sg2v_status sg2v_profile_read(sg2v_kernel_record *out, int32_t capacity, int32_t
             std::snprintf(out[i].name, sizeof out[i].name, "%s", kv.first.c_str());
             out[i].launches = kv.second.launches;
             out[i].total_ms = kv.second.total_ms;
-            out[i].bytes_per_launch = kv.second.bytes;
+            out[i].bytes_per_launch = kv.second.launches ? kv.second.bytes / (double)kv.second.launches : 0.0;
         }
         ++i;
     }

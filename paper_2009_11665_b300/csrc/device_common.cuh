@@ -436,7 +436,7 @@ __device__ __forceinline__ void spmm_z(const NodeArgs &A, int v, int64_t e0, int
         const int c_in = lane < cnt_in ? (int)__ldg(sclr + base + lane) : -1;
         bool t_in = c_in >= 0 && c_in != cv;
         const int u_in = t_in ? __ldg(scol + base + lane) : zero_row;
-        if (A.half_arcs && u_in <= v) t_in = false;
+        if (A.half_arcs && u_in >= v) t_in = false;
         // compact the batch to the arcs that add something (order kept, so
         // colour runs stay contiguous): lane j takes the j-th such arc
         const unsigned live_in = __ballot_sync(kFull, t_in);

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kNodeThreads, MinBlocks<T, 1>::value) node_gro
                 const int c_in = in ? (int)__ldg(sclr + base + gl) : -1;
                 bool t_in = c_in >= 0 && c_in != cv;
                 const int u_in = t_in ? __ldg(scol + base + gl) : zero_row;
-                if (A.half_arcs && u_in <= v) t_in = false;
+                if (A.half_arcs && u_in >= v) t_in = false;
                 const unsigned live = (__ballot_sync(kFull, t_in) & gbits) >> g0;
                 const int cnt = __popc(live);
                 const int cnt_w = __reduce_max_sync(kFull, (unsigned)cnt);

@@ -89,8 +89,10 @@ struct NodeArgs {
     int accumulate;
     // root whose active and passive children are one table, totals only: the
     // contribution of an arc (v, u) to v's count equals that of (u, v) to u's,
-    // so only arcs with u > v are gathered and the row sum is doubled (the
-    // per-vertex values are then not the per-vertex counts)
+    // so only arcs with u < v are gathered and the row sum is doubled (the
+    // per-vertex values are then not the per-vertex counts); with vertices
+    // numbered by decreasing degree the gathered row is the edge's hub end,
+    // the one most likely in L2
     int half_arcs;
     // large eMA: the gather kernel stores Y' rows in Yout (ldy) and skips the
     // eMA, which launch_ema_rows then runs over blocks of rows

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 const bool in = lane < cnt_in;
                 const int c_in = in ? (int)__ldg(sclr + base + lane) : -1;
                 const int u_in = in ? __ldg(scol + base + lane) : 0;
-                const bool t_in = cok && c_in >= 0 && c_in != cv && (!A.half_arcs || u_in > v);
+                const bool t_in = cok && c_in >= 0 && c_in != cv && (!A.half_arcs || u_in < v);
                 // compact the batch to the arcs that add something (order kept,
                 // so colour runs stay contiguous) through the warp's slots
                 const unsigned live = __ballot_sync(kFull, t_in);

@@ -470,6 +470,7 @@ def main():
                          dist)
         ses.sync(stream)
         wave3, graph_on = ses.info()
+        tuning3 = ses.tuning()
         # kernel records of separate (profiled) steps: algorithmic bytes per step over the step time
         sg.sg2v_profile_reset()
         sg.sg2v_profile_enable(True)
@@ -483,6 +484,8 @@ def main():
         batched = {"workload": "rmat18_d16 (R-MAT scale 18, avg degree 16), path7+star7+tree7, k=7, 64 colourings",
                    "ms_per_step": ms3, "s_per_colouring_template": ms3 * 1e-3 / (B3 * 3 * world),
                    "wave": wave3, "cuda_graph": graph_on, "dtype": "f32",
+                   "autotuned": [f"({n['t']},{n['a']},{n['p']}) {n['kernel']}{', lane groups' if n['lane_groups'] else ''}"
+                                 for n in tuning3["nodes"]],
                    "kernel_ms_per_step": kms3, "algorithmic_GB_per_step": bytes3 / 1e9,
                    "roofline": dict(hbm_roofline("whole step", bytes3, ms3, float(peaks["hbm_gbs"]), peak_kind),
                                     dominant_kernel=dom3[0], dominant_GBps=dom3[1]["GBps"]),

@@ -297,7 +297,7 @@ typedef struct sg2v_session sg2v_session;
 
 #define SG2V_SESSION_PER_VERTEX 0x1u /* keep per-vertex counts ([plans][B][n] doubles) */
 #define SG2V_SESSION_NO_GRAPH 0x2u   /* launch kernels directly instead of replaying a CUDA graph */
-#define SG2V_SESSION_AUTOTUNE 0x4u   /* the first run times candidate wave widths and keeps the fastest */
+#define SG2V_SESSION_AUTOTUNE 0x4u   /* the first run times candidate wave widths and node forms (below) */
 
 /*
  * sg2v_session_create -- plans as in sg2v_count_batched (same num_colours),
@@ -326,6 +326,27 @@ sg2v_status sg2v_session_sync(sg2v_session *session, sg2v_stream stream);
 /* Wave width in use (colourings sharing a table row) and whether runs replay
  * a CUDA graph.  Either output may be NULL. */
 sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_t *graph);
+
+/*
+ * Autotuning (SG2V_SESSION_AUTOTUNE).  The first run times the candidate
+ * wave widths, then, at the chosen width, the forms each DP node can take:
+ * the run-scatter kernel or per-colour accumulators, short narrow rows one
+ * per lane group or one per warp, histogram nodes 32 rows per warp or one,
+ * a large eMA in its own launch or in the gather's epilogue.  Each node
+ * keeps its fastest form (per-node CUDA-event times; results do not depend
+ * on the form).  When the environment variable SG2V_TUNE_CACHE names a file,
+ * the choices are stored there as JSON, keyed by graph statistics (vertices,
+ * arcs, largest degree, weights), colours, node shape, table type and wave,
+ * and a later session whose nodes are all in the file takes them without
+ * timing.
+ *
+ * sg2v_session_tuning -- the session's choices as JSON text
+ * ({"wave": W, "tuned": bool, "nodes": [{"t", "a", "p", "kernel",
+ * "lane_groups", "deferred_ema", "form"}, ...]}), NUL-terminated in out
+ * (capacity bytes, truncated if short); *length (may be NULL) gets the full
+ * length without the NUL.
+ */
+sg2v_status sg2v_session_tuning(const sg2v_session *session, char *out, int64_t capacity, int64_t *length);
 
 sg2v_status sg2v_session_destroy(sg2v_session *session);
 

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "sg2v_session_run": [_p, _p, _p, _p, _p, _p],
     "sg2v_session_sync": [_p, _p],
     "sg2v_session_info": [_p, _p, _p],
+    "sg2v_session_tuning": [_p, ctypes.c_char_p, _i64, _p],
     "sg2v_session_destroy": [_p],
     "sg2v_count_backward": [_p, _p, _p, ctypes.c_int, _p, _p, _p, _u32, _p],
     "sg2v_graph_set_weights": [_p, _p, _p],
@@ -359,6 +360,17 @@ def sg2v_session_info(session):
     return w.value, bool(gr.value)
 
 
+def sg2v_session_tuning(session) -> dict:
+    """The session's wave and per-node kernel forms (see include/sg2v.h)."""
+    import json
+
+    n = ctypes.c_int64()
+    _check(_lib.sg2v_session_tuning(session, None, 0, ctypes.byref(n)), "sg2v_session_tuning")
+    buf = ctypes.create_string_buffer(int(n.value) + 1)
+    _check(_lib.sg2v_session_tuning(session, buf, len(buf), None), "sg2v_session_tuning")
+    return json.loads(buf.value.decode())
+
+
 def sg2v_session_destroy(session) -> None:
     _check(_lib.sg2v_session_destroy(session), "sg2v_session_destroy")
 
@@ -475,6 +487,9 @@ class Session:
 
     def info(self):
         return sg2v_session_info(self.handle)
+
+    def tuning(self):
+        return sg2v_session_tuning(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

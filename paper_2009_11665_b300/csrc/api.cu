@@ -231,18 +231,21 @@ struct CallTimer {
         std::string name;
         double bytes;
         cudaEvent_t a, b;
+        int node;
     };
     std::vector<Item> items;
     cudaStream_t stream = nullptr;
     int open = -1;
+    bool global = true;                   // add to the process-wide records
+    std::vector<double> *node_ms = nullptr;  // per-node milliseconds (autotuning)
     CallTimer(cudaStream_t s) : stream(s) {
         std::lock_guard<std::mutex> lock(g_prof_mutex);
         on = g_prof_enabled;
     }
-    void begin(const std::string &name, double bytes) {
+    void begin(const std::string &name, double bytes, int node = -1) {
         if (count) g_launches.fetch_add(1);
         if (!on) return;
-        Item it{name, bytes, nullptr, nullptr};
+        Item it{name, bytes, nullptr, nullptr, node};
         cudaEventCreate(&it.a);
         cudaEventCreate(&it.b);
         cudaEventRecord(it.a, stream);
@@ -264,6 +267,8 @@ struct CallTimer {
         for (auto &it : items) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, it.a, it.b) == cudaSuccess) {
+                if (node_ms && it.node >= 0 && it.node < (int)node_ms->size()) (*node_ms)[(size_t)it.node] += ms;
+                if (!global) continue;
                 ProfRecord &r = g_prof[it.name];
                 r.launches += 1;
                 r.total_ms += ms;
@@ -551,6 +556,7 @@ struct CNode {
     int active, passive;  // combined ids or kLeaf
     bool is_root;
     int last_use;
+    std::string canon;    // AHU form of the rooted sub-template
 };
 
 // Launch shape of one node: gather width, Z layout, shared memory, block size.
@@ -569,6 +575,12 @@ struct Shape {
     // launch: its run maps into Y' (forms 0 and 1) and into the active row
     // (form 2: root with t = kc), and its own launch shape
     bool run = false;
+    // the forms this node can take (the autotuner picks among them) and the
+    // launch shapes they need: the plain one-task-per-warp kernel, the
+    // lane-group kernel for short rows, the 32-rows-per-warp histogram kernel
+    bool can_run = false, can_group = false, can_rows = false, can_defer = false;
+    int p_threads = 0, p_bps = 0, g_threads = 0, g_bps = 0, r_threads = 0, r_bps = 0;
+    size_t p_smem = 0, g_smem = 0, r_smem = 0;
     const uint16_t *runmap_y = nullptr;
     const uint16_t *runmap_m = nullptr;
     int wmap = 0, mzero = 0;
@@ -601,6 +613,31 @@ struct Prepared {
     int64_t defer_words = 0;      // largest deferred node's Y' row stride (0: none)
     size_t zglobal_bytes = 0;     // global Z of CTA-wide rows that do not fit shared memory
 };
+
+// Sets a node's form and the launch shape it needs (only forms the node can
+// take are set).
+void apply_form(Shape &sh, bool group, bool rows, bool run_off, bool defer_off) {
+    sh.group = group && sh.can_group;
+    sh.rows = rows && sh.can_rows;
+    if (sh.can_run) sh.run = !run_off;
+    if (sh.can_defer) sh.defer = !defer_off;
+    if (sh.rows) {
+        sh.threads = sh.r_threads;
+        sh.smem = sh.r_smem;
+        sh.blocks_per_sm = sh.r_bps;
+    } else if (sh.group) {
+        sh.wthreads = sh.p_threads;
+        sh.wsmem = sh.p_smem;
+        sh.wbps = sh.p_bps;
+        sh.threads = sh.g_threads;
+        sh.smem = sh.g_smem;
+        sh.blocks_per_sm = sh.g_bps;
+    } else {
+        sh.threads = sh.p_threads;
+        sh.smem = sh.p_smem;
+        sh.blocks_per_sm = sh.p_bps;
+    }
+}
 
 const char *elem_name(const Prepared &P) {
     if (P.scaled) return "fp32s";
@@ -659,7 +696,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
                 }
             }
             CNode c{pn.t, pn.a, pn.p, pn.active == kLeaf ? kLeaf : remap[pn.active],
-                    pn.passive == kLeaf ? kLeaf : remap[pn.passive], pn.is_root, -1};
+                    pn.passive == kLeaf ? kLeaf : remap[pn.passive], pn.is_root, -1, pn.canon};
             P->nodes.push_back(c);
             remap[i] = (int)P->nodes.size() - 1;
             if (!pn.is_root) shared[pn.canon] = remap[i];
@@ -741,6 +778,9 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         if (sh.zglobal)
             P->zglobal_bytes = std::max(P->zglobal_bytes, (size_t)P->info.sms * std::max(sh.blocks_per_sm, 1) *
                                                               (size_t)sh.zwords * P->esz);
+        sh.p_threads = sh.threads;
+        sh.p_smem = sh.smem;
+        sh.p_bps = sh.blocks_per_sm;
         const char *group_env = std::getenv("SG2V_GROUP_ROWS");
         if (!hist && sh.grp < 32 && sh.nv == 1 && !(group_env && std::atoi(group_env) == 0)) {
             // narrow rows: every lane group takes its own row
@@ -755,14 +795,11 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
                                                                                  g->weights != nullptr, threads, smem,
                                                                                  true))
                                                : 0;
-            if (bps >= 1) {
-                sh.group = true;
-                sh.wthreads = sh.threads;
-                sh.wsmem = sh.smem;
-                sh.wbps = sh.blocks_per_sm;
-                sh.threads = threads;
-                sh.smem = smem;
-                sh.blocks_per_sm = bps;
+            if (bps >= 1 && sh.p_bps >= 1) {
+                sh.can_group = true;
+                sh.g_threads = threads;
+                sh.g_smem = smem;
+                sh.g_bps = bps;
             }
         }
         const char *rows_env = std::getenv("SG2V_HIST_ROWS");
@@ -777,12 +814,15 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
                                 ? hist_rows_blocks_per_sm(P->elem, P->scaled, g->weights != nullptr, threads, smem)
                                 : 0;
             if (bps >= 1) {
-                sh.rows = true;
-                sh.threads = threads;
-                sh.smem = smem;
-                sh.blocks_per_sm = bps;
+                sh.can_rows = true;
+                sh.r_threads = threads;
+                sh.r_smem = smem;
+                sh.r_bps = bps;
             }
         }
+        // the default forms: lane groups for short narrow rows, 32 rows per
+        // warp for histogram nodes (each measured faster on B300)
+        apply_form(sh, sh.can_group, sh.can_rows, false, false);
         if (sh.blocks_per_sm < 1) {
             set_error("node kernel cannot be resident with its shared memory");
             return SG2V_ERR_UNSUPPORTED;
@@ -808,7 +848,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             const int bps =
                 node_run_blocks_per_sm(P->elem, sh.grp, sh.nv, g->weights != nullptr, form, threads, smem);
             if (bps >= 1) {
-                sh.run = true;
+                sh.run = sh.can_run = true;
                 sh.wmap = sh.grp * sh.nv * E;
                 sh.mzero = mbase;
                 if ((st = run_map(P->dev, kc, c.t, c.a, 0, sh.wmap, ybase, &sh.runmap_y))) return st;
@@ -833,7 +873,7 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             probe.Ws = (int)binom(kc - 1, c.t - 1);
             const size_t smem = ema_rows_smem(probe, P->elem, P->scaled);
             if (ema_rows_blocks_per_sm(P->elem, P->scaled, smem) >= 1) {
-                sh.defer = true;
+                sh.defer = sh.can_defer = true;
                 sh.ldy = (probe.wy + P->vecn - 1) / P->vecn * P->vecn;
                 P->defer_words = std::max<int64_t>(P->defer_words, sh.ldy);
             }
@@ -1223,7 +1263,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                 char name[64];
                 std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p,
                               elem_name(P));
-                timer.begin(name, bytes);
+                timer.begin(name, bytes, (int)i);
             }
             if (sh.defer) {
                 A.defer = 1;
@@ -1238,7 +1278,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                 char name[64];
                 std::snprintf(name, sizeof name, "ema t=%d a=%d p=%d %s", c.t, c.a, c.p,
                               elem_name(P));
-                timer.begin(name, rows * esz * (double)(sh.ldy + binom(kc - 1, c.a - 1) + A.Ws));
+                timer.begin(name, rows * esz * (double)(sh.ldy + binom(kc - 1, c.a - 1) + A.Ws), (int)i);
                 SG2V_CUDA(launch_ema_rows(A, P.elem, P.scaled, P.info.sms, stream), "eMA launch");
                 timer.end();
             }
@@ -1404,10 +1444,17 @@ struct FixedTables : TableSource {
 };
 
 // One run of the session's sequence on stream (no synchronisation).
-sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bool capturing = false) {
+sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bool capturing = false,
+                            std::vector<double> *node_ms = nullptr) {
     CallTimer timer(stream);
     if (!timed) timer.on = false;
     if (capturing) timer.count = false;
+    if (node_ms) {
+        // autotuning: per-node times only, nothing in the process-wide records
+        timer.on = true;
+        timer.global = false;
+        timer.node_ms = node_ms;
+    }
     FixedTables src(S->R.table);
     sg2v_status st = enqueue(S->P, S->R, S->colours, S->pv, src, stream, timer);
     if (st) return st;
@@ -1415,11 +1462,145 @@ sg2v_status session_enqueue(sg2v_session *S, cudaStream_t stream, bool timed, bo
     SG2V_CUDA(launch_finalize(S->R.sums, nseg, S->P.nb, S->scale, S->scale + S->P.plans.size(), S->totals,
                               S->estimates, S->R.status, stream),
               "finalize");
-    if (timed) {
+    if (timed || node_ms) {
         cudaError_t e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
         timer.collect();
     }
+    return SG2V_OK;
+}
+
+// ---- autotuning of the node kernels' forms
+//
+// Every node may take a few forms (Shape::can_*): the run-scatter kernel or
+// per-colour accumulators (node_kernel), lane groups for short narrow rows
+// or one row per warp, 32 histogram rows per warp or one, the eMA in its own
+// launch or in the gather's epilogue.  The first run of an autotuning
+// session times, besides the default, each single change of every node's
+// form (all nodes changed at once, one configuration per run: the node
+// launches are independent, so their CUDA-event times separate) and keeps
+// each node's fastest form.  Choices are cached by (graph statistics,
+// colours, node shape, table type, wave) in the JSON file named by
+// SG2V_TUNE_CACHE, when set, so that later sessions skip the timing.
+
+struct Form {
+    bool group, rows, run_off, defer_off;
+};
+
+std::vector<Form> form_alternatives(const Shape &sh) {
+    const Form d{sh.group, sh.rows, sh.can_run && !sh.run, sh.can_defer && !sh.defer};
+    std::vector<Form> out{d};
+    if (sh.can_group) out.push_back(Form{!d.group, d.rows, d.run_off, d.defer_off});
+    if (sh.can_rows) out.push_back(Form{d.group, !d.rows, d.run_off, d.defer_off});
+    if (sh.can_run) out.push_back(Form{d.group, d.rows, !d.run_off, d.defer_off});
+    if (sh.can_defer) out.push_back(Form{d.group, d.rows, d.run_off, !d.defer_off});
+    return out;
+}
+
+std::string form_code(const Shape &sh) {
+    std::string c;
+    c += sh.run ? 'R' : 'N';
+    c += sh.group ? 'G' : 'W';
+    c += sh.rows ? 'H' : 'h';
+    c += sh.defer ? 'D' : 'd';
+    return c;
+}
+
+std::string tune_key(const Prepared &P, size_t i, int wave) {
+    const CNode &c = P.nodes[i];
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "n%lld_m%lld_d%lld_w%d|kc%d|t%d_a%d_p%d_r%d|%s|wave%d|nb%d|",
+                  (long long)P.n, (long long)P.g->nnz, (long long)P.g->max_degree, P.g->weighted ? 1 : 0, P.kc,
+                  c.t, c.a, c.p, c.is_root ? 1 : 0, elem_name(P), wave, P.nb);
+    // the sub-template itself (nodes of one shape can be different trees);
+    // its AHU form uses only parentheses, safe inside a JSON string
+    return std::string(buf) + c.canon;
+}
+
+// The cache file: one flat JSON object {"key": "form code", ...}.
+std::map<std::string, std::string> read_tune_cache(const char *path) {
+    std::map<std::string, std::string> out;
+    FILE *f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return out;
+    std::string text;
+    char buf[4096];
+    size_t r;
+    while ((r = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, r);
+    std::fclose(f);
+    size_t pos = 0;
+    while (true) {
+        const size_t k0 = text.find('"', pos);
+        if (k0 == std::string::npos) break;
+        const size_t k1 = text.find('"', k0 + 1);
+        const size_t v0 = k1 == std::string::npos ? k1 : text.find('"', k1 + 1);
+        const size_t v1 = v0 == std::string::npos ? v0 : text.find('"', v0 + 1);
+        if (v1 == std::string::npos) break;
+        out[text.substr(k0 + 1, k1 - k0 - 1)] = text.substr(v0 + 1, v1 - v0 - 1);
+        pos = v1 + 1;
+    }
+    return out;
+}
+
+void write_tune_cache(const char *path, const std::map<std::string, std::string> &m) {
+    if (!path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    size_t k = 0;
+    for (const auto &kv : m)
+        std::fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second.c_str(), ++k < m.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
+void set_form_code(Shape &sh, const std::string &code) {
+    if (code.size() != 4) return;
+    apply_form(sh, code[1] == 'G', code[2] == 'H', code[0] == 'N', code[3] == 'd');
+}
+
+sg2v_status tune_forms(sg2v_session *S, cudaStream_t stream) {
+    Prepared &P = S->P;
+    const size_t nn = P.nodes.size();
+    const char *path = std::getenv("SG2V_TUNE_CACHE");
+    std::map<std::string, std::string> cache = read_tune_cache(path);
+    std::vector<std::vector<Form>> alts(nn);
+    size_t most = 1;
+    bool all_cached = true;
+    for (size_t i = 0; i < nn; ++i) {
+        alts[i] = form_alternatives(P.shape[i]);
+        most = std::max(most, alts[i].size());
+        if (!cache.count(tune_key(P, i, S->R.wave))) all_cached = false;
+    }
+    if (all_cached) {
+        for (size_t i = 0; i < nn; ++i) set_form_code(P.shape[i], cache[tune_key(P, i, S->R.wave)]);
+        return SG2V_OK;
+    }
+    std::vector<double> best(nn, -1.0);
+    std::vector<std::string> best_code(nn);
+    for (size_t k = 0; k < most; ++k) {
+        for (size_t i = 0; i < nn; ++i) {
+            const Form &f = alts[i][k < alts[i].size() ? k : 0];
+            apply_form(P.shape[i], f.group, f.rows, f.run_off, f.defer_off);
+        }
+        sg2v_status st = session_enqueue(S, stream, false);  // warm-up
+        if (st) return st;
+        std::vector<double> ms(nn, 0.0);
+        if ((st = session_enqueue(S, stream, false, false, &ms))) return st;
+        for (size_t i = 0; i < nn; ++i) {
+            if (k > 0 && k >= alts[i].size()) continue;
+            if (best[i] < 0.0 || ms[i] < best[i]) {
+                best[i] = ms[i];
+                best_code[i] = form_code(P.shape[i]);
+            }
+        }
+    }
+    for (size_t i = 0; i < nn; ++i) {
+        set_form_code(P.shape[i], best_code[i]);
+        cache[tune_key(P, i, S->R.wave)] = best_code[i];
+    }
+    write_tune_cache(path, cache);
     return SG2V_OK;
 }
 
@@ -1779,6 +1960,7 @@ sg2v_status sg2v_session_run(sg2v_session *S, const int8_t *colours, double *tot
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         if ((st = session_alloc_wave(S, best))) return st;
+        if ((st = tune_forms(S, stream))) return st;
         S->tuned = true;
         S->launches_per_run = count_launches(P, best);
     }
@@ -1846,6 +2028,35 @@ sg2v_status sg2v_session_info(const sg2v_session *S, int32_t *wave, int32_t *gra
     }
     if (wave) *wave = S->R.wave;
     if (graph) *graph = S->exec != nullptr;
+    return SG2V_OK;
+}
+
+sg2v_status sg2v_session_tuning(const sg2v_session *S, char *out, int64_t capacity, int64_t *length) {
+    if (!S || (!out && capacity > 0)) {
+        set_error("invalid argument");
+        return SG2V_ERR_INVALID_ARGUMENT;
+    }
+    std::string j = "{\"wave\": " + std::to_string(S->R.wave) + ", \"tuned\": " + (S->tuned ? "true" : "false") +
+                    ", \"nodes\": [";
+    for (size_t i = 0; i < S->P.nodes.size(); ++i) {
+        const CNode &c = S->P.nodes[i];
+        const Shape &sh = S->P.shape[i];
+        const char *kernel = sh.rows ? "histogram rows" : (sh.run ? "run-scatter" : "per-colour accumulators");
+        char buf[256];
+        std::snprintf(buf, sizeof buf,
+                      "%s{\"t\": %d, \"a\": %d, \"p\": %d, \"kernel\": \"%s\", \"lane_groups\": %s, "
+                      "\"deferred_ema\": %s, \"form\": \"%s\"}",
+                      i ? ", " : "", c.t, c.a, c.p, kernel, sh.group ? "true" : "false", sh.defer ? "true" : "false",
+                      form_code(sh).c_str());
+        j += buf;
+    }
+    j += "]}";
+    if (length) *length = (int64_t)j.size();
+    if (out && capacity > 0) {
+        const size_t nb = std::min<size_t>((size_t)capacity - 1, j.size());
+        std::memcpy(out, j.data(), nb);
+        out[nb] = 0;
+    }
     return SG2V_OK;
 }
 

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     const int kc = A.kc;
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int nvec = (A.Wz + E - 1) / E;
+    const uint32_t sink = (uint32_t)(A.ywords - E);  // the run map's Y' sink (forms 0 and 1)
     // the vector each lane loads (lanes past the row's end repeat the last
     // one: same line, no extra traffic) and which of its entries are real
     int lv_[NV];
@@ -188,7 +189,9 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                         } else if constexpr (RMW) {
                             ybuf[ix[k]] += rv[k];
                         } else {
-                            atomicAdd(ybuf + ix[k], rv[k]);
+                            // one shared-memory reduction per entry; the sink's
+                            // entries are skipped (their adds would serialise)
+                            if (ix[k] != sink) atomicAdd(ybuf + ix[k], rv[k]);
                         }
                     }
                     run[q] = V::zero();

@@ -109,8 +109,8 @@ def test_u64_exact_beyond_fp64(sg):
 
 
 def test_u64_overflow_is_reported(sg):
-    """tree10, k = 10 on R-MAT scale 13 with 2^17 edges: table entries reach
-    2^66, so the call (and a session) reports the overflow."""
+    """tree10, k = 10 on R-MAT scale 13 with 2^17 edges: per-vertex counts
+    reach 2^66, so a call (and a session) keeping them reports the overflow."""
     g = si.rmat(13, 1 << 17, seed=0)
     graph = sg.Graph(g.row_ptr, g.col_idx)
     plan = sg.Plan(si.TREE10.parent, 0, 10)
@@ -120,12 +120,23 @@ def test_u64_overflow_is_reported(sg):
     assert e.value.status == sg.SG2V_ERR_FP_OVERFLOW
     import torch
 
-    ses = sg.Session(graph, [plan], 1, "u64", graph_replay=True)
+    # a session keeping per-vertex counts (the root's rows are those counts)
+    ses = sg.Session(graph, [plan], 1, "u64", per_vertex=True, graph_replay=True)
     tot = torch.empty((1, 1), dtype=torch.float64, device="cuda")
     ses.run(_dev(col[None, :]), tot, None, None)
     with pytest.raises(sg.Sg2vError) as e:
         ses.sync()
     assert e.value.status == sg.SG2V_ERR_FP_OVERFLOW
+    # totals only: the root sums each edge once (half of each row's arcs), so
+    # its rows may fit 64 bits; then the exact 128-bit total comes back
+    ref10 = oracle.count(g.row_ptr, g.col_idx, si.TREE10.parent, 0, col, 10, per_vertex=False)
+    ses2 = sg.Session(graph, [plan], 1, "u64", graph_replay=True)
+    ses2.run(_dev(col[None, :]), tot, None, None)
+    try:
+        ses2.sync()
+        assert tot.item() == float(ref10.total)
+    except sg.Sg2vError as e2:
+        assert e2.status == sg.SG2V_ERR_FP_OVERFLOW
     # the same graph with a smaller template fits
     plan5 = sg.Plan(si.PATH5.parent, 0, 5)
     col5 = si.colouring(g.n, 5, 0, 1)

@@ -153,3 +153,43 @@ def test_estimator_loop_on_a_session(sg):
         tot = oracle.count(g.row_ptr, g.col_idx, si.PATH5.parent, 0, colouring(i), per_vertex=False).total
         vals.append(float(oracle.estimate(tot, 5, alpha)))
     assert res.estimate[0] == pytest.approx(np.mean(vals), rel=1e-12)
+
+
+def test_form_autotuning_is_exact_and_cached(sg, tmp_path, monkeypatch):
+    """Autotuning picks each node's kernel form by timing; every form gives
+    the same counts (oracle-exact totals in FP64), and a second session with
+    the same cache file takes the stored forms."""
+    import json
+
+    import torch
+
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("SG2V_TUNE_CACHE", str(cache))
+    g = si.rmat(12, 40000, seed=11)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    parents = [si.PATH7.parent, si.STAR7.parent, si.TREE7.parent]
+    plans = [sg.Plan(p) for p in parents]
+    B = 4
+    cols = si.colourings(g.n, 7, B, seed=6)
+    refs = [[oracle.count(g.row_ptr, g.col_idx, p, 0, cols[b]) for b in range(B)] for p in parents]
+    forms = []
+    for rep in range(2):
+        ses = sg.Session(graph, plans, B, "fp64", autotune=True)
+        tot = torch.empty((len(plans), B), dtype=torch.float64, device="cuda")
+        ses.run(torch.from_numpy(cols).cuda(), tot)
+        ses.sync()
+        info = ses.tuning()
+        assert info["tuned"] and len(info["nodes"]) > 0
+        forms.append([n["form"] for n in info["nodes"]])
+        t = tot.cpu().numpy()
+        for i in range(len(plans)):
+            for b in range(B):
+                r = refs[i][b]
+                if r.max_bits <= 53:
+                    assert t[i, b] == float(r.total)
+                else:
+                    assert abs(t[i, b] - r.total) <= 1e-12 * r.total
+        ses.close()
+        stored = json.loads(cache.read_text())
+        assert len(stored) >= len(info["nodes"])
+    assert forms[0] == forms[1]

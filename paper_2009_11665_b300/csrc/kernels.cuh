@@ -117,6 +117,9 @@ struct NodeArgs {
     const uint16_t *runmap;
     int wmap;
     int mzero;
+    // run-scatter kernel: 16-byte vectors between consecutive vertex rows of
+    // the passive table (nb * ldp / entries per vector; set by its launcher)
+    unsigned uvec;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;

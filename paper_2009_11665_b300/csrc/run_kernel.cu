@@ -84,6 +84,9 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                                                   (size_t)(blockDim.x >> 5) * (A.ywords + A.mwords) * sizeof(T) +
                                                   (size_t)wib * kRunCompactBytes);
     float *wbuf = reinterpret_cast<float *>(cbuf + 32);
+    // the warp's next task descriptor, copied in while the current task runs
+    // (kept out of registers: they are the kernel's scarce resource)
+    int4 *nslot = reinterpret_cast<int4 *>(cbuf + 64);
     const int kc = A.kc;
     const int mchunks = (A.a_leaf || A.defer) ? 0 : (A.Wa * (int)sizeof(T) + 15) / 16;
     const int nvec = (A.Wz + E - 1) / E;
@@ -105,14 +108,21 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
         if (lane < E) mbuf[A.mzero + lane] = T(0);
         if (A.a_leaf && lane == 0) mbuf[0] = T(1);
     }
-    const unsigned uvec = (unsigned)((int64_t)A.nb * A.ldp / E);  // vectors between vertex rows
     const unsigned zero_word = (unsigned)A.n << 4;                 // the zero row
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib;
-    int4 task = ti < A.ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
+    // (a work list has fewer than 2^32 tasks: one per row plus the chunks)
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned ntasks = (unsigned)A.ntasks;
+    unsigned ti = ((blockIdx.x * blockDim.x) >> 5) + wib;
+    int4 task = ti < ntasks ? A.tasks[ti] : make_int4(0, -1, 0, 0);
     unsigned ovf = 0;
-    for (; ti < A.ntasks; ti += nwarps) {
-        const int4 next = ti + nwarps < A.ntasks ? A.tasks[ti + nwarps] : task;
+    for (; ti < ntasks; ti += nwarps) {
+        const bool more = ti + nwarps < ntasks;
+        if (more && lane == 0) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(nslot);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(A.tasks + ti + nwarps)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
         const int v = task.x;
         const int slot = task.y;
         const int64_t e0 = task.z, e1 = task.w;
@@ -149,14 +159,15 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 for (int j = lane; j < A.ywords; j += 32) ybuf[j] = T(0);
             bool mready = mchunks == 0 || !cok;
             T acc = T(0);  // FORM 2: this lane's part of the row sum
-            const VT *Mb = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)b * A.ldp);
-            const VT *lrow[NV];
+            // lane vectors as 32-bit offsets from the table (fewer live registers)
+            unsigned lvo[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) lrow[q] = Mb + lv_[q];
-            const int32_t *scol = A.scol + (int64_t)b * A.nnz;
-            const int8_t *sclr = A.sclr + (int64_t)b * A.nnz;
-            const float *sw = WEIGHTED ? A.sw + (int64_t)b * A.nnz : nullptr;
-            const uint16_t *rmap = A.runmap + (int64_t)(cok ? cv : 0) * kc * A.wmap + gl * E;
+            for (int q = 0; q < NV; ++q) lvo[q] = (unsigned)(b * A.ldp / E) + (unsigned)lv_[q];
+            // the task's sorted arcs (a task holds at most a chunk of arcs:
+            // 32-bit offsets from its first arc)
+            const int64_t aoff = (int64_t)b * A.nnz + e0;
+            const int len = (int)(e1 - e0);
+            const unsigned rmo = (unsigned)((cok ? cv : 0) * kc * A.wmap + gl * E);
             VT run[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) run[q] = V::zero();
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
             // the end of a colour run of this lane's group (called by the
             // group's lanes only; warp-wide groups call it uniformly)
             auto flush = [&](int c) {
-                const uint16_t *mp = rmap + (int64_t)c * A.wmap;
+                const uint16_t *mp = A.runmap + (rmo + (unsigned)(c * A.wmap));
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     uint32_t ix[E];
@@ -199,11 +210,11 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 // the next run may add to the same entries of Y'
                 if (FORM != 2 && RMW) __syncwarp();
             };
-            for (int64_t base = e0; base < e1; base += 32) {
-                const int cnt_in = (int)(e1 - base < 32 ? e1 - base : 32);
+            for (int base = 0; base < len; base += 32) {
+                const int cnt_in = len - base < 32 ? len - base : 32;
                 const bool in = lane < cnt_in;
-                const int c_in = in ? (int)__ldg(sclr + base + lane) : -1;
-                const int u_in = in ? __ldg(scol + base + lane) : 0;
+                const int c_in = in ? (int)__ldg(A.sclr + aoff + base + lane) : -1;
+                const int u_in = in ? __ldg(A.scol + aoff + base + lane) : 0;
                 const bool t_in = cok && c_in >= 0 && c_in != cv && (!A.half_arcs || u_in < v);
                 // compact the batch to the arcs that add something (order kept,
                 // so colour runs stay contiguous) through the warp's slots
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 if (t_in) {
                     const int r = __popc(live & ((1u << lane) - 1u));
                     cbuf[r] = ((unsigned)u_in << 4) | (unsigned)c_in;
-                    if (WEIGHTED) wbuf[r] = __ldg(sw + base + lane);
+                    if (WEIGHTED) wbuf[r] = __ldg(A.sw + aoff + base + lane);
                 }
                 __syncwarp();
                 // slots past the live arcs read the zero row into the batch's
@@ -242,7 +253,9 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                         w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
 #pragma unroll
                         for (int q = 0; q < NV; ++q)
-                            x[r][q] = (!SKIP_ZERO || j < cnt) ? ldg_row(lrow[q] + (size_t)u * uvec) : V::zero();
+                            x[r][q] = (!SKIP_ZERO || j < cnt)
+                                          ? ldg_row(reinterpret_cast<const VT *>(A.Mp) + ((size_t)u * A.uvec + lvo[q]))
+                                          : V::zero();
                     }
                     const bool same = G == 32 ? cr[U - 1] == cur : __all_sync(kFull, cr[U - 1] == cur);
                     if (same) {
@@ -351,7 +364,11 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
             epilogue<T>(A, v, b, cok, ybuf, mbuf, lane, ovf);
             __syncwarp();
         }
-        task = next;
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncwarp();
+        if (more) task = *nslot;
+        // every lane has read the slot before the next copy overwrites it
+        __syncwarp();
     }
 }
 
@@ -396,6 +413,7 @@ cudaError_t launch_node_run(const NodeArgs &args, Elem e, int g, int nv, int for
     if (err != cudaSuccess) return err;
     NodeArgs a = args;
     a.group_rows = 0;  // one task per warp
+    a.uvec = (unsigned)((int64_t)a.nb * a.ldp / (e == Elem::F64 ? 2 : 4));
     return launch_variant(k, a, 32, threads, smem, grid_cap, stream);
 }
 

@@ -379,6 +379,11 @@ struct sg2v_graph {
     int chunk = 0;
     int64_t short_begin = 0;  // first task of at most kShortTaskArcs arcs (the rest, sorted by work, are too)
     int64_t small_begin = 0;  // first task of at most kSortSmallArcs arcs
+    // isolated vertices: when the work list ends in the empty tasks of rows
+    // [live_rows, n) (vertices numbered by decreasing degree put them there),
+    // forward counting launches only tasks [0, live_tasks); else live_tasks =
+    // ntasks and live_rows = n
+    int64_t live_tasks = 0, live_rows = 0;
     int32_t *rev = nullptr;  // reverse arc of every arc, built on the first backward call
     // vertices relabelled by decreasing degree (unless SG2V_GRAPH_KEEP_ORDER):
     // the device CSR is in the new order; iperm[new] = the caller's vertex,
@@ -908,6 +913,11 @@ struct RunBuffers {
     int8_t *colp = nullptr;       // colourings in the graph's vertex order (relabelled graphs)
     double *ones = nullptr;       // [nb][n] ones for single-vertex templates
     int chunks = 1;
+    // forward counting of a graph whose isolated vertices are rows
+    // [live_rows, n): no task of theirs runs and no table row of theirs is
+    // written or read (a gathered row belongs to a neighbour, an active row to
+    // the task's own vertex); the root reduction counts them as zeros
+    bool live = false;
     RootSum *partials = nullptr;  // [plans][nb][chunks]
     RootSum *sums = nullptr;      // [plans][nb]
 };
@@ -993,7 +1003,8 @@ sg2v_status alloc_run(const Prepared &P, int wave, Alloc alloc, RunBuffers *R) {
     R->ld.assign(P.nodes.size(), 0);
     if ((st = alloc(16, (void **)&R->status))) return st;
     if (g->iperm && (st = alloc((size_t)P.nb * P.n, (void **)&R->colp))) return st;
-    R->chunks = (int)std::max<int64_t>(1, std::min<int64_t>(256, (P.n + 65535) / 65536 * 4));
+    // about 4,096 values per block of the partial sums (enough blocks to fill the GPU)
+    R->chunks = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (P.n + 4095) / 4096));
     const size_t segs = P.plans.size() * (size_t)P.nb;
     if ((st = alloc(sizeof(RootSum) * segs * R->chunks, (void **)&R->partials))) return st;
     if ((st = alloc(sizeof(RootSum) * segs, (void **)&R->sums))) return st;
@@ -1012,9 +1023,10 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
     A.col_idx = g->col_idx;
     A.weights = g->weights;
     A.tasks = g->tasks;
-    A.ntasks = g->ntasks;
+    A.ntasks = R.live ? g->live_tasks : g->ntasks;
     A.heavy_chunks = g->heavy_chunks;
     A.n = P.n;
+    A.live_rows = R.live ? g->live_rows : P.n;
     A.nb = wb;
     A.colours = wcol;
     A.kc = kc;
@@ -1179,6 +1191,11 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     }
     timer.count_extra(1);
     SG2V_CUDA(launch_check_colours(d_col, (int64_t)nb * n, kc, R.status, stream), "colour check");
+    const char *skip_env = std::getenv("SG2V_SKIP_EMPTY");
+    R.live = !(skip_env && std::atoi(skip_env) == 0) && g->live_rows < n;
+    const int64_t ntasks = R.live ? g->live_tasks : g->ntasks;
+    const int64_t small_begin = std::min(g->small_begin, ntasks);
+    const int64_t live_rows = R.live ? g->live_rows : n;
     const char *half_env = std::getenv("SG2V_HALF_ROOT");
     const bool half_root = !(half_env && std::atoi(half_env) == 0);
     const int fused = sort_hist_node(P);
@@ -1210,11 +1227,11 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
         }
         timer.begin("colour_sort",
                     (double)wb * (8.0 * (n + 1) + g->nnz * (4.0 + 4.0 + 1.0 + (g->weighted ? 8.0 : 0.0))) + hist_bytes);
-        SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, g->nnz, wcol, wb,
-                                     kc, R.scol, R.sclr, R.sw, hist, P.info.sms, stream),
+        SG2V_CUDA(launch_colour_sort(g->tasks, ntasks, small_begin, g->col_idx, g->weights, n, g->nnz, wcol, wb, kc,
+                                     R.scol, R.sclr, R.sw, hist, P.info.sms, stream),
                   "colour sort");
         timer.end();
-        if (g->small_begin > 0 && g->small_begin < g->ntasks) timer.count_extra(1);  // the small-task sort
+        if (small_begin > 0 && small_begin < ntasks) timer.count_extra(1);  // the small-task sort
         for (size_t i = 0; i < P.nodes.size(); ++i) {
             const CNode &c = P.nodes[i];
             const Shape &sh = P.shape[i];
@@ -1243,8 +1260,8 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             if (P.scaled && !A.hist) {
                 // reference exponent of every row: the largest among the rows it gathers
                 SG2V_CUDA(cudaMemsetAsync(R.eref, 0x80, (size_t)n * wb * sizeof(int32_t), stream), "memset");
-                timer.begin("eref", (double)wb * (g->nnz * 5.0 + n * 6.0) + 16.0 * g->ntasks);
-                SG2V_CUDA(launch_eref(g->tasks, g->ntasks, R.scol, R.sclr, wcol, n, g->nnz, wb, kc, A.Ep, R.eref,
+                timer.begin("eref", (double)wb * (g->nnz * 5.0 + live_rows * 6.0) + 16.0 * ntasks);
+                SG2V_CUDA(launch_eref(g->tasks, ntasks, R.scol, R.sclr, wcol, n, g->nnz, wb, kc, A.Ep, R.eref,
                                       P.info.sms, stream),
                           "eref");
                 timer.end();
@@ -1252,8 +1269,9 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             {
                 // algorithmic bytes: each input table, the sorted arc list
                 // (neighbour, its colour, weight) and the colouring read once,
-                // the output written once
-                const double rows = (double)n * wb;
+                // the output written once (rows of isolated vertices, when
+                // skipped, are neither read nor written)
+                const double rows = (double)live_rows * wb;
                 double bytes = 8.0 * (n + 1) + (double)wb * g->nnz * (5.0 + (g->weighted ? 4.0 : 0.0));
                 bytes += rows;  // colours
                 if (!A.hist) bytes += rows * A.Wz * esz;
@@ -1274,7 +1292,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             timer.end();
             if (sh.group) timer.count_extra(1);  // short and long tasks launch apart
             if (sh.defer) {
-                const double rows = (double)n * wb;
+                const double rows = (double)live_rows * wb;
                 char name[64];
                 std::snprintf(name, sizeof name, "ema t=%d a=%d p=%d %s", c.t, c.a, c.p,
                               elem_name(P));
@@ -1292,10 +1310,13 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
         const void *vals = P.plan_root[pi] >= 0 ? R.rootbuf[pi] : R.ones;
         // root values: the table type, doubles for scaled tables and single-vertex plans
         const Elem ve = P.plan_root[pi] >= 0 ? (P.scaled ? Elem::F64 : P.elem) : Elem::F64;
-        timer.begin("root_reduce", (double)nb * n * ((ve == Elem::F32 ? 4 : (ve == Elem::U128 ? 16 : 8)) + (pvp ? 8 : 0)));
+        // (a single-vertex template counts every vertex, isolated ones too)
+        const int64_t live = P.plan_root[pi] >= 0 ? live_rows : n;
+        timer.begin("root_reduce", (double)nb * live * (ve == Elem::F32 ? 4 : (ve == Elem::U128 ? 16 : 8)) +
+                                       (pvp ? (double)nb * n * 8 : 0.0));
         timer.count_extra(1);
-        SG2V_CUDA(launch_root_reduce(vals, ve, n, nb, pvp, g->iperm, R.partials + pi * (size_t)nb * R.chunks, R.chunks,
-                                     R.sums + pi * (size_t)nb, stream),
+        SG2V_CUDA(launch_root_reduce(vals, ve, n, live, nb, pvp, g->iperm, R.partials + pi * (size_t)nb * R.chunks,
+                                     R.chunks, R.sums + pi * (size_t)nb, stream),
                   "root reduction");
         timer.end();
     }
@@ -1682,6 +1703,17 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
                 g->small_begin = i;
                 break;
             }
+        // the work list's trailing empty tasks: skipped by forward counting
+        // when their rows are exactly the last ones (each isolated vertex has
+        // one empty task, every other row none)
+        int64_t nempty = 0;
+        while (nempty < g->ntasks && tasks[(size_t)(g->ntasks - 1 - nempty)].z == tasks[(size_t)(g->ntasks - 1 - nempty)].w)
+            ++nempty;
+        bool tail = true;
+        for (int64_t i = g->ntasks - nempty; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].x < n - nempty) tail = false;
+        g->live_tasks = tail ? g->ntasks - nempty : g->ntasks;
+        g->live_rows = tail ? n - nempty : n;
     }
     cudaError_t e = cudaSuccess;
     auto up = [&](void **dst, const void *src, size_t bytes) {
@@ -2337,7 +2369,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     }
     if (total) {
         timer.count_extra(2);
-        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.elem, n, 1, nullptr, nullptr, R.partials, R.chunks, R.sums, stream),
+        SG2V_CUDA(launch_root_reduce(R.rootbuf[0], P.elem, n, n, 1, nullptr, nullptr, R.partials, R.chunks, R.sums, stream),
                   "root reduction");
     }
     // seed: gradient of the per-vertex counts

@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(256) ema_rows_kernel(const NodeArgs A) {
     T *mas = ys + (int64_t)wy * R;                       // [wa][R]
     __shared__ T s_max[R][8];
     __shared__ int s_ok[R];
-    const int64_t rows = A.n * A.nb;
+    const int64_t rows = A.live_rows * A.nb;
     unsigned ovf = 0;
     for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < rows; r0 += (int64_t)gridDim.x * R) {
         if (tid < R) {
@@ -1130,27 +1130,50 @@ __device__ __forceinline__ RootSum rs_from(double v) {
 }
 
 template <typename T>
-__global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, const int32_t *pvmap, RootSum *partials,
-                                    int chunks) {
+__global__ void root_partial_kernel(const T *vals, int64_t n, int64_t live, double *pv, const int32_t *pvmap,
+                                    RootSum *partials, int chunks) {
     __shared__ RootSum red[32];
     const int seg = blockIdx.y;
     const int chunk = blockIdx.x;
     const int64_t per = (n + chunks - 1) / chunks;
     const int64_t lo = (int64_t)chunk * per;
-    const int64_t hi = (lo + per < n) ? lo + per : n;
+    const int64_t hi_all = (lo + per < n) ? lo + per : n;
+    // entries past `live` are zeros (isolated vertices): not read
+    const int64_t hi = hi_all < live ? hi_all : live;
+    if (pv)
+        for (int64_t i = (lo > live ? lo : live) + threadIdx.x; i < hi_all; i += blockDim.x)
+            pv[(int64_t)seg * n + (pvmap ? (int64_t)pvmap[i] : i)] = 0.0;
     RootSum acc = rs_from(0.0);
     if constexpr (sizeof(T) == 4) {
         // FP32 tables: the exact integer path buys nothing; each thread sums
         // in double (the per-thread sums are then combined compensated)
         double sum = 0.0;
         unsigned bad = 0;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const T x = vals[(int64_t)seg * n + i];
-            if (pv) pv[(int64_t)seg * n + (pvmap ? (int64_t)pvmap[i] : i)] = (double)x;
-            if (isfinite(x))
+        const T *sv = vals + (int64_t)seg * n;
+        if (pv) {
+            for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                const T x = sv[i];
+                pv[(int64_t)seg * n + (pvmap ? (int64_t)pvmap[i] : i)] = (double)x;
+                if (isfinite(x))
+                    sum += (double)x;
+                else
+                    bad = 1;
+            }
+        } else {
+            // four loads in flight per thread
+            const int64_t step = blockDim.x;
+            int64_t i = lo + threadIdx.x;
+            for (; i + 3 * step < hi; i += 4 * step) {
+                const T x0 = sv[i], x1 = sv[i + step], x2 = sv[i + 2 * step], x3 = sv[i + 3 * step];
+                bad |= !isfinite(x0) | !isfinite(x1) | !isfinite(x2) | !isfinite(x3);
+                sum += ((double)x0 + (double)x1) + ((double)x2 + (double)x3);
+            }
+            for (; i < hi; i += step) {
+                const T x = sv[i];
+                bad |= !isfinite(x);
                 sum += (double)x;
-            else
-                bad = 1;
+            }
+            if (bad) sum = 0.0;
         }
         acc.s = sum;
         acc.flags = kFlagNotIntegral | (bad ? kFlagNonFinite : 0u);
@@ -1192,12 +1215,28 @@ __global__ void root_partial_kernel(const T *vals, int64_t n, double *pv, const 
     }
 }
 
-__global__ void root_final_kernel(const RootSum *partials, int chunks, int nseg, RootSum *out) {
-    const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+// One block per segment: each thread combines a strided share of the
+// segment's partials, then the block combines its threads' results (the
+// 128-bit integer sum is exact in any order).
+__global__ void __launch_bounds__(256) root_final_kernel(const RootSum *partials, int chunks, int nseg,
+                                                         RootSum *out) {
+    __shared__ RootSum red[8];
+    const int seg = blockIdx.x;
     if (seg >= nseg) return;
-    RootSum t = partials[(int64_t)seg * chunks];
-    for (int i = 1; i < chunks; ++i) rs_combine(t, partials[(int64_t)seg * chunks + i]);
-    out[seg] = t;
+    RootSum t = rs_from(0.0);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) rs_combine(t, partials[(int64_t)seg * chunks + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const RootSum y = rs_shfl_xor(t, o);
+        rs_combine(t, y);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) rs_combine(t, red[i]);
+        out[seg] = t;
+    }
 }
 
 // Reference exponent of each row for the scaled FP32 gather: the largest
@@ -1959,7 +1998,7 @@ cudaError_t launch_ema_rows(const NodeArgs &args, Elem e, bool scaled, int sms, 
     const size_t smem = ema_rows_smem(args, e, scaled);
     const int per_sm = ema_rows_blocks_per_sm(e, scaled, smem);
     if (per_sm < 1) return cudaErrorInvalidValue;
-    const int64_t rows = args.n * args.nb;
+    const int64_t rows = args.live_rows * args.nb;
     const int64_t blocks = std::min<int64_t>((rows + kEmaRows - 1) / kEmaRows, (int64_t)sms * per_sm);
     NodeArgs a = args;
     void *params[] = {&a};
@@ -1967,24 +2006,25 @@ cudaError_t launch_ema_rows(const NodeArgs &args, Elem e, bool scaled, int sms, 
                             params, smem, stream);
 }
 
-cudaError_t launch_root_reduce(const void *vals, Elem ve, int64_t n, int nseg, double *pv, const int32_t *pvmap,
-                               RootSum *partials, int chunks, RootSum *out, cudaStream_t stream) {
+cudaError_t launch_root_reduce(const void *vals, Elem ve, int64_t n, int64_t live, int nseg, double *pv,
+                               const int32_t *pvmap, RootSum *partials, int chunks, RootSum *out,
+                               cudaStream_t stream) {
     dim3 grid((unsigned)chunks, (unsigned)nseg);
     if (ve == Elem::U64)
-        root_partial_kernel<u64><<<grid, 256, 0, stream>>>(static_cast<const u64 *>(vals), n, pv, pvmap, partials,
+        root_partial_kernel<u64><<<grid, 256, 0, stream>>>(static_cast<const u64 *>(vals), n, live, pv, pvmap, partials,
                                                              chunks);
     else if (ve == Elem::U128)
-        root_partial_kernel<u128><<<grid, 256, 0, stream>>>(static_cast<const u128 *>(vals), n, pv, pvmap, partials,
+        root_partial_kernel<u128><<<grid, 256, 0, stream>>>(static_cast<const u128 *>(vals), n, live, pv, pvmap, partials,
                                                               chunks);
     else if (ve == Elem::F64)
-        root_partial_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double *>(vals), n, pv, pvmap,
+        root_partial_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double *>(vals), n, live, pv, pvmap,
                                                                 partials, chunks);
     else
-        root_partial_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float *>(vals), n, pv, pvmap,
+        root_partial_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float *>(vals), n, live, pv, pvmap,
                                                                partials, chunks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    root_final_kernel<<<(nseg + 127) / 128, 128, 0, stream>>>(partials, chunks, nseg, out);
+    root_final_kernel<<<(unsigned)nseg, 256, 0, stream>>>(partials, chunks, nseg, out);
     return cudaGetLastError();
 }
 

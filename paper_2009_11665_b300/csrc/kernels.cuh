@@ -120,6 +120,9 @@ struct NodeArgs {
     // run-scatter kernel: 16-byte vectors between consecutive vertex rows of
     // the passive table (nb * ldp / entries per vector; set by its launcher)
     unsigned uvec;
+    // rows [live_rows, n) belong to isolated vertices whose tasks do not run
+    // (their table rows are never read); n when every row runs
+    int64_t live_rows;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;
@@ -271,10 +274,12 @@ cudaError_t launch_hist_rows(const NodeArgs &args, Elem e, bool scaled, int thre
                              cudaStream_t stream);
 
 // Root reduction: vals is [nseg][n] of float, double or unsigned 64-bit
-// counts; writes per-vertex doubles when pv != null (value of vertex i at
+// counts, of which entries [live, n) of each segment are zeros that are not
+// read; writes per-vertex doubles when pv != null (value of vertex i at
 // pv[seg * n + pvmap[i]], or at i when pvmap is null) and one RootSum per
 // segment.
-cudaError_t launch_root_reduce(const void *vals, Elem e, int64_t n, int nseg, double *pv, const int32_t *pvmap,
+cudaError_t launch_root_reduce(const void *vals, Elem e, int64_t n, int64_t live, int nseg, double *pv,
+                               const int32_t *pvmap,
                                RootSum *partials, int chunks, RootSum *out, cudaStream_t stream);
 
 // Eref[row] = max over the row's arcs to neighbours of another valid colour

@@ -127,3 +127,58 @@ def test_set_weights_follow_their_arcs(sg):
     want = np.array([float(x) for x in ref.per_vertex_values()])
     np.testing.assert_allclose(pv.cpu().numpy(), want, rtol=1e-12, atol=0)
     assert abs(tot - float(ref.total_value())) <= 1e-12 * float(ref.total_value())
+
+
+def _with_isolated(g, extra: int, seed: int):
+    """g with `extra` isolated vertices inserted at random places of the
+    caller's vertex order (an R-MAT graph has isolated vertices of its own)."""
+    rng = np.random.default_rng(seed)
+    n2 = g.n + extra
+    keep = np.sort(rng.choice(n2, size=g.n, replace=False))  # new id of each old vertex
+    deg = np.zeros(n2, dtype=np.int64)
+    deg[keep] = np.diff(g.row_ptr)
+    rp = np.zeros(n2 + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(deg)
+    ci = keep[g.col_idx].astype(np.int32)  # rows keep their order; ids stay increasing
+    return n2, rp, ci
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "u64", "fp32_scaled"])
+def test_isolated_vertices_skipped(sg, prec, monkeypatch):
+    """Forward counting launches no task for isolated vertices (their table
+    rows are neither written nor read) and reports them as zeros: the same
+    totals and per-vertex counts as with every row run (SG2V_SKIP_EMPTY=0),
+    and the oracle's.  Also with the deferred eMA, whose launch walks rows."""
+    g0 = si.rmat(10, 6000, seed=3)
+    n, rp, ci = _with_isolated(g0, 700, seed=1)
+    assert np.sum(np.diff(rp) == 0) > 700
+    cols = si.colourings(n, 10, 2, seed=8)
+    plans = [sg.Plan(si.TREE10.parent), sg.Plan((-1,), num_colours=10)]
+    graph = sg.Graph(rp, ci)
+    res = {}
+    for env in ({}, {"SG2V_SKIP_EMPTY": "0"}, {"SG2V_DEFER_EMA": "1"}):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        pv, tot, est = sg.count_batched(graph, plans, _dev(cols), prec, per_vertex=True)
+        res[tuple(env)] = (pv.cpu().numpy(), tot.cpu().numpy(), est.cpu().numpy())
+        for k in env:
+            monkeypatch.delenv(k)
+    iso = np.diff(rp) == 0
+    for b in range(2):
+        ref = oracle.count(rp, ci, si.TREE10.parent, 0, cols[b])
+        want = np.array(ref.per_vertex, dtype=np.float64)
+        for key, (pv, tot, _) in res.items():
+            assert np.all(pv[0, b][iso] == 0), key
+            nz = want != 0
+            assert np.all(pv[0, b][~nz] == 0), key
+            rtol = 1e-12 if prec in ("fp64", "u64") else 1e-4
+            assert np.all(np.abs(pv[0, b][nz] - want[nz]) <= rtol * want[nz]), key
+            assert abs(tot[0, b] - float(ref.total)) <= rtol * float(ref.total), key
+            # a single-vertex template counts every vertex, isolated ones too
+            assert tot[1, b] == float(n), key
+            assert np.all(pv[1, b] == 1.0), key
+    if prec in ("fp64", "u64"):
+        base = res[()]
+        for key, val in res.items():
+            for x, y in zip(base, val):
+                assert np.array_equal(x, y), key

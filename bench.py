@@ -145,7 +145,7 @@ def source_digest() -> str:
     """Digest of the sources that decide what a node launch does (kernels and
     the executor that sets its launch configuration)."""
     h = hashlib.sha256()
-    for name in ("kernels.cu", "api.cu"):
+    for name in ("kernels.cu", "run_kernel.cu", "device_common.cuh", "kernels.cuh", "api.cu"):
         h.update(open(os.path.join(ROOT, "paper_2009_11665_b300", "csrc", name), "rb").read())
     return h.hexdigest()
 

@@ -109,7 +109,10 @@ typedef enum {
  * given, the device copy numbers the vertices by decreasing degree (the rows
  * most arcs gather share cache lines); this is invisible to the caller:
  * colourings, per-vertex counts, per-vertex gradient seeds, weights and
- * per-arc gradients are always in the caller's vertex and arc order.
+ * per-arc gradients are always in the caller's vertex and arc order.  In that
+ * order the vertices without arcs come last, and forward counting runs no
+ * work for them (their per-vertex counts are zero; a single-vertex template
+ * counts them as usual).
  * Errors: INVALID_ARGUMENT, GRAPH_NOT_SIMPLE, OUT_OF_MEMORY, CUDA.
  */
 sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col_idx,

@@ -2519,13 +2519,14 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         D.arc = d_arc[ii];
         D.narc = btab[ii].narc;
         D.grad = part;
+        // every form walks the forward work list (long rows in chunks)
+        D.tasks = g->tasks;
+        D.ntasks = g->ntasks;
         if (c.p >= 2) {
-            // row-oriented form over the forward work list, gather shape of M_p' rows
+            // row-oriented form, gather shape of M_p' rows
             int lanes = 32, vecs = 1;
             node_shape(P.vecn, D.wmp, &lanes, &vecs);
             if (lanes != kWideLanes && vecs >= 1) {
-                D.tasks = g->tasks;
-                D.ntasks = g->ntasks;
                 D.lanes = lanes;
                 D.vecs = vecs;
                 D.wz_pad = lanes * vecs * vecn;

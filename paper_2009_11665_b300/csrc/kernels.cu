@@ -1642,13 +1642,31 @@ __global__ void bwd_ema_kernel(const BwdEmaArgs A) {
     }
 }
 
+// Per-arc weight gradient, one warp per unit of work: a work-list task (a
+// row, or a chunk of at most a chunk's arcs of a long row) when A.tasks is
+// set, else a whole row.  Each arc's gradient is its own output, so the
+// chunks of a split row need no combining; hub rows cut into chunks keep one
+// warp from walking tens of thousands of arcs alone.
 template <typename T>
 __global__ void sddmm_kernel(const SddmmArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     T *mp = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * ((A.wmp + 3) / 4 * 4);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; u < A.n; u += nwarps) {
+    const int64_t units = A.tasks ? A.ntasks : A.n;
+    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < units; t += nwarps) {
+        int64_t u, e0, e1;
+        if (A.tasks) {
+            const int4 task = A.tasks[t];
+            u = task.x;
+            e0 = task.z;
+            e1 = task.w;
+        } else {
+            u = t;
+            e0 = A.row_ptr[u];
+            e1 = A.row_ptr[u + 1];
+        }
+        if (e0 == e1) continue;
         const int cu = A.colours[u];
         if ((unsigned)cu >= (unsigned)A.kc) continue;
         if (!A.hist) {
@@ -1656,7 +1674,6 @@ __global__ void sddmm_kernel(const SddmmArgs A) {
             for (int j = lane; j < A.wmp; j += 32) mp[j] = mr[j];
         }
         __syncwarp();
-        const int64_t e0 = A.row_ptr[u], e1 = A.row_ptr[u + 1];
         for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int v = __ldg(A.col_idx + e);
             const int cv = A.colours[v];
@@ -2105,7 +2122,7 @@ void *pick_sddmm_rows(int g, int nv) {
 }  // namespace
 
 cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream) {
-    if (!args.hist && args.tasks) {
+    if (!args.hist && args.tasks && args.lanes > 0) {
         // row-oriented form
         void *k = fp64 ? pick_sddmm_rows<double>(args.lanes, args.vecs) : pick_sddmm_rows<float>(args.lanes, args.vecs);
         const size_t smem = (size_t)8 * args.kc * args.wz_pad * (fp64 ? 8 : 4);
@@ -2129,7 +2146,8 @@ cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t
     }
     const size_t smem = (size_t)8 * ((args.wmp + 3) / 4 * 4) * (fp64 ? 8 : 4);
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
-    const int64_t blocks = std::min<int64_t>((args.n + 7) / 8, (int64_t)sms * 8);
+    const int64_t units = args.tasks ? args.ntasks : args.n;
+    const int64_t blocks = std::min<int64_t>((units + 7) / 8, (int64_t)sms * 8);
     if (fp64)
         sddmm_kernel<double><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
     else

@@ -175,8 +175,9 @@ struct SddmmArgs {
     const uint32_t *arc;          // [kc][kc][narc]
     int narc;
     double *grad;                 // [nnz]
-    // row-oriented form (p >= 2): the work list of the forward pass and the
-    // gather shape of rows of wmp elements (lanes per group, vectors per lane)
+    // the work list of the forward pass (null: one warp per row), and for the
+    // row-oriented form (p >= 2, lanes > 0) the gather shape of rows of wmp
+    // elements (lanes per group, vectors per lane)
     const int4 *tasks;
     int64_t ntasks;
     int lanes, vecs, wz_pad;

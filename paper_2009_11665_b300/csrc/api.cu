@@ -212,6 +212,51 @@ sg2v_status run_map(int dev, int kc, int t, int a, int form, int wmap, int sink,
     return SG2V_OK;
 }
 
+// Backward tables of a node (host copy for the counts, device copies for the
+// kernels), built and uploaded once per device and node shape, kept for the
+// life of the process like the run maps.
+struct DeviceBackward {
+    BackwardTables host;
+    const uint32_t *ybar = nullptr, *mabar = nullptr, *arc = nullptr;
+    const uint16_t *expand = nullptr;
+};
+std::map<std::tuple<int, int, int, int, int>, const DeviceBackward *> g_bwd_tables;
+
+sg2v_status backward_tables(int dev, int kc, int t, int a, int wz_pad, const DeviceBackward **out) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    const auto key = std::make_tuple(dev, kc, t, a, wz_pad);
+    auto it = g_bwd_tables.find(key);
+    if (it != g_bwd_tables.end()) {
+        *out = it->second;
+        return SG2V_OK;
+    }
+    auto *d = new (std::nothrow) DeviceBackward();
+    if (!d) return SG2V_ERR_OUT_OF_MEMORY;
+    build_backward_tables(kc, t, a, wz_pad, &d->host);
+    auto upload = [&](const void *h, size_t bytes, const void **dst) -> sg2v_status {
+        void *p = nullptr;
+        SG2V_CUDA(cudaMalloc(&p, std::max<size_t>(bytes, 16)), "table upload");
+        if (bytes) SG2V_CUDA(cudaMemcpy(p, h, bytes, cudaMemcpyHostToDevice), "table upload");
+        *dst = p;
+        return SG2V_OK;
+    };
+    sg2v_status st;
+    if ((st = upload(d->host.ybar.data(), d->host.ybar.size() * 4, (const void **)&d->ybar)) ||
+        (st = upload(d->host.mabar.data(), d->host.mabar.size() * 4, (const void **)&d->mabar)) ||
+        (st = upload(d->host.arc.data(), d->host.arc.size() * 4, (const void **)&d->arc)) ||
+        (st = upload(d->host.expand.data(), d->host.expand.size() * 2, (const void **)&d->expand))) {
+        cudaFree((void *)d->ybar);
+        cudaFree((void *)d->mabar);
+        cudaFree((void *)d->arc);
+        cudaFree((void *)d->expand);
+        delete d;
+        return st;
+    }
+    g_bwd_tables[key] = d;
+    *out = d;
+    return SG2V_OK;
+}
+
 // ---- kernel timing records (measurement support)
 struct ProfRecord {
     int64_t launches = 0;
@@ -2196,7 +2241,10 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     // backward launch shapes of the transposed SpMM (gathers gradient rows of width C(kc-1, p))
     const size_t nn = P.nodes.size();
     std::vector<Shape> bshape(nn);
-    std::vector<BackwardTables> btab(nn);
+    // the backward tables of each node (cached per device and shape)
+    std::vector<const BackwardTables *> btab(nn);
+    std::vector<const uint32_t *> d_ybar(nn), d_mabar(nn), d_arc(nn);
+    std::vector<const uint16_t *> d_bexp(nn);
     int64_t scratch_ld = P.scratch_ld;
     for (size_t i = 0; i < nn; ++i) {
         const CNode &c = P.nodes[i];
@@ -2230,25 +2278,13 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             }
             scratch_ld = std::max<int64_t>(scratch_ld, (int64_t)kc * sh.wz_pad);
         }
-        build_backward_tables(kc, c.t, c.a, sh.wz_pad, &btab[i]);
-    }
-    // device copies of the backward tables (per call; they are small)
-    std::vector<const uint32_t *> d_ybar(nn), d_mabar(nn), d_arc(nn);
-    std::vector<const uint16_t *> d_bexp(nn);
-    auto upload = [&](const void *h, size_t bytes, const void **d) -> sg2v_status {
-        void *p = nullptr;
-        sg2v_status s2 = ws.alloc(&p, bytes);
-        if (s2) return s2;
-        if (bytes) SG2V_CUDA(cudaMemcpyAsync(p, h, bytes, cudaMemcpyHostToDevice, stream), "table upload");
-        *d = p;
-        return SG2V_OK;
-    };
-    for (size_t i = 0; i < nn; ++i) {
-        if ((st = upload(btab[i].ybar.data(), btab[i].ybar.size() * 4, (const void **)&d_ybar[i])) ||
-            (st = upload(btab[i].mabar.data(), btab[i].mabar.size() * 4, (const void **)&d_mabar[i])) ||
-            (st = upload(btab[i].arc.data(), btab[i].arc.size() * 4, (const void **)&d_arc[i])) ||
-            (st = upload(btab[i].expand.data(), btab[i].expand.size() * 2, (const void **)&d_bexp[i])))
-            return st;
+        const DeviceBackward *db = nullptr;
+        if ((st = backward_tables(P.dev, kc, c.t, c.a, sh.wz_pad, &db))) return st;
+        btab[i] = &db->host;
+        d_ybar[i] = db->ybar;
+        d_mabar[i] = db->mabar;
+        d_arc[i] = db->arc;
+        d_bexp[i] = db->expand;
     }
     // run buffers (one colouring), with split-row scratch wide enough for both directions
     Prepared Pw = P;
@@ -2443,9 +2479,9 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         E.Ybar = ybar;
         E.ldyb = ldyb;
         E.ybar = d_ybar[ii];
-        E.nybar = btab[ii].nybar;
+        E.nybar = btab[ii]->nybar;
         E.mabar = d_mabar[ii];
-        E.nmabar = btab[ii].nmabar;
+        E.nmabar = btab[ii]->nmabar;
         {
             // algorithmic bytes: G (or the seed), M_a and Y' read, Ybar written,
             // the active child's gradient read and written
@@ -2472,9 +2508,9 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             A.defer = 0;
             A.npass = 1;
             A.zglobal = nullptr;
-            A.p = btab[ii].nterms;
-            A.pstride = btab[ii].nterms;
-            A.wy = btab[ii].wout;
+            A.p = btab[ii]->nterms;
+            A.pstride = btab[ii]->nterms;
+            A.wy = btab[ii]->wout;
             A.expand = d_bexp[ii];
             A.a_leaf = 1;
             A.Ma = nullptr;
@@ -2482,7 +2518,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             A.nsplit = 0;
             A.root = 0;
             A.root_out = nullptr;
-            A.Ws = btab[ii].wout;
+            A.Ws = btab[ii]->wout;
             A.Ms = gt[c.passive];
             A.ldt = R.ld[c.passive];
             A.accumulate = 1;
@@ -2517,7 +2553,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         }
         D.wmp = (int)binom(kc - 1, c.p - 1);
         D.arc = d_arc[ii];
-        D.narc = btab[ii].narc;
+        D.narc = btab[ii]->narc;
         D.grad = part;
         // every form walks the forward work list (long rows in chunks)
         D.tasks = g->tasks;

@@ -23,7 +23,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 #include <unordered_map>
 
@@ -1872,8 +1874,7 @@ void node_shape(int vecn, int wz, int *g, int *nv) {
     }
 }
 
-int blocks_per_sm(void *k, int threads, size_t smem) {
-    if (!k) return 0;
+static int blocks_per_sm_query(void *k, int threads, size_t smem) {
     if (smem > 48 * 1024) {
         // one limit per kernel variant, shared by every node that uses it: the device maximum
         int dev = 0, optin = 0;
@@ -1892,6 +1893,30 @@ int blocks_per_sm(void *k, int threads, size_t smem) {
         cudaGetLastError();
         return 0;
     }
+    return blocks;
+}
+
+// Resident blocks per SM of kernel k (0 when it cannot run with this shared
+// memory), remembered per device: every request preparation asks for the same
+// few launch shapes, and each driver query costs microseconds of host time.
+int blocks_per_sm(void *k, int threads, size_t smem) {
+    if (!k) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    static std::mutex mu;
+    static std::map<std::tuple<int, void *, int, size_t>, int> known;
+    const auto key = std::make_tuple(dev, k, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = known.find(key);
+        if (it != known.end()) return it->second;
+    }
+    const int blocks = blocks_per_sm_query(k, threads, smem);
+    std::lock_guard<std::mutex> lock(mu);
+    known[key] = blocks;
     return blocks;
 }
 
@@ -2128,17 +2153,9 @@ cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t
         const size_t smem = (size_t)8 * args.kc * args.wz_pad * (fp64 ? 8 : 4);
         if (!k) return cudaErrorInvalidValue;
         if (args.ntasks == 0) return cudaSuccess;
-        if (smem > 48 * 1024) {
-            int dev = 0, optin = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-            if (smem > (size_t)optin) return cudaErrorInvalidValue;
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
-        if (e != cudaSuccess) return e;
+        // (raises the kernel's shared-memory limit when it needs more than 48 KB)
+        const int per_sm = blocks_per_sm(k, 256, smem);
+        if (per_sm < 1) return cudaErrorInvalidValue;
         const int64_t blocks = std::min<int64_t>((args.ntasks + 7) / 8, (int64_t)sms * std::max(per_sm, 1));
         SddmmArgs a = args;
         void *params[] = {&a};

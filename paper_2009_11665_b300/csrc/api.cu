@@ -1247,7 +1247,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     for (int b0 = 0; b0 < nb; b0 += wave) {
         const int wb = std::min(wave, nb - b0);
         const int8_t *wcol = d_col + (int64_t)b0 * n;
-        SortHist hist{nullptr, 0, P.elem, nullptr, 0};
+        SortHist hist{nullptr, 0, P.elem, nullptr, 0, nullptr};
         double hist_bytes = 0.0;
         if (R.hcount) {
             // neighbour counts per colour for the histogram nodes
@@ -2293,7 +2293,16 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
     if ((st = alloc_run(Pw, 1, alloc, &R))) return st;
     SG2V_CUDA(cudaMemsetAsync(R.status, 0, 16, stream), "memset");
     SG2V_CUDA(launch_check_colours(d_col, n, kc, R.status, stream), "colour check");
-    const SortHist no_hist{nullptr, 0, Elem::F32, nullptr, 0};
+    SortHist no_hist{nullptr, 0, Elem::F32, nullptr, 0, nullptr};
+    // the arc index of every sorted arc, for the per-arc gradient over sorted
+    // arcs (SG2V_SDDMM_SORTED=0 keeps the per-row form)
+    const char *sorted_env = std::getenv("SG2V_SDDMM_SORTED");
+    const bool sorted_sddmm = !(sorted_env && std::atoi(sorted_env) == 0);
+    int32_t *sperm = nullptr;
+    if (sorted_sddmm) {
+        if ((st = alloc((size_t)nnz * sizeof(int32_t), (void **)&sperm))) return st;
+        no_hist.perm = sperm;
+    }
     SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, nnz, d_col, 1, kc,
                                  R.scol, R.sclr, R.sw, no_hist, P.info.sms, stream),
               "colour sort");
@@ -2566,6 +2575,19 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
                 D.lanes = lanes;
                 D.vecs = vecs;
                 D.wz_pad = lanes * vecs * vecn;
+                if (sorted_sddmm && sddmm_sorted_available(P.fp64, lanes, vecs)) {
+                    // over the colour-sorted arcs: v's Ybar' row staged with a zero slot
+                    const int ysink = (int)((wy + vecn - 1) / vecn * vecn);
+                    const uint16_t *rm = nullptr;
+                    if ((st = run_map(P.dev, kc, c.t, c.a, 0, lanes * vecs * vecn, ysink, &rm))) return st;
+                    D.scol = R.scol;
+                    D.sclr = R.sclr;
+                    D.perm = sperm;
+                    D.runmap = rm;
+                    D.wmap = lanes * vecs * vecn;
+                    D.ysink = ysink;
+                    D.ywords = ysink + vecn;
+                }
             }
         }
         // algorithmic bytes: the CSR, the colouring, Ybar and M_p read once,

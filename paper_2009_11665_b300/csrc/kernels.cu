@@ -1365,6 +1365,7 @@ __global__ void colour_sort_small_kernel(const int4 *__restrict__ tasks, int64_t
             if (in) {
                 const int64_t pos = (int64_t)b * nnz + task.z + rank;
                 scol[pos] = u;
+                if (H.perm) H.perm[pos] = task.z + gl;
                 sclr[pos] = (int8_t)(c == kc ? -1 : c);
                 if (sw) sw[pos] = __ldg(weights + task.z + gl);
             }
@@ -1452,6 +1453,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
             int32_t *so = scol + (int64_t)b * nnz + e0;
             int8_t *co = sclr + (int64_t)b * nnz + e0;
             float *wo = sw ? sw + (int64_t)b * nnz + e0 : nullptr;
+            int32_t *po = H.perm ? H.perm + (int64_t)b * nnz + e0 : nullptr;
             if (single) {
                 // one batch: bucket sizes from the groups of equal colours
                 const bool ok = e_one < e1;
@@ -1479,6 +1481,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                     so[pos] = u_one;
                     co[pos] = (int8_t)(c == kc ? -1 : c);
                     if (wo) wo[pos] = __ldg(weights + e_one);
+                    if (po) po[pos] = (int32_t)e_one;
                 }
                 __syncwarp();
                 continue;
@@ -1536,6 +1539,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                         so[pos] = u;
                         co[pos] = (int8_t)(c == kc ? -1 : c);
                         if (wo) wo[pos] = __ldg(weights + e);
+                        if (po) po[pos] = (int32_t)e;
                     }
                     __syncwarp();
                     if (ok && (same & lt) == 0) start[c] += __popc(same);
@@ -1576,6 +1580,7 @@ __global__ void colour_sort_kernel(const int4 *__restrict__ tasks, int64_t ntask
                     so[pos] = u;
                     co[pos] = (int8_t)(c == kc ? -1 : c);
                     if (wo) wo[pos] = __ldg(weights + e);
+                    if (po) po[pos] = (int32_t)e;
                 }
                 __syncwarp();
                 // advance every bucket by its arcs in this batch (leader lane of each group)
@@ -1687,7 +1692,8 @@ __global__ void sddmm_kernel(const SddmmArgs A) {
                 const uint32_t x = __ldg(pr + i);
                 acc = A.hist ? acc + yr[x & 0xffffu] : fma(yr[x & 0xffffu], mp[x >> 16], acc);
             }
-            A.grad[e] += (double)acc;
+            // each arc's slot gains one term per launch: a reduction nothing waits on
+            atomicAdd(A.grad + e, (double)acc);
         }
         __syncwarp();
     }
@@ -1773,10 +1779,123 @@ __global__ void __launch_bounds__(256) sddmm_rows_kernel(const SddmmArgs A) {
                 }
 #pragma unroll
                 for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-                if (gl == 0 && j < cnt) A.grad[base + sj] += (double)acc;
+                if (gl == 0 && j < cnt) atomicAdd(A.grad + base + sj, (double)acc);  // (one term per arc)
             }
         }
         __syncwarp();
+    }
+}
+
+// Per-arc weight gradient over the colour-sorted arcs (row form, p >= 2):
+// the gradient of arc (v, u) is the sum over the entries e of u's compressed
+// row M_p'(u, .) of M_p'(u, e) * Ybar'(v, P_e), P_e = {col u} + the e-th
+// (p-1)-set of col(u)'s squeezed universe, over the sets without col(v): the
+// SpMM of Alg. 4 read backwards.  v's arcs come sorted by neighbour colour,
+// so each colour is one run: when a lane group's run starts, each lane reads
+// the Ybar' entries its vectors pair with (the node's run map, as in the
+// forward run kernel) into registers, and an arc then costs one row load per
+// lane, the products and a reduction over the group.  Groups of G lanes take
+// one arc each; each result goes to its arc's slot through the sort's
+// permutation.  v's Ybar' row is staged in shared memory per warp, with zeros
+// at ysink for the entries whose set holds col(v).
+template <typename T, int G, int NV>
+__global__ void __launch_bounds__(256) sddmm_sorted_kernel(const SddmmArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = Vec16<T>;
+    using VT = typename V::type;
+    constexpr int E = V::n;
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G;
+    const int kc = A.kc;
+    T *yb = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * A.ywords;
+    if (lane < E) yb[A.ysink + lane] = T(0);
+    // entries of this lane's vectors inside the row (the row padding past
+    // wmp is never written, and 0 times its contents need not be 0)
+    int lim[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const int left = A.wmp - (gl + G * q) * E;
+        lim[q] = left < 0 ? 0 : (left > E ? E : left);
+    }
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ti = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; ti < A.ntasks; ti += nwarps) {
+        const int4 task = A.tasks[ti];
+        const int v = task.x;
+        const int cv = A.colours[v];
+        if ((unsigned)cv >= (unsigned)kc || task.z == task.w) continue;
+        // the previous task's reads of yb are done
+        __syncwarp();
+        const T *yr = static_cast<const T *>(A.Ybar) + (int64_t)v * A.ldyb;
+        for (int j = lane; j < A.ysink; j += 32) yb[j] = yr[j];
+        __syncwarp();
+        const uint16_t *rm = A.runmap + (int64_t)cv * kc * A.wmap + gl * E;
+        T zq[NV][E];
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+#pragma unroll
+            for (int k = 0; k < E; ++k) zq[q][k] = T(0);
+        int cur = -1;
+        for (int64_t base = task.z; base < task.w; base += 32) {
+            const int cnt_in = (int)(task.w - base < 32 ? task.w - base : 32);
+            const bool in = lane < cnt_in;
+            const int c_in = in ? (int)__ldg(A.sclr + base + lane) : -1;
+            const bool t_in = c_in >= 0 && c_in != cv;  // (-1: a colour outside [0, kc))
+            const int u_in = t_in ? __ldg(A.scol + base + lane) : 0;
+            const int p_in = t_in ? __ldg(A.perm + base + lane) : 0;
+            // compacted: lane j takes the j-th arc that has a gradient here
+            const unsigned live = __ballot_sync(kFull, t_in);
+            const int cnt = __popc(live);
+            if (cnt == 0) continue;
+            const int src = lane < cnt ? (int)__fns(live, 0, lane + 1) : lane;
+            const int u_l = __shfl_sync(kFull, u_in, src);
+            const int c_l = __shfl_sync(kFull, c_in, src);
+            const int p_l = __shfl_sync(kFull, p_in, src);
+            for (int j0 = 0; j0 < cnt; j0 += NG) {
+                const int j = j0 + grp;
+                const bool ok = j < cnt;
+                const int jj = ok ? j : cnt - 1;
+                const int u = __shfl_sync(kFull, u_l, jj);
+                const int c = __shfl_sync(kFull, c_l, jj);
+                const int pe = __shfl_sync(kFull, p_l, jj);
+                if (c != cur) {
+                    // the group's run changes colour: its lanes' Ybar' entries
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        const uint16_t *mp = rm + (int64_t)c * A.wmap + G * E * q;
+                        if constexpr (E == 4) {
+                            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(mp));
+                            zq[q][0] = yb[w.x & 0xffffu];
+                            zq[q][1] = yb[w.x >> 16];
+                            zq[q][2] = yb[w.y & 0xffffu];
+                            zq[q][3] = yb[w.y >> 16];
+                        } else {
+                            const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(mp));
+                            zq[q][0] = yb[w & 0xffffu];
+                            zq[q][1] = yb[w >> 16];
+                        }
+                    }
+                    cur = c;
+                }
+                T acc = T(0);
+                if (ok) {
+                    const VT *mr = reinterpret_cast<const VT *>(static_cast<const T *>(A.Mp) + (int64_t)u * A.ldp) + gl;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        if (lim[q] > 0) {
+                            const VT mq = __ldg(mr + G * q);
+                            const T *mm = reinterpret_cast<const T *>(&mq);
+#pragma unroll
+                            for (int k = 0; k < E; ++k)
+                                if (k < lim[q]) acc = fma(zq[q][k], mm[k], acc);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+                if (gl == 0 && ok) atomicAdd(A.grad + pe, (double)acc);  // (one term per arc)
+            }
+        }
     }
 }
 
@@ -2120,13 +2239,15 @@ cudaError_t launch_finalize(const RootSum *sums, int nseg, int nb, const double 
 
 cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStream_t stream) {
     const size_t smem = (size_t)8 * (args.ws + args.wa + args.wy) * (fp64 ? 8 : 4);
-    if (smem > 48 * 1024) return cudaErrorInvalidValue;
-    const int64_t blocks = std::min<int64_t>((args.n + 7) / 8, (int64_t)sms * 8);
-    if (fp64)
-        bwd_ema_kernel<double><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
-    else
-        bwd_ema_kernel<float><<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, stream>>>(args);
-    return cudaGetLastError();
+    void *k = fp64 ? reinterpret_cast<void *>(&bwd_ema_kernel<double>)
+                   : reinterpret_cast<void *>(&bwd_ema_kernel<float>);
+    // (raises the kernel's shared-memory limit past 48 KB when the rows need it)
+    const int per_sm = blocks_per_sm(k, 256, smem);
+    if (per_sm < 1) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((args.n + 7) / 8, (int64_t)sms * per_sm);
+    BwdEmaArgs a = args;
+    void *params[] = {&a};
+    return cudaLaunchKernel(k, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), params, smem, stream);
 }
 
 namespace {
@@ -2144,9 +2265,38 @@ void *pick_sddmm_rows(int g, int nv) {
         default: return nullptr;
     }
 }
+template <typename T>
+void *pick_sddmm_sorted(int g, int nv) {
+    if (nv == 1) {
+        if (g == 4) return reinterpret_cast<void *>(&sddmm_sorted_kernel<T, 4, 1>);
+        if (g == 8) return reinterpret_cast<void *>(&sddmm_sorted_kernel<T, 8, 1>);
+        if (g == 16) return reinterpret_cast<void *>(&sddmm_sorted_kernel<T, 16, 1>);
+        if (g == 32) return reinterpret_cast<void *>(&sddmm_sorted_kernel<T, 32, 1>);
+    }
+    if (nv == 2 && g == 32) return reinterpret_cast<void *>(&sddmm_sorted_kernel<T, 32, 2>);
+    return nullptr;
+}
 }  // namespace
 
+bool sddmm_sorted_available(bool fp64, int lanes, int vecs) {
+    return (fp64 ? pick_sddmm_sorted<double>(lanes, vecs) : pick_sddmm_sorted<float>(lanes, vecs)) != nullptr;
+}
+
 cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream) {
+    if (!args.hist && args.tasks && args.lanes > 0 && args.scol) {
+        // sorted form
+        void *k = fp64 ? pick_sddmm_sorted<double>(args.lanes, args.vecs)
+                       : pick_sddmm_sorted<float>(args.lanes, args.vecs);
+        if (!k || !args.runmap || !args.perm) return cudaErrorInvalidValue;
+        if (args.ntasks == 0) return cudaSuccess;
+        const size_t smem = (size_t)8 * args.ywords * (fp64 ? 8 : 4);
+        const int per_sm = blocks_per_sm(k, 256, smem);
+        if (per_sm < 1) return cudaErrorInvalidValue;
+        const int64_t blocks = std::min<int64_t>((args.ntasks + 7) / 8, (int64_t)sms * per_sm);
+        SddmmArgs a = args;
+        void *params[] = {&a};
+        return cudaLaunchKernel(k, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), params, smem, stream);
+    }
     if (!args.hist && args.tasks && args.lanes > 0) {
         // row-oriented form
         void *k = fp64 ? pick_sddmm_rows<double>(args.lanes, args.vecs) : pick_sddmm_rows<float>(args.lanes, args.vecs);

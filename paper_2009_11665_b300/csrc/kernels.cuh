@@ -181,10 +181,21 @@ struct SddmmArgs {
     const int4 *tasks;
     int64_t ntasks;
     int lanes, vecs, wz_pad;
+    // sorted form (row form with scol != null): the forward's colour-sorted
+    // arcs of every task with each one's arc index (perm), and the node's run
+    // map ([kc][kc][wmap]: for v's colour and the neighbour's colour, where
+    // entry e of the neighbour's row sits in v's Ybar' row, or ysink, a zero)
+    const int32_t *scol;
+    const int8_t *sclr;
+    const int32_t *perm;
+    const uint16_t *runmap;
+    int wmap, ysink, ywords;
 };
 
 cudaError_t launch_bwd_ema(const BwdEmaArgs &args, bool fp64, int sms, cudaStream_t stream);
 cudaError_t launch_sddmm(const SddmmArgs &args, bool fp64, int sms, cudaStream_t stream);
+// whether the sorted form of the per-arc gradient exists for this row shape
+bool sddmm_sorted_available(bool fp64, int lanes, int vecs);
 // grad_w[arcmap[e]] = part[e] + part[rev[e]] (arcmap null: grad_w[e])
 cudaError_t launch_symmetrize(const double *part, const int32_t *rev, const int32_t *arcmap, int64_t nnz,
                               double *grad_w, cudaStream_t stream);
@@ -310,6 +321,9 @@ struct SortHist {
     // split rows add atomically into a zeroed buffer); null: none
     int32_t *hcount;
     int hld;
+    // the arc index (into col_idx) of every sorted arc ([nb][nnz],
+    // sorted positions), or null: maps per-arc results back to arc order
+    int32_t *perm;
 };
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,

@@ -32,17 +32,17 @@ def sg():
     return s
 
 
-def _exact_grad(g, w, parent, col, edges, seedv=None):
+def _exact_grad(g, w, parent, col, edges, seedv=None, num_colours=None):
     """dF/dw_e for the listed undirected edges, exact, from the oracle."""
     ids = si.arc_edge_ids(g)
-    base = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, weights=w)
+    base = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, num_colours=num_colours, weights=w)
     bpv = base.per_vertex_values()
     F = sum(Fraction(float(s)) * x for s, x in zip(seedv, bpv)) if seedv is not None else base.total_value()
     out = {}
     for e in edges:
         w0 = w.copy()
         w0[ids == e] = 0.0
-        r = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, weights=w0)
+        r = oracle.count(g.row_ptr, g.col_idx, parent, 0, col, num_colours=num_colours, weights=w0)
         F0 = sum(Fraction(float(s)) * x for s, x in zip(seedv, r.per_vertex_values())) if seedv is not None \
             else r.total_value()
         out[e] = (F - F0) / Fraction(float(w[ids == e][0]))
@@ -236,3 +236,38 @@ def test_recompute_form_with_split_rows(sg, monkeypatch):
     for e in edges:
         for a in np.nonzero(ids == e)[0]:
             assert abs(res["recompute"][a] - float(exact[e])) <= 1e-12 * abs(float(exact[e])) + 1e-300
+
+
+@pytest.mark.parametrize("parent,kc", [(si.TREE8.parent, 8), (si.TREE10.parent, 10), (si.TREE8.parent, 12),
+                                       ((-1, 0, 1, 2, 3), 5)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sorted_per_arc_gradient_matches_row_form(sg, parent, kc, prec, monkeypatch):
+    """The per-arc gradient over colour-sorted arcs (each result sent to its
+    arc through the sort's permutation) equals the per-row form
+    (SG2V_SDDMM_SORTED=0), with rows split into chunks of 64 arcs (the forward
+    folds split rows with atomic adds, so FP64 agrees to rounding, not bit for
+    bit), and matches exact differences of the oracle."""
+    import torch
+
+    monkeypatch.setenv("SG2V_CHUNK", "64")
+    g = si.chung_lu(1500, 9000, 2.3, seed=11)
+    assert int(np.diff(g.row_ptr).max()) > 64
+    w = si.arc_weights(g, si.edge_weights(g, seed=5))
+    col = si.colouring(g.n, kc, 4)
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(parent, num_colours=kc)
+    res = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("SG2V_SDDMM_SORTED", env)
+        gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        sg.sg2v_count_backward(graph.handle, plan.handle, torch.from_numpy(col).cuda(), sg.PRECISIONS[prec], gw)
+        res[env] = gw.cpu().numpy()
+    rtol = 1e-12 if prec == "fp64" else 1e-5
+    np.testing.assert_allclose(res["1"], res["0"], rtol=rtol, atol=rtol * np.abs(res["0"]).max())
+    ids = si.arc_edge_ids(g)
+    edges = [int(e) for e in si.sample_indices(6, g.m, seed=kc)]
+    _, exact = _exact_grad(g, w, parent, col, edges, num_colours=kc)
+    tol = 1e-11 if prec == "fp64" else 1e-4
+    for e in edges:
+        for a in np.nonzero(ids == e)[0]:
+            assert abs(res["1"][a] - float(exact[e])) <= tol * abs(float(exact[e])) + 1e-300, (e, res["1"][a])

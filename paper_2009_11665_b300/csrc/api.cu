@@ -883,7 +883,10 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         // per-colour accumulators of node_kernel); short tasks of narrow rows
         // stay one per lane group (node_group_kernel)
         const char *run_env = std::getenv("SG2V_RUN_KERNEL");
+        const char *narrow_env = std::getenv("SG2V_RUN_NARROW");  // 0: warp-wide rows only
+        const bool narrow_ok = !(narrow_env && std::atoi(narrow_env) == 0);
         if (!(run_env && std::atoi(run_env) == 0) && !hist && sh.grp != kWideLanes && !sh.rows &&
+            (sh.grp == 32 || narrow_ok) &&
             (sh.nv == 1 || (sh.nv == 2 && sh.grp == 32)) && !P->scaled &&
             (P->elem == Elem::F32 || P->elem == Elem::F64)) {
             const int E = P->vecn;
@@ -893,7 +896,9 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
             const int ywords = ybase + E;
             const int mwords = (c.a >= 2 || c.is_root) ? mbase + E : 0;
             const int threads = kNodeThreads;
-            const size_t smem = (size_t)(threads / 32) * ((size_t)(ywords + mwords) * P->esz + kRunCompactBytes);
+            // per warp: a copy of Y' per lane group, the active row, the compacted arcs
+            const size_t smem =
+                (size_t)(threads / 32) * ((size_t)((32 / sh.grp) * ywords + mwords) * P->esz + kRunCompactBytes);
             const int form = (c.is_root && c.t == kc) ? 2 : ((c.a == 1 && !c.is_root) ? 1 : 0);
             const int bps =
                 node_run_blocks_per_sm(P->elem, sh.grp, sh.nv, g->weights != nullptr, form, threads, smem);

@@ -22,15 +22,18 @@
 // colours they have.
 //
 // Lanes form groups of G that cover one neighbour row (G * NV 16-byte
-// vectors), so a warp instruction gathers 32 / G arcs; only G = 32 is
-// instantiated (see pick_run).  The gather
-// loop is kept short because these launches are bound by issue slots: each
+// vectors), so a warp instruction gathers 32 / G arcs (group g takes every
+// (32/G)-th arc of the task, so every group walks the same colour runs).
+// The gather loop is kept short because these launches are bound by issue
+// slots: each
 // batch of 32 sorted arcs is compacted (through shared memory) to the arcs
 // that add something, each as one word u << 4 | colour, so an arc costs one
 // shuffle, one address, one 16-byte load and the adds; lanes past the row's
 // last vector load that vector again (no predicate), and a step that stays
-// in every group's current run skips the per-arc colour test.  Groups scatter
-// with shared-memory atomic adds (their runs end at different times).
+// in every group's current run skips the per-arc colour test.  Groups
+// narrower than the warp end their runs at different times, so each scatters
+// into its own copy of Y'; the copies are summed once the task's arcs are
+// done.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -71,17 +74,23 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     // FP64 adds are scarce on this part: slots past a batch's live arcs skip
     // their load and adds; FP32 slots read the zero row instead
     constexpr bool SKIP_ZERO = sizeof(T) >= 8;
-    constexpr bool RMW = G == 32 && SG2V_RUN_RMW32;
+    // warp-wide groups scatter with plain read-modify-writes (or atomics when
+    // SG2V_RUN_RMW32 = 0); narrower groups each own a copy of Y' (no group
+    // races another), folded once the task's arcs are done
+    constexpr bool RMW = G < 32 || SG2V_RUN_RMW32;
     static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
     // per warp: Y' with its sink (FORM 0 / 1), the active row with its zero
     // (a >= 2 or FORM 2), and the batch's compacted arcs
-    T *ybuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (A.ywords + A.mwords);
-    T *mbuf = ybuf + A.ywords;
+    const int yreg = NG * A.ywords;  // Y' copies of the warp's groups
+    T *ybuf = reinterpret_cast<T *>(smem_raw) + (int64_t)wib * (yreg + A.mwords);
+    T *mbuf = ybuf + yreg;
+    T *ygrp = ybuf + grp * A.ywords;  // this group's copy
+    const unsigned gmask = (G == 32 ? kFull : ((1u << G) - 1u)) << (grp * G);
     unsigned *cbuf = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(smem_raw) +
-                                                  (size_t)(blockDim.x >> 5) * (A.ywords + A.mwords) * sizeof(T) +
+                                                  (size_t)(blockDim.x >> 5) * (NG * A.ywords + A.mwords) * sizeof(T) +
                                                   (size_t)wib * kRunCompactBytes);
     float *wbuf = reinterpret_cast<float *>(cbuf + 32);
     // the warp's next task descriptor, copied in while the current task runs
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
             if (FORM != 2)
-                for (int j = lane; j < A.ywords; j += 32) ybuf[j] = T(0);
+                for (int j = lane; j < yreg; j += 32) ybuf[j] = T(0);
             bool mready = mchunks == 0 || !cok;
             T acc = T(0);  // FORM 2: this lane's part of the row sum
             // lane vectors as 32-bit offsets from the table (fewer live registers)
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                             const T x = (emask >> (q * E + k) & 1u) ? rv[k] : T(0);
                             acc = fma(x, mbuf[ix[k]], acc);
                         } else if constexpr (RMW) {
-                            ybuf[ix[k]] += rv[k];
+                            ygrp[ix[k]] += rv[k];
                         } else {
                             // one shared-memory reduction per entry; the sink's
                             // entries are skipped (their adds would serialise)
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     run[q] = V::zero();
                 }
                 // the next run may add to the same entries of Y'
-                if (FORM != 2 && RMW) __syncwarp();
+                if (FORM != 2 && RMW) __syncwarp(gmask);
             };
             for (int base = 0; base < len; base += 32) {
                 const int cnt_in = len - base < 32 ? len - base : 32;
@@ -293,6 +302,16 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
             if (cur >= 0) flush(cur);
             if (FORM == 2 && !mready) asm volatile("cp.async.wait_all;\n" ::: "memory");
             __syncwarp();
+            if constexpr (NG > 1 && FORM != 2) {
+                // fold the groups' copies of Y' into the first
+                for (int j = lane; j < A.ywords; j += 32) {
+                    T y = ybuf[j];
+#pragma unroll
+                    for (int g2 = 1; g2 < NG; ++g2) y += ybuf[g2 * A.ywords + j];
+                    ybuf[j] = y;
+                }
+                __syncwarp();
+            }
             if constexpr (FORM == 2) {
                 T s = warp_sum(acc);
                 if (slot >= 0) {
@@ -379,16 +398,19 @@ void *pick_form(int form) {
     return reinterpret_cast<void *>(&node_run_kernel<T, G, NV, W, 0>);
 }
 
-// Warp-wide rows only: for narrow rows (g < 32) the lane groups see their
-// colour runs cut into pieces (each group takes every (32/g)-th arc), and
-// the per-colour accumulators of node_kernel / node_group_kernel measured
-// faster ((4,2,2) on the 1M-vertex R-MAT graph: 0.76 ms there, 1.06 ms here).
+// Warp-wide rows (one or two vectors per lane) and narrow rows of one vector
+// per lane in groups of 4, 8 or 16 lanes (each group with its own Y').
 template <typename T, bool W>
 void *pick_run(int g, int nv, int form) {
-    if (g != 32) return nullptr;
-    if (nv == 2) return pick_form<T, 32, 2, W>(form);
-    if (nv == 1) return pick_form<T, 32, 1, W>(form);
-    return nullptr;
+    if (nv == 2) return g == 32 ? pick_form<T, 32, 2, W>(form) : nullptr;
+    if (nv != 1) return nullptr;
+    switch (g) {
+        case 32: return pick_form<T, 32, 1, W>(form);
+        case 16: return pick_form<T, 16, 1, W>(form);
+        case 8: return pick_form<T, 8, 1, W>(form);
+        case 4: return pick_form<T, 4, 1, W>(form);
+        default: return nullptr;
+    }
 }
 
 // FP32 weighted and unweighted, FP64 unweighted (the weighted FP64 form stays

@@ -317,13 +317,16 @@ def test_min_work_plans_match_oracle(sg, seed):
 
 
 @pytest.mark.parametrize("knob", ["SG2V_HIST_ROWS", "SG2V_GROUP_ROWS", "SG2V_HALF_ROOT", "SG2V_ROOT_PAIRS",
-                                  "SG2V_SORT_HIST", "SG2V_SORT_COUNTS", "SG2V_RUN_KERNEL", "SG2V_PRED_LANES"])
+                                  "SG2V_SORT_HIST", "SG2V_SORT_COUNTS", "SG2V_RUN_KERNEL", "SG2V_PRED_LANES",
+                                  "SG2V_RUN_NARROW", "SG2V_SKIP_EMPTY"])
 def test_alternative_kernel_forms(sg, knob, monkeypatch):
     """The forms that the 32-row histogram kernel, the lane-group kernel, the
     half-arc root, the paired root sum, the sort-written (2, 1, 1) table, the
-    run-scatter kernel and the FP32 gathers without lane predicates replace
-    on unweighted graphs (they still serve weighted graphs, long tasks,
-    other table types and roots with several output sets) equal the oracle."""
+    run-scatter kernel (for every row width, or for narrow rows), the FP32
+    gathers without lane predicates and the skipping of isolated vertices
+    replace on unweighted graphs (they still serve weighted graphs, long
+    tasks, other table types and roots with several output sets) equal the
+    oracle."""
     monkeypatch.setenv(knob, "0")
     g = _hub_graph(9)
     for parent in (si.TREE10.parent, si.TREE7.parent, si.PATH7.parent, (-1, 0, 0, 2)):

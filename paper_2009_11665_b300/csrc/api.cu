@@ -651,6 +651,7 @@ struct Prepared {
     Elem elem = Elem::F32;        // table element type
     size_t esz = 4;
     int vecn = 4;
+    int l2_stream = 1;            // run-scatter kernel: evict-first hints on data used once
     int64_t n = 0;
     DeviceInfo info;
     std::vector<CNode> nodes;
@@ -730,6 +731,11 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
                       : (precision == SG2V_U64 ? Elem::U64 : (precision == SG2V_U128 ? Elem::U128 : Elem::F32));
     P->esz = P->elem == Elem::F32 ? 4 : (P->elem == Elem::U128 ? 16 : 8);
     P->vecn = (int)(16 / P->esz);
+    {
+        // SG2V_L2_STREAM=0: no evict-first hints in the run-scatter kernel
+        const char *ls = std::getenv("SG2V_L2_STREAM");
+        P->l2_stream = (ls && std::atoi(ls) == 0) ? 0 : 1;
+    }
     P->n = g->n;
     P->plan_root.assign(num_plans, -1);
     std::map<std::string, int> shared;
@@ -1127,6 +1133,7 @@ NodeArgs node_args(const Prepared &P, const RunBuffers &R, size_t i, int b0, int
         const char *pl = std::getenv("SG2V_PRED_LANES");
         A.pred_lanes = (pl && std::atoi(pl) == 0) ? 0 : 1;
     }
+    A.l2_stream = P.l2_stream;
     if (P.scaled) {
         A.scaled = 1;
         A.owords = sh.owords;

@@ -123,6 +123,10 @@ struct NodeArgs {
     // rows [live_rows, n) belong to isolated vertices whose tasks do not run
     // (their table rows are never read); n when every row runs
     int64_t live_rows;
+    // run-scatter kernel: data read or written once per launch (sorted arcs,
+    // active rows, output rows) carry an L2 evict-first hint (l2_stream != 0),
+    // so the gathered table keeps more of L2
+    int l2_stream;
     // partial Z of split (heavy) rows
     void *scratch;                // [slots][nb][scratch_ld]
     int64_t scratch_ld;

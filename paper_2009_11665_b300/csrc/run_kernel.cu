@@ -63,6 +63,35 @@ struct RunMinBlocks {
     static constexpr int value = sizeof(T) == 4 ? SG2V_RUN_MINB_F32 : (NV == 1 ? 3 : 2);
 };
 
+// L2 cache policies (createpolicy): evict-first for data used once per
+// launch, evict-normal otherwise.
+__device__ __forceinline__ uint64_t l2_policy(bool evict_first) {
+    uint64_t p;
+    if (evict_first)
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int ld_hint_s8(const int8_t *p, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.s8 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ld_hint_s32(const int32_t *p, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <typename VT>
+__device__ __forceinline__ void st_hint_v16(VT *p, const VT &x, uint64_t pol) {
+    static_assert(sizeof(VT) == 16, "16-byte vectors");
+    const uint4 w = *reinterpret_cast<const uint4 *>(&x);
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(w.x), "r"(w.y), "r"(w.z),
+                 "r"(w.w), "l"(pol)
+                 : "memory");
+}
+
 template <typename T, int G, int NV, bool WEIGHTED, int FORM>
 __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node_run_kernel(const NodeArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -118,6 +147,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
         if (A.a_leaf && lane == 0) mbuf[0] = T(1);
     }
     const unsigned zero_word = (unsigned)A.n << 4;                 // the zero row
+    const uint64_t pol_once = l2_policy(A.l2_stream != 0);
     // (a work list has fewer than 2^32 tasks: one per row plus the chunks)
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     const unsigned ntasks = (unsigned)A.ntasks;
@@ -148,7 +178,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = T(0);
                 } else if constexpr (FORM == 1) {
                     VT *out = reinterpret_cast<VT *>(static_cast<T *>(A.Ms) + rowb * A.ldt);
-                    for (int j = lane; j < (int)(A.ldt / E); j += 32) out[j] = V::zero();
+                    for (int j = lane; j < (A.ywords - E) / E; j += 32) out[j] = V::zero();
                 } else {
                     epilogue<T>(A, v, b, false, ybuf, mbuf, lane, ovf);
                 }
@@ -160,7 +190,9 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 const char *src = static_cast<const char *>(A.Ma) + rowb * A.lda * sizeof(T);
                 for (int c = lane; c < mchunks; c += 32) {
                     const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(mbuf) + 16 * c);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + 16 * c) : "memory");
+                    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(dst),
+                                 "l"(src + 16 * c), "l"(pol_once)
+                                 : "memory");
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
@@ -222,8 +254,8 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
             for (int base = 0; base < len; base += 32) {
                 const int cnt_in = len - base < 32 ? len - base : 32;
                 const bool in = lane < cnt_in;
-                const int c_in = in ? (int)__ldg(A.sclr + aoff + base + lane) : -1;
-                const int u_in = in ? __ldg(A.scol + aoff + base + lane) : 0;
+                const int c_in = in ? ld_hint_s8(A.sclr + aoff + base + lane, pol_once) : -1;
+                const int u_in = in ? ld_hint_s32(A.scol + aoff + base + lane, pol_once) : 0;
                 const bool t_in = cok && c_in >= 0 && c_in != cv && (!A.half_arcs || u_in < v);
                 // compact the batch to the arcs that add something (order kept,
                 // so colour runs stay contiguous) through the warp's slots
@@ -367,7 +399,9 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 // M_s' = Y' (the row's padding gets Y's zeros)
                 VT *out = reinterpret_cast<VT *>(static_cast<T *>(A.Ms) + rowb * A.ldt);
                 const VT *yv = reinterpret_cast<const VT *>(ybuf);
-                for (int j = lane; j < (int)(A.ldt / E); j += 32) out[j] = cok ? yv[j] : V::zero();
+                // (Y' vectors only: a wider row stride leaves padding nothing reads)
+                const int nout = (A.ywords - E) / E;
+                for (int j = lane; j < nout; j += 32) st_hint_v16(out + j, cok ? yv[j] : V::zero(), pol_once);
                 __syncwarp();
                 continue;
             }

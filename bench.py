@@ -483,7 +483,7 @@ def main():
         dom3 = max(tab3.items(), key=lambda kv: kv[1]["ms_per_launch"] * kv[1]["launches_per_step"])
         batched = {"workload": "rmat18_d16 (R-MAT scale 18, avg degree 16), path7+star7+tree7, k=7, 64 colourings",
                    "ms_per_step": ms3, "s_per_colouring_template": ms3 * 1e-3 / (B3 * 3 * world),
-                   "wave": wave3, "cuda_graph": graph_on, "dtype": "f32",
+                   "wave": wave3, "split_chunk": tuning3.get("chunk"), "cuda_graph": graph_on, "dtype": "f32",
                    "autotuned": [f"({n['t']},{n['a']},{n['p']}) {n['kernel']}{', lane groups' if n['lane_groups'] else ''}"
                                  for n in tuning3["nodes"]],
                    "kernel_ms_per_step": kms3, "algorithmic_GB_per_step": bytes3 / 1e9,

@@ -331,20 +331,26 @@ sg2v_status sg2v_session_sync(sg2v_session *session, sg2v_stream stream);
 sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_t *graph);
 
 /*
- * Autotuning (SG2V_SESSION_AUTOTUNE).  The first run times the candidate
- * wave widths, then, at the chosen width, the forms each DP node can take:
+ * Autotuning (SG2V_SESSION_AUTOTUNE).  The first run times the split
+ * schedule first: the chunk size (256 to 8192 arcs, up to the first size
+ * that splits no row) at which rows longer than it are cut into tasks whose
+ * partial results fold into the row, the whole step timed on each
+ * candidate's work list (skipped when the environment variable SG2V_CHUNK,
+ * read at graph creation, fixes the size).  It then times the candidate
+ * wave widths and, at the chosen width, the forms each DP node can take:
  * the run-scatter kernel or per-colour accumulators, short narrow rows one
  * per lane group or one per warp, histogram nodes 32 rows per warp or one,
  * a large eMA in its own launch or in the gather's epilogue.  Each node
  * keeps its fastest form (per-node CUDA-event times; results do not depend
  * on the form).  When the environment variable SG2V_TUNE_CACHE names a file,
  * the choices are stored there as JSON, keyed by graph statistics (vertices,
- * arcs, largest degree, weights), colours, node shape, table type and wave,
- * and a later session whose nodes are all in the file takes them without
- * timing.
+ * arcs, largest degree, weights), colours, node shape, table type, wave and
+ * chunk size (the split schedule by the graph statistics, colours, table
+ * type, colourings and templates), and a later session finding its keys in
+ * the file takes them without timing.
  *
  * sg2v_session_tuning -- the session's choices as JSON text
- * ({"wave": W, "tuned": bool, "nodes": [{"t", "a", "p", "kernel",
+ * ({"wave": W, "chunk": C, "tuned": bool, "nodes": [{"t", "a", "p", "kernel",
  * "lane_groups", "deferred_ema", "form"}, ...]}), NUL-terminated in out
  * (capacity bytes, truncated if short); *length (may be NULL) gets the full
  * length without the NUL.

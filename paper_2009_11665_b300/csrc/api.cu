@@ -435,6 +435,10 @@ struct sg2v_graph {
     // arcmap[new arc] = the caller's arc (null when the caller's order is kept)
     int32_t *iperm = nullptr;
     int32_t *arcmap = nullptr;
+    // work-list variants (another chunk size) that share every array above
+    // except tasks, heavy_chunks and rev; built on demand, owned here
+    bool view = false;
+    std::vector<sg2v_graph *> views;
 };
 
 namespace sg2v {
@@ -442,6 +446,14 @@ namespace {
 
 void free_graph(sg2v_graph *g) {
     if (!g) return;
+    if (g->view) {
+        cudaFree(g->tasks);
+        cudaFree(g->heavy_chunks);
+        cudaFree(g->rev);
+        delete g;
+        return;
+    }
+    for (sg2v_graph *v : g->views) free_graph(v);
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
     cudaFree(g->weights);
@@ -1404,6 +1416,7 @@ struct sg2v_session {
     cudaStream_t capture = nullptr;  // private stream the graph is recorded on (any stream may replay it)
     bool tuned = false;
     int64_t launches_per_run = 0;
+    const sg2v_graph *base = nullptr;  // the caller's graph (P.g may be a work-list variant of it)
 };
 
 namespace sg2v {
@@ -1587,9 +1600,9 @@ std::string form_code(const Shape &sh) {
 std::string tune_key(const Prepared &P, size_t i, int wave) {
     const CNode &c = P.nodes[i];
     char buf[256];
-    std::snprintf(buf, sizeof buf, "n%lld_m%lld_d%lld_w%d|kc%d|t%d_a%d_p%d_r%d|%s|wave%d|nb%d|",
+    std::snprintf(buf, sizeof buf, "n%lld_m%lld_d%lld_w%d|kc%d|t%d_a%d_p%d_r%d|%s|wave%d|nb%d|chunk%d|",
                   (long long)P.n, (long long)P.g->nnz, (long long)P.g->max_degree, P.g->weighted ? 1 : 0, P.kc,
-                  c.t, c.a, c.p, c.is_root ? 1 : 0, elem_name(P), wave, P.nb);
+                  c.t, c.a, c.p, c.is_root ? 1 : 0, elem_name(P), wave, P.nb, P.g->chunk);
     // the sub-template itself (nodes of one shape can be different trees);
     // its AHU form uses only parentheses, safe inside a JSON string
     return std::string(buf) + c.canon;
@@ -1682,6 +1695,76 @@ sg2v_status tune_forms(sg2v_session *S, cudaStream_t stream) {
     return SG2V_OK;
 }
 
+sg2v_status graph_view(const sg2v_graph *g, int chunk, const sg2v_graph **out);
+
+// Split schedule: the chunk size at which long rows are cut into tasks.  The
+// session's whole step is timed (CUDA events, after a warm-up) on the work
+// list of each candidate size and the fastest is kept; SG2V_CHUNK fixes it
+// instead.  The choice is cached like the node forms, keyed by the graph
+// statistics, colours, table type, colourings and the plans' sub-templates.
+sg2v_status tune_chunk(sg2v_session *S, cudaStream_t stream) {
+    if (std::getenv("SG2V_CHUNK")) return SG2V_OK;
+    Prepared &P = S->P;
+    const sg2v_graph *base = S->base;
+    const char *path = std::getenv("SG2V_TUNE_CACHE");
+    std::map<std::string, std::string> cache = read_tune_cache(path);
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "split|n%lld_m%lld_d%lld_w%d|kc%d|%s|nb%d|", (long long)P.n,
+                  (long long)base->nnz, (long long)base->max_degree, base->weighted ? 1 : 0, P.kc, elem_name(P), P.nb);
+    std::string key(buf);
+    for (const CNode &c : P.nodes)
+        if (c.is_root) key += c.canon + ";";
+    int best = base->chunk;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        best = std::atoi(it->second.c_str());
+    } else {
+        // candidates: sizes below the largest degree (each splits some row)
+        // and the first that splits none
+        std::vector<int> cands;
+        for (int c : {256, 512, 1024, 2048, 4096, 8192}) {
+            cands.push_back(c);
+            if (c >= base->max_degree) break;
+        }
+        if (std::find(cands.begin(), cands.end(), base->chunk) == cands.end()) cands.push_back(base->chunk);
+        cudaEvent_t a, b;
+        SG2V_CUDA(cudaEventCreate(&a), "event");
+        SG2V_CUDA(cudaEventCreate(&b), "event");
+        float best_ms = 0.f;
+        sg2v_status st = SG2V_OK;
+        for (int c : cands) {
+            const sg2v_graph *v = nullptr;
+            if ((st = graph_view(base, c, &v))) break;
+            P.g = v;
+            if ((st = session_alloc_wave(S, P.auto_wave))) {
+                if (st != SG2V_ERR_OUT_OF_MEMORY) break;
+                st = SG2V_OK;
+                continue;  // a schedule whose scratch does not fit is not a candidate
+            }
+            if ((st = session_enqueue(S, stream, false))) break;  // warm-up
+            if (cudaEventRecord(a, stream) != cudaSuccess) break;
+            if ((st = session_enqueue(S, stream, false))) break;
+            if (cudaEventRecord(b, stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        if (st) return st;
+        cache[key] = std::to_string(best);
+        write_tune_cache(path, cache);
+    }
+    const sg2v_graph *v = nullptr;
+    sg2v_status st = graph_view(base, best, &v);
+    if (st) return st;
+    P.g = v;
+    return session_alloc_wave(S, P.auto_wave);
+}
+
 int64_t count_launches(const Prepared &P, int wave) {
     const int64_t waves = (P.nb + wave - 1) / wave;
     int64_t per_wave = 1 + (int64_t)P.nodes.size() - (sort_hist_node(P) >= 0 ? 1 : 0);
@@ -1695,6 +1778,94 @@ int64_t count_launches(const Prepared &P, int wave) {
 sg2v_status copy_out(double *dst, const double *src, size_t count, cudaStream_t stream) {
     if (!dst) return SG2V_OK;
     SG2V_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, stream), "result copy");
+    return SG2V_OK;
+}
+
+}  // namespace
+}  // namespace sg2v
+
+namespace sg2v {
+namespace {
+
+// The load-balanced work list of a graph for a chunk size: rows longer than
+// `chunk` arcs are cut into chunk tasks sharing a split slot (the split
+// schedule); sets the graph's task counts and boundaries, not its buffers.
+void plan_worklist(sg2v_graph *g, const std::vector<int64_t> &rp, int chunk, std::vector<int4> *tasks_out,
+                   std::vector<int32_t> *hc_out) {
+    const int64_t n = g->n;
+    std::vector<int4> &tasks = *tasks_out;
+    std::vector<int32_t> &hc = *hc_out;
+    g->chunk = chunk;
+    build_tasks(n, rp, chunk, &tasks, &hc);
+    g->ntasks = (int64_t)tasks.size();
+    g->nheavy = (int64_t)hc.size();
+    {
+        int64_t nchunks = 0;
+        for (int32_t c : hc) nchunks += c;
+        g->short_begin = g->ntasks;
+        for (int64_t i = nchunks; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kShortTaskArcs) {
+                g->short_begin = i;
+                break;
+            }
+        g->small_begin = g->ntasks;
+        for (int64_t i = g->short_begin; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kSortSmallArcs) {
+                g->small_begin = i;
+                break;
+            }
+        // the work list's trailing empty tasks: skipped by forward counting
+        // when their rows are exactly the last ones (each isolated vertex has
+        // one empty task, every other row none)
+        int64_t nempty = 0;
+        while (nempty < g->ntasks && tasks[(size_t)(g->ntasks - 1 - nempty)].z == tasks[(size_t)(g->ntasks - 1 - nempty)].w)
+            ++nempty;
+        bool tail = true;
+        for (int64_t i = g->ntasks - nempty; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].x < n - nempty) tail = false;
+        g->live_tasks = tail ? g->ntasks - nempty : g->ntasks;
+        g->live_rows = tail ? n - nempty : n;
+    }
+}
+
+// A graph whose work list uses another chunk size (the graph itself when the
+// size is its own): built once per size from the device row pointers and
+// kept with the graph, whose other arrays it shares.
+sg2v_status graph_view(const sg2v_graph *g, int chunk, const sg2v_graph **out) {
+    if (chunk == g->chunk || g->view) {
+        *out = g;
+        return SG2V_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_mutex);
+    for (const sg2v_graph *v : g->views)
+        if (v->chunk == chunk) {
+            *out = v;
+            return SG2V_OK;
+        }
+    std::vector<int64_t> rp((size_t)g->n + 1);
+    SG2V_CUDA(cudaMemcpy(rp.data(), g->row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost), "row pointers");
+    sg2v_graph *v = new (std::nothrow) sg2v_graph(*g);
+    if (!v) return SG2V_ERR_OUT_OF_MEMORY;
+    v->views.clear();
+    v->view = true;
+    v->tasks = nullptr;
+    v->heavy_chunks = nullptr;
+    v->rev = nullptr;
+    std::vector<int4> tasks;
+    std::vector<int32_t> hc;
+    plan_worklist(v, rp, chunk, &tasks, &hc);
+    cudaError_t e = cudaMalloc((void **)&v->tasks, std::max<size_t>(tasks.size() * sizeof(int4), 16));
+    if (e == cudaSuccess && !tasks.empty())
+        e = cudaMemcpy(v->tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v->heavy_chunks, std::max<size_t>(hc.size() * sizeof(int32_t), 16));
+    if (e == cudaSuccess && !hc.empty())
+        e = cudaMemcpy(v->heavy_chunks, hc.data(), hc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_graph(v);
+        return cuda_fail(e, "work list upload");
+    }
+    const_cast<sg2v_graph *>(g)->views.push_back(v);
+    *out = v;
     return SG2V_OK;
 }
 
@@ -1742,36 +1913,7 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
     g->chunk = env_int("SG2V_CHUNK", 1024);
     std::vector<int4> tasks;
     std::vector<int32_t> hc;
-    build_tasks(n, rp, g->chunk, &tasks, &hc);
-    g->ntasks = (int64_t)tasks.size();
-    g->nheavy = (int64_t)hc.size();
-    {
-        int64_t nchunks = 0;
-        for (int32_t c : hc) nchunks += c;
-        g->short_begin = g->ntasks;
-        for (int64_t i = nchunks; i < g->ntasks; ++i)
-            if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kShortTaskArcs) {
-                g->short_begin = i;
-                break;
-            }
-        g->small_begin = g->ntasks;
-        for (int64_t i = g->short_begin; i < g->ntasks; ++i)
-            if (tasks[(size_t)i].w - tasks[(size_t)i].z <= kSortSmallArcs) {
-                g->small_begin = i;
-                break;
-            }
-        // the work list's trailing empty tasks: skipped by forward counting
-        // when their rows are exactly the last ones (each isolated vertex has
-        // one empty task, every other row none)
-        int64_t nempty = 0;
-        while (nempty < g->ntasks && tasks[(size_t)(g->ntasks - 1 - nempty)].z == tasks[(size_t)(g->ntasks - 1 - nempty)].w)
-            ++nempty;
-        bool tail = true;
-        for (int64_t i = g->ntasks - nempty; i < g->ntasks; ++i)
-            if (tasks[(size_t)i].x < n - nempty) tail = false;
-        g->live_tasks = tail ? g->ntasks - nempty : g->ntasks;
-        g->live_rows = tail ? n - nempty : n;
-    }
+    plan_worklist(g, rp, g->chunk, &tasks, &hc);
     cudaError_t e = cudaSuccess;
     auto up = [&](void **dst, const void *src, size_t bytes) {
         if (e != cudaSuccess) return;
@@ -1954,6 +2096,7 @@ sg2v_status sg2v_session_create(const sg2v_graph *graph, const sg2v_plan *const 
     if (!S) return SG2V_ERR_OUT_OF_MEMORY;
     S->flags = flags;
     S->hook = current_hook();
+    S->base = graph;
     sg2v_status st = prepare(graph, plans, num_plans, B, precision, &S->P);
     if (st) {
         session_free(S);
@@ -2019,6 +2162,8 @@ sg2v_status sg2v_session_run(sg2v_session *S, const int8_t *colours, double *tot
     sg2v_status st;
     SG2V_CUDA(cudaMemcpyAsync(S->colours, colours, (size_t)P.nb * P.n, cudaMemcpyDefault, stream), "colour copy");
     if (!S->tuned) {
+        // the split schedule first, then the wave width, then each node's form
+        if ((st = tune_chunk(S, stream))) return st;
         // time every candidate wave width on these colourings, keep the fastest
         std::vector<int> cands;
         for (int w = 1; w < P.nb; w *= 2) cands.push_back(w);
@@ -2125,8 +2270,8 @@ sg2v_status sg2v_session_tuning(const sg2v_session *S, char *out, int64_t capaci
         set_error("invalid argument");
         return SG2V_ERR_INVALID_ARGUMENT;
     }
-    std::string j = "{\"wave\": " + std::to_string(S->R.wave) + ", \"tuned\": " + (S->tuned ? "true" : "false") +
-                    ", \"nodes\": [";
+    std::string j = "{\"wave\": " + std::to_string(S->R.wave) + ", \"chunk\": " + std::to_string(S->P.g->chunk) +
+                    ", \"tuned\": " + (S->tuned ? "true" : "false") + ", \"nodes\": [";
     for (size_t i = 0; i < S->P.nodes.size(); ++i) {
         const CNode &c = S->P.nodes[i];
         const Shape &sh = S->P.shape[i];

@@ -193,3 +193,67 @@ def test_form_autotuning_is_exact_and_cached(sg, tmp_path, monkeypatch):
         stored = json.loads(cache.read_text())
         assert len(stored) >= len(info["nodes"])
     assert forms[0] == forms[1]
+
+
+def test_split_schedule_autotuning(sg, tmp_path, monkeypatch):
+    """The autotuner also picks the split schedule (the chunk size at which
+    long rows are cut into tasks) by timing the session's step on each
+    candidate work list; counts do not depend on it (FP64 oracle-exact),
+    the choice is cached, and SG2V_CHUNK fixes it instead."""
+    import json
+
+    import torch
+
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("SG2V_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("SG2V_CHUNK", raising=False)
+    g = si.rmat(12, 40000, seed=11)
+    deg = np.diff(g.row_ptr)
+    assert deg.max() > 256  # rows that every candidate below 512 splits
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    parents = [si.PATH7.parent, si.TREE7.parent]
+    plans = [sg.Plan(p) for p in parents]
+    B = 3
+    cols = si.colourings(g.n, 7, B, seed=9)
+    refs = [[oracle.count(g.row_ptr, g.col_idx, p, 0, cols[b], per_vertex=False) for b in range(B)]
+            for p in parents]
+    chunks = []
+    for rep in range(2):
+        ses = sg.Session(graph, plans, B, "fp64", autotune=True)
+        tot = torch.empty((len(plans), B), dtype=torch.float64, device="cuda")
+        ses.run(torch.from_numpy(cols).cuda(), tot)
+        ses.sync()
+        # a second run replays the captured graph on the chosen work list
+        ses.run(torch.from_numpy(cols).cuda(), tot)
+        ses.sync()
+        info = ses.tuning()
+        assert info["chunk"] in (256, 512, 1024, 2048, 4096, 8192)
+        chunks.append(info["chunk"])
+        t = tot.cpu().numpy()
+        for i in range(len(plans)):
+            for b in range(B):
+                _exact_or_close(t[i, b], refs[i][b])
+        ses.close()
+    stored = json.loads(cache.read_text())
+    split = [v for k, v in stored.items() if k.startswith("split|")]
+    assert split and int(split[0]) == chunks[0] == chunks[1]
+    # a fixed chunk size (read when the graph is created) is kept
+    monkeypatch.setenv("SG2V_CHUNK", "300")
+    graph2 = sg.Graph(g.row_ptr, g.col_idx)
+    ses = sg.Session(graph2, plans, B, "fp64", autotune=True)
+    tot = torch.empty((len(plans), B), dtype=torch.float64, device="cuda")
+    ses.run(torch.from_numpy(cols).cuda(), tot)
+    ses.sync()
+    assert ses.tuning()["chunk"] == 300
+    t = tot.cpu().numpy()
+    for i in range(len(plans)):
+        for b in range(B):
+            _exact_or_close(t[i, b], refs[i][b])
+    ses.close()
+
+
+def _exact_or_close(got: float, ref) -> None:
+    if ref.max_bits <= 53:
+        assert got == float(ref.total)
+    else:
+        assert abs(got - ref.total) <= 1e-12 * ref.total

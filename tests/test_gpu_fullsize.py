@@ -103,6 +103,19 @@ def test_bench_step_matches_oracle(sg):
         for b in range(B):
             assert abs(tot[b] - totals[b]) <= tol * totals[b], (prec, b)
             assert abs(est[b] - float(exact_est[b])) <= tol * float(exact_est[b]), (prec, b)
+    # the benchmark's autotuned session: the first run tunes (split schedule,
+    # wave width, node forms), the second replays the captured CUDA graph
+    ses = sg.Session(graph, [plan], B, "fp32", autotune=True)
+    stot = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    sest = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    for rep in range(2):
+        ses.run(cols, stot, sest)
+        ses.sync()
+        tot, est = stot.cpu().numpy()[0], sest.cpu().numpy()[0]
+        for b in range(B):
+            assert abs(tot[b] - totals[b]) <= FP32_RTOL * totals[b], ("session", rep, b)
+            assert abs(est[b] - float(exact_est[b])) <= FP32_RTOL * float(exact_est[b]), ("session", rep, b)
+    ses.close()
     # exact integer tables: the totals bit for bit, the estimates within 2 ulp
     _, tot, est = sg.count_batched(graph, [plan], cols, "u128", per_vertex=False)
     tot, est = tot.cpu().numpy()[0], est.cpu().numpy()[0]

@@ -172,6 +172,11 @@ sg2v_status device_tables(int dev, int kc, int t, int a, int wz_pad, DeviceTable
 //   form 0 / 1: the colex rank of S in cv's squeezed p-sets (Y'),
 //   form 2 (t = kc): the rank of the active set S' - S that completes S,
 // or `sink` when S holds cv (and for d = cv, e >= C(kc-1, p-1)).
+// Form 3 is the transposed SpMM of the backward pass: the gathered row is the
+// neighbour's Ybar' (entry e: the e-th p-subset P of d's squeezed universe, a
+// p-set without d) and the destination, for the row's colour cv, is the
+// colex rank of P - {cv} in cv's squeezed (p-1)-sets (the compressed row of
+// the passive table's gradient), or `sink` when P lacks cv.
 // [kc][kc][wmap] 16-bit entries, cached per device.
 std::map<std::tuple<int, int, int, int, int, int, int>, const uint16_t *> g_runmaps;
 
@@ -184,20 +189,27 @@ sg2v_status run_map(int dev, int kc, int t, int a, int form, int wmap, int sink,
         return SG2V_OK;
     }
     const int p = t - a;
-    const int wz = (int)binom(kc - 1, p - 1);
+    const bool transposed = form == 3;
+    const int q_bits = transposed ? p : p - 1;  // colours of a gathered entry besides d
+    const int wz = (int)binom(kc - 1, q_bits);
     const uint32_t full = (1u << (kc - 1)) - 1u;  // every colour of a squeezed universe
     std::vector<uint16_t> m((size_t)kc * kc * wmap, (uint16_t)sink);
     for (int d = 0; d < kc; ++d) {
-        // the gathered row's sets in colex order: (p-1)-subsets by increasing mask
+        // the gathered row's sets in colex order: subsets by increasing mask
         std::vector<uint32_t> sets;
         sets.reserve((size_t)wz);
         for (uint32_t q = 0; q <= full; ++q)
-            if (__builtin_popcount(q) == p - 1) sets.push_back(unsqueeze_colour(q, d) | (1u << d));
+            if (__builtin_popcount(q) == q_bits)
+                sets.push_back(transposed ? unsqueeze_colour(q, d) : unsqueeze_colour(q, d) | (1u << d));
         for (int cv = 0; cv < kc; ++cv) {
             if (cv == d) continue;
             uint16_t *row = m.data() + ((size_t)cv * kc + d) * wmap;
             for (int e = 0; e < wz && e < wmap; ++e) {
                 const uint32_t S = sets[(size_t)e];
+                if (transposed) {
+                    if (S >> cv & 1u) row[e] = (uint16_t)colex_rank(squeeze_colour(S & ~(1u << cv), cv));
+                    continue;
+                }
                 if (S >> cv & 1u) continue;
                 const uint32_t Sq = squeeze_colour(S, cv);
                 row[e] = (uint16_t)(form == 2 ? colex_rank(full ^ Sq) : colex_rank(Sq));
@@ -2460,6 +2472,13 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         if ((st = alloc((size_t)nnz * sizeof(int32_t), (void **)&sperm))) return st;
         no_hist.perm = sperm;
     }
+    if (R.hcount) {
+        // histogram nodes read each row's neighbour counts per colour from the
+        // sort (unweighted graphs): split rows add theirs into a zeroed buffer
+        SG2V_CUDA(cudaMemsetAsync(R.hcount, 0, (size_t)n * R.hld * sizeof(int32_t), stream), "memset");
+        no_hist.hcount = R.hcount;
+        no_hist.hld = R.hld;
+    }
     SG2V_CUDA(launch_colour_sort(g->tasks, g->ntasks, g->small_begin, g->col_idx, g->weights, n, nnz, d_col, 1, kc,
                                  R.scol, R.sclr, R.sw, no_hist, P.info.sms, stream),
               "colour sort");
@@ -2698,9 +2717,44 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             timer.begin("backward: transposed SpMM",
                         (double)nnz * (5.0 + (g->weighted ? 4.0 : 0.0)) + 8.0 * (n + 1) +
                             (double)n * (wy + 2.0 * binom(kc - 1, c.p - 1)) * (double)esz);
-            SG2V_CUDA(launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
-                                  stream),
-                      "transposed SpMM launch");
+            // on the run-scatter kernel where it has a variant for the row shape
+            // (SG2V_BWD_RUN=0: per-colour accumulators and the expansion): each
+            // colour run of neighbours' Ybar' rows goes through the transposed
+            // run map straight into the gradient row, which it adds to
+            const char *brun = std::getenv("SG2V_BWD_RUN");
+            const bool run_ok = !(brun && std::atoi(brun) == 0) && !P.scaled && sh.grp != kWideLanes &&
+                                (sh.nv == 1 || (sh.nv == 2 && sh.grp == 32)) &&
+                                (P.elem == Elem::F32 || (P.elem == Elem::F64 && !g->weights));
+            int run_bps = 0;
+            size_t run_smem = 0;
+            const int rE = P.vecn;
+            const int rybase = (btab[ii]->wout + rE - 1) / rE * rE;
+            if (run_ok) {
+                run_smem = (size_t)(kNodeThreads / 32) *
+                           ((size_t)(32 / sh.grp) * (rybase + rE) * esz + (size_t)kRunCompactBytes);
+                run_bps = node_run_blocks_per_sm(P.elem, sh.grp, sh.nv, g->weights != nullptr, 1, kNodeThreads,
+                                                 run_smem);
+            }
+            if (run_bps >= 1) {
+                const int wmap = sh.grp * sh.nv * rE;
+                const uint16_t *rm = nullptr;
+                if ((st = run_map(P.dev, kc, c.t, c.a, 3, wmap, rybase, &rm))) return st;
+                NodeArgs Rn = A;
+                Rn.runmap = rm;
+                Rn.wmap = wmap;
+                Rn.mzero = 0;
+                Rn.ywords = rybase + rE;
+                Rn.mwords = 0;
+                Rn.half_arcs = 0;
+                Rn.Yout = nullptr;
+                SG2V_CUDA(launch_node_run(Rn, P.elem, sh.grp, sh.nv, 1, kNodeThreads, run_smem,
+                                          P.info.sms * run_bps, stream),
+                          "transposed SpMM launch");
+            } else {
+                SG2V_CUDA(launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, P.info.sms * sh.blocks_per_sm,
+                                      stream),
+                          "transposed SpMM launch");
+            }
             timer.end();
         }
         SddmmArgs D;

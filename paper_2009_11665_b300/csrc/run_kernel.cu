@@ -177,8 +177,10 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 } else if constexpr (FORM == 2) {
                     if (lane == 0) static_cast<T *>(A.root_out)[(int64_t)b * A.n + v] = T(0);
                 } else if constexpr (FORM == 1) {
+                    // (an accumulated output keeps its row: nothing to add)
                     VT *out = reinterpret_cast<VT *>(static_cast<T *>(A.Ms) + rowb * A.ldt);
-                    for (int j = lane; j < (A.ywords - E) / E; j += 32) out[j] = V::zero();
+                    if (!A.accumulate)
+                        for (int j = lane; j < (A.ywords - E) / E; j += 32) out[j] = V::zero();
                 } else {
                     epilogue<T>(A, v, b, false, ybuf, mbuf, lane, ovf);
                 }
@@ -401,7 +403,17 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 const VT *yv = reinterpret_cast<const VT *>(ybuf);
                 // (Y' vectors only: a wider row stride leaves padding nothing reads)
                 const int nout = (A.ywords - E) / E;
-                for (int j = lane; j < nout; j += 32) st_hint_v16(out + j, cok ? yv[j] : V::zero(), pol_once);
+                if (A.accumulate) {
+                    // the backward's transposed SpMM adds to the gradient row
+                    if (cok)
+                        for (int j = lane; j < nout; j += 32) {
+                            VT o = out[j];
+                            V::add(o, yv[j]);
+                            out[j] = o;
+                        }
+                } else {
+                    for (int j = lane; j < nout; j += 32) st_hint_v16(out + j, cok ? yv[j] : V::zero(), pol_once);
+                }
                 __syncwarp();
                 continue;
             }

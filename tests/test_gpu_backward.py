@@ -271,3 +271,44 @@ def test_sorted_per_arc_gradient_matches_row_form(sg, parent, kc, prec, monkeypa
     for e in edges:
         for a in np.nonzero(ids == e)[0]:
             assert abs(res["1"][a] - float(exact[e])) <= tol * abs(float(exact[e])) + 1e-300, (e, res["1"][a])
+
+
+@pytest.mark.parametrize("parent,kc", [(si.TREE8.parent, 8), (si.TREE10.parent, 10), (si.TREE8.parent, 12),
+                                       ((-1, 0, 1, 2, 3), 5), ((-1, 0, 0, 0, 0), 5)])
+@pytest.mark.parametrize("prec,weighted", [("fp32", True), ("fp32", False), ("fp64", False), ("fp64", True)])
+def test_transposed_spmm_on_run_kernel(sg, parent, kc, prec, weighted, monkeypatch):
+    """The transposed SpMM of the backward pass on the run-scatter kernel
+    (colour runs of the neighbours' Ybar' rows scattered through the
+    transposed run map into the gradient row) gives the gradients of the
+    per-colour-accumulator form (SG2V_BWD_RUN=0), with rows split into
+    chunks of 64 arcs: bit for bit for unweighted FP64 (integer
+    participation counts), to rounding otherwise; and they match exact
+    differences of the oracle (weighted) or exact participation counts."""
+    import torch
+
+    monkeypatch.setenv("SG2V_CHUNK", "64")
+    g = si.chung_lu(1500, 9000, 2.3, seed=13)
+    assert int(np.diff(g.row_ptr).max()) > 64
+    w = si.arc_weights(g, si.edge_weights(g, seed=7)) if weighted else None
+    col = si.colouring(g.n, kc, 6)
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(parent, num_colours=kc)
+    res = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("SG2V_BWD_RUN", env)
+        gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        sg.sg2v_count_backward(graph.handle, plan.handle, torch.from_numpy(col).cuda(), sg.PRECISIONS[prec], gw)
+        res[env] = gw.cpu().numpy()
+    if prec == "fp64" and not weighted:
+        assert np.array_equal(res["1"], res["0"])
+    else:
+        rtol = 1e-12 if prec == "fp64" else 1e-5
+        np.testing.assert_allclose(res["1"], res["0"], rtol=rtol, atol=rtol * np.abs(res["0"]).max())
+    ids = si.arc_edge_ids(g)
+    edges = [int(e) for e in si.sample_indices(6, g.m, seed=kc + 1)]
+    ww = w if weighted else np.ones(g.nnz, dtype=np.float32)
+    _, exact = _exact_grad(g, ww, parent, col, edges, num_colours=kc)
+    tol = 1e-11 if prec == "fp64" else 1e-4
+    for e in edges:
+        for a in np.nonzero(ids == e)[0]:
+            assert abs(res["1"][a] - float(exact[e])) <= tol * abs(float(exact[e])) + 1e-300, (e, res["1"][a])

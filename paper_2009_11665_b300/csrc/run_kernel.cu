@@ -27,7 +27,8 @@
 // The gather loop is kept short because these launches are bound by issue
 // slots: each
 // batch of 32 sorted arcs is compacted (through shared memory) to the arcs
-// that add something, each as one word u << 4 | colour, so an arc costs one
+// that add something, each as one word u << 4 | colour (so graphs of fewer
+// than 2^28 vertices: the launcher checks), so an arc costs one
 // shuffle, one address, one 16-byte load and the adds; lanes past the row's
 // last vector load that vector again (no predicate), and a step that stays
 // in every group's current run skips the per-arc colour test.  Groups

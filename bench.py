@@ -337,6 +337,22 @@ def profile_call(args):
                       "totals": tot.cpu().tolist()}))
 
 
+def session_headline(sg, torch, graph, plan, B, d_cols, h_cols, tot, est, h_tot, h_est, stream, args, dist):
+    """The headline step through an autotuned session: its first run (a
+    warm-up step) times the split schedule, wave width and node forms; later
+    runs replay a CUDA graph.  Timed from device colourings and, end to end,
+    from pinned host colourings with host totals and estimates."""
+    ses = sg.Session(graph, [plan], B, "fp32", autotune=True)
+    ms = time_steps(torch, lambda: ses.run(d_cols, tot, est, None, stream), args.steps, args.warmup, stream, dist)
+    ms_e2e = time_steps(torch, lambda: ses.run(h_cols, h_tot, h_est, None, stream), max(3, args.steps // 2),
+                        args.warmup, stream, dist)
+    tuning = ses.tuning()
+    ses.close()
+    return {"s_per_colouring": ms * 1e-3 / B, "e2e_s_per_colouring": ms_e2e * 1e-3 / B, "wave": tuning["wave"],
+            "split_chunk": tuning["chunk"], "cuda_graph": True,
+            "forms": [f"({n['t']},{n['a']},{n['p']}) {n['kernel']}" for n in tuning["nodes"]]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,6 +365,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 3-template x 64-colouring session block")
     ap.add_argument("--no-large", action="store_true", help="skip the tree15 (k = 15) large-form block")
+    ap.add_argument("--no-session", action="store_true", help="skip the headline step through an autotuned session")
     ap.add_argument("--profile-call", choices=["rmat18", "rmat19", "rmat20", "large17"], default=None,
                     help="run exactly one count call (R-MAT scale 18, 19 or 20 with avg degree 32 and tree10, or the "
                          "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
@@ -455,20 +472,11 @@ def main():
     ms_e2e = time_steps(torch, step_e2e, max(3, args.steps // 2), args.warmup, stream, dist)
     ms_e2e_pv = time_steps(torch, step_e2e_pv, max(3, args.steps // 2), args.warmup, stream, dist)
 
-    # the same step through an autotuned session (split schedule, wave width
-    # and node forms timed in its first run, a warm-up step; later runs replay
-    # a CUDA graph), device and host colourings
-    ses32 = sg.Session(graph, [plan], B, "fp32", autotune=True)
-    ms_ses = time_steps(torch, lambda: ses32.run(d_cols, tot32, est32, None, stream), args.steps, args.warmup,
-                        stream, dist)
-    ms_ses_e2e = time_steps(torch, lambda: ses32.run(h_cols, h_tot, h_est, None, stream), max(3, args.steps // 2),
-                            args.warmup, stream, dist)
-    tuning32 = ses32.tuning()
-    session_block = {"s_per_colouring": ms_ses * 1e-3 / B, "e2e_s_per_colouring": ms_ses_e2e * 1e-3 / B,
-                     "wave": tuning32["wave"], "split_chunk": tuning32["chunk"],
-                     "forms": [f"({n['t']},{n['a']},{n['p']}) {n['kernel']}" for n in tuning32["nodes"]],
-                     "cuda_graph": True}
-    ses32.close()
+    # the same step through an autotuned session
+    session_block = None
+    if not args.no_session:
+        session_block = session_headline(sg, torch, graph, plan, B, d_cols, h_cols, tot32, est32, h_tot, h_est,
+                                         stream, args, dist)
 
     # batched form: 64 colourings x 3 templates (path7, star7, tree7, k = 7) on
     # R-MAT scale 18 (avg degree 16), one CUDA-graph replay per step, autotuned waves

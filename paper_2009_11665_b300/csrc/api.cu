@@ -434,6 +434,10 @@ struct sg2v_graph {
     int32_t *heavy_chunks = nullptr;
     int64_t nheavy = 0;
     int chunk = 0;
+    // column panels of the work list (1: none): rows longer than
+    // kShortTaskArcs are cut where their neighbours cross into the next of
+    // `panels` equal ranges of vertices, and tasks are ordered panel by panel
+    int panels = 1;
     int64_t short_begin = 0;  // first task of at most kShortTaskArcs arcs (the rest, sorted by work, are too)
     int64_t small_begin = 0;  // first task of at most kSortSmallArcs arcs
     // isolated vertices: when the work list ends in the empty tasks of rows
@@ -1615,9 +1619,9 @@ std::string form_code(const Shape &sh) {
 std::string tune_key(const Prepared &P, size_t i, int wave) {
     const CNode &c = P.nodes[i];
     char buf[256];
-    std::snprintf(buf, sizeof buf, "n%lld_m%lld_d%lld_w%d|kc%d|t%d_a%d_p%d_r%d|%s|wave%d|nb%d|chunk%d|",
+    std::snprintf(buf, sizeof buf, "n%lld_m%lld_d%lld_w%d|kc%d|t%d_a%d_p%d_r%d|%s|wave%d|nb%d|chunk%d_p%d|",
                   (long long)P.n, (long long)P.g->nnz, (long long)P.g->max_degree, P.g->weighted ? 1 : 0, P.kc,
-                  c.t, c.a, c.p, c.is_root ? 1 : 0, elem_name(P), wave, P.nb, P.g->chunk);
+                  c.t, c.a, c.p, c.is_root ? 1 : 0, elem_name(P), wave, P.nb, P.g->chunk, P.g->panels);
     // the sub-template itself (nodes of one shape can be different trees);
     // its AHU form uses only parentheses, safe inside a JSON string
     return std::string(buf) + c.canon;
@@ -1710,71 +1714,91 @@ sg2v_status tune_forms(sg2v_session *S, cudaStream_t stream) {
     return SG2V_OK;
 }
 
-sg2v_status graph_view(const sg2v_graph *g, int chunk, const sg2v_graph **out);
+sg2v_status graph_view(const sg2v_graph *g, int chunk, int panels, const sg2v_graph **out);
 
-// Split schedule: the chunk size at which long rows are cut into tasks.  The
-// session's whole step is timed (CUDA events, after a warm-up) on the work
-// list of each candidate size and the fastest is kept; SG2V_CHUNK fixes it
-// instead.  The choice is cached like the node forms, keyed by the graph
-// statistics, colours, table type, colourings and the plans' sub-templates.
-sg2v_status tune_chunk(sg2v_session *S, cudaStream_t stream) {
-    if (std::getenv("SG2V_CHUNK")) return SG2V_OK;
+// Split schedule: the chunk size at which long rows are cut into tasks, and
+// the number of column panels of the work list (1: none).  The session's
+// whole step is timed (CUDA events, after a warm-up) on the work list of each
+// candidate chunk size without panels, then on 2 and 4 panels at the best
+// size, and the fastest is kept; SG2V_CHUNK fixes the chunk size and
+// SG2V_PANELS the panels instead.  The choice is cached like the node forms,
+// keyed by the graph statistics, colours, table type, colourings and the
+// plans' sub-templates.
+sg2v_status tune_split(sg2v_session *S, cudaStream_t stream) {
+    const bool fix_chunk = std::getenv("SG2V_CHUNK") != nullptr;
+    const bool fix_panels = std::getenv("SG2V_PANELS") != nullptr;
+    if (fix_chunk && fix_panels) return SG2V_OK;
     Prepared &P = S->P;
     const sg2v_graph *base = S->base;
     const char *path = std::getenv("SG2V_TUNE_CACHE");
     std::map<std::string, std::string> cache = read_tune_cache(path);
     char buf[256];
-    std::snprintf(buf, sizeof buf, "split|n%lld_m%lld_d%lld_w%d|kc%d|%s|nb%d|", (long long)P.n,
-                  (long long)base->nnz, (long long)base->max_degree, base->weighted ? 1 : 0, P.kc, elem_name(P), P.nb);
+    std::snprintf(buf, sizeof buf, "split|n%lld_m%lld_d%lld_w%d|kc%d|%s|nb%d|c%d_p%d|", (long long)P.n,
+                  (long long)base->nnz, (long long)base->max_degree, base->weighted ? 1 : 0, P.kc, elem_name(P), P.nb,
+                  fix_chunk ? base->chunk : 0, fix_panels ? base->panels : 0);
     std::string key(buf);
     for (const CNode &c : P.nodes)
         if (c.is_root) key += c.canon + ";";
-    int best = base->chunk;
+    int best_c = base->chunk, best_p = base->panels;
     auto it = cache.find(key);
-    if (it != cache.end()) {
-        best = std::atoi(it->second.c_str());
+    if (it != cache.end() && std::sscanf(it->second.c_str(), "%d,%d", &best_c, &best_p) == 2) {
+        // taken from the cache
     } else {
-        // candidates: sizes below the largest degree (each splits some row)
-        // and the first that splits none
-        std::vector<int> cands;
-        for (int c : {256, 512, 1024, 2048, 4096, 8192}) {
-            cands.push_back(c);
-            if (c >= base->max_degree) break;
-        }
-        if (std::find(cands.begin(), cands.end(), base->chunk) == cands.end()) cands.push_back(base->chunk);
         cudaEvent_t a, b;
         SG2V_CUDA(cudaEventCreate(&a), "event");
         SG2V_CUDA(cudaEventCreate(&b), "event");
         float best_ms = 0.f;
         sg2v_status st = SG2V_OK;
-        for (int c : cands) {
+        auto time_one = [&](int c, int pn) -> sg2v_status {
             const sg2v_graph *v = nullptr;
-            if ((st = graph_view(base, c, &v))) break;
+            sg2v_status s2 = graph_view(base, c, pn, &v);
+            if (s2) return s2;
             P.g = v;
-            if ((st = session_alloc_wave(S, P.auto_wave))) {
-                if (st != SG2V_ERR_OUT_OF_MEMORY) break;
-                st = SG2V_OK;
-                continue;  // a schedule whose scratch does not fit is not a candidate
-            }
-            if ((st = session_enqueue(S, stream, false))) break;  // warm-up
-            if (cudaEventRecord(a, stream) != cudaSuccess) break;
-            if ((st = session_enqueue(S, stream, false))) break;
-            if (cudaEventRecord(b, stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) break;
+            if ((s2 = session_alloc_wave(S, P.auto_wave)))
+                // a schedule whose scratch does not fit is not a candidate
+                return s2 == SG2V_ERR_OUT_OF_MEMORY ? SG2V_OK : s2;
+            if ((s2 = session_enqueue(S, stream, false))) return s2;  // warm-up
+            SG2V_CUDA(cudaEventRecord(a, stream), "event");
+            if ((s2 = session_enqueue(S, stream, false))) return s2;
+            SG2V_CUDA(cudaEventRecord(b, stream), "event");
+            SG2V_CUDA(cudaEventSynchronize(b), "event");
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
+            SG2V_CUDA(cudaEventElapsedTime(&ms, a, b), "event");
             if (best_ms == 0.f || ms < best_ms) {
                 best_ms = ms;
-                best = c;
+                best_c = c;
+                best_p = pn;
             }
+            return SG2V_OK;
+        };
+        // chunk sizes below the largest degree (each splits some row) and the
+        // first that splits none, without panels
+        std::vector<int> cands;
+        if (fix_chunk) {
+            cands.push_back(base->chunk);
+        } else {
+            for (int c : {256, 512, 1024, 2048, 4096, 8192}) {
+                cands.push_back(c);
+                if (c >= base->max_degree) break;
+            }
+            if (std::find(cands.begin(), cands.end(), base->chunk) == cands.end()) cands.push_back(base->chunk);
+        }
+        const int p0 = fix_panels ? base->panels : 1;
+        for (int c : cands)
+            if ((st = time_one(c, p0))) break;
+        if (!st && !fix_panels) {
+            const int c = best_c;
+            for (int pn : {2, 4})
+                if ((st = time_one(c, pn))) break;
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         if (st) return st;
-        cache[key] = std::to_string(best);
+        cache[key] = std::to_string(best_c) + "," + std::to_string(best_p);
         write_tune_cache(path, cache);
     }
     const sg2v_graph *v = nullptr;
-    sg2v_status st = graph_view(base, best, &v);
+    sg2v_status st = graph_view(base, best_c, best_p, &v);
     if (st) return st;
     P.g = v;
     return session_alloc_wave(S, P.auto_wave);
@@ -1805,13 +1829,93 @@ namespace {
 // The load-balanced work list of a graph for a chunk size: rows longer than
 // `chunk` arcs are cut into chunk tasks sharing a split slot (the split
 // schedule); sets the graph's task counts and boundaries, not its buffers.
-void plan_worklist(sg2v_graph *g, const std::vector<int64_t> &rp, int chunk, std::vector<int4> *tasks_out,
-                   std::vector<int32_t> *hc_out) {
+// With panels > 1 (the column-panel form of the paper's CSC-Split, Alg. 6):
+// the vertices that have arcs are cut into `panels` equal ranges; a row of
+// more than kShortTaskArcs arcs (columns ascending) is also cut where its
+// neighbours cross into the next range, and the tasks of each class (rows
+// over kShortTaskArcs arcs, rows over kSortSmallArcs, the rest, then empty
+// rows) run panel by panel (a shorter row goes with the panel of its first
+// neighbour), so that the tasks in flight together gather from one range of
+// the tables.  Every piece of a cut row shares its split slot and stays in
+// the first class, which the one-task-per-warp kernels run.
+void plan_worklist(sg2v_graph *g, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci, int chunk,
+                   int panels, std::vector<int4> *tasks_out, std::vector<int32_t> *hc_out) {
     const int64_t n = g->n;
     std::vector<int4> &tasks = *tasks_out;
     std::vector<int32_t> &hc = *hc_out;
     g->chunk = chunk;
-    build_tasks(n, rp, chunk, &tasks, &hc);
+    g->panels = std::max(1, panels);
+    if (g->panels == 1 || ci.size() != (size_t)rp[(size_t)n]) {
+        g->panels = 1;
+        build_tasks(n, rp, chunk, &tasks, &hc);
+    } else {
+        // vertices with arcs come first when numbered by decreasing degree;
+        // the ranges split them (a caller's order: all n vertices)
+        int64_t live = n;
+        while (live > 0 && rp[(size_t)live] == rp[(size_t)live - 1]) --live;
+        const int64_t psize = std::max<int64_t>(1, (live + g->panels - 1) / g->panels);
+        auto panel_of = [&](int64_t u) { return (int)std::min<int64_t>(g->panels - 1, u / psize); };
+        std::vector<int32_t> order((size_t)n);
+        for (int64_t i = 0; i < n; ++i) order[(size_t)i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+        // [class][panel] task lists; class 0 long rows (and their pieces),
+        // 1 rows of kSortSmallArcs+1 .. kShortTaskArcs arcs, 2 shorter, 3 empty
+        std::vector<std::vector<std::vector<int4>>> bucket(4, std::vector<std::vector<int4>>((size_t)g->panels));
+        for (int32_t v : order) {
+            const int64_t e0 = rp[v], e1 = rp[v + 1], d = e1 - e0;
+            if (d == 0) {
+                bucket[3][0].push_back(make_int4(v, -1, (int)e0, (int)e1));
+                continue;
+            }
+            if (d <= kShortTaskArcs) {
+                // the panel of its first neighbour (the arcs come in column order)
+                const int cls = d <= kSortSmallArcs ? 2 : 1;
+                bucket[(size_t)cls][(size_t)panel_of(ci[(size_t)e0])].push_back(make_int4(v, -1, (int)e0, (int)e1));
+                continue;
+            }
+            // pieces: panel boundaries, then chunks within a panel
+            std::vector<int4> pieces;
+            std::vector<int> ppanel;
+            int64_t a = e0;
+            while (a < e1) {
+                const int pa = panel_of(ci[(size_t)a]);
+                int64_t b = a + 1;
+                while (b < e1 && panel_of(ci[(size_t)b]) == pa && b - a < chunk) ++b;
+                pieces.push_back(make_int4(v, -1, (int)a, (int)b));
+                ppanel.push_back(pa);
+                a = b;
+            }
+            const int32_t slot = pieces.size() > 1 ? (int32_t)hc.size() : -1;
+            if (slot >= 0) hc.push_back((int32_t)pieces.size());
+            for (size_t k = 0; k < pieces.size(); ++k) {
+                pieces[k].y = slot;
+                bucket[0][(size_t)ppanel[k]].push_back(pieces[k]);
+            }
+        }
+        tasks.clear();
+        int64_t bounds[4];
+        for (int cls = 0; cls < 4; ++cls) {
+            for (const auto &bk : bucket[(size_t)cls]) tasks.insert(tasks.end(), bk.begin(), bk.end());
+            bounds[cls] = (int64_t)tasks.size();
+        }
+        g->ntasks = (int64_t)tasks.size();
+        g->nheavy = (int64_t)hc.size();
+        g->short_begin = bounds[0];
+        g->small_begin = bounds[1];
+        g->live_tasks = bounds[2];
+        g->live_rows = live;
+        // forward counting skips the empty tasks only when their rows are the
+        // last ones (vertices numbered by decreasing degree)
+        bool tail = true;
+        for (int64_t i = bounds[2]; i < g->ntasks; ++i)
+            if (tasks[(size_t)i].x < live) tail = false;
+        if (!tail) {
+            g->live_tasks = g->ntasks;
+            g->live_rows = n;
+        }
+        return;
+    }
     g->ntasks = (int64_t)tasks.size();
     g->nheavy = (int64_t)hc.size();
     {
@@ -1843,22 +1947,28 @@ void plan_worklist(sg2v_graph *g, const std::vector<int64_t> &rp, int chunk, std
     }
 }
 
-// A graph whose work list uses another chunk size (the graph itself when the
-// size is its own): built once per size from the device row pointers and
+// A graph whose work list uses another chunk size or panel count (the graph
+// itself when both are its own): built once per pair from the device CSR and
 // kept with the graph, whose other arrays it shares.
-sg2v_status graph_view(const sg2v_graph *g, int chunk, const sg2v_graph **out) {
-    if (chunk == g->chunk || g->view) {
+sg2v_status graph_view(const sg2v_graph *g, int chunk, int panels, const sg2v_graph **out) {
+    if ((chunk == g->chunk && panels == g->panels) || g->view) {
         *out = g;
         return SG2V_OK;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
     for (const sg2v_graph *v : g->views)
-        if (v->chunk == chunk) {
+        if (v->chunk == chunk && v->panels == panels) {
             *out = v;
             return SG2V_OK;
         }
     std::vector<int64_t> rp((size_t)g->n + 1);
     SG2V_CUDA(cudaMemcpy(rp.data(), g->row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost), "row pointers");
+    std::vector<int32_t> ci;
+    if (panels > 1) {
+        ci.resize((size_t)g->nnz);
+        SG2V_CUDA(cudaMemcpy(ci.data(), g->col_idx, ci.size() * sizeof(int32_t), cudaMemcpyDeviceToHost),
+                  "column indices");
+    }
     sg2v_graph *v = new (std::nothrow) sg2v_graph(*g);
     if (!v) return SG2V_ERR_OUT_OF_MEMORY;
     v->views.clear();
@@ -1868,7 +1978,7 @@ sg2v_status graph_view(const sg2v_graph *g, int chunk, const sg2v_graph **out) {
     v->rev = nullptr;
     std::vector<int4> tasks;
     std::vector<int32_t> hc;
-    plan_worklist(v, rp, chunk, &tasks, &hc);
+    plan_worklist(v, rp, ci, chunk, panels, &tasks, &hc);
     cudaError_t e = cudaMalloc((void **)&v->tasks, std::max<size_t>(tasks.size() * sizeof(int4), 16));
     if (e == cudaSuccess && !tasks.empty())
         e = cudaMemcpy(v->tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
@@ -1928,7 +2038,7 @@ sg2v_status sg2v_graph_create(int64_t n, int64_t nnz, const int64_t *row_ptr, co
     g->chunk = env_int("SG2V_CHUNK", 1024);
     std::vector<int4> tasks;
     std::vector<int32_t> hc;
-    plan_worklist(g, rp, g->chunk, &tasks, &hc);
+    plan_worklist(g, rp, ci, g->chunk, env_int("SG2V_PANELS", 1), &tasks, &hc);
     cudaError_t e = cudaSuccess;
     auto up = [&](void **dst, const void *src, size_t bytes) {
         if (e != cudaSuccess) return;
@@ -2178,7 +2288,7 @@ sg2v_status sg2v_session_run(sg2v_session *S, const int8_t *colours, double *tot
     SG2V_CUDA(cudaMemcpyAsync(S->colours, colours, (size_t)P.nb * P.n, cudaMemcpyDefault, stream), "colour copy");
     if (!S->tuned) {
         // the split schedule first, then the wave width, then each node's form
-        if ((st = tune_chunk(S, stream))) return st;
+        if ((st = tune_split(S, stream))) return st;
         // time every candidate wave width on these colourings, keep the fastest
         std::vector<int> cands;
         for (int w = 1; w < P.nb; w *= 2) cands.push_back(w);
@@ -2286,6 +2396,7 @@ sg2v_status sg2v_session_tuning(const sg2v_session *S, char *out, int64_t capaci
         return SG2V_ERR_INVALID_ARGUMENT;
     }
     std::string j = "{\"wave\": " + std::to_string(S->R.wave) + ", \"chunk\": " + std::to_string(S->P.g->chunk) +
+                    ", \"panels\": " + std::to_string(S->P.g->panels) +
                     ", \"tuned\": " + (S->tuned ? "true" : "false") + ", \"nodes\": [";
     for (size_t i = 0; i < S->P.nodes.size(); ++i) {
         const CNode &c = S->P.nodes[i];

@@ -312,3 +312,29 @@ def test_transposed_spmm_on_run_kernel(sg, parent, kc, prec, weighted, monkeypat
     for e in edges:
         for a in np.nonzero(ids == e)[0]:
             assert abs(res["1"][a] - float(exact[e])) <= tol * abs(float(exact[e])) + 1e-300, (e, res["1"][a])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_backward_on_column_panel_work_list(sg, prec, monkeypatch):
+    """Gradients on a work list in column panels (rows cut at panel
+    boundaries and into chunks of 64 arcs, read at graph creation) match
+    exact differences of the oracle."""
+    import torch
+
+    monkeypatch.setenv("SG2V_PANELS", "2")
+    monkeypatch.setenv("SG2V_CHUNK", "64")
+    g = si.chung_lu(1500, 9000, 2.3, seed=17)
+    w = si.arc_weights(g, si.edge_weights(g, seed=3))
+    col = si.colouring(g.n, 8, 2)
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plan = sg.Plan(si.TREE8.parent)
+    gw = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+    sg.sg2v_count_backward(graph.handle, plan.handle, torch.from_numpy(col).cuda(), sg.PRECISIONS[prec], gw)
+    got = gw.cpu().numpy()
+    ids = si.arc_edge_ids(g)
+    edges = [int(e) for e in si.sample_indices(8, g.m, seed=21)]
+    _, exact = _exact_grad(g, w, si.TREE8.parent, col, edges)
+    tol = 1e-11 if prec == "fp64" else 1e-4
+    for e in edges:
+        for a in np.nonzero(ids == e)[0]:
+            assert abs(got[a] - float(exact[e])) <= tol * abs(float(exact[e])) + 1e-300, (e, got[a])

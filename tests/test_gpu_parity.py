@@ -367,3 +367,51 @@ def test_split_rows_in_waves(sg, monkeypatch):
                     assert tot[i, b] == float(int(ref.total))
                 else:
                     _check_fp64(pv[i, b], tot[i, b], ref, exact=False)
+
+
+@pytest.mark.parametrize("panels", ["2", "4"])
+@pytest.mark.parametrize("chunk", ["1024", "64"])
+def test_column_panel_work_lists(sg, panels, chunk, monkeypatch):
+    """Work lists in column panels (the CSC-Split form, Alg. 6: rows of more
+    than 64 arcs cut where their neighbours cross into the next range of
+    vertices, tasks ordered panel by panel; read at graph creation) give the
+    oracle's counts, per vertex and in total, with and without split rows,
+    with the symmetric half-arc root and on a graph kept in the caller's
+    vertex order (isolated vertices not last)."""
+    monkeypatch.setenv("SG2V_PANELS", panels)
+    monkeypatch.setenv("SG2V_CHUNK", chunk)
+    g = _hub_graph(5)
+    col = si.colouring(g.n, 10, 3)
+    for parent in (si.TREE10.parent, si.PATH7.parent, (-1, 0, 0, 2)):
+        k = len(parent)
+        ref, plan, r64, r32 = _run(sg, g, parent, 0, col if k == 10 else si.colouring(g.n, k, 3))
+        _check_fp64(r64[0], r64[1], ref, exact=ref.max_bits <= 53)
+        _check_fp32(r32[0], r32[1], ref)
+    # totals only (the half-arc root) and several colourings per wave
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(si.TREE10.parent, 0, 10)
+    cols = si.colourings(g.n, 10, 3, seed=4)
+    _, tot, _ = sg.count_batched(graph, [plan], _dev(cols), "fp64", per_vertex=False)
+    tot = tot.cpu().numpy()[0]
+    for b in range(3):
+        r = oracle.count(g.row_ptr, g.col_idx, si.TREE10.parent, 0, cols[b], per_vertex=False)
+        assert tot[b] == float(r.total) if r.max_bits <= 53 else abs(tot[b] - r.total) <= FP64_RTOL * r.total
+    # the caller's vertex order, with isolated vertices scattered through it
+    rng = np.random.default_rng(2)
+    n2 = g.n + 300
+    keep = np.sort(rng.choice(n2, size=g.n, replace=False))
+    deg = np.zeros(n2, dtype=np.int64)
+    deg[keep] = np.diff(g.row_ptr)
+    rp = np.zeros(n2 + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(deg)
+    ci = keep[g.col_idx].astype(np.int32)
+    coli = si.colouring(n2, 7, 8)
+    ref = oracle.count(rp, ci, si.TREE7.parent, 0, coli)
+    graph = sg.Graph(rp, ci, keep_order=True)
+    plan = sg.Plan(si.TREE7.parent, 0)
+    for prec in ("fp64", "fp32"):
+        pv, t, _ = sg.count(graph, plan, _dev(coli), prec)
+        if prec == "fp64":
+            _check_fp64(pv.cpu().numpy(), t, ref, exact=ref.max_bits <= 53)
+        else:
+            _check_fp32(pv.cpu().numpy(), t, ref)

@@ -227,7 +227,7 @@ def test_split_schedule_autotuning(sg, tmp_path, monkeypatch):
         ses.run(torch.from_numpy(cols).cuda(), tot)
         ses.sync()
         info = ses.tuning()
-        assert info["chunk"] in (256, 512, 1024, 2048, 4096, 8192)
+        assert info["chunk"] in (256, 512, 1024, 2048, 4096, 8192) and info["panels"] in (1, 2, 4)
         chunks.append(info["chunk"])
         t = tot.cpu().numpy()
         for i in range(len(plans)):
@@ -236,7 +236,7 @@ def test_split_schedule_autotuning(sg, tmp_path, monkeypatch):
         ses.close()
     stored = json.loads(cache.read_text())
     split = [v for k, v in stored.items() if k.startswith("split|")]
-    assert split and int(split[0]) == chunks[0] == chunks[1]
+    assert split and int(split[0].split(",")[0]) == chunks[0] == chunks[1]
     # a fixed chunk size (read when the graph is created) is kept
     monkeypatch.setenv("SG2V_CHUNK", "300")
     graph2 = sg.Graph(g.row_ptr, g.col_idx)

@@ -334,9 +334,12 @@ sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_
  * Autotuning (SG2V_SESSION_AUTOTUNE).  The first run times the split
  * schedule first: the chunk size (256 to 8192 arcs, up to the first size
  * that splits no row) at which rows longer than it are cut into tasks whose
- * partial results fold into the row, the whole step timed on each
- * candidate's work list (skipped when the environment variable SG2V_CHUNK,
- * read at graph creation, fixes the size).  It then times the candidate
+ * partial results fold into the row, then, at the best size, work lists in
+ * 2 and 4 column panels (rows also cut where their neighbours cross into the
+ * next range of vertices, tasks run panel by panel: the CSC-Split form of
+ * Alg. 6); the whole step is timed on each candidate's work list.  The
+ * environment variables SG2V_CHUNK and SG2V_PANELS, read at graph creation,
+ * fix either instead.  It then times the candidate
  * wave widths and, at the chosen width, the forms each DP node can take:
  * the run-scatter kernel or per-colour accumulators, short narrow rows one
  * per lane group or one per warp, histogram nodes 32 rows per warp or one,
@@ -350,7 +353,7 @@ sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_
  * the file takes them without timing.
  *
  * sg2v_session_tuning -- the session's choices as JSON text
- * ({"wave": W, "chunk": C, "tuned": bool, "nodes": [{"t", "a", "p", "kernel",
+ * ({"wave": W, "chunk": C, "panels": P, "tuned": bool, "nodes": [{"t", "a", "p", "kernel",
  * "lane_groups", "deferred_ema", "form"}, ...]}), NUL-terminated in out
  * (capacity bytes, truncated if short); *length (may be NULL) gets the full
  * length without the NUL.

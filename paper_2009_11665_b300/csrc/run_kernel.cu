@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 // M_s' = Y' (the row's padding gets Y's zeros)
                 VT *out = reinterpret_cast<VT *>(static_cast<T *>(A.Ms) + rowb * A.ldt);
                 const VT *yv = reinterpret_cast<const VT *>(ybuf);
-                // (Y' vectors only: a wider row stride leaves padding nothing reads)
+                // (the Y' vectors: the output row's width rounded to whole vectors)
                 const int nout = (A.ywords - E) / E;
                 if (A.accumulate) {
                     // the backward's transposed SpMM adds to the gradient row

@@ -320,6 +320,27 @@ def profile_call(args):
     import paper_2009_11665_b300 as sg
 
     torch.cuda.set_device(0)
+    if args.profile_call == "er_degrees":
+        # the same 2^24 edges on 2^22 .. 2^18 vertices (average degree 8 .. 128): the
+        # run kernels' cost per row, per colour run and per gathered arc
+        for scale in (22, 21, 20, 19, 18):
+            g = si.erdos_renyi(1 << scale, 1 << 24, seed=1)
+            graph = sg.Graph(g.row_ptr, g.col_idx)
+            plan = sg.Plan(TEMPLATE.parent, 0, K_COLOURS, cut=PLAN_CUT, avg_degree=32.0)
+            cols = si.colourings(g.n, K_COLOURS, 1, seed=0)
+            tot = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+            sg.sg2v_count_batched(graph.handle, [plan.handle], torch.from_numpy(cols).cuda(), 1, sg.SG2V_FP32, None,
+                                  tot)
+            torch.cuda.synchronize()
+            c = cols[0].astype(np.int64)
+            rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+            nc = c[g.col_idx]
+            keep = nc != c[rows]
+            runs = np.unique(rows[keep] * 16 + nc[keep]).size
+            print(json.dumps({"vertices": g.n, "gathered_arcs": int(keep.sum()), "colour_runs": int(runs),
+                              "total": float(tot[0, 0])}))
+            del graph
+        return
     if args.profile_call == "large17":
         g = si.rmat(17, 50_000_000 >> 3, seed=0)
         template, kc = si.TREE15, 15
@@ -366,7 +387,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 3-template x 64-colouring session block")
     ap.add_argument("--no-large", action="store_true", help="skip the tree15 (k = 15) large-form block")
     ap.add_argument("--no-session", action="store_true", help="skip the headline step through an autotuned session")
-    ap.add_argument("--profile-call", choices=["rmat18", "rmat19", "rmat20", "large17"], default=None,
+    ap.add_argument("--profile-call", choices=["rmat18", "rmat19", "rmat20", "large17", "er_degrees"], default=None,
                     help="run exactly one count call (R-MAT scale 18, 19 or 20 with avg degree 32 and tree10, or the "
                          "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
                          "summaries capture")

@@ -919,10 +919,12 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         const char *run_env = std::getenv("SG2V_RUN_KERNEL");
         const char *narrow_env = std::getenv("SG2V_RUN_NARROW");  // 0: warp-wide rows only
         const bool narrow_ok = !(narrow_env && std::atoi(narrow_env) == 0);
-        // (the run kernel packs a neighbour and its colour into one 32-bit word,
-        // u << 4 | colour, and its zero row is row n: fewer than 2^28 rows)
+        // (the run kernel packs a neighbour's first table vector and its colour
+        // into one 32-bit word, (u * vectors per vertex) << 4 | colour, the zero
+        // row n included: (n + 1) x vectors per vertex below 2^28 at the widest wave)
+        const int64_t pvecs = (int64_t)B * ((binom(kc - 1, c.p - 1) + P->vecn - 1) / P->vecn);
         if (!(run_env && std::atoi(run_env) == 0) && !hist && sh.grp != kWideLanes && !sh.rows &&
-            P->n < (int64_t(1) << 28) &&
+            (P->n + 1) * pvecs < (int64_t(1) << 28) &&
             (sh.grp == 32 || narrow_ok) &&
             (sh.nv == 1 || (sh.nv == 2 && sh.grp == 32)) && !P->scaled &&
             (P->elem == Elem::F32 || P->elem == Elem::F64)) {
@@ -2837,7 +2839,7 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             // run map straight into the gradient row, which it adds to
             const char *brun = std::getenv("SG2V_BWD_RUN");
             const bool run_ok = !(brun && std::atoi(brun) == 0) && !P.scaled && sh.grp != kWideLanes &&
-                                n < (int64_t(1) << 28) &&
+                                (n + 1) * (ldyb / vecn) < (int64_t(1) << 28) &&
                                 (sh.nv == 1 || (sh.nv == 2 && sh.grp == 32)) &&
                                 (P.elem == Elem::F32 || (P.elem == Elem::F64 && !g->weights));
             int run_bps = 0;

@@ -27,8 +27,8 @@
 // The gather loop is kept short because these launches are bound by issue
 // slots: each
 // batch of 32 sorted arcs is compacted (through shared memory) to the arcs
-// that add something, each as one word u << 4 | colour (so graphs of fewer
-// than 2^28 vertices: the launcher checks), so an arc costs one
+// that add something, each as one word (u * vectors per vertex) << 4 |
+// colour (below 2^28 vectors: the launcher checks), so an arc costs one
 // shuffle, one address, one 16-byte load and the adds; lanes past the row's
 // last vector load that vector again (no predicate), and a step that stays
 // in every group's current run skips the per-arc colour test.  Groups
@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
         if (lane < E) mbuf[A.mzero + lane] = T(0);
         if (A.a_leaf && lane == 0) mbuf[0] = T(1);
     }
-    const unsigned zero_word = (unsigned)A.n << 4;                 // the zero row
+    // packed arcs carry the gathered row's first vector, u * uvec (the launcher
+    // keeps (n + 1) * uvec below 2^28), so an arc's address is one multiply-add
+    const unsigned zero_word = ((unsigned)A.n * A.uvec) << 4;      // the zero row
     const uint64_t pol_once = l2_policy(A.l2_stream != 0);
     // (a work list has fewer than 2^32 tasks: one per row plus the chunks)
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 if (cnt == 0) continue;
                 if (t_in) {
                     const int r = __popc(live & ((1u << lane) - 1u));
-                    cbuf[r] = ((unsigned)u_in << 4) | (unsigned)c_in;
+                    cbuf[r] = (((unsigned)u_in * A.uvec) << 4) | (unsigned)c_in;
                     if (WEIGHTED) wbuf[r] = __ldg(A.sw + aoff + base + lane);
                 }
                 __syncwarp();
@@ -292,13 +294,13 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     for (int r = 0; r < U; ++r) {
                         const int j = j0 + r * NG + grp;
                         const unsigned pw = __shfl_sync(kFull, pk, j);
-                        const unsigned u = pw >> 4;
+                        const unsigned uo = pw >> 4;  // the row's first vector
                         cr[r] = (int)(pw & 15u);
                         w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
 #pragma unroll
                         for (int q = 0; q < NV; ++q)
                             x[r][q] = (!SKIP_ZERO || j < cnt)
-                                          ? ldg_row(reinterpret_cast<const VT *>(A.Mp) + ((size_t)u * A.uvec + lvo[q]))
+                                          ? ldg_row(reinterpret_cast<const VT *>(A.Mp) + (uo + lvo[q]))
                                           : V::zero();
                     }
                     const bool same = G == 32 ? cr[U - 1] == cur : __all_sync(kFull, cr[U - 1] == cur);
@@ -482,7 +484,10 @@ cudaError_t launch_node_run(const NodeArgs &args, Elem e, int g, int nv, int for
     if (err != cudaSuccess) return err;
     NodeArgs a = args;
     a.group_rows = 0;  // one task per warp
-    a.uvec = (unsigned)((int64_t)a.nb * a.ldp / (e == Elem::F64 ? 2 : 4));
+    const int64_t uvec = (int64_t)a.nb * a.ldp / (e == Elem::F64 ? 2 : 4);
+    // packed arcs hold u * uvec in 28 bits (the zero row n included)
+    if ((a.n + 1) * uvec >= (int64_t(1) << 28)) return cudaErrorInvalidValue;
+    a.uvec = (unsigned)uvec;
     return launch_variant(k, a, 32, threads, smem, grid_cap, stream);
 }
 

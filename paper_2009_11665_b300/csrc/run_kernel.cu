@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     // races another), folded once the task's arcs are done
     constexpr bool RMW = G < 32 || SG2V_RUN_RMW32;
     static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
+    static_assert(G != 32 || U == 4, "warp-wide groups read a step's four packed arcs with one load");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
@@ -275,10 +276,21 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 __syncwarp();
                 // slots past the live arcs read the zero row into the batch's
                 // last run, so a run that continues in the next batch is not cut
-                const unsigned wl = cbuf[lane < cnt ? lane : cnt - 1];
-                const unsigned pk = lane < cnt ? wl : (zero_word | (wl & 15u));
+                unsigned pk = 0;
                 T w_l = T(1);
-                if (WEIGHTED) w_l = lane < cnt ? T(wbuf[lane]) : T(0);
+                if constexpr (G == 32) {
+                    // warp-wide groups read the packed arcs four at a time from
+                    // the slots (one broadcast load per step instead of a
+                    // shuffle per arc): the padding slots are filled here
+                    if (lane >= cnt) {
+                        cbuf[lane] = zero_word | (cbuf[cnt - 1] & 15u);
+                        if (WEIGHTED) wbuf[lane] = 0.f;
+                    }
+                } else {
+                    const unsigned wl = cbuf[lane < cnt ? lane : cnt - 1];
+                    pk = lane < cnt ? wl : (zero_word | (wl & 15u));
+                    if (WEIGHTED) w_l = lane < cnt ? T(wbuf[lane]) : T(0);
+                }
                 __syncwarp();
                 if (FORM == 2 && !mready) {
                     // the active row is read from the first run end on
@@ -290,13 +302,25 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     VT x[U][NV];
                     T w[U];
                     int cr[U];
+                    uint4 pw4 = make_uint4(0u, 0u, 0u, 0u);
+                    float4 w4 = make_float4(1.f, 1.f, 1.f, 1.f);
+                    if constexpr (G == 32) {
+                        pw4 = *reinterpret_cast<const uint4 *>(cbuf + j0);
+                        if (WEIGHTED) w4 = *reinterpret_cast<const float4 *>(wbuf + j0);
+                    }
 #pragma unroll
                     for (int r = 0; r < U; ++r) {
                         const int j = j0 + r * NG + grp;
-                        const unsigned pw = __shfl_sync(kFull, pk, j);
+                        unsigned pw;
+                        if constexpr (G == 32) {
+                            pw = r == 0 ? pw4.x : (r == 1 ? pw4.y : (r == 2 ? pw4.z : pw4.w));
+                            w[r] = WEIGHTED ? T(r == 0 ? w4.x : (r == 1 ? w4.y : (r == 2 ? w4.z : w4.w))) : T(1);
+                        } else {
+                            pw = __shfl_sync(kFull, pk, j);
+                            w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
+                        }
                         const unsigned uo = pw >> 4;  // the row's first vector
                         cr[r] = (int)(pw & 15u);
-                        w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);
 #pragma unroll
                         for (int q = 0; q < NV; ++q)
                             x[r][q] = (!SKIP_ZERO || j < cnt)
@@ -335,6 +359,8 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                         }
                     }
                 }
+                // every lane has read the slots before the next batch refills them
+                if constexpr (G == 32) __syncwarp();
             }
             if (cur >= 0) flush(cur);
             if (FORM == 2 && !mready) asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     using VT = typename V::type;
     constexpr int E = V::n;    // entries per 16-byte vector
     constexpr int NG = 32 / G; // arcs per warp instruction
-    constexpr int U = (NV == 1 && sizeof(T) == 4) ? SG2V_RUN_U_F32 : 4;  // arcs in flight per group and step
+    constexpr int U = (NV == 1 && sizeof(T) == 4 && G == 32) ? SG2V_RUN_U_F32 : 4;  // arcs in flight per group and step
     // FP64 adds are scarce on this part: slots past a batch's live arcs skip
     // their load and adds; FP32 slots read the zero row instead
     constexpr bool SKIP_ZERO = sizeof(T) >= 8;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     // races another), folded once the task's arcs are done
     constexpr bool RMW = G < 32 || SG2V_RUN_RMW32;
     static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
-    static_assert(G != 32 || U == 4, "warp-wide groups read a step's four packed arcs with one load");
+    static_assert(G != 32 || U % 4 == 0, "warp-wide groups read a step's packed arcs four at a time");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
@@ -302,19 +302,29 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     VT x[U][NV];
                     T w[U];
                     int cr[U];
-                    uint4 pw4 = make_uint4(0u, 0u, 0u, 0u);
-                    float4 w4 = make_float4(1.f, 1.f, 1.f, 1.f);
+                    uint4 pw4[G == 32 ? U / 4 : 1];
+                    float4 w4[G == 32 ? U / 4 : 1];
                     if constexpr (G == 32) {
-                        pw4 = *reinterpret_cast<const uint4 *>(cbuf + j0);
-                        if (WEIGHTED) w4 = *reinterpret_cast<const float4 *>(wbuf + j0);
+#pragma unroll
+                        for (int h = 0; h < U / 4; ++h) {
+                            pw4[h] = *reinterpret_cast<const uint4 *>(cbuf + j0 + 4 * h);
+                            if (WEIGHTED) w4[h] = *reinterpret_cast<const float4 *>(wbuf + j0 + 4 * h);
+                        }
                     }
 #pragma unroll
                     for (int r = 0; r < U; ++r) {
                         const int j = j0 + r * NG + grp;
                         unsigned pw;
                         if constexpr (G == 32) {
-                            pw = r == 0 ? pw4.x : (r == 1 ? pw4.y : (r == 2 ? pw4.z : pw4.w));
-                            w[r] = WEIGHTED ? T(r == 0 ? w4.x : (r == 1 ? w4.y : (r == 2 ? w4.z : w4.w))) : T(1);
+                            const uint4 &p4 = pw4[r / 4];
+                            const int k4 = r % 4;
+                            pw = k4 == 0 ? p4.x : (k4 == 1 ? p4.y : (k4 == 2 ? p4.z : p4.w));
+                            if (WEIGHTED) {
+                                const float4 &q4 = w4[r / 4];
+                                w[r] = T(k4 == 0 ? q4.x : (k4 == 1 ? q4.y : (k4 == 2 ? q4.z : q4.w)));
+                            } else {
+                                w[r] = T(1);
+                            }
                         } else {
                             pw = __shfl_sync(kFull, pk, j);
                             w[r] = WEIGHTED ? __shfl_sync(kFull, w_l, j) : T(1);

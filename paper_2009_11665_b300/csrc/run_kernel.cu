@@ -56,6 +56,9 @@ namespace {
 #ifndef SG2V_RUN_RMW32
 #define SG2V_RUN_RMW32 1
 #endif
+#ifndef SG2V_RUN_BLOCKS
+#define SG2V_RUN_BLOCKS 1
+#endif
 
 // Resident blocks per SM requested from the compiler (the register cap);
 // tuned on B300 (occupancy matters more than a few spills).
@@ -110,6 +113,10 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
     constexpr bool RMW = G < 32 || SG2V_RUN_RMW32;
     static_assert(32 % (NG * U) == 0, "a step's arcs must stay inside one batch of 32");
     static_assert(G != 32 || U % 4 == 0, "warp-wide groups read a step's packed arcs four at a time");
+    // narrower groups take a block of U consecutive slots per step (group g:
+    // slots g U .. g U + U - 1) and read them with one 16-byte shared load;
+    // SG2V_RUN_BLOCKS=0 deals the slots round-robin through shuffles
+    constexpr bool SLOTS = G == 32 || (SG2V_RUN_BLOCKS && U == 4);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
@@ -278,8 +285,8 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                 // last run, so a run that continues in the next batch is not cut
                 unsigned pk = 0;
                 T w_l = T(1);
-                if constexpr (G == 32) {
-                    // warp-wide groups read the packed arcs four at a time from
+                if constexpr (SLOTS) {
+                    // the groups read the packed arcs four at a time from
                     // the slots (one broadcast load per step instead of a
                     // shuffle per arc): the padding slots are filled here
                     if (lane >= cnt) {
@@ -302,20 +309,22 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     VT x[U][NV];
                     T w[U];
                     int cr[U];
-                    uint4 pw4[G == 32 ? U / 4 : 1];
-                    float4 w4[G == 32 ? U / 4 : 1];
-                    if constexpr (G == 32) {
+                    uint4 pw4[SLOTS ? U / 4 : 1];
+                    float4 w4[SLOTS ? U / 4 : 1];
+                    // this group's first slot of the step
+                    const int g0s = j0 + (G == 32 ? 0 : grp * U);
+                    if constexpr (SLOTS) {
 #pragma unroll
                         for (int h = 0; h < U / 4; ++h) {
-                            pw4[h] = *reinterpret_cast<const uint4 *>(cbuf + j0 + 4 * h);
-                            if (WEIGHTED) w4[h] = *reinterpret_cast<const float4 *>(wbuf + j0 + 4 * h);
+                            pw4[h] = *reinterpret_cast<const uint4 *>(cbuf + g0s + 4 * h);
+                            if (WEIGHTED) w4[h] = *reinterpret_cast<const float4 *>(wbuf + g0s + 4 * h);
                         }
                     }
 #pragma unroll
                     for (int r = 0; r < U; ++r) {
-                        const int j = j0 + r * NG + grp;
+                        const int j = SLOTS ? g0s + r : j0 + r * NG + grp;
                         unsigned pw;
-                        if constexpr (G == 32) {
+                        if constexpr (SLOTS) {
                             const uint4 &p4 = pw4[r / 4];
                             const int k4 = r % 4;
                             pw = k4 == 0 ? p4.x : (k4 == 1 ? p4.y : (k4 == 2 ? p4.z : p4.w));
@@ -342,7 +351,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                         // the whole step continues every group's current run
 #pragma unroll
                         for (int r = 0; r < U; ++r) {
-                            if (SKIP_ZERO && j0 + r * NG + grp >= cnt) continue;
+                            if (SKIP_ZERO && (SLOTS ? g0s + r : j0 + r * NG + grp) >= cnt) continue;
 #pragma unroll
                             for (int q = 0; q < NV; ++q) {
                                 if (WEIGHTED)
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     } else {
 #pragma unroll
                         for (int r = 0; r < U; ++r) {
-                            if (SKIP_ZERO && j0 + r * NG + grp >= cnt) continue;
+                            if (SKIP_ZERO && (SLOTS ? g0s + r : j0 + r * NG + grp) >= cnt) continue;
                             if (cr[r] != cur) {
                                 if (cur >= 0) flush(cur);
                                 cur = cr[r];
@@ -370,7 +379,7 @@ __global__ void __launch_bounds__(kNodeThreads, RunMinBlocks<T, NV>::value) node
                     }
                 }
                 // every lane has read the slots before the next batch refills them
-                if constexpr (G == 32) __syncwarp();
+                if constexpr (SLOTS) __syncwarp();
             }
             if (cur >= 0) flush(cur);
             if (FORM == 2 && !mready) asm volatile("cp.async.wait_all;\n" ::: "memory");

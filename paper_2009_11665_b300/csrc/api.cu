@@ -921,8 +921,9 @@ sg2v_status prepare(const sg2v_graph *g, const sg2v_plan *const *plans, int32_t 
         const bool narrow_ok = !(narrow_env && std::atoi(narrow_env) == 0);
         // (the run kernel packs a neighbour's first table vector and its colour
         // into one 32-bit word, (u * vectors per vertex) << 4 | colour, the zero
-        // row n included: (n + 1) x vectors per vertex below 2^28 at the widest wave)
-        const int64_t pvecs = (int64_t)B * ((binom(kc - 1, c.p - 1) + P->vecn - 1) / P->vecn);
+        // row n included: (n + 1) x vectors per vertex below 2^28; checked here
+        // for one colouring per row and again at each launch for its wave)
+        const int64_t pvecs = (binom(kc - 1, c.p - 1) + P->vecn - 1) / P->vecn;  // one colouring per row
         if (!(run_env && std::atoi(run_env) == 0) && !hist && sh.grp != kWideLanes && !sh.rows &&
             (P->n + 1) * pvecs < (int64_t(1) << 28) &&
             (sh.grp == 32 || narrow_ok) &&
@@ -1207,9 +1208,17 @@ cudaError_t launch_run_node(const Prepared &P, size_t i, const NodeArgs &A, cuda
 }
 
 // Launches the forward kernel of node i with the prepared shape.
+// Whether the run-scatter kernel's packed arcs can address every gathered row
+// of this launch's wave ((n + 1) x vectors per vertex below 2^28); a wider
+// wave runs the per-colour-accumulator kernel instead.
+bool run_fits(const Prepared &P, const NodeArgs &A) {
+    return (P.n + 1) * ((int64_t)A.nb * A.ldp / P.vecn) < (int64_t(1) << 28);
+}
+
 cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, cudaStream_t stream) {
     const Shape &sh = P.shape[i];
     const int grid_cap = P.info.sms * sh.blocks_per_sm;
+    const bool run = sh.run && run_fits(P, A);
     if (sh.rows) return launch_hist_rows(A, P.elem, P.scaled, sh.threads, sh.smem, grid_cap, stream);
     if (sh.group) {
         // the longer tasks (the front of the work list) one per warp, the short
@@ -1218,7 +1227,7 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
         NodeArgs W = A;
         W.group_rows = 0;
         W.ntasks = split;
-        cudaError_t e = sh.run ? launch_run_node(P, i, W, stream)
+        cudaError_t e = run ? launch_run_node(P, i, W, stream)
                         : P.scaled ? launch_node_scaled(W, sh.grp, sh.nv, sh.wthreads, sh.wsmem,
                                                         P.info.sms * sh.wbps, stream)
                                    : launch_node(W, P.elem, sh.grp, sh.nv, sh.wthreads, sh.wsmem,
@@ -1230,7 +1239,7 @@ cudaError_t launch_forward_node(const Prepared &P, size_t i, const NodeArgs &A, 
         return P.scaled ? launch_node_scaled(S, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream)
                         : launch_node(S, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     }
-    if (sh.run) return launch_run_node(P, i, A, stream);
+    if (run) return launch_run_node(P, i, A, stream);
     if (P.scaled) return launch_node_scaled(A, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
     return launch_node(A, P.elem, sh.grp, sh.nv, sh.threads, sh.smem, grid_cap, stream);
 }

@@ -415,3 +415,26 @@ def test_column_panel_work_lists(sg, panels, chunk, monkeypatch):
             _check_fp64(pv.cpu().numpy(), t, ref, exact=ref.max_bits <= 53)
         else:
             _check_fp32(pv.cpu().numpy(), t, ref)
+
+
+def test_wave_beyond_packed_arc_limit(sg, monkeypatch):
+    """The run-scatter kernel addresses a gathered row through a packed 28-bit
+    vector offset; a wave of colourings wide enough to pass 2^28 vectors
+    (2^20 vertices x 16 colourings x 21 vectors for tree10's (5,1,4)) runs
+    those launches on the per-colour-accumulator kernel instead, with the
+    same exact counts as one colouring per wave and as the oracle."""
+    import torch
+
+    g = si.erdos_renyi(1 << 20, 1 << 20, seed=3)
+    graph = sg.Graph(g.row_ptr, g.col_idx)
+    plan = sg.Plan(si.TREE10.parent, 0, 10, cut="min_work", avg_degree=2.0)
+    B = 16
+    cols = si.colourings(g.n, 10, B, seed=8)
+    res = {}
+    for wave in ("16", "1"):
+        monkeypatch.setenv("SG2V_WAVE", wave)
+        _, tot, _ = sg.count_batched(graph, [plan], _dev(cols), "fp64", per_vertex=False)
+        res[wave] = tot.cpu().numpy()[0]
+    assert np.array_equal(res["16"], res["1"])
+    ref = oracle.count(g.row_ptr, g.col_idx, si.TREE10.parent, 0, cols[0], per_vertex=False)
+    assert ref.max_bits <= 53 and res["16"][0] == float(ref.total)

@@ -331,8 +331,8 @@ sg2v_status sg2v_session_sync(sg2v_session *session, sg2v_stream stream);
 sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_t *graph);
 
 /*
- * Autotuning (SG2V_SESSION_AUTOTUNE).  The first run times the split
- * schedule first: the chunk size (256 to 8192 arcs, up to the first size
+ * Autotuning (SG2V_SESSION_AUTOTUNE).  The first run times, in this order,
+ * the split schedule: the chunk size (256 to 8192 arcs, up to the first size
  * that splits no row) at which rows longer than it are cut into tasks whose
  * partial results fold into the row, then, at the best size, work lists in
  * 2 and 4 column panels (rows also cut where their neighbours cross into the
@@ -350,7 +350,8 @@ sg2v_status sg2v_session_info(const sg2v_session *session, int32_t *wave, int32_
  * arcs, largest degree, weights), colours, node shape, table type, wave and
  * chunk size (the split schedule by the graph statistics, colours, table
  * type, colourings and templates), and a later session finding its keys in
- * the file takes them without timing.
+ * the file takes them without timing them again (the wave width is always
+ * timed).
  *
  * sg2v_session_tuning -- the session's choices as JSON text
  * ({"wave": W, "chunk": C, "panels": P, "tuned": bool, "nodes": [{"t", "a", "p", "kernel",

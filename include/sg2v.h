@@ -105,7 +105,11 @@ typedef enum {
  * self-loops and no repeated arcs (Sec. 2.2.1: simple graph); violations give
  * SG2V_ERR_GRAPH_NOT_SIMPLE unless validation is skipped.  The library copies
  * the arrays onto the current device (the caller may free its copies) and
- * derives its load-balanced work list there.  Unless SG2V_GRAPH_KEEP_ORDER is
+ * derives its load-balanced work list there: rows longer than a chunk (the
+ * environment variable SG2V_CHUNK, else 512 arcs when the average degree is
+ * at most 64 and 1,024 above) become several tasks whose partial results fold
+ * into the row; SG2V_PANELS > 1 also cuts the work list into that many column
+ * panels (the CSC-Split form of Alg. 6).  Unless SG2V_GRAPH_KEEP_ORDER is
  * given, the device copy numbers the vertices by decreasing degree (the rows
  * most arcs gather share cache lines); this is invisible to the caller:
  * colourings, per-vertex counts, per-vertex gradient seeds, weights and

@@ -1264,6 +1264,21 @@ bool sort_counts_used(const Prepared &P) {
     return false;
 }
 
+// The (2, 1, 1) node of a weighted graph with plain FP32 / FP64 tables: its
+// table is summed from the colour-sorted arcs by its own small kernel
+// (SG2V_SORT_HIST=0 keeps the node kernels); -1 when there is none.
+int weighted_hist_node(const Prepared &P) {
+    const char *env = std::getenv("SG2V_SORT_HIST");
+    if ((env && std::atoi(env) == 0) || P.scaled || !P.g->weighted || !P.g->weights || P.kc > 16 ||
+        !(P.elem == Elem::F32 || P.elem == Elem::F64))
+        return -1;
+    for (size_t i = 0; i < P.nodes.size(); ++i) {
+        const CNode &c = P.nodes[i];
+        if (c.t == 2 && c.a == 1 && c.p == 1 && !c.is_root) return (int)i;
+    }
+    return -1;
+}
+
 int sort_hist_node(const Prepared &P) {
     const char *env = std::getenv("SG2V_SORT_HIST");
     if ((env && std::atoi(env) == 0) || P.scaled || P.g->weights) return -1;
@@ -1298,6 +1313,7 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
     const char *half_env = std::getenv("SG2V_HALF_ROOT");
     const bool half_root = !(half_env && std::atoi(half_env) == 0);
     const int fused = sort_hist_node(P);
+    const int whist = weighted_hist_node(P);
     for (int b0 = 0; b0 < nb; b0 += wave) {
         const int wb = std::min(wave, nb - b0);
         const int8_t *wcol = d_col + (int64_t)b0 * n;
@@ -1335,6 +1351,27 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
             const CNode &c = P.nodes[i];
             const Shape &sh = P.shape[i];
             if ((int)i == fused) continue;  // written by the sort
+            if ((int)i == whist) {
+                // weighted (2, 1, 1): colour sums of the sorted arcs' weights
+                R.ld[i] = table_ld(P, c);
+                if ((st = src.get(i, table_bytes(P, c, wb), &R.table[i]))) return st;
+                if ((st = zero_gather_row(R.table[i], n, wb, R.ld[i], esz, stream))) return st;
+                if (g->nheavy)  // chunks of split rows add into zeroed rows
+                    SG2V_CUDA(cudaMemsetAsync(R.table[i], 0, (size_t)n * wb * R.ld[i] * esz, stream), "memset");
+                char name[64];
+                std::snprintf(name, sizeof name, "node t=%d a=%d p=%d %s", c.t, c.a, c.p, elem_name(P));
+                // algorithmic bytes: the sorted arcs' colours and weights, the
+                // colouring and the work list read once, the table written once
+                timer.begin(name,
+                            (double)wb * g->nnz * 5.0 + (double)live_rows * wb * (1.0 + (kc - 1) * (double)esz) +
+                                16.0 * ntasks,
+                            (int)i);
+                SG2V_CUDA(launch_weighted_hist(g->tasks, ntasks, R.sclr, R.sw, g->nnz, wcol, n, wb, kc, R.table[i],
+                                               R.ld[i], nullptr, 0, P.elem, P.info.sms, stream),
+                          "weighted histogram");
+                timer.end();
+                continue;
+            }
             NodeArgs A = node_args(P, R, i, b0, wb, wcol);
             if (!c.is_root) {
                 R.ld[i] = table_ld(P, c);
@@ -1821,7 +1858,9 @@ int64_t count_launches(const Prepared &P, int wave) {
     if (P.g->small_begin > 0 && P.g->small_begin < P.g->ntasks) per_wave += 1;  // two sort launches
     if (P.scaled)
         for (const CNode &c : P.nodes) per_wave += c.p != 1;
-    for (const Shape &sh : P.shape) per_wave += sh.defer + sh.group;
+    const int whist = weighted_hist_node(P);  // one launch, whatever its shape
+    for (size_t i = 0; i < P.shape.size(); ++i)
+        if ((int)i != whist) per_wave += P.shape[i].defer + P.shape[i].group;
     return 1 + waves * per_wave + 2 * (int64_t)P.plans.size() + 1;
 }
 
@@ -2643,7 +2682,28 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
         return ch;
     };
     // one forward node launch writing table j (Yout: also its Y')
+    const int whist = weighted_hist_node(P);
     auto run_node = [&](size_t j, void *Yout) -> sg2v_status {
+        if ((int)j == whist) {
+            // weighted (2, 1, 1): table and Y' hold the same colour sums
+            if (!R.table[j]) {
+                sg2v_status s2 = alloc(gather_table_bytes(n, 1, R.ld[j], esz), &R.table[j]);
+                if (s2) return s2;
+                if ((s2 = zero_gather_row(R.table[j], n, 1, R.ld[j], esz, stream))) return s2;
+            }
+            if (g->nheavy) {  // chunks of split rows add into zeroed rows
+                SG2V_CUDA(cudaMemsetAsync(R.table[j], 0, (size_t)n * R.ld[j] * esz, stream), "memset");
+                if (Yout) SG2V_CUDA(cudaMemsetAsync(Yout, 0, (size_t)n * ldy[j] * esz, stream), "memset");
+            }
+            double b = (double)nnz * 5.0 + (double)n * (1.0 + (kc - 1) * (double)esz) + 16.0 * g->ntasks;
+            if (Yout) b += (double)n * (kc - 1) * (double)esz;
+            timer.begin(recompute ? "backward: recomputed forward node" : "backward: forward node", b);
+            SG2V_CUDA(launch_weighted_hist(g->tasks, g->ntasks, R.sclr, R.sw, nnz, d_col, n, 1, kc, R.table[j],
+                                           R.ld[j], Yout, Yout ? ldy[j] : 0, P.elem, P.info.sms, stream),
+                      "weighted histogram");
+            timer.end();
+            return SG2V_OK;
+        }
         NodeArgs A = node_args(Pw, R, j, 0, 1, d_col);
         if (!P.nodes[j].is_root) {
             if (!R.table[j]) {

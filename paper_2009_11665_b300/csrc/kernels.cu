@@ -2201,6 +2201,96 @@ cudaError_t launch_eref(const int4 *tasks, int64_t ntasks, const int32_t *scol, 
     return cudaGetLastError();
 }
 
+namespace {
+
+// The (2, 1, 1) table of a weighted graph from the colour-sorted arcs (the
+// colour histogram of Sec. 4 with the weights A.val of Alg. 4): for row v and
+// each colour x other than col(v), the sum of the weights of v's arcs to
+// neighbours of colour x.  One warp per task; the arcs of a task come sorted
+// by neighbour colour (invalid colours last), so each colour is one run, summed
+// by a segmented scan over each batch of 32 arcs and then batch by batch, an
+// order that does not depend on scheduling.  Chunks of a split row add their
+// sums into a zeroed row.  With a leaf active child the node's Y' row holds
+// the same values (entry j: the j-th colour other than col(v)); out2, when
+// given, receives it too.
+template <typename T>
+__global__ void __launch_bounds__(256) weighted_hist_kernel(const int4 *__restrict__ tasks, int64_t ntasks,
+                                                            const int8_t *__restrict__ sclr,
+                                                            const float *__restrict__ sw, int64_t nnz,
+                                                            const int8_t *__restrict__ colours, int64_t n, int nb,
+                                                            int kc, T *out, int64_t ld, T *out2, int64_t ld2) {
+    __shared__ T tot_s[8][kMaxHistColours + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T *tot = tot_s[wib];
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < ntasks; t += nwarps) {
+        const int4 task = tasks[t];
+        const int v = task.x;
+        for (int b = 0; b < nb; ++b) {
+            const int cv = (int)colours[(int64_t)b * n + v];
+            const bool ok = (unsigned)cv < (unsigned)kc;
+            if (lane <= kMaxHistColours) tot[lane] = T(0);
+            __syncwarp();
+            const int8_t *cl = sclr + (int64_t)b * nnz;
+            const float *wl = sw + (int64_t)b * nnz;
+            for (int64_t base = task.z; ok && base < task.w; base += 32) {
+                const int64_t e = base + lane;
+                const bool in = e < task.w;
+                const int c = in ? (int)__ldg(cl + e) : -1;
+                T s = in ? T(__ldg(wl + e)) : T(0);
+                // segmented inclusive scan: colours run in order, so equal
+                // colours o lanes apart enclose only that colour
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const T y = __shfl_up_sync(0xffffffffu, s, o);
+                    const int cy = __shfl_up_sync(0xffffffffu, c, o);
+                    if (lane >= o && cy == c) s += y;
+                }
+                const int cn = __shfl_down_sync(0xffffffffu, c, 1);
+                if (c >= 0 && (lane == 31 || cn != c)) tot[c] += s;  // one run end per colour
+                __syncwarp();
+            }
+            T *row = out + ((int64_t)v * nb + b) * ld;
+            T *row2 = out2 ? out2 + ((int64_t)v * nb + b) * ld2 : nullptr;
+            const int64_t width = out2 && ld2 > ld ? ld2 : ld;
+            for (int j = lane; j < width; j += 32) {
+                const int x = j < cv ? j : j + 1;
+                const T val = ok && j < kc - 1 ? tot[x] : T(0);
+                if (task.y < 0) {
+                    if (j < ld) row[j] = val;
+                    if (row2 && j < ld2) row2[j] = val;
+                } else if (val != T(0)) {
+                    if (j < ld) atomicAdd(row + j, val);
+                    if (row2 && j < ld2) atomicAdd(row2 + j, val);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_weighted_hist(const int4 *tasks, int64_t ntasks, const int8_t *sclr, const float *sw, int64_t nnz,
+                                 const int8_t *colours, int64_t n, int nb, int kc, void *out, int64_t ld, void *out2,
+                                 int64_t ld2, Elem e, int sms, cudaStream_t stream) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (kc > kMaxHistColours || !sw) return cudaErrorInvalidValue;
+    int64_t blocks = (ntasks + 7) / 8;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    if (e == Elem::F64)
+        weighted_hist_kernel<double><<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, sclr, sw, nnz, colours, n, nb,
+                                                                           kc, static_cast<double *>(out), ld,
+                                                                           static_cast<double *>(out2), ld2);
+    else if (e == Elem::F32)
+        weighted_hist_kernel<float><<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, sclr, sw, nnz, colours, n, nb,
+                                                                          kc, static_cast<float *>(out), ld,
+                                                                          static_cast<float *>(out2), ld2);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
                                int32_t *scol, int8_t *sclr, float *sw, const SortHist &hist, int sms,

@@ -151,6 +151,27 @@ def test_weighted_graph(sg):
     _check_fp32(r32[0], r32[1], ref)
 
 
+@pytest.mark.parametrize("chunk", ["1024", "64"])
+@pytest.mark.parametrize("hist", ["", "0"])
+def test_weighted_split_rows(sg, chunk, hist, monkeypatch):
+    """Weighted graphs whose hub rows are split across warps: the (2, 1, 1)
+    table summed from the sorted arcs' weights (with SG2V_SORT_HIST=0: by the
+    node kernels), split chunks adding into zeroed rows, equals the exact
+    dyadic oracle in FP64 and FP32, up to 16 colours."""
+    monkeypatch.setenv("SG2V_CHUNK", chunk)
+    if hist:
+        monkeypatch.setenv("SG2V_SORT_HIST", hist)
+    g = _hub_graph(11)
+    assert g.degrees().max() > 4 * int(chunk)
+    w = si.arc_weights(g, si.edge_weights(g, seed=6))
+    for parent, colours in ((si.TREE7.parent, (7, 12)), ((-1, 0, 1), (3, 16)), (si.PATH5.parent, (5, 16))):
+        for kc in colours:
+            col = si.colouring(g.n, kc, 3)
+            ref, plan, r64, r32 = _run(sg, g, parent, 0, col, kc, weights=w)
+            _check_fp64(r64[0], r64[1], ref, exact=False)
+            _check_fp32(r32[0], r32[1], ref)
+
+
 @pytest.mark.parametrize("wave", ["", "1", "2"])
 def test_batched_templates_and_colourings(sg, wave, monkeypatch):
     """Several colourings x several templates in one call equal one oracle

@@ -566,6 +566,13 @@ def main():
             return records_block(sg.sg2v_profile_read(), reps, 1)
 
         ms_f = time_steps(torch, fwd4, reps4, args.warmup, stream, dist)
+        # the same forward through an autotuned session (its warm-up run tunes
+        # the split schedule and forms; the timed runs replay a CUDA graph)
+        ses4 = sg.Session(graph4, [plan4], 1, "fp32", autotune=True)
+        col4b = col4.view(1, -1)
+        ms_fs = time_steps(torch, lambda: ses4.run(col4b, tot4, None, None, stream), reps4, args.warmup, stream, dist)
+        chunk4 = ses4.tuning()["chunk"]
+        ses4.close()
         ms_b = time_steps(torch, bwd4(sg.SG2V_BACKWARD_STORE), reps4, args.warmup, stream, dist)
         peak_store = sg.sg2v_last_call_peak_bytes()
         ms_r = time_steps(torch, bwd4(sg.SG2V_BACKWARD_RECOMPUTE), reps4, args.warmup, stream, dist)
@@ -575,10 +582,14 @@ def main():
         tab_r, bytes_r, _ = profiled(bwd4(sg.SG2V_BACKWARD_RECOMPUTE), 3)
         hbm = float(peaks["hbm_gbs"])
         differentiable = {"workload": "chunglu200k (200k vertices, 2M edges, gamma 2.3, weights [0.5,1.5)), tree8, "
-                                      "k=8, one colouring", "forward_ms": ms_f, "forward_and_gradient_ms": ms_b,
+                                      "k=8, one colouring", "forward_ms": ms_f,
+                          "forward_session_ms": ms_fs, "forward_session_split_chunk": chunk4,
+                          "forward_and_gradient_ms": ms_b,
                           "forward_and_gradient_recompute_ms": ms_r, "peak_workspace_bytes": peak_store,
                           "peak_workspace_bytes_recompute": peak_rec, "dtype": "f32",
                           "roofline_forward": hbm_roofline("forward step", bytes_f, ms_f, hbm, peak_kind),
+                          "roofline_forward_session": hbm_roofline("forward step (session replay)", bytes_f, ms_fs,
+                                                                   hbm, peak_kind),
                           "roofline_forward_and_gradient": hbm_roofline("forward+gradient step", bytes_b, ms_b, hbm,
                                                                         peak_kind),
                           "roofline_forward_and_gradient_recompute": hbm_roofline("forward+gradient step (recompute)",

@@ -252,6 +252,36 @@ def test_split_schedule_autotuning(sg, tmp_path, monkeypatch):
     ses.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotuned_session_on_weighted_graph(sg, prec, tmp_path, monkeypatch):
+    """An autotuned session on a weighted graph with rows long enough to be
+    split: whichever split schedule, wave width and node forms the tuner
+    picks (the weighted (2, 1, 1) node has one form), the replayed step's
+    per-vertex counts and totals equal the exact dyadic oracle."""
+    import torch
+
+    monkeypatch.setenv("SG2V_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.delenv("SG2V_CHUNK", raising=False)
+    g = si.rmat(12, 40000, seed=11)
+    assert np.diff(g.row_ptr).max() > 256
+    w = si.arc_weights(g, si.edge_weights(g, seed=8))
+    graph = sg.Graph(g.row_ptr, g.col_idx, w)
+    plans = [sg.Plan(si.TREE8.parent), sg.Plan(si.PATH5.parent, 0, 8)]
+    B = 2
+    cols = si.colourings(g.n, 8, B, seed=12)
+    ses = sg.Session(graph, plans, B, prec, per_vertex=True, autotune=True)
+    tot = torch.empty((len(plans), B), dtype=torch.float64, device="cuda")
+    pv = torch.empty((len(plans), B, g.n), dtype=torch.float64, device="cuda")
+    for _ in range(2):  # the tuning run, then a graph replay
+        ses.run(torch.from_numpy(cols).cuda(), tot, None, pv)
+        ses.sync()
+        for i, parent in enumerate((si.TREE8.parent, si.PATH5.parent)):
+            for b in range(B):
+                ref = oracle.count(g.row_ptr, g.col_idx, parent, 0, cols[b], 8, w)
+                _check(prec, pv[i, b].cpu().numpy(), tot[i, b].item(), ref)
+    ses.close()
+
+
 def _exact_or_close(got: float, ref) -> None:
     if ref.max_bits <= 53:
         assert got == float(ref.total)

@@ -311,7 +311,8 @@ def profile_call(args):
     """One sg2v_count_batched call (B = --batch colourings): tree10 on an
     R-MAT graph with the workload's parameters and average degree 32
     (rmat18, rmat19, rmat20), or tree15 with k = 15 on the large form's scale-17
-    sibling (large17: 6.25e6 edges, average degree about 95)."""
+    sibling (large17: 6.25e6 edges, average degree about 95); chunglu200k_grad
+    runs the differentiable form's forward and forward + gradient calls."""
     import torch
 
     import __graft_entry__
@@ -340,6 +341,23 @@ def profile_call(args):
             print(json.dumps({"vertices": g.n, "gathered_arcs": int(keep.sum()), "colour_runs": int(runs),
                               "total": float(tot[0, 0])}))
             del graph
+        return
+    if args.profile_call == "chunglu200k_grad":
+        # the differentiable form's workload: one forward call, then one
+        # forward + gradient call (stored form), FP32, tree8, k = 8
+        g = si.workload_graph("chunglu200k")
+        w = si.arc_weights(g, si.edge_weights(g, seed=0))
+        graph = sg.Graph(g.row_ptr, g.col_idx, w)
+        plan = sg.Plan(si.TREE8.parent, 0, 8)
+        col = torch.from_numpy(si.colouring(g.n, 8, 0)).cuda()
+        tot = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+        grad = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        sg.sg2v_count_batched(graph.handle, [plan.handle], col, 1, sg.SG2V_FP32, None, tot)
+        total = sg.sg2v_count_backward(graph.handle, plan.handle, col, sg.SG2V_FP32, grad, None,
+                                       flags=sg.SG2V_BACKWARD_STORE)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_call": args.profile_call, "total": float(tot[0, 0]), "backward_total": total,
+                          "grad_abs_sum": float(grad.abs().sum())}))
         return
     if args.profile_call == "large17":
         g = si.rmat(17, 50_000_000 >> 3, seed=0)
@@ -387,9 +405,11 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 3-template x 64-colouring session block")
     ap.add_argument("--no-large", action="store_true", help="skip the tree15 (k = 15) large-form block")
     ap.add_argument("--no-session", action="store_true", help="skip the headline step through an autotuned session")
-    ap.add_argument("--profile-call", choices=["rmat18", "rmat19", "rmat20", "large17", "er_degrees"], default=None,
+    ap.add_argument("--profile-call", choices=["rmat18", "rmat19", "rmat20", "large17", "er_degrees",
+                                               "chunglu200k_grad"], default=None,
                     help="run exactly one count call (R-MAT scale 18, 19 or 20 with avg degree 32 and tree10, or the "
-                         "large form's scale-17 sibling with tree15) and exit: the cases the committed ncu "
+                         "large form's scale-17 sibling with tree15; chunglu200k_grad: the differentiable form's "
+                         "forward call and forward + gradient call) and exit: the cases the committed ncu "
                          "summaries capture")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp32_scaled", "u64", "u128"], default="fp32")
     args = ap.parse_args()

@@ -1366,8 +1366,8 @@ sg2v_status enqueue(const Prepared &P, RunBuffers &R, const int8_t *d_col, doubl
                             (double)wb * g->nnz * 5.0 + (double)live_rows * wb * (1.0 + (kc - 1) * (double)esz) +
                                 16.0 * ntasks,
                             (int)i);
-                SG2V_CUDA(launch_weighted_hist(g->tasks, ntasks, R.sclr, R.sw, g->nnz, wcol, n, wb, kc, R.table[i],
-                                               R.ld[i], nullptr, 0, P.elem, P.info.sms, stream),
+                SG2V_CUDA(launch_weighted_hist(g->tasks, ntasks, small_begin, R.sclr, R.sw, g->nnz, wcol, n, wb, kc,
+                                               R.table[i], R.ld[i], nullptr, 0, P.elem, P.info.sms, stream),
                           "weighted histogram");
                 timer.end();
                 continue;
@@ -2698,8 +2698,8 @@ sg2v_status sg2v_count_backward(const sg2v_graph *g, const sg2v_plan *plan, cons
             double b = (double)nnz * 5.0 + (double)n * (1.0 + (kc - 1) * (double)esz) + 16.0 * g->ntasks;
             if (Yout) b += (double)n * (kc - 1) * (double)esz;
             timer.begin(recompute ? "backward: recomputed forward node" : "backward: forward node", b);
-            SG2V_CUDA(launch_weighted_hist(g->tasks, g->ntasks, R.sclr, R.sw, nnz, d_col, n, 1, kc, R.table[j],
-                                           R.ld[j], Yout, Yout ? ldy[j] : 0, P.elem, P.info.sms, stream),
+            SG2V_CUDA(launch_weighted_hist(g->tasks, g->ntasks, g->small_begin, R.sclr, R.sw, nnz, d_col, n, 1, kc,
+                                           R.table[j], R.ld[j], Yout, Yout ? ldy[j] : 0, P.elem, P.info.sms, stream),
                       "weighted histogram");
             timer.end();
             return SG2V_OK;

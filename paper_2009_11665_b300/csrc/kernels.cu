@@ -2206,54 +2206,52 @@ namespace {
 // The (2, 1, 1) table of a weighted graph from the colour-sorted arcs (the
 // colour histogram of Sec. 4 with the weights A.val of Alg. 4): for row v and
 // each colour x other than col(v), the sum of the weights of v's arcs to
-// neighbours of colour x.  One warp per task; the arcs of a task come sorted
-// by neighbour colour (invalid colours last), so each colour is one run, summed
-// by a segmented scan over each batch of 32 arcs and then batch by batch, an
-// order that does not depend on scheduling.  Chunks of a split row add their
-// sums into a zeroed row.  With a leaf active child the node's Y' row holds
-// the same values (entry j: the j-th colour other than col(v)); out2, when
-// given, receives it too.
-template <typename T>
-__global__ void __launch_bounds__(256) weighted_hist_kernel(const int4 *__restrict__ tasks, int64_t ntasks,
-                                                            const int8_t *__restrict__ sclr,
-                                                            const float *__restrict__ sw, int64_t nnz,
-                                                            const int8_t *__restrict__ colours, int64_t n, int nb,
-                                                            int kc, T *out, int64_t ld, T *out2, int64_t ld2) {
-    __shared__ T tot_s[8][kMaxHistColours + 1];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    T *tot = tot_s[wib];
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) >> 5) + wib; t < ntasks; t += nwarps) {
-        const int4 task = tasks[t];
-        const int v = task.x;
-        for (int b = 0; b < nb; ++b) {
-            const int cv = (int)colours[(int64_t)b * n + v];
-            const bool ok = (unsigned)cv < (unsigned)kc;
-            if (lane <= kMaxHistColours) tot[lane] = T(0);
-            __syncwarp();
-            const int8_t *cl = sclr + (int64_t)b * nnz;
-            const float *wl = sw + (int64_t)b * nnz;
-            for (int64_t base = task.z; ok && base < task.w; base += 32) {
-                const int64_t e = base + lane;
-                const bool in = e < task.w;
-                const int c = in ? (int)__ldg(cl + e) : -1;
-                T s = in ? T(__ldg(wl + e)) : T(0);
-                // segmented inclusive scan: colours run in order, so equal
-                // colours o lanes apart enclose only that colour
+// neighbours of colour x.  The arcs of a task come sorted by neighbour colour
+// (invalid colours last), so each colour is one run, summed by a segmented
+// scan over each batch of arcs and then batch by batch, an order that does not
+// depend on scheduling.  Blocks below long_blocks take the tasks before
+// small_begin, one per warp in batches of 32 arcs; the others take the tasks
+// of at most kSortSmallArcs arcs from small_begin on, one per group of 8 lanes.
+// Chunks of a split row add their sums into a zeroed row.  With a leaf active
+// child the node's Y' row holds the same values (entry j: the j-th colour
+// other than col(v)); out2, when given, receives it too.
+template <typename T, int G>
+__device__ __forceinline__ void weighted_hist_task(const int4 &task, bool have, int gl, T *tot,
+                                                   const int8_t *__restrict__ sclr, const float *__restrict__ sw,
+                                                   int64_t nnz, const int8_t *__restrict__ colours, int64_t n, int nb,
+                                                   int kc, T *out, int64_t ld, T *out2, int64_t ld2) {
+    const int v = task.x;
+    // batches of G arcs of the longest task among the warp's groups
+    const int nbat = (int)__reduce_max_sync(kFull, have ? (unsigned)((task.w - task.z + G - 1) / G) : 0u);
+    for (int b = 0; b < nb; ++b) {
+        const int cv = have ? (int)colours[(int64_t)b * n + v] : -1;
+        const bool ok = (unsigned)cv < (unsigned)kc;
+        for (int j = gl; j <= kMaxHistColours; j += G) tot[j] = T(0);
+        __syncwarp();
+        const int8_t *cl = sclr + (int64_t)b * nnz;
+        const float *wl = sw + (int64_t)b * nnz;
+        for (int kb = 0; kb < nbat; ++kb) {
+            const int64_t e = task.z + (int64_t)G * kb + gl;
+            const bool in = ok && e < task.w;
+            const int c = in ? (int)__ldg(cl + e) : -1;
+            T s = in ? T(__ldg(wl + e)) : T(0);
+            // segmented inclusive scan: colours run in order, so equal
+            // colours o lanes apart enclose only that colour
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const T y = __shfl_up_sync(0xffffffffu, s, o);
-                    const int cy = __shfl_up_sync(0xffffffffu, c, o);
-                    if (lane >= o && cy == c) s += y;
-                }
-                const int cn = __shfl_down_sync(0xffffffffu, c, 1);
-                if (c >= 0 && (lane == 31 || cn != c)) tot[c] += s;  // one run end per colour
-                __syncwarp();
+            for (int o = 1; o < G; o <<= 1) {
+                const T y = __shfl_up_sync(kFull, s, o, G);
+                const int cy = __shfl_up_sync(kFull, c, o, G);
+                if (gl >= o && cy == c) s += y;
             }
+            const int cn = __shfl_down_sync(kFull, c, 1, G);
+            if (c >= 0 && (gl == G - 1 || cn != c)) tot[c] += s;  // one run end per colour
+            __syncwarp();
+        }
+        if (have) {
             T *row = out + ((int64_t)v * nb + b) * ld;
             T *row2 = out2 ? out2 + ((int64_t)v * nb + b) * ld2 : nullptr;
             const int64_t width = out2 && ld2 > ld ? ld2 : ld;
-            for (int j = lane; j < width; j += 32) {
+            for (int j = gl; j < width; j += G) {
                 const int x = j < cv ? j : j + 1;
                 const T val = ok && j < kc - 1 ? tot[x] : T(0);
                 if (task.y < 0) {
@@ -2264,28 +2262,64 @@ __global__ void __launch_bounds__(256) weighted_hist_kernel(const int4 *__restri
                     if (row2 && j < ld2) atomicAdd(row2 + j, val);
                 }
             }
-            __syncwarp();
         }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) weighted_hist_kernel(const int4 *__restrict__ tasks, int64_t ntasks,
+                                                            int64_t small_begin, int64_t long_blocks,
+                                                            const int8_t *__restrict__ sclr,
+                                                            const float *__restrict__ sw, int64_t nnz,
+                                                            const int8_t *__restrict__ colours, int64_t n, int nb,
+                                                            int kc, T *out, int64_t ld, T *out2, int64_t ld2) {
+    __shared__ T tot_s[8][4][kMaxHistColours + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if ((int64_t)blockIdx.x < long_blocks) {
+        const int64_t nwarps = long_blocks * 8;
+        for (int64_t t = (int64_t)blockIdx.x * 8 + wib; t < small_begin; t += nwarps)
+            weighted_hist_task<T, 32>(tasks[t], true, lane, tot_s[wib][0], sclr, sw, nnz, colours, n, nb, kc, out, ld,
+                                      out2, ld2);
+        return;
+    }
+    constexpr int G = 8;
+    const int grp = lane / G;
+    const int64_t nwarps = ((int64_t)gridDim.x - long_blocks) * 8;
+    const int64_t rounds = (ntasks - small_begin + 32 / G - 1) / (32 / G);
+    for (int64_t rd = ((int64_t)blockIdx.x - long_blocks) * 8 + wib; rd < rounds; rd += nwarps) {
+        const int64_t t = small_begin + rd * (32 / G) + grp;
+        const bool have = t < ntasks;
+        const int4 task = have ? tasks[t] : make_int4(0, -1, 0, 0);
+        weighted_hist_task<T, G>(task, have, lane % G, tot_s[wib][grp], sclr, sw, nnz, colours, n, nb, kc, out, ld,
+                                 out2, ld2);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_weighted_hist(const int4 *tasks, int64_t ntasks, const int8_t *sclr, const float *sw, int64_t nnz,
-                                 const int8_t *colours, int64_t n, int nb, int kc, void *out, int64_t ld, void *out2,
-                                 int64_t ld2, Elem e, int sms, cudaStream_t stream) {
+cudaError_t launch_weighted_hist(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int8_t *sclr,
+                                 const float *sw, int64_t nnz, const int8_t *colours, int64_t n, int nb, int kc,
+                                 void *out, int64_t ld, void *out2, int64_t ld2, Elem e, int sms,
+                                 cudaStream_t stream) {
     if (ntasks <= 0) return cudaSuccess;
     if (kc > kMaxHistColours || !sw) return cudaErrorInvalidValue;
-    int64_t blocks = (ntasks + 7) / 8;
-    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    small_begin = small_begin < 0 ? 0 : (small_begin > ntasks ? ntasks : small_begin);
+    // one wave of 8 blocks per SM, split between the two kinds of task
+    const int64_t cap = (int64_t)sms * (small_begin > 0 && small_begin < ntasks ? 4 : 8);
+    int64_t long_blocks = (small_begin + 7) / 8;
+    if (long_blocks > cap) long_blocks = cap;
+    int64_t small_blocks = ((ntasks - small_begin + 3) / 4 + 7) / 8;
+    if (small_blocks > cap) small_blocks = cap;
+    const unsigned grid = (unsigned)(long_blocks + small_blocks);
     if (e == Elem::F64)
-        weighted_hist_kernel<double><<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, sclr, sw, nnz, colours, n, nb,
-                                                                           kc, static_cast<double *>(out), ld,
-                                                                           static_cast<double *>(out2), ld2);
+        weighted_hist_kernel<double><<<grid, 256, 0, stream>>>(tasks, ntasks, small_begin, long_blocks, sclr, sw, nnz,
+                                                               colours, n, nb, kc, static_cast<double *>(out), ld,
+                                                               static_cast<double *>(out2), ld2);
     else if (e == Elem::F32)
-        weighted_hist_kernel<float><<<(unsigned)blocks, 256, 0, stream>>>(tasks, ntasks, sclr, sw, nnz, colours, n, nb,
-                                                                          kc, static_cast<float *>(out), ld,
-                                                                          static_cast<float *>(out2), ld2);
+        weighted_hist_kernel<float><<<grid, 256, 0, stream>>>(tasks, ntasks, small_begin, long_blocks, sclr, sw, nnz,
+                                                              colours, n, nb, kc, static_cast<float *>(out), ld,
+                                                              static_cast<float *>(out2), ld2);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -332,10 +332,12 @@ struct SortHist {
 // The (2, 1, 1) table of a weighted graph (FP32 or FP64 tables) from the
 // colour-sorted arcs: out[(v * nb + b) * ld + j] = the weights of v's arcs to
 // the j-th colour other than col(v), summed; rows of split tasks must be zero.
-// out2 (stride ld2, or null) receives the same rows: the node's Y'.
-cudaError_t launch_weighted_hist(const int4 *tasks, int64_t ntasks, const int8_t *sclr, const float *sw, int64_t nnz,
-                                 const int8_t *colours, int64_t n, int nb, int kc, void *out, int64_t ld, void *out2,
-                                 int64_t ld2, Elem e, int sms, cudaStream_t stream);
+// out2 (stride ld2, or null) receives the same rows: the node's Y'.  Tasks
+// from small_begin on have at most kSortSmallArcs arcs (run 4 per warp).
+cudaError_t launch_weighted_hist(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int8_t *sclr,
+                                 const float *sw, int64_t nnz, const int8_t *colours, int64_t n, int nb, int kc,
+                                 void *out, int64_t ld, void *out2, int64_t ld2, Elem e, int sms,
+                                 cudaStream_t stream);
 cudaError_t launch_colour_sort(const int4 *tasks, int64_t ntasks, int64_t small_begin, const int32_t *col_idx,
                                const float *weights, int64_t n, int64_t nnz, const int8_t *colours, int nb, int kc,
                                int32_t *scol, int8_t *sclr, float *sw, const SortHist &hist, int sms,

@@ -128,3 +128,30 @@ def test_noalloc_sum_past_2_128_takes_the_compensated_sum(sg):
     sg.sg2v_sum_counts_noalloc(dv, 192, 1, out)
     torch.cuda.synchronize()
     assert out.item() == 2.0 ** 128 - 2.0 ** 11
+
+
+def test_noalloc_replays_inside_a_cuda_graph(sg):
+    """The entry point's purpose: after one warm-up call it can be recorded
+    in stream capture (it allocates nothing and does not synchronise), and
+    each replay of the captured graph sums the values the buffer holds at
+    that moment, exactly (integral values: the 128-bit integer path)."""
+    import torch
+
+    n, nseg = 100_003, 3
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    vals = torch.randint(0, 1 << 20, (nseg, n), generator=gen, device="cuda").to(torch.float64)
+    totals = torch.full((nseg,), -1.0, dtype=torch.float64, device="cuda")
+    sg.sg2v_sum_counts_noalloc(vals, n, nseg, totals)  # the warm-up call the header asks for
+    torch.cuda.synchronize()
+    assert torch.equal(totals, vals.sum(dim=1))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        sg.sg2v_sum_counts_noalloc(vals, n, nseg, totals)
+    for seed in (11, 12):
+        gen.manual_seed(seed)
+        vals.copy_(torch.randint(0, 1 << 20, (nseg, n), generator=gen, device="cuda").to(torch.float64))
+        totals.fill_(-1.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(totals, vals.sum(dim=1))
